@@ -1,0 +1,279 @@
+/*
+ * sst.h -- C ABI of the GB300 silicon-strip unpacking and clustering library.
+ *
+ * The library implements the hot path of arXiv 2101.11489 ("Parallelizing the
+ * Unpacking and Clustering of Detector Data for Reconstruction of Charged Particle
+ * Tracks on Multi-core CPUs and Many-core GPUs"), section 2 "Parallelization":
+ *   (1) unpack zero-suppressed FED raw data (96 channels x 256 strips per FED, a
+ *       CSR-like layout with the channel as row and the strip as column) into a
+ *       structure-of-arrays of digis, concurrently per channel;
+ *   (2) cluster the digis with the "three thresholds" algorithm: channel threshold
+ *       (active strips), seed threshold (seed strips), cluster forming around the
+ *       seeds (left and right boundaries, charge) and the cluster threshold; kept
+ *       clusters report boundaries, charge and centroid;
+ * and section 3 "Optimization": many events processed concurrently on one GPU.
+ *
+ * Every entry point returns an sst_status.  Calls that take a `stream` enqueue
+ * work on that CUDA stream (a cudaStream_t passed as void*, NULL = legacy default
+ * stream) and return without waiting; their device outputs are valid once the
+ * stream reaches that point.  Data errors in the raw buffers are NOT call errors:
+ * they are reported per channel and per event in device status words (see
+ * sst_event_status) and never make a kernel fault or trap.
+ *
+ * Ownership: inputs are owned by the caller and only read; the library copies
+ * what it keeps (calibration).  Output buffers are owned by the caller.  A context
+ * owns its device calibration tables and its internal scratch (look-back flags,
+ * work tickets), which it sizes on first use; a call that has to grow scratch
+ * synchronises the device, so make one warm-up call before capturing a stream
+ * into a CUDA graph.  Contexts are independent; one context must not be used from
+ * two host threads at once, except sst_submit / sst_poll, which are thread safe.
+ */
+#ifndef SST_H
+#define SST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+typedef int32_t sst_status;
+#define SST_OK 0
+#define SST_ERR_INVALID_ARG 1 /* null pointer, bad size, bad alignment, bad parameter */
+#define SST_ERR_NO_CALIB 2    /* sst_calib_upload has not been called */
+#define SST_ERR_BUDGET 3      /* served: event does not fit the free budget now; retry */
+#define SST_ERR_TOO_LARGE 4   /* served: event can never fit the budget / limits */
+#define SST_ERR_BUSY 5        /* served: no free request slot; retry */
+#define SST_ERR_NOT_READY 6   /* served: result not ready within the timeout */
+#define SST_ERR_TIMEOUT 7     /* a device wait ran out of iterations (see flags) */
+#define SST_ERR_CUDA 8        /* CUDA runtime error; text in sst_last_error() */
+#define SST_ERR_STATE 9       /* call not valid in the context's current state */
+
+/* ---- readout geometry (section 2) ----------------------------------------- */
+#define SST_CH_PER_FED 96
+#define SST_STRIPS_PER_CH 256 /* a module is one 256-strip channel */
+#define SST_FE_PER_FED 8
+#define SST_CH_PER_FE 12
+#define SST_STRIPS_PER_APV 128
+
+/* ---- FED byte format -------------------------------------------------------
+ * The paper's Figure 1 (raw data format) is lost; section 2 states only the
+ * geometry and that the zero-suppressed payload is CSR-like.  This library reads
+ * the following little-endian format:
+ *
+ *   event  = FED record 0, FED record 1, ... back to back; FED f occupies
+ *            fed_len[f] bytes (0 = FED absent: its channels are empty).
+ *   FED    = 32-byte header | FE unit 0 | ... | FE unit 7 | zero padding to 16 B
+ *   header = u32 magic (SST_FED_MAGIC) | u16 fed_id (== f) | u8 96 | u8 8 |
+ *            u32 fed_bytes (== fed_len[f]) | u32 reserved | u16 fe_len[8]
+ *   FE u   = 12 channel records back to back (fe_len[u] bytes), zero padding to 8 B
+ *   channel record = u16 len (incl. these 3 bytes) | u8 packet code (SST_ZS_CODE) |
+ *            runs: u8 first strip | u8 width (>= 1) | width x u8 ADC
+ *            runs ascend and do not overlap (first >= previous first + width),
+ *            first + width <= 256.
+ * Global strip index of a digi: g = (fed * 96 + channel) * 256 + strip.
+ */
+#define SST_FED_HEADER_BYTES 32
+#define SST_FED_MAGIC 0x46545353u /* bytes 'S','S','T','F' */
+#define SST_ZS_CODE 0x5Au
+#define SST_MAX_FEDS 65536u
+
+/* ---- data status ------------------------------------------------------------
+ * Each channel gets one status byte: 0 when valid, otherwise the bit of the first
+ * error found.  An invalid channel yields no digis; its neighbours are unaffected,
+ * except that a broken length chain invalidates all 12 channels of its FE unit and
+ * a bad FED header all 96 channels of the FED. */
+#define SST_CH_FED_HDR 0x01u   /* FED header / fed_len / FE lengths inconsistent */
+#define SST_CH_FRAMING 0x02u   /* channel lengths inconsistent within the FE unit */
+#define SST_CH_BAD_CODE 0x04u  /* packet code is not SST_ZS_CODE */
+#define SST_CH_RUN_RANGE 0x08u /* run width 0, or first + width > 256 */
+#define SST_CH_RUN_ORDER 0x10u /* run starts before the previous run ends */
+#define SST_CH_TRUNC 0x20u     /* run header or ADC bytes cross the record end */
+/* Event-level flags (ORed with the channel bits into sst_event_status.flags). */
+#define SST_EV_DIGI_CAPACITY 0x100u    /* digi output capacity exceeded; digis dropped */
+#define SST_EV_CLUSTER_CAPACITY 0x200u /* cluster output capacity exceeded; clusters dropped */
+#define SST_EV_TIMEOUT 0x400u          /* a device wait gave up; the event's output is invalid */
+#define SST_EV_SIZE 0x800u             /* batch: sum of fed_len != event_off[e+1] - event_off[e] */
+
+/* Per-event status record, in device memory. */
+typedef struct {
+  uint32_t n_digi;         /* digis found (valid channels only) */
+  uint32_t n_clusters;     /* clusters written (<= capacity) */
+  uint32_t flags;          /* OR of channel status bits and SST_EV_* flags */
+  uint32_t n_bad_channels; /* channels with a nonzero status */
+} sst_event_status;
+
+/* ---- clustering parameters (section 2, "three thresholds") ------------------
+ * active(s)  = !bad[s] && (float)adc[s] > t_channel * noise[s]
+ * seed(s)    = !bad[s] && (float)adc[s] > t_seed    * noise[s]
+ * Two successive active strips are linked when every maximal run of non-bad
+ * inactive strips between them is <= max_seq_holes long and every maximal run of
+ * bad strips between them is <= max_seq_bad long.  A candidate is a maximal chain
+ * of linked active strips; it is a cluster when it holds a seed and
+ *   (float)sum(adc) > t_cluster * sqrt(sum noise^2)      (active strips only)
+ * and it is then widened by up to max_adj_bad bad strips on each side.  Every
+ * product, sum, quotient and square root is one binary32 operation rounded to
+ * nearest, in strip order; "larger than" is strict.
+ * Requirements: 0 < t_channel <= t_seed, t_cluster >= 0, all finite. */
+typedef struct {
+  float t_channel;
+  float t_seed;
+  float t_cluster;
+  uint8_t max_seq_holes;
+  uint8_t max_seq_bad;
+  uint8_t max_adj_bad;
+  uint8_t reserved; /* must be 0 */
+} sst_params;
+
+/* ---- outputs ---------------------------------------------------------------- */
+
+/* Digi structure-of-arrays of one event (device memory, caller-owned).
+ * Digis are in ascending global strip order; the digis of channel c are
+ * [chan_off[c], chan_off[c+1]).  n_digi <= total raw bytes always holds (each
+ * digi costs one payload byte), so capacity = raw bytes is always enough. */
+typedef struct {
+  uint32_t* strip;          /* [capacity] global strip index g */
+  uint8_t* adc;             /* [capacity] 8-bit ADC */
+  uint32_t* chan_off;       /* [n_feds*96 + 1] CSR row pointers */
+  uint8_t* chan_status;     /* [n_feds*96] channel status byte */
+  sst_event_status* status; /* [1] sst_unpack resets it and sets n_digi, flags, n_bad_channels */
+  uint64_t capacity;        /* elements of strip[] and adc[] */
+} sst_digis;
+
+/* Cluster structure-of-arrays (device memory, caller-owned), sorted by
+ * (det, first).  det = global module id = fed * 96 + channel; first = first strip
+ * in the module; width in strips; charge = sum of gain-corrected ADC; barycenter =
+ * charge-weighted centroid in module strip units (strip i spans [i, i+1)). */
+typedef struct {
+  uint32_t* det;
+  uint16_t* first;
+  uint16_t* width;
+  uint32_t* charge;
+  float* barycenter;
+  uint64_t capacity; /* per-event path: elements of each array */
+} sst_clusters;
+
+/* ---- context ------------------------------------------------------------------ */
+typedef struct sst_ctx sst_ctx;
+
+/* Creates a context on CUDA device `device` for a detector of n_feds FEDs
+ * (calibration covers n_feds * 96 * 256 strips).  INVALID_ARG if n_feds is 0 or
+ * above SST_MAX_FEDS; CUDA if the device cannot be used. */
+sst_status sst_create(sst_ctx** out, int device, uint32_t n_feds);
+
+/* Waits for the context's work, stops the server if running, frees everything. */
+sst_status sst_destroy(sst_ctx* ctx);
+
+/* Text of the last error on this context (static storage, never NULL). */
+const char* sst_last_error(const sst_ctx* ctx);
+
+/* Uploads calibration (section 2: pre-measured gain and noise per strip, plus the
+ * bad-strip list) from HOST memory, in global strip order:
+ *   noise [n_feds*96*256] float, finite, >= 0   (ADC counts)
+ *   gain  [n_feds*96*2]   float, finite, > 0    (one per 128-strip APV)
+ *   bad   [n_feds*96*256] uint8, 0 = good, else bad
+ * and the thresholds.  The tables are copied to device memory and stay resident;
+ * a new upload replaces them after work already queued on `stream`.
+ * INVALID_ARG on a null pointer, a non-finite or negative value, or parameters
+ * outside their requirements; the previous calibration then stays in place. */
+sst_status sst_calib_upload(sst_ctx* ctx, const float* noise, const float* gain, const uint8_t* bad,
+                            const sst_params* params, void* stream);
+
+/* ---- per-event path ----------------------------------------------------------- */
+
+/* Unpacks one event (section 2: "unpack the data to SoA format ... concurrently
+ * for each channel").  raw: device pointer, 16-byte aligned, the event's FED
+ * records back to back; fed_len: device pointer, [n_feds] bytes per FED record
+ * (the event builder's sizes).  Writes `out` (device).  1 <= n_feds <= context
+ * FEDs.  Digis beyond out->capacity are dropped and flagged SST_EV_DIGI_CAPACITY.
+ * Does not need calibration. */
+sst_status sst_unpack(sst_ctx* ctx, const uint8_t* raw, const uint32_t* fed_len, uint32_t n_feds,
+                      const sst_digis* out, void* stream);
+
+/* Clusters one event's digis (as sst_unpack wrote them, for n_feds FEDs) with the
+ * three-threshold algorithm (section 2).  Writes the cluster SoA and sets
+ * in->status->n_clusters; ORs SST_EV_CLUSTER_CAPACITY / SST_EV_TIMEOUT into
+ * in->status->flags.  NO_CALIB before sst_calib_upload. */
+sst_status sst_cluster(sst_ctx* ctx, const sst_digis* in, uint32_t n_feds, const sst_clusters* out,
+                       void* stream);
+
+/* ---- batched path (section 3: many events concurrently on one GPU) -------------- */
+
+/* Unpacks and clusters n_events events in one persistent launch; digis stay on
+ * chip.  All pointers are device memory:
+ *   raw        events back to back; event e occupies [event_off[e], event_off[e+1]),
+ *              every event_off[e] a multiple of 16
+ *   event_off  [n_events + 1] uint64
+ *   fed_len    [n_events * n_feds] uint32, event-major
+ *   clu_off    [n_events + 1] uint64: event e's clusters go to
+ *              [clu_off[e], clu_off[e+1]) of out's arrays (capacity per event)
+ *   status     [n_events] per-event status records
+ * Output is identical, event by event, to sst_unpack + sst_cluster on each event
+ * alone.  NO_CALIB before sst_calib_upload. */
+sst_status sst_batch(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len,
+                     uint32_t n_events, uint32_t n_feds, const uint64_t* clu_off, const sst_clusters* out,
+                     sst_event_status* status, void* stream);
+
+/* Launch-shape knobs of the batched kernel (picked by sst_autotune). */
+typedef struct {
+  uint32_t block;       /* threads per CTA: 128, 256 or 512 */
+  uint32_t ctas_per_sm; /* persistent CTAs per SM: 1..8 (clamped to what fits) */
+  uint32_t tile_digis;  /* digis per on-chip tile: 1024, 2048 or 4096 */
+  uint32_t lanes_per_channel; /* lanes that copy one channel's runs: 1, 2, 4, 8, 16 or 32 */
+} sst_tune;
+
+sst_status sst_set_tune(sst_ctx* ctx, const sst_tune* t);
+sst_status sst_get_tune(const sst_ctx* ctx, sst_tune* t);
+
+/* Times every candidate launch shape of sst_batch on the given batch (same
+ * arguments as sst_batch; the outputs are overwritten), keeps the fastest in the
+ * context and returns it in *best with its time per launch in *best_us.
+ * Synchronises the stream. */
+sst_status sst_autotune(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len,
+                        uint32_t n_events, uint32_t n_feds, const uint64_t* clu_off, const sst_clusters* out,
+                        sst_event_status* status, void* stream, sst_tune* best, float* best_us);
+
+/* ---- served path: continuous batching ------------------------------------------ */
+
+typedef struct {
+  uint64_t mem_budget_bytes; /* device memory for in-flight events (admission budget) */
+  uint32_t max_batch_events; /* events per launch */
+  uint32_t max_inflight;     /* launches in flight at once (streams) */
+  uint32_t max_requests;     /* request slots (admitted + finished-not-polled) */
+  uint32_t n_feds;           /* FEDs per event */
+} sst_server_opts;
+
+/* Starts the request loop (one host thread, max_inflight streams).  Requires
+ * calibration.  STATE if already running. */
+sst_status sst_server_start(sst_ctx* ctx, const sst_server_opts* opts);
+
+/* Drains in-flight work and stops the loop; unpolled results are discarded. */
+sst_status sst_server_stop(sst_ctx* ctx);
+
+/* Submits one event from HOST memory (raw: raw_bytes bytes, fed_len: [n_feds]).
+ * The bytes are copied before the call returns.  Admission: the event's device
+ * footprint (raw bytes + cluster capacity raw_bytes/2 * 16 B + fixed overhead)
+ * must fit the free budget.  Returns OK and a ticket, BUSY (no free slot) or
+ * BUDGET (budget full now; retry after polling), or TOO_LARGE (never fits). */
+sst_status sst_submit(sst_ctx* ctx, const uint8_t* raw, uint64_t raw_bytes, const uint32_t* fed_len,
+                      uint64_t* ticket);
+
+typedef struct {
+  sst_event_status status;
+  double t_submit_us; /* host clock, microseconds, at sst_submit */
+  double t_done_us;   /* host clock when the loop saw the event's launch complete */
+} sst_result_info;
+
+/* Waits up to timeout_us (0 = just check, < 0 = forever) for ticket's result.
+ * On OK copies the status and up to `capacity` clusters to the HOST arrays (any
+ * may be NULL to skip) and releases the slot and budget.  NOT_READY on timeout;
+ * INVALID_ARG for an unknown ticket. */
+sst_status sst_poll(sst_ctx* ctx, uint64_t ticket, int64_t timeout_us, sst_result_info* info, uint32_t* det,
+                    uint16_t* first, uint16_t* width, uint32_t* charge, float* barycenter, uint64_t capacity);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
