@@ -184,13 +184,16 @@ sst_status sst_calib_upload(sst_ctx* ctx, const float* noise, const float* gain,
 /* ---- per-event path ----------------------------------------------------------- */
 
 /* Unpacks one event (section 2: "unpack the data to SoA format ... concurrently
- * for each channel").  raw: device pointer, 16-byte aligned, the event's FED
- * records back to back; fed_len: device pointer, [n_feds] bytes per FED record
- * (the event builder's sizes).  Writes `out` (device).  1 <= n_feds <= context
- * FEDs.  Digis beyond out->capacity are dropped and flagged SST_EV_DIGI_CAPACITY.
- * Does not need calibration. */
-sst_status sst_unpack(sst_ctx* ctx, const uint8_t* raw, const uint32_t* fed_len, uint32_t n_feds,
-                      const sst_digis* out, void* stream);
+ * for each channel").  raw: device pointer, 16-byte aligned, raw_bytes bytes: the
+ * event's FED records back to back; fed_len: device pointer, [n_feds] bytes per
+ * FED record (the event builder's sizes); a FED whose record would end past
+ * raw_bytes is treated as corrupt (SST_CH_FED_HDR) and SST_EV_SIZE is set when the
+ * sizes do not add up to raw_bytes.  Writes `out` (device).  1 <= n_feds <=
+ * context FEDs.  Digis beyond out->capacity are dropped and flagged
+ * SST_EV_DIGI_CAPACITY (chan_off is then clamped to the capacity).  Does not need
+ * calibration. */
+sst_status sst_unpack(sst_ctx* ctx, const uint8_t* raw, uint64_t raw_bytes, const uint32_t* fed_len,
+                      uint32_t n_feds, const sst_digis* out, void* stream);
 
 /* Clusters one event's digis (as sst_unpack wrote them, for n_feds FEDs) with the
  * three-threshold algorithm (section 2).  Writes the cluster SoA and sets

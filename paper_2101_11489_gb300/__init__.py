@@ -1,0 +1,334 @@
+"""Python binding of the GB300 silicon-strip unpacking and clustering library.
+
+The library (``_lib/libsst.so``, built from ``csrc/`` by ``_build.py``) implements
+the hot path of arXiv 2101.11489: unpacking zero-suppressed FED raw data into a
+digi structure-of-arrays and three-threshold clustering (section 2), per event,
+batched and served (section 3).  Its C ABI is ``include/sst.h``.
+
+This module only marshals arguments: PyTorch tensors supply device memory (their
+``data_ptr()``) and streams (``torch.cuda.current_stream().cuda_stream``); every
+step of the path runs in the library's CUDA kernels.  There is no CPU fallback: if
+the library is missing or fails to load, importing the functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsst.so")
+
+CH_PER_FED = 96
+STRIPS_PER_CH = 256
+STRIPS_PER_APV = 128
+
+SST_OK = 0
+SST_ERR_INVALID_ARG = 1
+SST_ERR_NO_CALIB = 2
+SST_ERR_BUDGET = 3
+SST_ERR_TOO_LARGE = 4
+SST_ERR_BUSY = 5
+SST_ERR_NOT_READY = 6
+SST_ERR_TIMEOUT = 7
+SST_ERR_CUDA = 8
+SST_ERR_STATE = 9
+
+SST_CH_FED_HDR = 0x01
+SST_CH_FRAMING = 0x02
+SST_CH_BAD_CODE = 0x04
+SST_CH_RUN_RANGE = 0x08
+SST_CH_RUN_ORDER = 0x10
+SST_CH_TRUNC = 0x20
+SST_EV_DIGI_CAPACITY = 0x100
+SST_EV_CLUSTER_CAPACITY = 0x200
+SST_EV_TIMEOUT = 0x400
+SST_EV_SIZE = 0x800
+
+
+class SstError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"sst error {code}: {msg}")
+        self.code = code
+
+
+class sst_params(ctypes.Structure):
+    _fields_ = [("t_channel", ctypes.c_float), ("t_seed", ctypes.c_float), ("t_cluster", ctypes.c_float),
+                ("max_seq_holes", ctypes.c_uint8), ("max_seq_bad", ctypes.c_uint8), ("max_adj_bad", ctypes.c_uint8),
+                ("reserved", ctypes.c_uint8)]
+
+
+class sst_event_status(ctypes.Structure):
+    _fields_ = [("n_digi", ctypes.c_uint32), ("n_clusters", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("n_bad_channels", ctypes.c_uint32)]
+
+
+class sst_digis(ctypes.Structure):
+    _fields_ = [("strip", ctypes.c_void_p), ("adc", ctypes.c_void_p), ("chan_off", ctypes.c_void_p),
+                ("chan_status", ctypes.c_void_p), ("status", ctypes.c_void_p), ("capacity", ctypes.c_uint64)]
+
+
+class sst_clusters(ctypes.Structure):
+    _fields_ = [("det", ctypes.c_void_p), ("first", ctypes.c_void_p), ("width", ctypes.c_void_p),
+                ("charge", ctypes.c_void_p), ("barycenter", ctypes.c_void_p), ("capacity", ctypes.c_uint64)]
+
+
+class sst_tune(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("tile_digis", ctypes.c_uint32),
+                ("lanes_per_channel", ctypes.c_uint32)]
+
+
+class sst_server_opts(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("max_batch_events", ctypes.c_uint32),
+                ("max_inflight", ctypes.c_uint32), ("max_requests", ctypes.c_uint32), ("n_feds", ctypes.c_uint32)]
+
+
+class sst_result_info(ctypes.Structure):
+    _fields_ = [("status", sst_event_status), ("t_submit_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library():
+    """Loads libsst.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} not built; run __graft_entry__.build() or python -m {__name__}._build")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, u32, u64, i32, i64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64
+    P = ctypes.POINTER
+    sigs = {
+        "sst_create": ([P(vp), ctypes.c_int, u32], i32),
+        "sst_destroy": ([vp], i32),
+        "sst_last_error": ([vp], ctypes.c_char_p),
+        "sst_calib_upload": ([vp, vp, vp, vp, P(sst_params), vp], i32),
+        "sst_unpack": ([vp, vp, u64, vp, u32, P(sst_digis), vp], i32),
+        "sst_cluster": ([vp, P(sst_digis), u32, P(sst_clusters), vp], i32),
+        "sst_batch": ([vp, vp, vp, vp, u32, u32, vp, P(sst_clusters), vp, vp], i32),
+        "sst_set_tune": ([vp, P(sst_tune)], i32),
+        "sst_get_tune": ([vp, P(sst_tune)], i32),
+        "sst_autotune": ([vp, vp, vp, vp, u32, u32, vp, P(sst_clusters), vp, vp, P(sst_tune), P(ctypes.c_float)], i32),
+        "sst_server_start": ([vp, P(sst_server_opts)], i32),
+        "sst_server_stop": ([vp], i32),
+        "sst_submit": ([vp, vp, u64, vp, P(u64)], i32),
+        "sst_poll": ([vp, u64, i64, P(sst_result_info), vp, vp, vp, vp, vp, u64], i32),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list[str]:
+    return ["sst_create", "sst_destroy", "sst_last_error", "sst_calib_upload", "sst_unpack", "sst_cluster",
+            "sst_batch", "sst_set_tune", "sst_get_tune", "sst_autotune", "sst_server_start", "sst_server_stop",
+            "sst_submit", "sst_poll"]
+
+
+def _check(ctx, code: int, what: str):
+    if code != SST_OK:
+        msg = load_library().sst_last_error(ctx).decode(errors="replace") if ctx else what
+        raise SstError(code, f"{what}: {msg}")
+
+
+def _dp(t) -> int:
+    """Device pointer of a CUDA tensor (no copy; must be contiguous)."""
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return t.data_ptr()
+
+
+def _hp(a: np.ndarray) -> int:
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def _stream(stream) -> int:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+# ---------------------------------------------------------------- C-ABI wrappers
+
+def sst_create(device: int, n_feds: int) -> int:
+    lib = load_library()
+    h = ctypes.c_void_p()
+    code = lib.sst_create(ctypes.byref(h), device, n_feds)
+    if code != SST_OK:
+        raise SstError(code, "sst_create failed")
+    return h.value
+
+
+def sst_destroy(ctx: int) -> None:
+    _check(None, load_library().sst_destroy(ctx), "sst_destroy")
+
+
+def sst_last_error(ctx: int) -> str:
+    return load_library().sst_last_error(ctx).decode(errors="replace")
+
+
+def sst_calib_upload(ctx: int, noise: np.ndarray, gain: np.ndarray, bad: np.ndarray, params: sst_params,
+                     stream=None) -> None:
+    noise = np.ascontiguousarray(noise, dtype=np.float32)
+    gain = np.ascontiguousarray(gain, dtype=np.float32)
+    bad = np.ascontiguousarray(bad, dtype=np.uint8)
+    code = load_library().sst_calib_upload(ctx, _hp(noise), _hp(gain), _hp(bad), ctypes.byref(params),
+                                           _stream(stream))
+    _check(ctx, code, "sst_calib_upload")
+
+
+def sst_unpack(ctx: int, raw, fed_len, n_feds: int, digis: sst_digis, stream=None) -> None:
+    code = load_library().sst_unpack(ctx, _dp(raw), raw.numel(), _dp(fed_len), n_feds, ctypes.byref(digis),
+                                     _stream(stream))
+    _check(ctx, code, "sst_unpack")
+
+
+def sst_cluster(ctx: int, digis: sst_digis, n_feds: int, clusters: sst_clusters, stream=None) -> None:
+    code = load_library().sst_cluster(ctx, ctypes.byref(digis), n_feds, ctypes.byref(clusters), _stream(stream))
+    _check(ctx, code, "sst_cluster")
+
+
+def sst_batch(ctx: int, raw, event_off, fed_len, n_events: int, n_feds: int, clu_off, clusters: sst_clusters,
+              status, stream=None) -> None:
+    code = load_library().sst_batch(ctx, _dp(raw), _dp(event_off), _dp(fed_len), n_events, n_feds, _dp(clu_off),
+                                    ctypes.byref(clusters), _dp(status), _stream(stream))
+    _check(ctx, code, "sst_batch")
+
+
+def sst_set_tune(ctx: int, block: int, ctas_per_sm: int, tile_digis: int, lanes_per_channel: int) -> None:
+    t = sst_tune(block, ctas_per_sm, tile_digis, lanes_per_channel)
+    _check(ctx, load_library().sst_set_tune(ctx, ctypes.byref(t)), "sst_set_tune")
+
+
+def sst_get_tune(ctx: int) -> dict:
+    t = sst_tune()
+    _check(ctx, load_library().sst_get_tune(ctx, ctypes.byref(t)), "sst_get_tune")
+    return {"block": t.block, "ctas_per_sm": t.ctas_per_sm, "tile_digis": t.tile_digis,
+            "lanes_per_channel": t.lanes_per_channel}
+
+
+def sst_autotune(ctx: int, raw, event_off, fed_len, n_events: int, n_feds: int, clu_off, clusters: sst_clusters,
+                 status, stream=None) -> tuple[dict, float]:
+    t = sst_tune()
+    us = ctypes.c_float()
+    code = load_library().sst_autotune(ctx, _dp(raw), _dp(event_off), _dp(fed_len), n_events, n_feds,
+                                       _dp(clu_off), ctypes.byref(clusters), _dp(status), _stream(stream),
+                                       ctypes.byref(t), ctypes.byref(us))
+    _check(ctx, code, "sst_autotune")
+    return {"block": t.block, "ctas_per_sm": t.ctas_per_sm, "tile_digis": t.tile_digis,
+            "lanes_per_channel": t.lanes_per_channel}, us.value
+
+
+def sst_server_start(ctx: int, mem_budget_bytes: int, max_batch_events: int, max_inflight: int, max_requests: int,
+                     n_feds: int) -> None:
+    o = sst_server_opts(mem_budget_bytes, max_batch_events, max_inflight, max_requests, n_feds)
+    _check(ctx, load_library().sst_server_start(ctx, ctypes.byref(o)), "sst_server_start")
+
+
+def sst_server_stop(ctx: int) -> None:
+    _check(ctx, load_library().sst_server_stop(ctx), "sst_server_stop")
+
+
+def sst_submit(ctx: int, raw: np.ndarray, fed_len: np.ndarray) -> tuple[int, int]:
+    """Returns (status code, ticket); BUSY / BUDGET are returned, not raised."""
+    raw = np.ascontiguousarray(raw, dtype=np.uint8)
+    fed_len = np.ascontiguousarray(fed_len, dtype=np.uint32)
+    t = ctypes.c_uint64()
+    code = load_library().sst_submit(ctx, _hp(raw), raw.size, _hp(fed_len), ctypes.byref(t))
+    if code not in (SST_OK, SST_ERR_BUSY, SST_ERR_BUDGET):
+        _check(ctx, code, "sst_submit")
+    return code, t.value
+
+
+def sst_poll(ctx: int, ticket: int, timeout_us: int, capacity: int = 0):
+    """Returns (status code, info, clusters dict or None); NOT_READY is returned."""
+    info = sst_result_info()
+    arrs = {"det": np.zeros(capacity, np.uint32), "first": np.zeros(capacity, np.uint16),
+            "width": np.zeros(capacity, np.uint16), "charge": np.zeros(capacity, np.uint32),
+            "barycenter": np.zeros(capacity, np.float32)}
+    ptrs = [(_hp(arrs[k]) if capacity else None) for k in ("det", "first", "width", "charge", "barycenter")]
+    code = load_library().sst_poll(ctx, ticket, timeout_us, ctypes.byref(info), *ptrs, capacity)
+    if code == SST_ERR_NOT_READY:
+        return code, info, None
+    _check(ctx, code, "sst_poll")
+    n = min(info.status.n_clusters, capacity)
+    return code, info, {k: v[:n] for k, v in arrs.items()}
+
+
+# ---------------------------------------------------------------- tensor helpers
+
+@dataclass
+class DigiBuffers:
+    """Device tensors behind an sst_digis record."""
+    strip: object
+    adc: object
+    chan_off: object
+    chan_status: object
+    status: object
+
+    @classmethod
+    def alloc(cls, capacity: int, n_feds: int, device="cuda"):
+        import torch
+        return cls(torch.empty(max(capacity, 1), dtype=torch.int32, device=device),
+                   torch.empty(max(capacity, 1), dtype=torch.uint8, device=device),
+                   torch.empty(n_feds * CH_PER_FED + 1, dtype=torch.int32, device=device),
+                   torch.empty(n_feds * CH_PER_FED, dtype=torch.uint8, device=device),
+                   torch.zeros(4, dtype=torch.int32, device=device))
+
+    def record(self) -> sst_digis:
+        return sst_digis(_dp(self.strip), _dp(self.adc), _dp(self.chan_off), _dp(self.chan_status), _dp(self.status),
+                         self.strip.numel())
+
+    def to_host(self) -> dict:
+        st = self.status.cpu().numpy().view(np.uint32)
+        n = int(st[0])
+        return {"strip": self.strip[:n].cpu().numpy().view(np.uint32).copy(),
+                "adc": self.adc[:n].cpu().numpy().copy(),
+                "chan_off": self.chan_off.cpu().numpy().view(np.uint32).copy(),
+                "chan_status": self.chan_status.cpu().numpy().copy(),
+                "n_digi": n, "n_clusters": int(st[1]), "flags": int(st[2]), "n_bad_channels": int(st[3])}
+
+
+@dataclass
+class ClusterBuffers:
+    """Device tensors behind an sst_clusters record (int32 / int16 tensors hold the
+    unsigned fields bit for bit)."""
+    det: object
+    first: object
+    width: object
+    charge: object
+    barycenter: object
+
+    @classmethod
+    def alloc(cls, capacity: int, device="cuda"):
+        import torch
+        c = max(capacity, 1)
+        return cls(torch.empty(c, dtype=torch.int32, device=device), torch.empty(c, dtype=torch.int16, device=device),
+                   torch.empty(c, dtype=torch.int16, device=device), torch.empty(c, dtype=torch.int32, device=device),
+                   torch.empty(c, dtype=torch.float32, device=device))
+
+    def record(self) -> sst_clusters:
+        return sst_clusters(_dp(self.det), _dp(self.first), _dp(self.width), _dp(self.charge), _dp(self.barycenter),
+                            self.det.numel())
+
+    def to_host(self, start: int = 0, n: int | None = None) -> dict:
+        end = self.det.numel() if n is None else start + n
+        return {"det": self.det[start:end].cpu().numpy().view(np.uint32).copy(),
+                "first": self.first[start:end].cpu().numpy().view(np.uint16).copy(),
+                "width": self.width[start:end].cpu().numpy().view(np.uint16).copy(),
+                "charge": self.charge[start:end].cpu().numpy().view(np.uint32).copy(),
+                "barycenter": self.barycenter[start:end].cpu().numpy().copy()}
+
+
+def params(t_channel=2.0, t_seed=3.0, t_cluster=5.0, max_seq_holes=0, max_seq_bad=1, max_adj_bad=0) -> sst_params:
+    return sst_params(t_channel, t_seed, t_cluster, max_seq_holes, max_seq_bad, max_adj_bad, 0)

@@ -1,0 +1,307 @@
+// sst_api.cu -- host side of the C ABI declared in include/sst.h: contexts,
+// calibration upload (arXiv 2101.11489 section 2: noise and gain per strip, here
+// plus the bad-strip list), argument checks and kernel launches.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "sst_internal.h"
+
+namespace sst {
+
+sst_status set_err(sst_ctx* c, sst_status code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+sst_status cuda_err(sst_ctx* c, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return SST_OK;
+  return set_err(c, SST_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+KParams kparams(const sst_ctx* c) {
+  KParams k;
+  k.t_channel = c->params.t_channel;
+  k.t_seed = c->params.t_seed;
+  k.t_cluster = c->params.t_cluster;
+  k.max_holes = c->params.max_seq_holes;
+  k.max_bad = c->params.max_seq_bad;
+  k.max_adj = c->params.max_adj_bad;
+  k.noise = c->noise;
+  k.badmask = c->badmask;
+  k.gain = c->gain;
+  return k;
+}
+
+cudaError_t ensure_scratch(Scratch& s, size_t lb_needed, size_t fed_off_needed) {
+  cudaError_t e = cudaSuccess;
+  if (!s.tickets) {
+    if ((e = cudaMalloc(&s.tickets, 16 * sizeof(uint32_t)))) return e;
+    if ((e = cudaMemset(s.tickets, 0, 16 * sizeof(uint32_t)))) return e;
+  }
+  if (lb_needed > s.lb_cap || fed_off_needed > s.fed_off_cap) {
+    // growing: wait for all work that may still use the old buffers
+    if ((e = cudaDeviceSynchronize())) return e;
+    if (lb_needed > s.lb_cap) {
+      if (s.lb) cudaFree(s.lb);
+      s.lb = nullptr;
+      s.lb_cap = 0;
+      if ((e = cudaMalloc(&s.lb, lb_needed * sizeof(unsigned long long)))) return e;
+      s.lb_cap = lb_needed;
+    }
+    if (fed_off_needed > s.fed_off_cap) {
+      if (s.fed_off) cudaFree(s.fed_off);
+      s.fed_off = nullptr;
+      s.fed_off_cap = 0;
+      if ((e = cudaMalloc(&s.fed_off, fed_off_needed * sizeof(uint64_t)))) return e;
+      s.fed_off_cap = fed_off_needed;
+    }
+  }
+  return cudaSuccess;
+}
+
+void free_scratch(Scratch& s) {
+  if (s.lb) cudaFree(s.lb);
+  if (s.fed_off) cudaFree(s.fed_off);
+  if (s.tickets) cudaFree(s.tickets);
+  s = Scratch{};
+}
+
+static bool params_ok(const sst_params* p) {
+  if (!p) return false;
+  auto fin = [](float x) { return std::isfinite(x); };
+  return fin(p->t_channel) && fin(p->t_seed) && fin(p->t_cluster) && p->t_channel > 0.f &&
+         p->t_seed >= p->t_channel && p->t_cluster >= 0.f && p->reserved == 0;
+}
+
+}  // namespace sst
+
+using namespace sst;
+
+namespace {
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+}  // namespace
+
+extern "C" {
+
+sst_status sst_create(sst_ctx** out, int device, uint32_t n_feds) {
+  if (!out) return SST_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n_feds == 0 || n_feds > SST_MAX_FEDS) return SST_ERR_INVALID_ARG;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return SST_ERR_CUDA;
+  auto* c = new sst_ctx();
+  c->device = device;
+  c->n_feds = n_feds;
+  c->shape = default_shape();
+  DeviceGuard g(device);
+  cudaError_t e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = ensure_scratch(c->scratch, (size_t)n_feds, (size_t)n_feds);
+  if (e != cudaSuccess) {
+    free_scratch(c->scratch);
+    delete c;
+    return SST_ERR_CUDA;
+  }
+  *out = c;
+  return SST_OK;
+}
+
+sst_status sst_server_stop(sst_ctx* ctx);
+
+sst_status sst_destroy(sst_ctx* ctx) {
+  if (!ctx) return SST_ERR_INVALID_ARG;
+  if (ctx->server) sst_server_stop(ctx);
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  free_scratch(ctx->scratch);
+  if (ctx->noise) cudaFree(ctx->noise);
+  if (ctx->badmask) cudaFree(ctx->badmask);
+  if (ctx->gain) cudaFree(ctx->gain);
+  delete ctx;
+  return SST_OK;
+}
+
+const char* sst_last_error(const sst_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+sst_status sst_calib_upload(sst_ctx* ctx, const float* noise, const float* gain, const uint8_t* bad,
+                            const sst_params* params, void* stream) {
+  if (!ctx) return SST_ERR_INVALID_ARG;
+  if (!noise || !gain || !bad) return set_err(ctx, SST_ERR_INVALID_ARG, "sst_calib_upload: null table");
+  if (!params_ok(params))
+    return set_err(ctx, SST_ERR_INVALID_ARG,
+                   "sst_calib_upload: thresholds must be finite with 0 < t_channel <= t_seed, t_cluster >= 0");
+  const uint64_t n = (uint64_t)ctx->n_feds * kCh * kStrips;
+  const uint64_t n_apv = n / kApv;
+  for (uint64_t i = 0; i < n; i++)
+    if (!(noise[i] >= 0.f) || !std::isfinite(noise[i]))
+      return set_err(ctx, SST_ERR_INVALID_ARG, "sst_calib_upload: noise must be finite and >= 0");
+  for (uint64_t i = 0; i < n_apv; i++)
+    if (!(gain[i] > 0.f) || !std::isfinite(gain[i]))
+      return set_err(ctx, SST_ERR_INVALID_ARG, "sst_calib_upload: gain must be finite and > 0");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (!ctx->noise) {
+    if ((e = cudaMalloc(&ctx->noise, n * sizeof(float)))) return cuda_err(ctx, e, "cudaMalloc noise");
+    if ((e = cudaMalloc(&ctx->badmask, n / 8))) return cuda_err(ctx, e, "cudaMalloc badmask");
+    if ((e = cudaMalloc(&ctx->gain, n_apv * sizeof(float)))) return cuda_err(ctx, e, "cudaMalloc gain");
+  }
+  uint8_t* bad_dev = nullptr;
+  if ((e = cudaMalloc(&bad_dev, n))) return cuda_err(ctx, e, "cudaMalloc bad");
+  // Copies are stream-ordered after earlier work on `st`; synchronise before the
+  // pageable host buffers go out of the caller's hands and before freeing bad_dev.
+  if (!e) e = cudaMemcpyAsync(ctx->noise, noise, n * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemcpyAsync(ctx->gain, gain, n_apv * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemcpyAsync(bad_dev, bad, n, cudaMemcpyHostToDevice, st);
+  if (!e) e = build_badmask(bad_dev, ctx->badmask, n, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  cudaFree(bad_dev);
+  if (e) return cuda_err(ctx, e, "sst_calib_upload");
+  ctx->params = *params;
+  ctx->has_calib = true;
+  return SST_OK;
+}
+
+sst_status sst_unpack(sst_ctx* ctx, const uint8_t* raw, uint64_t raw_bytes, const uint32_t* fed_len, uint32_t n_feds,
+                      const sst_digis* out, void* stream) {
+  if (!ctx) return SST_ERR_INVALID_ARG;
+  if (!raw || !fed_len || !out || !out->strip || !out->adc || !out->chan_off || !out->chan_status || !out->status)
+    return set_err(ctx, SST_ERR_INVALID_ARG, "sst_unpack: null pointer");
+  if (((uintptr_t)raw & 15u) != 0) return set_err(ctx, SST_ERR_INVALID_ARG, "sst_unpack: raw not 16-byte aligned");
+  if (n_feds == 0 || n_feds > ctx->n_feds)
+    return set_err(ctx, SST_ERR_INVALID_ARG, "sst_unpack: n_feds outside 1..context FEDs");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = ensure_scratch(ctx->scratch, n_feds, n_feds);
+  if (e) return cuda_err(ctx, e, "sst_unpack scratch");
+  e = launch_unpack(raw, raw_bytes, fed_len, n_feds, *out, ctx->scratch, ctx->shape, (cudaStream_t)stream);
+  return cuda_err(ctx, e, "sst_unpack");
+}
+
+sst_status sst_cluster(sst_ctx* ctx, const sst_digis* in, uint32_t n_feds, const sst_clusters* out, void* stream) {
+  if (!ctx) return SST_ERR_INVALID_ARG;
+  if (!ctx->has_calib) return set_err(ctx, SST_ERR_NO_CALIB, "sst_cluster: no calibration");
+  if (!in || !in->strip || !in->adc || !in->chan_off || !in->status || !out || !out->det || !out->first ||
+      !out->width || !out->charge || !out->barycenter)
+    return set_err(ctx, SST_ERR_INVALID_ARG, "sst_cluster: null pointer");
+  if (n_feds == 0 || n_feds > ctx->n_feds)
+    return set_err(ctx, SST_ERR_INVALID_ARG, "sst_cluster: n_feds outside 1..context FEDs");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = ensure_scratch(ctx->scratch, n_feds, n_feds);
+  if (e) return cuda_err(ctx, e, "sst_cluster scratch");
+  e = launch_cluster(*in, n_feds, *out, kparams(ctx), ctx->scratch, ctx->shape, (cudaStream_t)stream);
+  return cuda_err(ctx, e, "sst_cluster");
+}
+
+sst_status sst_batch(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len,
+                     uint32_t n_events, uint32_t n_feds, const uint64_t* clu_off, const sst_clusters* out,
+                     sst_event_status* status, void* stream) {
+  if (!ctx) return SST_ERR_INVALID_ARG;
+  if (!ctx->has_calib) return set_err(ctx, SST_ERR_NO_CALIB, "sst_batch: no calibration");
+  if (!raw || !event_off || !fed_len || !clu_off || !out || !status || !out->det || !out->first || !out->width ||
+      !out->charge || !out->barycenter)
+    return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch: null pointer");
+  if (((uintptr_t)raw & 15u) != 0) return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch: raw not 16-byte aligned");
+  if (n_events == 0 || n_feds == 0 || n_feds > ctx->n_feds)
+    return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch: bad n_events / n_feds");
+  if ((uint64_t)n_events * n_feds >= (1ull << 31))
+    return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch: too many FED records in one batch");
+  DeviceGuard g(ctx->device);
+  const size_t items = (size_t)n_events * n_feds;
+  cudaError_t e = ensure_scratch(ctx->scratch, items, items);
+  if (e) return cuda_err(ctx, e, "sst_batch scratch");
+  e = launch_batch(raw, event_off, fed_len, n_events, n_feds, clu_off, *out, status, kparams(ctx), ctx->scratch,
+                   ctx->shape, ctx->n_sm, (cudaStream_t)stream);
+  return cuda_err(ctx, e, "sst_batch");
+}
+
+sst_status sst_set_tune(sst_ctx* ctx, const sst_tune* t) {
+  if (!ctx || !t) return SST_ERR_INVALID_ARG;
+  Shape s{(int)t->block, (int)t->tile_digis, (int)t->lanes_per_channel, (int)t->ctas_per_sm};
+  if (!shape_valid(s)) return set_err(ctx, SST_ERR_INVALID_ARG, "sst_set_tune: unsupported launch shape");
+  ctx->shape = s;
+  return SST_OK;
+}
+
+sst_status sst_get_tune(const sst_ctx* ctx, sst_tune* t) {
+  if (!ctx || !t) return SST_ERR_INVALID_ARG;
+  t->block = (uint32_t)ctx->shape.block;
+  t->tile_digis = (uint32_t)ctx->shape.tile;
+  t->lanes_per_channel = (uint32_t)ctx->shape.lanes;
+  t->ctas_per_sm = (uint32_t)ctx->shape.ctas_per_sm;
+  return SST_OK;
+}
+
+sst_status sst_autotune(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len,
+                        uint32_t n_events, uint32_t n_feds, const uint64_t* clu_off, const sst_clusters* out,
+                        sst_event_status* status, void* stream, sst_tune* best, float* best_us) {
+  if (!ctx) return SST_ERR_INVALID_ARG;
+  const Shape keep = ctx->shape;
+  cudaStream_t st = (cudaStream_t)stream;
+  // one untimed call sizes the scratch and checks the arguments
+  sst_status r = sst_batch(ctx, raw, event_off, fed_len, n_events, n_feds, clu_off, out, status, stream);
+  if (r != SST_OK) return r;
+  DeviceGuard g(ctx->device);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return cuda_err(ctx, cudaGetLastError(), "autotune event");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_err(ctx, cudaGetLastError(), "autotune event");
+  }
+  const int blocks[] = {128, 256, 512};
+  const int tiles[] = {1024, 2048, 4096};
+  const int lanes[] = {1, 2, 4, 8};
+  const int per_sm[] = {2, 3, 4, 6, 8};
+  float best_t = 1e30f;
+  Shape best_s = keep;
+  cudaError_t ce = cudaSuccess;
+  for (int b : blocks)
+    for (int t : tiles)
+      for (int l : lanes)
+        for (int p : per_sm) {
+          Shape s{b, t, l, p};
+          if (!shape_valid(s) || smem_bytes(t) * (size_t)p > 227u * 1024u) continue;
+          ctx->shape = s;
+          float ms_total = 0.f;
+          for (int rep = 0; rep < 3 && ce == cudaSuccess; rep++) {
+            ce = cudaEventRecord(e0, st);
+            if (!ce) ce = launch_batch(raw, event_off, fed_len, n_events, n_feds, clu_off, *out, status,
+                                       kparams(ctx), ctx->scratch, s, ctx->n_sm, st);
+            if (!ce) ce = cudaEventRecord(e1, st);
+            if (!ce) ce = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (!ce) ce = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_total += ms;  // first launch is a warm-up
+          }
+          if (ce != cudaSuccess) break;
+          const float us = ms_total * 1000.f / 2.f;
+          if (us < best_t) {
+            best_t = us;
+            best_s = s;
+          }
+        }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ce != cudaSuccess) {
+    ctx->shape = keep;
+    return cuda_err(ctx, ce, "sst_autotune");
+  }
+  ctx->shape = best_s;
+  if (best) sst_get_tune(ctx, best);
+  if (best_us) *best_us = best_t;
+  return SST_OK;
+}
+
+}  // extern "C"

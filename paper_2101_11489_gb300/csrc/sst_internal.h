@@ -1,0 +1,90 @@
+// sst_internal.h -- internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+
+#include "../../include/sst.h"
+
+namespace sst {
+
+constexpr int kCh = SST_CH_PER_FED;          // channels per FED
+constexpr int kStrips = SST_STRIPS_PER_CH;   // strips per channel (module)
+constexpr int kFe = SST_FE_PER_FED;          // FE units per FED
+constexpr int kChPerFe = SST_CH_PER_FE;      // channels per FE unit
+constexpr int kApv = SST_STRIPS_PER_APV;     // strips per APV
+constexpr int kHdr = SST_FED_HEADER_BYTES;   // FED header bytes
+constexpr int kFedStrips = kCh * kStrips;    // 24,576 strips per FED
+constexpr int kMaskWords = kStrips / 32;     // 8 words of 32 strips per channel
+
+// Calibration and thresholds as the kernels see them.
+struct KParams {
+  float t_channel, t_seed, t_cluster;
+  int max_holes, max_bad, max_adj;
+  const float* noise;       // [n_strips]
+  const uint32_t* badmask;  // [n_strips / 32], bit (s & 31) of word s / 32
+  const float* gain;        // [n_strips / 128]
+};
+
+// Launch shape of the tile kernels.
+struct Shape {
+  int block;        // threads per CTA
+  int tile;         // digis per on-chip tile
+  int lanes;        // lanes per channel when copying runs
+  int ctas_per_sm;  // persistent CTAs per SM (batched kernel)
+};
+
+// Device scratch for one stream of work: look-back states, work tickets and
+// per-FED byte offsets.  Owned by a context (or by one server stream).
+struct Scratch {
+  unsigned long long* lb = nullptr;  // look-back states
+  size_t lb_cap = 0;
+  uint64_t* fed_off = nullptr;       // absolute byte offset per (event, FED)
+  size_t fed_off_cap = 0;
+  uint32_t* tickets = nullptr;       // [4] work counters
+};
+
+size_t smem_bytes(int tile);
+Shape default_shape();
+bool shape_valid(const Shape& s);
+
+// Kernel launchers (sst_kernels.cu).  They only enqueue work on `st`.
+cudaError_t launch_unpack(const uint8_t* raw, uint64_t raw_bytes, const uint32_t* fed_len, uint32_t n_feds,
+                          const sst_digis& out, const Scratch& s, const Shape& sh, cudaStream_t st);
+cudaError_t launch_cluster(const sst_digis& in, uint32_t n_feds, const sst_clusters& out, const KParams& kp,
+                           const Scratch& s, const Shape& sh, cudaStream_t st);
+cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len, uint32_t n_events,
+                         uint32_t n_feds, const uint64_t* clu_off, const sst_clusters& out, sst_event_status* status,
+                         const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st);
+cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st);
+
+}  // namespace sst
+
+struct sst_server;
+
+struct sst_ctx {
+  int device = 0;
+  uint32_t n_feds = 0;
+  int n_sm = 0;
+  bool has_calib = false;
+  sst_params params{};
+  float* noise = nullptr;
+  uint32_t* badmask = nullptr;
+  float* gain = nullptr;
+  sst::Scratch scratch;
+  sst::Shape shape{};
+  std::string err;
+  std::mutex mu;
+  sst_server* server = nullptr;
+};
+
+namespace sst {
+sst_status set_err(sst_ctx* c, sst_status code, const std::string& msg);
+sst_status cuda_err(sst_ctx* c, cudaError_t e, const char* where);
+KParams kparams(const sst_ctx* c);
+cudaError_t ensure_scratch(Scratch& s, size_t lb_needed, size_t fed_off_needed);
+void free_scratch(Scratch& s);
+}  // namespace sst

@@ -1,0 +1,150 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Digis, channel statuses, event statuses and cluster det / first / width / charge
+must match bit for bit; barycenters within 1e-6 strip (the same binary32
+expression is evaluated on both sides, so they are expected to be equal).
+Method: arXiv 2101.11489 section 2 (unpack, three-threshold clustering) and
+section 3 (many events per launch).
+"""
+import numpy as np
+import pytest
+
+import eventgen as eg
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2101_11489_gb300 as sst  # noqa: E402
+from _gpu_util import Gpu, assert_clusters_equal, assert_digis_equal  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def w0():
+    w = eg.WORKLOADS[0]
+    calib = eg.make_calibration(w.n_feds, w.seed, w.p_bad)
+    g = Gpu(calib.noise, calib.gain, calib.bad)
+    yield w, calib, g
+    g.close()
+
+
+def check_event(g, raw, fl, n_feds, **kw):
+    dh, ch = g.event(raw, fl, n_feds, **kw)
+    od, oc, ost = g.oracle(raw, fl, n_feds)
+    assert_digis_equal(dh, od)
+    assert_clusters_equal(ch, oc)
+    for k in ("n_digi", "n_clusters", "flags", "n_bad_channels"):
+        assert dh[k] == ost[k], k
+    return dh, ch, oc
+
+
+def test_small_event_parity(w0):
+    w, calib, g = w0
+    e = eg.make_event(w, calib, 0)
+    dh, ch, oc = check_event(g, e.raw, e.fed_len, w.n_feds)
+    assert oc["det"].size > 1000
+
+
+@pytest.mark.parametrize("event", [1, 2, 3])
+def test_small_event_parity_more_events(w0, event):
+    w, calib, g = w0
+    e = eg.make_event(w, calib, event, occupancy=0.004 * event)
+    check_event(g, e.raw, e.fed_len, w.n_feds)
+
+
+@pytest.mark.parametrize("occ", [0.0, 0.2, 0.6])
+def test_occupancy_extremes_and_tile_chunking(w0, occ):
+    # 20% and 60% signal occupancy put several thousand digis in one FED: more
+    # than one tile (chunked clustering) and FED records above the staging buffer
+    w, calib, g = w0
+    e = eg.make_event(w, calib, 7, n_feds=4, occupancy=occ)
+    check_event(g, e.raw, e.fed_len, 4)
+
+
+def test_absent_feds_and_subset(w0):
+    w, calib, g = w0
+    e = eg.make_event(w, calib, 11, n_feds=6)
+    # drop FEDs 1 and 4 (fed_len 0, records removed)
+    offs = np.concatenate([[0], np.cumsum(e.fed_len)]).astype(np.int64)
+    keep = [0, 2, 3, 5]
+    raw = np.concatenate([e.raw[offs[f]:offs[f + 1]] for f in keep])
+    fl = e.fed_len.copy()
+    fl[[1, 4]] = 0
+    check_event(g, raw, fl, 6)
+
+
+def test_single_fed_and_empty_channels(w0):
+    w, calib, g = w0
+    n = 96 * 256
+    adc = np.zeros(n, np.uint8)
+    rec = np.zeros(n, np.uint8)
+    raw, fl = eg.pack_event(adc, rec, 1)
+    dh, ch, oc = check_event(g, raw, fl, 1)
+    assert dh["n_digi"] == 0 and oc["det"].size == 0
+
+
+def test_full_channels_and_alternating_runs(w0):
+    w, calib, g = w0
+    n = 2 * 96 * 256
+    r = np.random.default_rng(5)
+    adc = r.integers(0, 256, n).astype(np.uint8)
+    rec = np.zeros(n, np.uint8)
+    rec[0:256] = 1                      # channel 0 fully recorded
+    rec[256:512:2] = 1                  # channel 1: 128 runs of width 1
+    rec[96 * 256 + 3 * 256:96 * 256 + 4 * 256] = 1
+    rec[5000:5400] = (r.random(400) < 0.5)
+    adc = np.where(rec != 0, adc, 0).astype(np.uint8)
+    raw, fl = eg.pack_event(adc, rec, 2)
+    check_event(g, raw, fl, 2)
+
+
+def test_full_detector_event_parity():
+    w = eg.WORKLOADS[1]
+    calib = eg.make_calibration(w.n_feds, w.seed, w.p_bad)
+    g = Gpu(calib.noise, calib.gain, calib.bad)
+    try:
+        e = eg.make_event(w, calib, 0)
+        dh, ch, oc = check_event(g, e.raw, e.fed_len, w.n_feds)
+        assert dh["n_digi"] > 300_000 and oc["det"].size > 40_000
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("params", [
+    dict(), dict(max_seq_bad=0), dict(max_seq_holes=1), dict(max_seq_holes=2, max_seq_bad=2, max_adj_bad=1),
+    dict(t_channel=2.5, t_seed=4.0, t_cluster=3.0), dict(t_cluster=0.0)])
+def test_parameter_variants(params):
+    w = eg.Workload("variant", 3, 1, ("fixed", 0.05), (1, 12), 0.03, 77, overlap=True, sat_frac=0.05)
+    calib = eg.make_calibration(3, 77, 0.03)
+    g = Gpu(calib.noise, calib.gain, calib.bad, sst.params(**params))
+    try:
+        for ev in range(3):
+            e = eg.make_event(w, calib, ev)
+            check_event(g, e.raw, e.fed_len, 3)
+    finally:
+        g.close()
+
+
+def test_batch_equals_per_event(w0):
+    w, calib, g = w0
+    evs = [eg.make_event(w, calib, 20 + i, occupancy=0.003 * (i + 1)) for i in range(5)]
+    out = g.batch([(e.raw, e.fed_len) for e in evs])
+    for e, (st, cl) in zip(evs, out):
+        od, oc, ost = g.oracle(e.raw, e.fed_len, w.n_feds)
+        assert st == ost
+        assert_clusters_equal(cl, oc)
+
+
+def test_batch_launch_shapes_give_identical_results(w0):
+    w, calib, g = w0
+    evs = [eg.make_event(w, calib, 40 + i, occupancy=0.01 * (i + 1)) for i in range(3)]
+    ref = g.batch([(e.raw, e.fed_len) for e in evs])
+    for block, cps, tile, lanes in [(128, 4, 1024, 1), (512, 2, 4096, 8), (256, 3, 2048, 32), (256, 8, 1024, 4)]:
+        sst.sst_set_tune(g.ctx, block, cps, tile, lanes)
+        got = g.batch([(e.raw, e.fed_len) for e in evs])
+        for (s0, c0), (s1, c1) in zip(ref, got):
+            assert s0 == s1
+            for k in c0:
+                assert np.array_equal(c0[k], c1[k])
+    sst.sst_set_tune(g.ctx, 256, 3, 2048, 2)
