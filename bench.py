@@ -1,0 +1,441 @@
+#!/usr/bin/env python3
+"""Throughput of silicon-strip unpacking + three-threshold clustering on GB300.
+
+Method: arXiv 2101.11489 (section 2: unpack zero-suppressed FED data, three-threshold
+clustering; section 3: many events concurrently on one GPU).  One step = one batched
+launch (sst_batch) over a batch of synthetic full-detector events already resident
+in HBM: every FED of every event is unpacked and clustered.
+
+Default workload: 64 full-detector events (440 FEDs x 96 channels x 256 strips),
+per-event signal occupancy uniform in [0.5%, 4%], cluster widths 1-5, 0.1% bad
+strips.  --workload batch256 selects 256 events at 5% occupancy, widths 1-12,
+2% bad strips, 3% saturated strips.
+
+Prints one JSON line (rank 0).  `value` is events/s of the batched path (device
+time, CUDA events, L2 flushed between steps); `e2e` is the same through the C ABI
+with host-resident events (pinned H2D of the raw bytes, D2H of statuses and
+clusters inside the timed region).  `per_event` times the plain per-event launches
+(sst_unpack + sst_cluster) on the same events.  --impl reference times the CPU
+oracle on the host cores instead.
+
+Under torchrun (N > 1) each rank is an independent replica on its own GPU with its
+own events (the path shards by event with no exchange); timing is the maximum over
+ranks and `value` the events of all ranks over that time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import eventgen as eg  # noqa: E402
+
+WORKLOADS = {
+    "batch64": (2, 64),
+    "batch256": (3, 256),
+}
+L2_FLUSH_BYTES = 512 << 20  # written between timed steps (L2 is 129 MB)
+
+
+# ---------------------------------------------------------------- CPU side (oracle)
+
+_W_CALIB = None
+
+
+def _worker_init(wid):
+    global _W_CALIB
+    w = eg.WORKLOADS[wid]
+    _W_CALIB = eg.make_calibration(w.n_feds, w.seed, w.p_bad)
+
+
+def _gen_event(args):
+    wid, ev = args
+    w = eg.WORKLOADS[wid]
+    e = eg.make_event(w, _W_CALIB, ev)
+    return e.raw, e.fed_len, e.n_digi
+
+
+def _oracle_event(args):
+    raw, fed_len = args
+    import oracle as orc
+    w_calib = _W_CALIB
+    t0 = time.perf_counter()
+    d, c = orc.process_event(raw, fed_len, fed_len.size, w_calib.noise, w_calib.gain, w_calib.bad, orc.Params())
+    return time.perf_counter() - t0, int(c["det"].size)
+
+
+def time_oracle(pool, cores, events, n_sample):
+    """Oracle (unpack + cluster, sequential C) over n_sample events on `cores`
+    processes; returns events/s and the sample description."""
+    sample = [(events[i % len(events)][0], events[i % len(events)][1]) for i in range(n_sample)]
+    pool.map(_oracle_event, sample[:cores], chunksize=1)  # warm the workers
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_event, sample, chunksize=1)
+    wall = time.perf_counter() - t0
+    cpu = sum(r[0] for r in res)
+    return n_sample / wall, wall, cpu
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    def __init__(self, index: int):
+        self.path = tempfile.mktemp(prefix="clocks", suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()) if rows else None,
+                "reasons": reasons}
+
+
+# ---------------------------------------------------------------- helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic():
+    """DRAM bytes per launch of the batched kernel from the committed ncu summary,
+    or None when the kernel source has changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "k_batch_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    src = open(os.path.join(ROOT, "paper_2101_11489_gb300", "csrc", "sst_kernels.cu"), "rb").read()
+    if hashlib.sha256(src).hexdigest() != d.get("kernel_source_sha256"):
+        return None
+    return d
+
+
+def algorithmic_bytes(events, n_digi, n_clusters):
+    """Bytes the batched kernel must move, per the path's dataflow: FED payload read
+    once, noise (4 B) of every recorded strip, the 256-bit bad-strip mask (32 B) and
+    two APV gains (8 B) of every channel, fed_len / fed_off (12 B) per FED, the
+    cluster SoA (16 B per cluster) and one 16-byte status per event."""
+    payload = sum(int(e[0].size) for e in events)
+    n_feds = sum(int(e[1].size) for e in events)
+    return payload + 4 * n_digi + n_feds * 96 * (32 + 8) + 12 * n_feds + 16 * n_clusters + 16 * len(events)
+
+
+# ---------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="sst", choices=["sst", "reference"])
+    ap.add_argument("--workload", default="batch64", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    wid, n_events = WORKLOADS[args.workload]
+    w = eg.WORKLOADS[wid]
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world, wid, n_events)
+
+    cores = os.cpu_count() or 1
+    # the process pool is started (spawn) before the first CUDA call
+    pool = mp.get_context("spawn").Pool(cores, initializer=_worker_init, initargs=(wid,))
+    base_event = rank * n_events
+    gen = pool.map(_gen_event, [(wid, base_event + i) for i in range(n_events)], chunksize=1)
+    events = [(r, f) for r, f, _ in gen]
+    calib = eg.make_calibration(w.n_feds, w.seed, w.p_bad)
+
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    import paper_2101_11489_gb300 as sst
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    ctx = sst.sst_create(local, w.n_feds)
+    sst.sst_calib_upload(ctx, calib.noise, calib.gain, calib.bad, sst.params())
+
+    sizes = np.array([e[0].size for e in events], np.int64)
+    eoff = np.zeros(n_events + 1, np.int64)
+    eoff[1:] = np.cumsum(sizes)
+    caps = sizes // 2 + 1
+    coff = np.zeros(n_events + 1, np.int64)
+    coff[1:] = np.cumsum(caps)
+    raw_h = np.concatenate([e[0] for e in events])
+    fl_h = np.concatenate([e[1] for e in events]).astype(np.uint32)
+    raw = torch.from_numpy(raw_h).to(dev)
+    eoff_d = torch.from_numpy(eoff).to(dev)
+    fl_d = torch.from_numpy(fl_h.view(np.int32)).to(dev)
+    coff_d = torch.from_numpy(coff).to(dev)
+    cb = sst.ClusterBuffers.alloc(int(coff[-1]), device=dev)
+    crec = cb.record()
+    st_d = torch.zeros(n_events * 4, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    tune = sst.sst_get_tune(ctx)
+    if not args.no_autotune:
+        tune, _ = sst.sst_autotune(ctx, raw, eoff_d, fl_d, n_events, w.n_feds, coff_d, crec, st_d)
+
+    def step():
+        sst.sst_batch(ctx, raw, eoff_d, fl_d, n_events, w.n_feds, coff_d, crec, st_d)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: device time of K batched steps, L2 flushed before each
+    clocks = Clocks(local)
+    sst.sst_profile_read(ctx, reset=True)
+    sst.sst_profile_enable(ctx, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    sst.sst_profile_enable(ctx, False)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    n_launch, kernel_ms = sst.sst_profile_read(ctx, reset=True)
+    ms_per_step = sum(step_ms) / len(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_per_step, kernel_ms / max(n_launch, 1)], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step, k_ms = float(t[0]), float(t[1])
+    else:
+        k_ms = kernel_ms / max(n_launch, 1)
+
+    st_h = st_d.cpu().numpy().view(np.uint32).reshape(n_events, 4)
+    n_digi = int(st_h[:, 0].sum())
+    n_clu = int(st_h[:, 1].sum())
+    flags = int(np.bitwise_or.reduce(st_h[:, 2]))
+
+    # ---- per-event launches on the same events (the paper's one-event-at-a-time form)
+    pe_raw = [torch.from_numpy(e[0]).to(dev) for e in events]
+    pe_fl = [torch.from_numpy(e[1].view(np.int32)).to(dev) for e in events]
+    dbuf = sst.DigiBuffers.alloc(int(sizes.max()), w.n_feds, device=dev)
+    drec = dbuf.record()
+    pcb = sst.ClusterBuffers.alloc(int(caps.max()), device=dev)
+    pcrec = pcb.record()
+
+    def per_event_pass():
+        for r, f in zip(pe_raw, pe_fl):
+            sst.sst_unpack(ctx, r, f, w.n_feds, drec)
+            sst.sst_cluster(ctx, drec, w.n_feds, pcrec)
+
+    per_event_pass()
+    torch.cuda.synchronize()
+    pe_steps = max(3, min(args.steps // 4, 40))
+    pe_ms = []
+    for i in range(pe_steps):
+        flush.fill_(i & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        per_event_pass()
+        b.record(stream)
+        torch.cuda.synchronize()
+        pe_ms.append(a.elapsed_time(b))
+    pe_value = n_events / (statistics.median(pe_ms) / 1e3)
+
+    # ---- end to end through the C ABI with host-resident events
+    raw_pin = torch.from_numpy(raw_h).pin_memory()
+    fl_pin = torch.from_numpy(fl_h.view(np.int32)).pin_memory()
+    eoff_pin = torch.from_numpy(eoff).pin_memory()
+    st_pin = torch.zeros(n_events * 4, dtype=torch.int32).pin_memory()
+    out_pin = {k: torch.empty(int(coff[-1]), dtype=getattr(cb, k).dtype).pin_memory()
+               for k in ("det", "first", "width", "charge", "barycenter")}
+
+    def e2e_step():
+        raw.copy_(raw_pin, non_blocking=True)
+        fl_d.copy_(fl_pin, non_blocking=True)
+        eoff_d.copy_(eoff_pin, non_blocking=True)
+        step()
+        st_pin.copy_(st_d, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        nc = st_pin.numpy().view(np.uint32).reshape(n_events, 4)[:, 1]
+        d2h = st_pin.numel() * 4
+        for e in range(n_events):
+            a, n = int(coff[e]), int(min(nc[e], caps[e]))
+            for k, dst in out_pin.items():
+                dst[a:a + n].copy_(getattr(cb, k)[a:a + n], non_blocking=True)
+                d2h += n * dst.element_size()
+        torch.cuda.current_stream().synchronize()
+        return d2h
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    d2h_total = 0
+    e2e_steps = max(3, min(args.steps, 100))
+    for i in range(e2e_steps):
+        d2h_total += e2e_step()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t[0])
+    h2d_bytes = raw_h.nbytes + fl_h.nbytes + eoff.nbytes
+
+    # ---- roofline of the dominant kernel (the batched kernel)
+    peak, peak_kind = measured_peaks()
+    b_alg = algorithmic_bytes(events, n_digi, n_clu)
+    achieved = b_alg / (k_ms / 1e3) / 1e9
+    tr = kernel_traffic()
+    traffic = None
+    if tr is not None and tr.get("workload") == args.workload:
+        traffic = tr.get("dram_bytes_per_launch")
+
+    # ---- oracle on the host cores (rank 0 at N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        n_sample = min(len(events), max(cores * 4, 16))
+        v, wall, cpu_s = time_oracle(pool, cores, events, n_sample)
+        cpu = {"value": round(v, 2), "unit": "events/s", "cores": cores, "kind": "oracle",
+               "sample": f"{n_sample} of the {n_events} events (unpack + cluster, sequential C, one event per "
+                         f"process), {wall:.1f} s wall, {cpu_s:.1f} s CPU"}
+    pool.terminate()
+
+    total_events = n_events * world
+    if rank == 0:
+        line = {
+            "metric": "events/s unpack+cluster (batched)",
+            "value": round(total_events / (ms_per_step / 1e3), 1),
+            "unit": "events/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(ms_per_step, 4),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {w.name}", "events_per_step": n_events, "n_feds": w.n_feds,
+                       "strips_per_event": w.n_feds * 96 * 256, "l2": "flushed: 512 MiB write before every step",
+                       "tune": tune, "digis_per_step": n_digi, "clusters_per_step": n_clu,
+                       "payload_bytes_per_step": int(sizes.sum()), "status_flags": flags,
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "strips_per_s": round(total_events * w.n_feds * 96 * 256 / (ms_per_step / 1e3), 1),
+            "per_event": {"value": round(pe_value * world, 1), "unit": "events/s",
+                          "ms_per_event": round(statistics.median(pe_ms) / n_events, 4),
+                          "what": "sst_unpack + sst_cluster, one event per launch pair, same events"},
+            "batched_over_per_event": round((total_events / (ms_per_step / 1e3)) / (pe_value * world), 2),
+            "e2e": {"value": round(total_events / e2e_s, 1), "unit": "events/s",
+                    "h2d_bytes_per_step": int(h2d_bytes), "d2h_bytes_per_step": int(d2h_total / e2e_steps),
+                    "steps": e2e_steps},
+            "gpu_launches": 2 * args.steps,
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "kernel": "k_batch", "kernel_ms": round(k_ms, 4), "algorithmic_bytes": int(b_alg),
+                         "peak_kind": peak_kind},
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "wall_s_timed_region": round(t_wall, 4),
+        }
+        print(json.dumps(line), flush=True)
+    sst.sst_destroy(ctx)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args, rank, world, wid, n_events):
+    """The CPU oracle as the reference arm: each step runs the oracle over a bounded
+    sample of the workload's events on all host cores."""
+    if rank != 0:
+        return
+    w = eg.WORKLOADS[wid]
+    cores = os.cpu_count() or 1
+    pool = mp.get_context("spawn").Pool(cores, initializer=_worker_init, initargs=(wid,))
+    sample = min(n_events, cores * 2)
+    gen = pool.map(_gen_event, [(wid, i) for i in range(sample)], chunksize=1)
+    events = [(r, f) for r, f, _ in gen]
+    for _ in range(args.warmup):
+        pool.map(_oracle_event, events[:cores], chunksize=1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        pool.map(_oracle_event, events, chunksize=1)
+        times.append(time.perf_counter() - t0)
+    pool.terminate()
+    ms = 1e3 * sum(times) / len(times)
+    v = sample / (ms / 1e3)
+    print(json.dumps({
+        "impl": "reference", "metric": "events/s unpack+cluster (batched)", "value": round(v, 2), "unit": "events/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {w.name}", "events_per_step": sample, "n_feds": w.n_feds},
+        "cpu_baseline": {"value": round(v, 2), "unit": "events/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} of the {n_events} events per step, one event per process"},
+        "e2e": {"value": round(v, 2), "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+if __name__ == "__main__":
+    main()

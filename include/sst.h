@@ -238,6 +238,16 @@ sst_status sst_autotune(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_
                         uint32_t n_events, uint32_t n_feds, const uint64_t* clu_off, const sst_clusters* out,
                         sst_event_status* status, void* stream, sst_tune* best, float* best_us);
 
+/* ---- kernel timing ------------------------------------------------------------
+ * When enabled, the context brackets every launch of its batched kernel (the one
+ * sst_batch and sst_autotune time) with CUDA events on the launching stream, so
+ * that a caller can read the kernel's own device time apart from the memsets and
+ * the FED-offset scan around it. */
+sst_status sst_profile_enable(sst_ctx* ctx, int enable);
+/* Waits for the recorded launches, returns their number and summed device time
+ * in milliseconds, and (reset != 0) forgets them. */
+sst_status sst_profile_read(sst_ctx* ctx, uint64_t* launches, double* total_ms, int reset);
+
 /* ---- served path: continuous batching ------------------------------------------ */
 
 typedef struct {

@@ -113,6 +113,8 @@ def load_library():
         "sst_set_tune": ([vp, P(sst_tune)], i32),
         "sst_get_tune": ([vp, P(sst_tune)], i32),
         "sst_autotune": ([vp, vp, vp, vp, u32, u32, vp, P(sst_clusters), vp, vp, P(sst_tune), P(ctypes.c_float)], i32),
+        "sst_profile_enable": ([vp, ctypes.c_int], i32),
+        "sst_profile_read": ([vp, P(u64), P(ctypes.c_double), ctypes.c_int], i32),
         "sst_server_start": ([vp, P(sst_server_opts)], i32),
         "sst_server_stop": ([vp], i32),
         "sst_submit": ([vp, vp, u64, vp, P(u64)], i32),
@@ -128,7 +130,8 @@ def load_library():
 
 def exported_symbols() -> list[str]:
     return ["sst_create", "sst_destroy", "sst_last_error", "sst_calib_upload", "sst_unpack", "sst_cluster",
-            "sst_batch", "sst_set_tune", "sst_get_tune", "sst_autotune", "sst_server_start", "sst_server_stop",
+            "sst_batch", "sst_set_tune", "sst_get_tune", "sst_autotune", "sst_profile_enable", "sst_profile_read",
+            "sst_server_start", "sst_server_stop",
             "sst_submit", "sst_poll"]
 
 
@@ -227,6 +230,19 @@ def sst_autotune(ctx: int, raw, event_off, fed_len, n_events: int, n_feds: int, 
     _check(ctx, code, "sst_autotune")
     return {"block": t.block, "ctas_per_sm": t.ctas_per_sm, "tile_digis": t.tile_digis,
             "lanes_per_channel": t.lanes_per_channel}, us.value
+
+
+def sst_profile_enable(ctx: int, enable: bool = True) -> None:
+    _check(ctx, load_library().sst_profile_enable(ctx, 1 if enable else 0), "sst_profile_enable")
+
+
+def sst_profile_read(ctx: int, reset: bool = True) -> tuple[int, float]:
+    """(launches, summed device milliseconds) of the batched kernel since the last reset."""
+    n = ctypes.c_uint64()
+    ms = ctypes.c_double()
+    _check(ctx, load_library().sst_profile_read(ctx, ctypes.byref(n), ctypes.byref(ms), 1 if reset else 0),
+           "sst_profile_read")
+    return n.value, ms.value
 
 
 def sst_server_start(ctx: int, mem_budget_bytes: int, max_batch_events: int, max_inflight: int, max_requests: int,

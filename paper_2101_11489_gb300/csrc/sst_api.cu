@@ -123,6 +123,11 @@ sst_status sst_destroy(sst_ctx* ctx) {
   if (ctx->server) sst_server_stop(ctx);
   DeviceGuard g(ctx->device);
   cudaDeviceSynchronize();
+  for (auto& pr : ctx->prof_events) ctx->prof_free.push_back(pr);
+  for (auto& pr : ctx->prof_free) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
   free_scratch(ctx->scratch);
   if (ctx->noise) cudaFree(ctx->noise);
   if (ctx->badmask) cudaFree(ctx->badmask);
@@ -222,9 +227,55 @@ sst_status sst_batch(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off
   const size_t items = (size_t)n_events * n_feds;
   cudaError_t e = ensure_scratch(ctx->scratch, items, items);
   if (e) return cuda_err(ctx, e, "sst_batch scratch");
+  cudaEvent_t eb = nullptr, ee = nullptr;
+  if (ctx->profiling) {
+    if (!ctx->prof_free.empty()) {
+      eb = ctx->prof_free.back().first;
+      ee = ctx->prof_free.back().second;
+      ctx->prof_free.pop_back();
+    } else {
+      if ((e = cudaEventCreate(&eb))) return cuda_err(ctx, e, "sst_batch profile event");
+      if ((e = cudaEventCreate(&ee))) {
+        cudaEventDestroy(eb);
+        return cuda_err(ctx, e, "sst_batch profile event");
+      }
+    }
+  }
   e = launch_batch(raw, event_off, fed_len, n_events, n_feds, clu_off, *out, status, kparams(ctx), ctx->scratch,
-                   ctx->shape, ctx->n_sm, (cudaStream_t)stream);
+                   ctx->shape, ctx->n_sm, (cudaStream_t)stream, eb, ee);
+  if (eb) {
+    if (e == cudaSuccess)
+      ctx->prof_events.emplace_back(eb, ee);
+    else
+      ctx->prof_free.emplace_back(eb, ee);
+  }
   return cuda_err(ctx, e, "sst_batch");
+}
+
+sst_status sst_profile_enable(sst_ctx* ctx, int enable) {
+  if (!ctx) return SST_ERR_INVALID_ARG;
+  ctx->profiling = enable != 0;
+  return SST_OK;
+}
+
+sst_status sst_profile_read(sst_ctx* ctx, uint64_t* launches, double* total_ms, int reset) {
+  if (!ctx) return SST_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  double sum = 0.0;
+  for (auto& pr : ctx->prof_events) {
+    cudaError_t e = cudaEventSynchronize(pr.second);
+    float ms = 0.f;
+    if (!e) e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+    if (e) return cuda_err(ctx, e, "sst_profile_read");
+    sum += ms;
+  }
+  if (launches) *launches = ctx->prof_events.size();
+  if (total_ms) *total_ms = sum;
+  if (reset) {
+    for (auto& pr : ctx->prof_events) ctx->prof_free.push_back(pr);
+    ctx->prof_events.clear();
+  }
+  return SST_OK;
 }
 
 sst_status sst_set_tune(sst_ctx* ctx, const sst_tune* t) {

@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <mutex>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/sst.h"
 
@@ -58,7 +60,8 @@ cudaError_t launch_cluster(const sst_digis& in, uint32_t n_feds, const sst_clust
                            const Scratch& s, const Shape& sh, cudaStream_t st);
 cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len, uint32_t n_events,
                          uint32_t n_feds, const uint64_t* clu_off, const sst_clusters& out, sst_event_status* status,
-                         const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st);
+                         const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st,
+                         cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st);
 
 }  // namespace sst
@@ -79,6 +82,9 @@ struct sst_ctx {
   std::string err;
   std::mutex mu;
   sst_server* server = nullptr;
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;  // recorded launches
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_free;    // reusable pairs
 };
 
 namespace sst {

@@ -3,25 +3,33 @@
 // (section 3).
 //
 // Work unit: one FED (96 channels x 256 strips) of one event, handled by one CTA.
-// A CTA stages the FED's bytes in shared memory with 16-byte loads, walks the
-// header and FE-unit lengths to locate the 96 channel records (the "map of channel
-// locations"), validates and counts each channel's runs (one thread per channel),
-// prefix-sums the counts, and copies the runs into an on-chip digi tile sorted by
-// strip (groups of `lanes` threads per channel).  The clustering then works on the
-// tile: flags against noise x threshold, per-channel 256-bit active / seed / bad
-// masks in shared memory, a left scan from every seed that keeps only the leftmost
-// seed of each candidate, a right scan, the charge / threshold / centroid sums in
-// strip order, and a block scan that ranks the kept clusters.  The cluster (or
-// digi) offset of a FED within its event comes from a decoupled look-back over the
-// FEDs of that event, so that output is sorted without a second pass.  FEDs with
-// more digis than one tile are processed in channel-aligned chunks.
+//   * The FED's bytes are staged in shared memory with 16-byte loads.
+//   * Warp 0 checks the header and walks the 8 FE units' length chains (one lane
+//     per FE unit) to locate the 96 channel records: the "map of channel
+//     locations" of the paper, here on the device.
+//   * One thread per channel validates the channel's runs, counts its digis and
+//     records every run header; a warp scan turns the counts into tile offsets.
+//   * The runs are copied into an on-chip digi tile sorted by strip, one thread
+//     per run (or, for FEDs that do not fit, groups of `lanes` threads per
+//     channel over channel-aligned chunks).
+//   * Clustering on the tile, one thread per digi: channel / seed thresholds,
+//     gain-corrected charge and noise^2; candidate first strips from the tile-order
+//     neighbour and the hole / bad-strip rules; the leftmost seed of each candidate
+//     found by a short backward walk and compacted with a block scan (the paper's
+//     array of seed strips); one thread per kept candidate sums its strips in strip
+//     order and applies the cluster threshold and centroid.
+//   * The FED's offset in its event's cluster (or digi) array comes from a
+//     warp-parallel decoupled look-back over the FEDs before it, so the output is
+//     sorted without a second pass.
 //
-// All floating point in the threshold tests and sums uses explicit round-to-nearest
-// intrinsics (__fmul_rn, __fadd_rn, __fdiv_rn, __fsqrt_rn), so no multiply-add is
-// contracted and results match a sequential binary32 evaluation bit for bit.
+// Floating point in the threshold tests and sums uses explicit round-to-nearest
+// intrinsics (__fmul_rn, __fadd_rn, __fdiv_rn, __fsqrt_rn): no multiply-add is
+// contracted and results equal a sequential binary32 evaluation bit for bit.
 //
 // Every device wait (the look-back) has an iteration limit; when it runs out the
 // event is flagged SST_EV_TIMEOUT and the CTA carries on without the value.
+#include <cstddef>
+
 #include "sst_internal.h"
 
 namespace sst {
@@ -30,112 +38,70 @@ namespace {
 
 // ---------------------------------------------------------------- constants
 
-constexpr unsigned long long kLbAgg = 1ull << 62;   // state carries this FED's own count
-constexpr unsigned long long kLbPre = 2ull << 62;   // state carries the inclusive prefix
+constexpr unsigned long long kLbAgg = 1ull << 62;  // state carries this FED's own count
+constexpr unsigned long long kLbPre = 2ull << 62;  // state carries the inclusive prefix
 constexpr unsigned long long kLbMask = 3ull << 62;
-constexpr int kLbSpinLimit = 1 << 21;               // polls before giving up (~seconds)
-constexpr uint64_t kBadOff = ~0ull;                 // fed_off marker: record outside the event
+constexpr int kLbSpinLimit = 1 << 20;              // polls before giving up (about a second)
+constexpr uint64_t kBadOff = ~0ull;                // fed_off marker: record outside the event
+constexpr int kFedBufMin = 16384;                  // bytes of FED record staged on chip (at least)
 
-// Shared-memory scalars (indices into s.scal).
+// Shared scalars.
 enum {
-  S_TICKET = 0, S_FEDOK, S_TOTAL, S_BASE, S_CHUNK_N, S_EMITS, S_FLAGS, S_NBAD, S_TIMEOUT, S_C1,
-  S_SCAL_N = 16
+  S_TICKET = 0, S_FEDOK, S_TOTAL, S_BASE, S_FLAGS, S_NBAD, S_TIMEOUT, S_SLOTS, S_NOWN,
+  S_NEXT_T, S_NEXT_LEN, S_NEXT_OFF_LO, S_NEXT_OFF_HI, S_SCAL_N = 16
 };
 
-constexpr int kFedBufMin = 16384;
+// ---------------------------------------------------------------- shared memory
 
-// ---------------------------------------------------------------- shared layout
-
-struct Smem {
-  uint32_t* scal;      // [16]
-  uint32_t* wsum;      // [32]
-  uint32_t* chan_pos;  // [96] byte offset of the channel record within the FED
-  uint32_t* chan_cnt;  // [97] digis per channel, then exclusive prefix (in place)
-  uint16_t* chan_len;  // [96]
-  uint8_t* chan_st;    // [96]
-  uint32_t* fe_len;    // [8]
-  uint32_t* bad;       // [96*8]
-  uint32_t* act;       // [96*8]
-  uint32_t* sed;       // [96*8]
-  float* gain;         // [96*2]
-  uint16_t* t_key;     // [tile] (channel << 8) | strip
-  uint8_t* t_adc;      // [tile]
-  uint8_t* t_flag;     // [tile] 1 active, 2 seed, 8 emits a cluster
-  float* t_noise;      // [tile] noise; reused as the rank of emitting digis
-  uint8_t* fedbuf;     // [fedbuf bytes]  union with the cluster staging below
-  uint16_t* st_first;  // [tile]
-  uint16_t* st_width;  // [tile]
-  uint32_t* st_charge; // [tile]
-  float* st_bary;      // [tile]
-  int tile;
-  int fedbuf_bytes;
+// Everything one CTA keeps on chip for one FED.  TILE = digis per tile.
+template <int TILE>
+struct __align__(16) Shm {
+  static constexpr int kRegion = (12 * TILE > kFedBufMin) ? 12 * TILE : kFedBufMin;
+  uint32_t scal[S_SCAL_N];
+  uint32_t wsum[32];
+  uint32_t chan_pos[kCh];       // byte offset of the channel record within the FED
+  uint32_t chan_cnt[kCh + 1];   // digis per channel, then exclusive prefix (in place)
+  uint32_t chan_slot[kCh + 1];  // first run slot of each channel
+  uint32_t fe_len[kFe];
+  alignas(16) uint32_t bad[kCh * kMaskWords];  // 256-bit bad-strip mask per channel (16-byte stores)
+  float gain[kCh * 2];                         // two APV gains per channel
+  uint16_t chan_len[kCh];
+  uint8_t chan_st[kCh];
+  uint16_t t_key[TILE];  // (channel << 8) | strip, sorted
+  uint8_t t_adc[TILE];
+  uint8_t t_flag[TILE];  // 1 active, 2 seed, 4 first strip of a candidate
+  union __align__(16) {
+    uint2 runs[TILE];  // run records, during the copy into the tile
+    struct {
+      float nsq[TILE];     // noise^2 of active digis; later the output rank of owners
+      uint16_t own[TILE];  // first digi of every candidate that holds a seed
+      uint8_t q[TILE];     // gain-corrected charge of active digis
+    } c;
+  } r;
+  union __align__(16) {
+    uint8_t fedbuf[kRegion];  // the staged FED record
+    struct {                  // results per owner, after the copy into the tile
+      uint32_t charge[TILE];
+      float bary[TILE];
+      uint16_t first[TILE];
+      uint16_t width[TILE];  // 0: rejected by the cluster threshold
+    } st;
+  } u;
 };
 
-__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
-
-struct Layout {
-  size_t scal, wsum, chan_pos, chan_cnt, chan_len, chan_st, fe_len, bad, act, sed, gain;
-  size_t t_key, t_adc, t_flag, t_noise, uni, st_first, st_width, st_charge, st_bary, total;
-  int fedbuf;
-};
-
-__host__ __device__ inline Layout make_layout(int tile) {
-  Layout L{};
-  size_t o = 0;
-  L.scal = o; o = al16(o + S_SCAL_N * 4);
-  L.wsum = o; o = al16(o + 32 * 4);
-  L.chan_pos = o; o = al16(o + kCh * 4);
-  L.chan_cnt = o; o = al16(o + (kCh + 1) * 4);
-  L.chan_len = o; o = al16(o + kCh * 2);
-  L.chan_st = o; o = al16(o + kCh);
-  L.fe_len = o; o = al16(o + kFe * 4);
-  L.bad = o; o = al16(o + kCh * kMaskWords * 4);
-  L.act = o; o = al16(o + kCh * kMaskWords * 4);
-  L.sed = o; o = al16(o + kCh * kMaskWords * 4);
-  L.gain = o; o = al16(o + kCh * 2 * 4);
-  L.t_noise = o; o = al16(o + (size_t)tile * 4);
-  L.t_key = o; o = al16(o + (size_t)tile * 2);
-  L.t_adc = o; o = al16(o + (size_t)tile);
-  L.t_flag = o; o = al16(o + (size_t)tile);
-  size_t staging = (size_t)tile * 12;
-  size_t uni = staging > (size_t)kFedBufMin ? staging : (size_t)kFedBufMin;
-  L.fedbuf = (int)uni;
-  L.uni = o;
-  L.st_charge = o;
-  L.st_bary = o + (size_t)tile * 4;
-  L.st_first = o + (size_t)tile * 8;
-  L.st_width = o + (size_t)tile * 10;
-  o = al16(o + uni);
-  L.total = o;
-  return L;
+// Fields written with 8- or 16-byte accesses must be aligned to that width.
+template <int TILE>
+constexpr bool shm_aligned() {
+  return offsetof(Shm<TILE>, bad) % 16 == 0 && offsetof(Shm<TILE>, r) % 16 == 0 &&
+         offsetof(Shm<TILE>, u) % 16 == 0 && sizeof(Shm<TILE>) % 16 == 0;
 }
+static_assert(shm_aligned<1024>() && shm_aligned<2048>() && shm_aligned<4096>(), "shared layout misaligned");
 
-__device__ inline Smem bind_smem(unsigned char* base, int tile) {
-  Layout L = make_layout(tile);
-  Smem s;
-  s.scal = (uint32_t*)(base + L.scal);
-  s.wsum = (uint32_t*)(base + L.wsum);
-  s.chan_pos = (uint32_t*)(base + L.chan_pos);
-  s.chan_cnt = (uint32_t*)(base + L.chan_cnt);
-  s.chan_len = (uint16_t*)(base + L.chan_len);
-  s.chan_st = (uint8_t*)(base + L.chan_st);
-  s.fe_len = (uint32_t*)(base + L.fe_len);
-  s.bad = (uint32_t*)(base + L.bad);
-  s.act = (uint32_t*)(base + L.act);
-  s.sed = (uint32_t*)(base + L.sed);
-  s.gain = (float*)(base + L.gain);
-  s.t_key = (uint16_t*)(base + L.t_key);
-  s.t_adc = (uint8_t*)(base + L.t_adc);
-  s.t_flag = (uint8_t*)(base + L.t_flag);
-  s.t_noise = (float*)(base + L.t_noise);
-  s.fedbuf = (uint8_t*)(base + L.uni);
-  s.st_first = (uint16_t*)(base + L.st_first);
-  s.st_width = (uint16_t*)(base + L.st_width);
-  s.st_charge = (uint32_t*)(base + L.st_charge);
-  s.st_bary = (float*)(base + L.st_bary);
-  s.tile = tile;
-  s.fedbuf_bytes = L.fedbuf;
-  return s;
+// Run record: x = byte offset of the run's first ADC byte in the FED record;
+// y = tile offset within the channel (9 bits) | first strip << 9 | width << 17 |
+// channel << 25.  Width 0 marks an unused slot.
+__device__ __forceinline__ uint32_t run_y(uint32_t toff, uint32_t first, uint32_t width, uint32_t ch) {
+  return toff | (first << 9) | (width << 17) | (ch << 25);
 }
 
 // ---------------------------------------------------------------- small helpers
@@ -150,7 +116,6 @@ __device__ __forceinline__ void st_release(unsigned long long* p, unsigned long 
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ uint32_t rd8(const uint8_t* p) { return *p; }
 __device__ __forceinline__ uint32_t rd16(const uint8_t* p) { return (uint32_t)p[0] | ((uint32_t)p[1] << 8); }
 __device__ __forceinline__ uint32_t rd32(const uint8_t* p) {
   return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
@@ -162,7 +127,7 @@ __device__ uint32_t block_excl_scan(uint32_t v, uint32_t* wsum, uint32_t* total)
   uint32_t x = v;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
     if (lane >= d) x += y;
   }
   if (lane == 31) wsum[warp] = x;
@@ -171,38 +136,66 @@ __device__ uint32_t block_excl_scan(uint32_t v, uint32_t* wsum, uint32_t* total)
     uint32_t w = lane < nw ? wsum[lane] : 0;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, w, d);
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, d);
       if (lane >= d) w += y;
     }
     wsum[lane] = w;
   }
   __syncthreads();
-  uint32_t pre = warp > 0 ? wsum[warp - 1] : 0u;
+  const uint32_t pre = warp > 0 ? wsum[warp - 1] : 0u;
   *total = wsum[nw - 1];
   __syncthreads();
   return pre + x - v;
 }
 
-// Decoupled look-back over items lo .. idx-1 of one event.  Returns the sum of the
-// counts of all earlier items.  Called by one thread.
-__device__ uint32_t lookback(unsigned long long* lb, long long idx, long long lo, bool* timed_out) {
+// Warp-wide exclusive scan, in place, of 96 entries (three consecutive per lane);
+// a[96] receives the total, which is also returned.
+__device__ __forceinline__ uint32_t warp_scan96(uint32_t* a, int lane) {
+  const uint32_t v0 = a[lane * 3], v1 = a[lane * 3 + 1], v2 = a[lane * 3 + 2];
+  const uint32_t local = v0 + v1 + v2;
+  uint32_t x = local;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  const uint32_t e = x - local;
+  a[lane * 3] = e;
+  a[lane * 3 + 1] = e + v0;
+  a[lane * 3 + 2] = e + v0 + v1;
+  const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
+  if (lane == 31) a[kCh] = total;
+  return total;
+}
+
+// Decoupled look-back over items lo .. idx-1 of one event, by one warp: each
+// round reads 32 predecessors at once and sums back to the nearest inclusive
+// prefix.  Returns the sum of the counts of all earlier items (on every lane).
+__device__ uint32_t lookback_warp(unsigned long long* lb, long long idx, long long lo, bool* timed_out) {
+  const int lane = threadIdx.x & 31;
   uint32_t excl = 0;
-  for (long long j = idx - 1; j >= lo; --j) {
-    unsigned long long v;
-    int spins = 0;
-    unsigned ns = 32;
-    for (;;) {
-      v = ld_acquire(lb + j);
-      if (v & kLbMask) break;
+  long long j = idx - 1;
+  int spins = 0;
+  unsigned ns = 32;
+  while (j >= lo) {
+    const long long jj = j - lane;
+    const unsigned long long v = jj >= lo ? ld_acquire(lb + jj) : kLbPre;
+    const unsigned pre = __ballot_sync(0xffffffffu, (v & kLbMask) == kLbPre);
+    const unsigned rdy = __ballot_sync(0xffffffffu, (v & kLbMask) != 0);
+    const int stop = pre ? __ffs(pre) - 1 : 31;
+    const unsigned need = stop == 31 ? 0xffffffffu : ((2u << stop) - 1u);
+    if ((rdy & need) != need) {
       if (++spins > kLbSpinLimit) {
         *timed_out = true;
         return excl;
       }
       __nanosleep(ns);
       if (ns < 1024) ns <<= 1;
+      continue;
     }
-    excl += (uint32_t)v;
-    if ((v & kLbMask) == kLbPre) break;
+    excl += __reduce_add_sync(0xffffffffu, lane <= stop ? (uint32_t)v : 0u);
+    if (pre) break;
+    j -= 32;
   }
   return excl;
 }
@@ -222,152 +215,199 @@ __device__ void stage_fed(const uint8_t* g, uint32_t len, uint8_t* dst) {
   }
 }
 
-// Parses one FED (a1 + the validating count of a2).  On return (after a barrier):
-// chan_pos/len/st hold each channel's record, chan_cnt[0..96] the exclusive
-// prefix of the per-channel digi counts, scal[S_TOTAL] the FED's digi count,
-// scal[S_FLAGS] / scal[S_NBAD] the OR of channel statuses and the number of bad
-// channels.  Returns the pointer the records are to be read from (shared or
-// global).  `len` is the FED record length; `present` is false for an absent FED
-// (fed_len 0) and `in_range` false when the record would leave the event.
-__device__ const uint8_t* parse_fed(const Smem& s, const uint8_t* gfed, uint32_t len, uint32_t fed_id,
-                                    bool in_range) {
-  const int tid = threadIdx.x;
+// Loads bad-strip masks and APV gains of the FED's 96 channels.
+template <int TILE>
+__device__ void load_fed_calib(Shm<TILE>& s, const KParams& kp, uint32_t fed) {
+  const uint4* bm = reinterpret_cast<const uint4*>(kp.badmask + (size_t)fed * kCh * kMaskWords);
+  uint4* bd = reinterpret_cast<uint4*>(s.bad);
+  for (int i = threadIdx.x; i < kCh * kMaskWords / 4; i += blockDim.x) bd[i] = __ldg(bm + i);
+  const float* gp = kp.gain + (size_t)fed * kCh * 2;
+  for (int i = threadIdx.x; i < kCh * 2; i += blockDim.x) s.gain[i] = __ldg(gp + i);
+}
+
+// Header, FE-unit walk, per-channel validation and digi counts (a1 + a2).  `src`
+// points at the record (shared or global memory).  On return (after a barrier):
+// chan_* describe each channel, chan_cnt holds the exclusive prefix of the digi
+// counts, scal[S_TOTAL] the FED's digis, scal[S_FLAGS] / scal[S_NBAD] the OR of
+// channel statuses and the number of bad channels, and - when the run slots
+// fitted (scal[S_SLOTS] != 0) - runs[] one record per run.
+template <int TILE>
+__device__ void parse_body(Shm<TILE>& s, const uint8_t* src, uint32_t len, uint32_t fed_id, bool in_range) {
+  const int tid = threadIdx.x, lane = tid & 31;
   const bool present = in_range && len > 0;
-  const bool staged = present && len <= (uint32_t)s.fedbuf_bytes;
-  if (staged) stage_fed(gfed, len, s.fedbuf);
-  const uint8_t* src = staged ? s.fedbuf : gfed;
-  __syncthreads();
-
-  // FED header (thread 0).
-  if (tid == 0) {
-    uint32_t ok = 0;
-    if (present && len >= (uint32_t)kHdr) {
-      uint64_t body = 0;
-      for (int u = 0; u < kFe; u++) {
-        uint32_t l = rd16(src + 16 + 2 * u);
-        s.fe_len[u] = l;
-        body += (l + 7u) & ~7u;
+  if (tid < 32) {
+    // header and FE-unit lengths: lanes 0..7 hold one FE unit each
+    bool ok = present && len >= (uint32_t)kHdr;
+    uint32_t fl = 0, start = 0;
+    if (ok) {
+      fl = lane < kFe ? rd16(src + 16 + 2 * lane) : 0u;
+      const uint32_t padded = (fl + 7u) & ~7u;
+      uint32_t x = padded;
+#pragma unroll
+      for (int d = 1; d < 8; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
       }
-      uint64_t total = (kHdr + body + 15u) & ~uint64_t(15);
-      ok = rd32(src) == SST_FED_MAGIC && rd16(src + 4) == fed_id && rd8(src + 6) == (uint32_t)kCh &&
-           rd8(src + 7) == (uint32_t)kFe && rd32(src + 8) == len && total == len;
+      start = kHdr + x - padded;
+      const uint32_t body = __shfl_sync(0xffffffffu, x, kFe - 1);
+      const uint32_t total = (kHdr + body + 15u) & ~15u;
+      bool hdr = true;
+      if (lane == 0)
+        hdr = rd32(src) == SST_FED_MAGIC && rd16(src + 4) == fed_id && src[6] == (uint8_t)kCh &&
+              src[7] == (uint8_t)kFe && rd32(src + 8) == len && total == len;
+      ok = __shfl_sync(0xffffffffu, hdr, 0);
     }
-    s.scal[S_FEDOK] = ok;
-  }
-  __syncthreads();
-  const bool fed_ok = s.scal[S_FEDOK] != 0;
-  const uint8_t fed_status = (!in_range || (present && !fed_ok)) ? (uint8_t)SST_CH_FED_HDR : (uint8_t)0;
-
-  // FE-unit walk: one thread per FE unit locates its 12 channel records.
-  if (tid < kFe) {
-    const int u = tid;
-    if (fed_ok) {
-      uint32_t start = kHdr;
-      for (int v = 0; v < u; v++) start += (s.fe_len[v] + 7u) & ~7u;
-      const uint32_t end = start + s.fe_len[u];
-      uint32_t p = start;
-      bool ok = true;
-      for (int k = 0; k < kChPerFe; k++) {
-        const int c = u * kChPerFe + k;
-        uint32_t l = 0;
-        if (ok) {
-          if (p + 2 > end) {
-            ok = false;
-          } else {
-            l = rd16(src + p);
-            if (l < 3 || p + l > end) ok = false;
+    const uint8_t fed_status = (!in_range || (present && !ok)) ? (uint8_t)SST_CH_FED_HDR : (uint8_t)0;
+    if (lane < kFe) {
+      // walk the 12 channel lengths of FE unit `lane`
+      if (ok) {
+        const uint32_t end = start + fl;
+        uint32_t p = start;
+        bool good = true;
+        for (int k = 0; k < kChPerFe; k++) {
+          const int c = lane * kChPerFe + k;
+          uint32_t l = 0;
+          if (good) {
+            if (p + 2 > end) {
+              good = false;
+            } else {
+              l = rd16(src + p);
+              if (l < 3 || p + l > end) good = false;
+            }
           }
+          s.chan_pos[c] = good ? p : 0u;
+          s.chan_len[c] = good ? (uint16_t)l : (uint16_t)0;
+          if (good) p += l;
         }
-        s.chan_pos[c] = ok ? p : 0;
-        s.chan_len[c] = ok ? (uint16_t)l : 0;
-        if (ok) p += l;
+        if (good && p != end) good = false;
+        for (int k = 0; k < kChPerFe; k++) s.chan_st[lane * kChPerFe + k] = good ? 0 : (uint8_t)SST_CH_FRAMING;
+      } else {
+        for (int k = 0; k < kChPerFe; k++) {
+          const int c = lane * kChPerFe + k;
+          s.chan_pos[c] = 0;
+          s.chan_len[c] = 0;
+          s.chan_st[c] = fed_status;
+        }
       }
-      if (ok && p != end) ok = false;
-      for (int k = 0; k < kChPerFe; k++) s.chan_st[u * kChPerFe + k] = ok ? 0 : (uint8_t)SST_CH_FRAMING;
-    } else {
-      for (int k = 0; k < kChPerFe; k++) {
-        const int c = u * kChPerFe + k;
-        s.chan_pos[c] = 0;
-        s.chan_len[c] = 0;
-        s.chan_st[c] = fed_status;
-      }
+    }
+    __syncwarp();
+    // run slots: a run takes at least 3 bytes, so (len - 3) / 3 slots per channel
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const int c = lane * 3 + k;
+      s.chan_slot[c] = s.chan_st[c] == 0 && s.chan_len[c] >= 3 ? (s.chan_len[c] - 3u) / 3u : 0u;
+    }
+    __syncwarp();
+    const uint32_t slots = warp_scan96(s.chan_slot, lane);
+    if (lane == 0) {
+      s.scal[S_FEDOK] = ok ? 1u : 0u;
+      s.scal[S_SLOTS] = slots <= (uint32_t)TILE ? 1u : 0u;
     }
   }
   __syncthreads();
+  const bool use_slots = s.scal[S_SLOTS] != 0;
 
-  // Channel records: validate every run and count digis (one thread per channel).
+  // one thread per channel: validate every run, count digis, record run headers
   if (tid < kCh) {
     const int c = tid;
-    uint32_t cnt = 0;
+    uint32_t cnt = 0, nrun = 0;
     uint8_t st = s.chan_st[c];
-    if (st == 0 && fed_ok) {
-      const uint8_t* r = src + s.chan_pos[c];
+    const uint32_t slot0 = s.chan_slot[c], slot1 = s.chan_slot[c + 1];
+    if (st == 0 && s.chan_len[c] >= 3) {
+      const uint32_t pos = s.chan_pos[c];
+      const uint8_t* r = src + pos;
       const uint32_t len_c = s.chan_len[c];
-      if (rd8(r + 2) != SST_ZS_CODE) {
+      if (r[2] != SST_ZS_CODE) {
         st = SST_CH_BAD_CODE;
       } else {
         uint32_t p = 3, prev_end = 0;
         while (p < len_c) {
           if (p + 2 > len_c) { st = SST_CH_TRUNC; break; }
-          const uint32_t first = rd8(r + p), w = rd8(r + p + 1);
+          const uint32_t first = r[p], w = r[p + 1];
           if (w == 0 || first + w > (uint32_t)kStrips) { st = SST_CH_RUN_RANGE; break; }
           if (first < prev_end) { st = SST_CH_RUN_ORDER; break; }
           if (p + 2 + w > len_c) { st = SST_CH_TRUNC; break; }
+          if (use_slots && slot0 + nrun < slot1)
+            s.r.runs[slot0 + nrun] = make_uint2(pos + p + 2, run_y(cnt, first, w, c));
           prev_end = first + w;
           cnt += w;
+          nrun++;
           p += 2 + w;
         }
       }
-      if (st) cnt = 0;
+      if (st) {
+        cnt = 0;
+        nrun = 0;
+      }
       s.chan_st[c] = st;
     }
+    if (use_slots)
+      for (uint32_t k = slot0 + nrun; k < slot1; k++) s.r.runs[k] = make_uint2(0u, 0u);
     s.chan_cnt[c] = cnt;
   }
   __syncthreads();
 
-  // Exclusive prefix over the 96 channel counts, plus status summary (warp 0).
+  // exclusive prefix over the 96 channel counts, plus the status summary
   if (tid < 32) {
-    uint32_t v[3], fl = 0, nb = 0;
+    uint32_t fl = 0, nb = 0;
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      v[k] = s.chan_cnt[tid * 3 + k];
-      const uint8_t st = s.chan_st[tid * 3 + k];
+      const uint8_t st = s.chan_st[lane * 3 + k];
       fl |= st;
       nb += st ? 1u : 0u;
     }
-    const uint32_t local = v[0] + v[1] + v[2];
-    uint32_t x = local;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-      if (tid >= d) x += y;
-    }
-    uint32_t e = x - local;
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-      s.chan_cnt[tid * 3 + k] = e;
-      e += v[k];
-    }
-    if (tid == 31) {
-      s.chan_cnt[kCh] = x;
-      s.scal[S_TOTAL] = x;
-    }
+    const uint32_t total = warp_scan96(s.chan_cnt, lane);
     fl = __reduce_or_sync(0xffffffffu, fl);
     nb = __reduce_add_sync(0xffffffffu, nb);
-    if (tid == 0) {
+    if (lane == 0) {
+      s.scal[S_TOTAL] = total;
       s.scal[S_FLAGS] = fl;
       s.scal[S_NBAD] = nb;
     }
   }
   __syncthreads();
-  return src;
 }
 
-// Copies the runs of channels [c0, c1) into the tile (digis sorted by strip).
-// Groups of `lanes` threads share a channel: all walk the run headers, each copies
-// every lanes-th ADC byte.  Records were validated by parse_fed; the copy is still
-// bounded by the counted digis so that it cannot leave the tile.
-__device__ void emit_tile(const Smem& s, const uint8_t* src, int c0, int c1, int lanes) {
+// Stages the FED record when it fits and parses it.  Returns true when the
+// record was staged in shared memory.
+template <int TILE>
+__device__ bool parse_fed(Shm<TILE>& s, const uint8_t* gfed, uint32_t len, uint32_t fed_id, bool in_range) {
+  const bool staged = in_range && len > 0 && len <= (uint32_t)Shm<TILE>::kRegion;
+  if (staged) {
+    stage_fed(gfed, len, s.u.fedbuf);
+    __syncthreads();
+    parse_body(s, s.u.fedbuf, len, fed_id, in_range);
+  } else {
+    parse_body(s, gfed, len, fed_id, in_range);
+  }
+  return staged;
+}
+
+// Copies all runs into the tile, one thread per run slot (single-chunk FEDs whose
+// run slots fitted).
+template <int TILE>
+__device__ void emit_slots(Shm<TILE>& s, const uint8_t* src) {
+  const uint32_t nslots = s.chan_slot[kCh];
+  for (uint32_t k = threadIdx.x; k < nslots; k += blockDim.x) {
+    const uint2 rr = s.r.runs[k];
+    const uint32_t w = (rr.y >> 17) & 0xFFu;
+    if (w == 0) continue;
+    const uint32_t c = rr.y >> 25, first = (rr.y >> 9) & 0xFFu;
+    const uint32_t o = s.chan_cnt[c] + (rr.y & 0x1FFu);
+    const uint8_t* a = src + rr.x;
+    for (uint32_t m = 0; m < w; m++) {
+      s.t_key[o + m] = (uint16_t)((c << 8) | (first + m));
+      s.t_adc[o + m] = a[m];
+    }
+  }
+}
+
+// Copies the runs of channels [c0, c1) into the tile: groups of `lanes` threads
+// share a channel, all walk its run headers, each copies every lanes-th ADC byte.
+// Records were validated by parse_body; the copy is still bounded by the counted
+// digis so that it cannot leave the tile.
+template <int TILE>
+__device__ void emit_channels(Shm<TILE>& s, const uint8_t* src, int c0, int c1, int lanes) {
   const int gid = threadIdx.x / lanes, li = threadIdx.x % lanes, ng = blockDim.x / lanes;
   const uint32_t base = s.chan_cnt[c0];
   for (int c = c0 + gid; c < c1; c += ng) {
@@ -378,8 +418,8 @@ __device__ void emit_tile(const Smem& s, const uint8_t* src, int c0, int c1, int
     const uint32_t len_c = s.chan_len[c];
     uint32_t p = 3, o = 0;
     while (p + 2 <= len_c && o < n) {
-      const uint32_t first = rd8(r + p);
-      uint32_t w = rd8(r + p + 1);
+      const uint32_t first = r[p];
+      uint32_t w = r[p + 1];
       if (w > n - o) w = n - o;
       for (uint32_t k = li; k < w; k += lanes) {
         s.t_key[o0 + o + k] = (uint16_t)((c << 8) | ((first + k) & 255u));
@@ -393,223 +433,302 @@ __device__ void emit_tile(const Smem& s, const uint8_t* src, int c0, int c1, int
 
 // ---------------------------------------------------------------- clustering (a3 - a6)
 
-// Loads bad-strip masks and APV gains of the FED's 96 channels.
-__device__ void load_fed_calib(const Smem& s, const KParams& kp, uint32_t fed) {
-  const uint32_t* bm = kp.badmask + (size_t)fed * kCh * kMaskWords;
-  for (int i = threadIdx.x; i < kCh * kMaskWords; i += blockDim.x) s.bad[i] = __ldg(bm + i);
-  const float* gp = kp.gain + (size_t)fed * kCh * 2;
-  for (int i = threadIdx.x; i < kCh * 2; i += blockDim.x) s.gain[i] = __ldg(gp + i);
+__device__ __forceinline__ bool bit(const uint32_t* m, int t) { return (m[t >> 5] >> (t & 31)) & 1u; }
+
+// Number of set strips in [lo, hi).
+__device__ __forceinline__ int count_range(const uint32_t* m, int lo, int hi) {
+  int n = 0;
+  while (lo < hi) {
+    const int w = lo >> 5, b = lo & 31;
+    const int e = min(hi, (w + 1) << 5);
+    const int len = e - lo;
+    const uint32_t mask = len == 32 ? 0xffffffffu : (((1u << len) - 1u) << b);
+    n += __popc(m[w] & mask);
+    lo = e;
+  }
+  return n;
 }
 
-// a3: active / seed flags of the n tile digis, and the per-channel masks.
-__device__ void flag_tile(const Smem& s, const KParams& kp, uint32_t fed, int c0, int c1, int n) {
-  for (int i = threadIdx.x; i < (c1 - c0) * kMaskWords; i += blockDim.x) {
-    s.act[c0 * kMaskWords + i] = 0;
-    s.sed[c0 * kMaskWords + i] = 0;
+// Are the successive active strips a < t linked?  Every maximal run of holes
+// (non-bad inactive strips) in (a, t) must be at most max_holes long and every
+// maximal run of bad strips at most max_bad long.
+__device__ bool linked_gap(const uint32_t* B, int a, int t, int max_holes, int max_bad) {
+  const int g = t - a - 1;
+  if (g == 0) return true;
+  if (max_holes == 0 && max_bad == 0) return false;
+  if (max_holes == 0) return g <= max_bad && count_range(B, a + 1, t) == g;  // one run of bad strips
+  if (max_bad == 0) return g <= max_holes && count_range(B, a + 1, t) == 0;  // one run of holes
+  int holes = 0, bads = 0;
+  for (int u = a + 1; u < t; ++u) {
+    if (bit(B, u)) {
+      if (++bads > max_bad) return false;
+      holes = 0;
+    } else {
+      if (++holes > max_holes) return false;
+      bads = 0;
+    }
   }
-  __syncthreads();
+  return true;
+}
+
+// a3: per digi, the channel and seed thresholds (binary32 product threshold x
+// noise, strict comparison), the gain-corrected charge and noise^2 of active digis.
+template <int TILE>
+__device__ void flag_tile(Shm<TILE>& s, const KParams& kp, uint32_t fed, int c0, int c1, int n) {
   const float* noise = kp.noise + (size_t)fed * kFedStrips;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const uint32_t key = s.t_key[i];
     const uint32_t c = key >> 8, st = key & 255u;
-    uint8_t fl = 0;
-    float nz = 0.f;
+    uint8_t fl = 0, q = 0;
+    float nsq = 0.f;
     if ((int)c >= c0 && (int)c < c1) {
-      nz = __ldg(noise + key);
-      const uint32_t w = c * kMaskWords + (st >> 5), m = 1u << (st & 31u);
-      const bool isbad = (s.bad[w] & m) != 0;
-      const float a = __uint2float_rn(s.t_adc[i]);
+      const float nz = __ldg(noise + key);
+      const bool isbad = (s.bad[c * kMaskWords + (st >> 5)] >> (st & 31u)) & 1u;
+      const uint32_t adc = s.t_adc[i];
+      const float a = __uint2float_rn(adc);
       const bool act = !isbad && a > __fmul_rn(kp.t_channel, nz);
       const bool sd = !isbad && a > __fmul_rn(kp.t_seed, nz);
+      if (act) {
+        if (adc >= 254u) {
+          q = (uint8_t)adc;  // saturation codes are kept
+        } else {
+          const float x = __fdiv_rn(a, s.gain[c * 2 + (st >> 7)]);
+          const int ci = __float2int_rz(__fadd_rn(x, 0.5f));
+          q = ci > 253 ? (uint8_t)254 : (uint8_t)ci;
+        }
+        nsq = __fmul_rn(nz, nz);
+      }
       fl = (act ? 1 : 0) | (sd ? 2 : 0);
-      if (act) atomicOr(&s.act[w], m);
-      if (sd) atomicOr(&s.sed[w], m);
     }
     s.t_flag[i] = fl;
-    s.t_noise[i] = nz;
+    s.r.c.q[i] = q;
+    s.r.c.nsq[i] = nsq;
   }
   __syncthreads();
 }
 
-__device__ __forceinline__ bool bit(const uint32_t* m, int t) { return (m[t >> 5] >> (t & 31)) & 1u; }
-
-// a4 + a5 + a6: for every seed, scan left (stopping at another seed = not the
-// leftmost seed of its candidate), scan right, widen over adjacent bad strips,
-// sum in strip order, test against the cluster threshold, and stage the result.
-__device__ void form_tile(const Smem& s, const KParams& kp, int n) {
+// Candidate first strips: an active digi not linked to the previous active strip
+// of its channel (found by walking back over the tile, which is sorted by strip).
+template <int TILE>
+__device__ void start_tile(Shm<TILE>& s, const KParams& kp, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    if (!(s.t_flag[i] & 2)) continue;
+    if (!(s.t_flag[i] & 1)) continue;
     const uint32_t key = s.t_key[i];
-    const int c = key >> 8, sp = key & 255;
-    const uint32_t* A = s.act + c * kMaskWords;
-    const uint32_t* S = s.sed + c * kMaskWords;
-    const uint32_t* B = s.bad + c * kMaskWords;
-    // left boundary; ownership
-    int l = sp, holes = 0, bads = 0;
-    bool owner = true;
-    for (int t = sp - 1; t >= 0; --t) {
-      if (bit(A, t)) {
-        if (bit(S, t)) { owner = false; break; }
-        l = t; holes = 0; bads = 0;
-      } else if (bit(B, t)) {
-        if (++bads > kp.max_bad) break;
-        holes = 0;
-      } else {
-        if (++holes > kp.max_holes) break;
-        bads = 0;
+    const uint32_t c = key >> 8;
+    int a = -1;
+    for (int j = i - 1; j >= 0; --j) {
+      const uint32_t kj = s.t_key[j];
+      if ((kj >> 8) != c) break;
+      if (s.t_flag[j] & 1) {
+        a = (int)(kj & 255u);
+        break;
       }
     }
-    if (!owner) continue;
-    // right boundary
-    int r = sp;
-    holes = 0; bads = 0;
-    for (int t = sp + 1; t < kStrips; ++t) {
-      if (bit(A, t)) {
-        r = t; holes = 0; bads = 0;
-      } else if (bit(B, t)) {
-        if (++bads > kp.max_bad) break;
-        holes = 0;
-      } else {
-        if (++holes > kp.max_holes) break;
-        bads = 0;
-      }
-    }
-    int lo = l, hi = r;
-    for (int k = 0; k < kp.max_adj && lo - 1 >= 0 && bit(B, lo - 1); k++) lo--;
-    for (int k = 0; k < kp.max_adj && hi + 1 < kStrips && bit(B, hi + 1); k++) hi++;
-    // sums over the active strips of [l, r], left to right
-    const uint32_t kl = ((uint32_t)c << 8) | (uint32_t)l, kr = ((uint32_t)c << 8) | (uint32_t)r;
-    int j = i;
-    while (j > 0 && s.t_key[j - 1] >= kl) --j;
-    uint32_t s_raw = 0, q_sum = 0, moment = 0;
-    float n2 = 0.f;
-    const float g0 = s.gain[c * 2], g1 = s.gain[c * 2 + 1];
-    for (; j < n && s.t_key[j] <= kr; ++j) {
-      if (!(s.t_flag[j] & 1)) continue;
-      const uint32_t a = s.t_adc[j];
-      const int strip = s.t_key[j] & 255;
-      const float nz = s.t_noise[j];
-      s_raw += a;
-      n2 = __fadd_rn(n2, __fmul_rn(nz, nz));
-      uint32_t q;
-      if (a >= 254u) {
-        q = a;
-      } else {
-        const float x = __fdiv_rn(__uint2float_rn(a), strip < kApv ? g0 : g1);
-        const int ci = __float2int_rz(__fadd_rn(x, 0.5f));
-        q = ci > 253 ? 254u : (uint32_t)ci;
-      }
-      q_sum += q;
-      moment += (uint32_t)(strip - lo) * q;
-    }
-    if (!(__uint2float_rn(s_raw) > __fmul_rn(kp.t_cluster, __fsqrt_rn(n2)))) continue;
-    const int w = hi - lo + 1;
-    float bary;
-    if (q_sum == 0) {
-      bary = __fadd_rn((float)lo, __fmul_rn(0.5f, (float)w));
-    } else {
-      bary = __fadd_rn(__fadd_rn((float)lo, 0.5f), __fdiv_rn(__uint2float_rn(moment), __uint2float_rn(q_sum)));
-    }
-    s.st_first[i] = (uint16_t)lo;
-    s.st_width[i] = (uint16_t)w;
-    s.st_charge[i] = q_sum;
-    s.st_bary[i] = bary;
-    s.t_flag[i] |= 8;
+    if (a < 0 || !linked_gap(s.bad + c * kMaskWords, a, (int)(key & 255u), kp.max_holes, kp.max_bad))
+      s.t_flag[i] |= 4;
   }
   __syncthreads();
 }
 
-// Ranks the emitting digis of the tile in tile order; returns their number.
-__device__ uint32_t rank_tile(const Smem& s, int n) {
+// a4: a seed owns its candidate when no other seed lies between the candidate's
+// first strip and it (the leftmost seed).  The first digis of owned candidates are
+// compacted in strip order with a block scan; returns their number.
+template <int TILE>
+__device__ int owners_tile(Shm<TILE>& s, int n) {
   const int T = blockDim.x;
   const int k = (n + T - 1) / T;
   const int b0 = threadIdx.x * k;
   const int b1 = min(n, b0 + k);
   uint32_t cnt = 0;
-  for (int i = b0; i < b1; i++) cnt += (s.t_flag[i] >> 3) & 1u;
+  for (int i = b0; i < b1; i++) {
+    const uint8_t f = s.t_flag[i];
+    if (!(f & 2)) continue;
+    if (f & 4) {
+      cnt++;
+      continue;
+    }
+    const uint32_t c = s.t_key[i] >> 8;
+    for (int j = i - 1; j >= 0 && (s.t_key[j] >> 8) == c; --j) {
+      const uint8_t g = s.t_flag[j];
+      if (!(g & 1)) continue;
+      if (g & 2) break;  // an earlier seed owns the candidate
+      if (g & 4) {
+        cnt++;
+        break;
+      }
+    }
+  }
   uint32_t total;
   uint32_t r = block_excl_scan(cnt, s.wsum, &total);
-  uint32_t* rank = reinterpret_cast<uint32_t*>(s.t_noise);
+  for (int i = b0; i < b1; i++) {
+    const uint8_t f = s.t_flag[i];
+    if (!(f & 2)) continue;
+    if (f & 4) {
+      s.r.c.own[r++] = (uint16_t)i;
+      continue;
+    }
+    const uint32_t c = s.t_key[i] >> 8;
+    for (int j = i - 1; j >= 0 && (s.t_key[j] >> 8) == c; --j) {
+      const uint8_t g = s.t_flag[j];
+      if (!(g & 1)) continue;
+      if (g & 2) break;
+      if (g & 4) {
+        s.r.c.own[r++] = (uint16_t)j;
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  return (int)total;
+}
+
+// a5 + a6: one thread per owned candidate: the candidate runs from its first digi
+// to the digi before the next candidate start; it is widened over up to max_adj
+// adjacent bad strips; its active strips are summed in strip order (raw ADC,
+// noise^2 left to right in binary32, gain-corrected charge, first moment); then
+// the cluster threshold and the centroid.  Results are staged per owner.
+template <int TILE>
+__device__ void form_owners(Shm<TILE>& s, const KParams& kp, int n, int n_own) {
+  for (int k = threadIdx.x; k < n_own; k += blockDim.x) {
+    const int i0 = s.r.c.own[k];
+    const uint32_t key0 = s.t_key[i0];
+    const uint32_t c = key0 >> 8;
+    const int l = (int)(key0 & 255u);
+    const uint32_t* B = s.bad + c * kMaskWords;
+    int lo = l;
+    for (int m = 0; m < kp.max_adj && lo - 1 >= 0 && bit(B, lo - 1); m++) lo--;
+    uint32_t s_raw = 0, q_sum = 0, moment = 0;
+    float n2 = 0.f;
+    int r = l;
+    int j = i0;
+    do {
+      if (s.t_flag[j] & 1) {
+        const int st = s.t_key[j] & 255;
+        const uint32_t q = s.r.c.q[j];
+        s_raw += s.t_adc[j];
+        n2 = __fadd_rn(n2, s.r.c.nsq[j]);
+        q_sum += q;
+        moment += (uint32_t)(st - lo) * q;
+        r = st;
+      }
+      ++j;
+    } while (j < n && (s.t_key[j] >> 8) == c && !(s.t_flag[j] & 4));
+    int hi = r;
+    for (int m = 0; m < kp.max_adj && hi + 1 < kStrips && bit(B, hi + 1); m++) hi++;
+    const bool pass = __uint2float_rn(s_raw) > __fmul_rn(kp.t_cluster, __fsqrt_rn(n2));
+    const int w = hi - lo + 1;
+    if (pass) {
+      float bary;
+      if (q_sum == 0)
+        bary = __fadd_rn((float)lo, __fmul_rn(0.5f, (float)w));
+      else
+        bary = __fadd_rn(__fadd_rn((float)lo, 0.5f), __fdiv_rn(__uint2float_rn(moment), __uint2float_rn(q_sum)));
+      s.u.st.first[k] = (uint16_t)lo;
+      s.u.st.charge[k] = q_sum;
+      s.u.st.bary[k] = bary;
+    }
+    s.u.st.width[k] = pass ? (uint16_t)w : (uint16_t)0;
+  }
+  __syncthreads();
+}
+
+// Output rank of every kept cluster among the owners; returns the number kept.
+template <int TILE>
+__device__ uint32_t rank_owners(Shm<TILE>& s, int n_own) {
+  const int T = blockDim.x;
+  const int k = (n_own + T - 1) / T;
+  const int b0 = threadIdx.x * k;
+  const int b1 = min(n_own, b0 + k);
+  uint32_t cnt = 0;
+  for (int i = b0; i < b1; i++) cnt += s.u.st.width[i] != 0;
+  uint32_t total;
+  uint32_t r = block_excl_scan(cnt, s.wsum, &total);
+  uint32_t* rank = reinterpret_cast<uint32_t*>(s.r.c.nsq);
   for (int i = b0; i < b1; i++)
-    if (s.t_flag[i] & 8) rank[i] = r++;
+    if (s.u.st.width[i]) rank[i] = r++;
   __syncthreads();
   return total;
 }
 
-// Writes the staged clusters of the tile to out[off + base + rank].
-__device__ void write_tile(const Smem& s, const sst_clusters& out, uint64_t off, uint64_t cap, uint32_t base,
-                           uint32_t fed, int n) {
-  const uint32_t* rank = reinterpret_cast<const uint32_t*>(s.t_noise);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    if (!(s.t_flag[i] & 8)) continue;
-    const uint64_t pos = (uint64_t)base + rank[i];
+// Writes the kept clusters to out[off + base + rank] (dropping those past cap).
+template <int TILE>
+__device__ void write_owners(Shm<TILE>& s, const sst_clusters& out, uint64_t off, uint64_t cap, uint32_t base,
+                             uint32_t fed, int n_own) {
+  const uint32_t* rank = reinterpret_cast<const uint32_t*>(s.r.c.nsq);
+  for (int k = threadIdx.x; k < n_own; k += blockDim.x) {
+    if (!s.u.st.width[k]) continue;
+    const uint64_t pos = (uint64_t)base + rank[k];
     if (pos >= cap) continue;
     const uint64_t o = off + pos;
-    out.det[o] = fed * kCh + (s.t_key[i] >> 8);
-    out.first[o] = s.st_first[i];
-    out.width[o] = s.st_width[i];
-    out.charge[o] = s.st_charge[i];
-    out.barycenter[o] = s.st_bary[i];
+    out.det[o] = fed * kCh + (s.t_key[s.r.c.own[k]] >> 8);
+    out.first[o] = s.u.st.first[k];
+    out.width[o] = s.u.st.width[k];
+    out.charge[o] = s.u.st.charge[k];
+    out.barycenter[o] = s.u.st.bary[k];
   }
 }
 
-// Greedy channel-aligned chunk [c0, c1) holding at most `tile` digis.
-__device__ int chunk_end(const Smem& s, int c0, int tile) {
+// Greedy channel-aligned chunk [c0, c1) holding at most TILE digis.
+template <int TILE>
+__device__ int chunk_end(Shm<TILE>& s, int c0) {
   int c1 = c0 + 1;
-  while (c1 < kCh && s.chan_cnt[c1 + 1] - s.chan_cnt[c0] <= (uint32_t)tile) ++c1;
+  while (c1 < kCh && s.chan_cnt[c1 + 1] - s.chan_cnt[c0] <= (uint32_t)TILE) ++c1;
   return c1;
 }
 
-// Clusters the digis of one FED (already parsed into chan_* or loaded by
-// `load`), writing to out[off ...] with per-event capacity `cap`; the FED's
-// cluster offset comes from the look-back over lb[lo .. idx-1].  `fill(c0, c1)`
-// puts the digis of channels [c0, c1) into the tile.  Returns the clusters found.
-template <typename Fill>
-__device__ void cluster_fed(const Smem& s, const KParams& kp, uint32_t fed, Fill fill, const sst_clusters& out,
+// Clusters the digis of one FED and writes them to out[off ...] (per-event
+// capacity `cap`); the FED's cluster offset in its event comes from the look-back
+// over lb[lo .. idx-1].  `fill(c0, c1)` puts the digis of channels [c0, c1) into
+// the tile (single chunk: c0 = 0, c1 = 96).
+template <int TILE, typename Fill>
+__device__ void cluster_fed(Shm<TILE>& s, const KParams& kp, uint32_t fed, Fill fill, const sst_clusters& out,
                             uint64_t off, uint64_t cap, unsigned long long* lb, long long idx, long long lo,
                             sst_event_status* status) {
   const int tid = threadIdx.x;
   const uint32_t total_digis = s.chan_cnt[kCh];
-  const bool single = total_digis <= (uint32_t)s.tile;
+  const bool single = total_digis <= (uint32_t)TILE;
   uint32_t base = 0, found = 0, written = 0;
   bool first_chunk = true;
   int c0 = 0;
   while (c0 < kCh) {
-    const int c1 = single ? kCh : chunk_end(s, c0, s.tile);
+    const int c1 = single ? kCh : chunk_end(s, c0);
     const int n = (int)(s.chan_cnt[c1] - s.chan_cnt[c0]);
-    if (n > 0 || first_chunk) {
-      if (n > 0) {
-        fill(c0, c1);
-        __syncthreads();
-        flag_tile(s, kp, fed, c0, c1, n);
-        form_tile(s, kp, n);
-      }
-      const uint32_t emits = n > 0 ? rank_tile(s, n) : 0u;
-      if (first_chunk) {
+    int n_own = 0;
+    if (n > 0) {
+      fill(c0, c1);
+      __syncthreads();
+      flag_tile(s, kp, fed, c0, c1, n);
+      start_tile(s, kp, n);
+      n_own = owners_tile(s, n);
+      form_owners(s, kp, n, n_own);
+    }
+    const uint32_t emits = n_own > 0 ? rank_owners(s, n_own) : 0u;
+    if (first_chunk) {
+      if (tid < 32) {
+        bool to = false;
+        uint32_t excl = 0;
+        if (idx > lo) {
+          if (single && tid == 0) st_release(lb + idx, kLbAgg | emits);
+          excl = lookback_warp(lb, idx, lo, &to);
+        }
         if (tid == 0) {
-          bool to = false;
-          uint32_t excl = 0;
-          if (idx > lo) {
-            if (single) st_release(lb + idx, kLbAgg | emits);
-            excl = lookback(lb, idx, lo, &to);
-          }
           if (single) st_release(lb + idx, kLbPre | (uint32_t)(excl + emits));
           s.scal[S_BASE] = excl;
           s.scal[S_TIMEOUT] = to ? 1u : 0u;
         }
-        __syncthreads();
-        base = s.scal[S_BASE];
-        first_chunk = false;
       }
-      if (n > 0) {
-        write_tile(s, out, off, cap, base + found, fed, n);
-        const uint64_t start = (uint64_t)base + found;
-        const uint64_t end = start + emits;
-        written += (uint32_t)(end <= cap ? emits : (start < cap ? cap - start : 0));
-        found += emits;
-        __syncthreads();
-      }
+      __syncthreads();
+      base = s.scal[S_BASE];
+      first_chunk = false;
     }
+    if (emits > 0) {
+      write_owners(s, out, off, cap, base + found, fed, n_own);
+      const uint64_t start = (uint64_t)base + found;
+      const uint64_t end = start + emits;
+      written += (uint32_t)(end <= cap ? emits : (start < cap ? cap - start : 0));
+      found += emits;
+    }
+    __syncthreads();
     c0 = c1;
   }
   if (tid == 0) {
@@ -641,12 +760,11 @@ __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_
     const uint32_t f = b + threadIdx.x;
     const uint32_t len = f < n_feds ? fed_len[(size_t)e * n_feds + f] : 0u;
     uint32_t tot;
-    // 32-bit scan of this chunk; carry kept in 64 bits
     const uint32_t ex = block_excl_scan(len, wsum, &tot);
     const uint64_t carry = carry_s;
     if (f < n_feds) {
       const uint64_t o = ev0 + carry + ex;
-      fed_off[(size_t)e * n_feds + f] = (ev1 >= ev0 && o + len <= ev1 && o >= ev0) ? o : kBadOff;
+      fed_off[(size_t)e * n_feds + f] = (ev1 >= ev0 && o + len <= ev1) ? o : kBadOff;
     }
     __syncthreads();
     if (threadIdx.x == 0) carry_s = carry + tot;
@@ -657,13 +775,13 @@ __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_
 
 // a1 + a2 per event: one CTA per FED (ticket order), digis written to the global
 // digi SoA at the FED's offset from the look-back over FED digi counts.
+template <int TILE>
 __global__ void __launch_bounds__(512) k_unpack(const uint8_t* __restrict__ raw,
                                                 const uint32_t* __restrict__ fed_len,
                                                 const uint64_t* __restrict__ fed_off, uint32_t n_feds,
-                                                sst_digis out, unsigned long long* lb, uint32_t* ticket,
-                                                int tile, int lanes) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const Smem s = bind_smem(smem, tile);
+                                                sst_digis out, unsigned long long* lb, uint32_t* ticket, int lanes) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Shm<TILE>& s = *reinterpret_cast<Shm<TILE>*>(smem_raw);
   const int tid = threadIdx.x;
   if (tid == 0) s.scal[S_TICKET] = atomicAdd(ticket, 1u);
   __syncthreads();
@@ -672,26 +790,29 @@ __global__ void __launch_bounds__(512) k_unpack(const uint8_t* __restrict__ raw,
   const uint64_t fo = fed_off[f];
   const bool in_range = fo != kBadOff;
   const uint32_t len = in_range ? fed_len[f] : 0u;
-  const uint8_t* src = parse_fed(s, in_range ? raw + fo : raw, len, f, in_range);
+  const uint8_t* gfed = in_range ? raw + fo : raw;
+  const bool staged = parse_fed(s, gfed, len, f, in_range);
   const uint32_t total = s.scal[S_TOTAL];
-  if (tid == 0) {
+  if (tid < 32) {
     bool to = false;
     uint32_t excl = 0;
     if (f > 0) {
-      st_release(lb + f, kLbAgg | total);
-      excl = lookback(lb, f, 0, &to);
+      if (tid == 0) st_release(lb + f, kLbAgg | total);
+      excl = lookback_warp(lb, f, 0, &to);
     }
-    st_release(lb + f, kLbPre | (excl + total));
-    s.scal[S_BASE] = excl;
-    uint32_t fl = s.scal[S_FLAGS];
-    if (to) fl |= SST_EV_TIMEOUT;
-    if ((uint64_t)excl + total > out.capacity) fl |= SST_EV_DIGI_CAPACITY;
-    if (fl) atomicOr(&out.status->flags, fl);
-    if (s.scal[S_NBAD]) atomicAdd(&out.status->n_bad_channels, s.scal[S_NBAD]);
-    const uint64_t end = (uint64_t)excl + total;
-    const uint32_t written =
-        end <= out.capacity ? total : ((uint64_t)excl < out.capacity ? (uint32_t)(out.capacity - excl) : 0u);
-    if (written) atomicAdd(&out.status->n_digi, written);
+    if (tid == 0) {
+      st_release(lb + f, kLbPre | (excl + total));
+      s.scal[S_BASE] = excl;
+      uint32_t fl = s.scal[S_FLAGS];
+      if (to) fl |= SST_EV_TIMEOUT;
+      if ((uint64_t)excl + total > out.capacity) fl |= SST_EV_DIGI_CAPACITY;
+      if (fl) atomicOr(&out.status->flags, fl);
+      if (s.scal[S_NBAD]) atomicAdd(&out.status->n_bad_channels, s.scal[S_NBAD]);
+      const uint64_t end = (uint64_t)excl + total;
+      const uint32_t written =
+          end <= out.capacity ? total : ((uint64_t)excl < out.capacity ? (uint32_t)(out.capacity - excl) : 0u);
+      if (written) atomicAdd(&out.status->n_digi, written);
+    }
   }
   __syncthreads();
   const uint32_t base = s.scal[S_BASE];
@@ -703,12 +824,17 @@ __global__ void __launch_bounds__(512) k_unpack(const uint8_t* __restrict__ raw,
     if (c < kCh) out.chan_status[(size_t)f * kCh + c] = s.chan_st[c];
   }
   // digis, one tile-sized chunk at a time, copied out with coalesced stores
+  const bool slots = total <= (uint32_t)TILE && s.scal[S_SLOTS] != 0;
   int c0 = 0;
   while (c0 < kCh) {
-    const int c1 = chunk_end(s, c0, tile);
+    const int c1 = slots ? kCh : chunk_end(s, c0);
     const int n = (int)(s.chan_cnt[c1] - s.chan_cnt[c0]);
     if (n > 0) {
-      emit_tile(s, src, c0, c1, lanes);
+      if (slots) {
+        if (staged) emit_slots(s, s.u.fedbuf); else emit_slots(s, gfed);
+      } else {
+        if (staged) emit_channels(s, s.u.fedbuf, c0, c1, lanes); else emit_channels(s, gfed, c0, c1, lanes);
+      }
       __syncthreads();
       const uint64_t o = (uint64_t)base + s.chan_cnt[c0];
       for (int i = tid; i < n; i += blockDim.x) {
@@ -725,10 +851,11 @@ __global__ void __launch_bounds__(512) k_unpack(const uint8_t* __restrict__ raw,
 }
 
 // a3 - a6 per event: one CTA per FED (ticket order) over the global digi SoA.
+template <int TILE>
 __global__ void __launch_bounds__(512) k_cluster(sst_digis in, uint32_t n_feds, sst_clusters out, KParams kp,
-                                                 unsigned long long* lb, uint32_t* ticket, int tile) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const Smem s = bind_smem(smem, tile);
+                                                 unsigned long long* lb, uint32_t* ticket) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Shm<TILE>& s = *reinterpret_cast<Shm<TILE>*>(smem_raw);
   const int tid = threadIdx.x;
   if (tid == 0) s.scal[S_TICKET] = atomicAdd(ticket, 1u);
   __syncthreads();
@@ -747,25 +874,7 @@ __global__ void __launch_bounds__(512) k_cluster(sst_digis in, uint32_t n_feds, 
   }
   load_fed_calib(s, kp, f);
   __syncthreads();
-  if (tid < 32) {  // exclusive prefix of the 96 counts
-    uint32_t v[3];
-#pragma unroll
-    for (int k = 0; k < 3; k++) v[k] = s.chan_cnt[tid * 3 + k];
-    const uint32_t local = v[0] + v[1] + v[2];
-    uint32_t x = local;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-      if (tid >= d) x += y;
-    }
-    uint32_t e = x - local;
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-      s.chan_cnt[tid * 3 + k] = e;
-      e += v[k];
-    }
-    if (tid == 31) s.chan_cnt[kCh] = x;
-  }
+  if (tid < 32) warp_scan96(s.chan_cnt, tid);
   __syncthreads();
   auto fill = [&](int c0, int c1) {
     const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -787,39 +896,68 @@ __global__ void __launch_bounds__(512) k_cluster(sst_digis in, uint32_t n_feds, 
 
 // a7: every FED of every event of a batch, unpacked and clustered on chip.  A
 // persistent grid takes (FED, event) tickets FED-major, so that the CTAs working
-// at any moment share the same FED's calibration in L2.
+// at any moment share the same FED's calibration in L2.  Thread 0 fetches the
+// next ticket and its FED's offset and length while the current FED is processed.
+template <int TILE>
 __global__ void __launch_bounds__(512) k_batch(const uint8_t* __restrict__ raw,
                                                const uint32_t* __restrict__ fed_len,
                                                const uint64_t* __restrict__ fed_off, uint32_t n_events,
                                                uint32_t n_feds, const uint64_t* __restrict__ clu_off,
                                                sst_clusters out, sst_event_status* status, KParams kp,
-                                               unsigned long long* lb, uint32_t* ticket, int tile, int lanes) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const Smem s = bind_smem(smem, tile);
+                                               unsigned long long* lb, uint32_t* ticket, int lanes) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Shm<TILE>& s = *reinterpret_cast<Shm<TILE>*>(smem_raw);
   const int tid = threadIdx.x;
-  const uint64_t n_items = (uint64_t)n_events * n_feds;
+  const uint32_t n_items = n_events * n_feds;
+  auto fetch = [&]() {
+    const uint32_t t = atomicAdd(ticket, 1u);
+    uint32_t len = 0;
+    uint64_t fo = kBadOff;
+    if (t < n_items) {
+      const uint32_t f = t / n_events, e = t % n_events;
+      const size_t item = (size_t)e * n_feds + f;
+      fo = fed_off[item];
+      len = fed_len[item];
+    }
+    s.scal[S_NEXT_T] = t;
+    s.scal[S_NEXT_LEN] = len;
+    s.scal[S_NEXT_OFF_LO] = (uint32_t)fo;
+    s.scal[S_NEXT_OFF_HI] = (uint32_t)(fo >> 32);
+  };
+  if (tid == 0) fetch();
+  __syncthreads();
   for (;;) {
-    if (tid == 0) s.scal[S_TICKET] = atomicAdd(ticket, 1u);
-    __syncthreads();
-    const uint32_t t = s.scal[S_TICKET];
+    const uint32_t t = s.scal[S_NEXT_T];
     if (t >= n_items) break;
+    const uint64_t fo = ((uint64_t)s.scal[S_NEXT_OFF_HI] << 32) | s.scal[S_NEXT_OFF_LO];
+    const bool in_range = fo != kBadOff;
+    const uint32_t len = in_range ? s.scal[S_NEXT_LEN] : 0u;
+    __syncthreads();
+    if (tid == 0) fetch();
     const uint32_t f = t / n_events, e = t % n_events;
     const size_t item = (size_t)e * n_feds + f;
-    const uint64_t fo = fed_off[item];
-    const bool in_range = fo != kBadOff;
-    const uint32_t len = in_range ? fed_len[item] : 0u;
     load_fed_calib(s, kp, f);
-    const uint8_t* src = parse_fed(s, in_range ? raw + fo : raw, len, f, in_range);
+    const uint8_t* gfed = in_range ? raw + fo : raw;
+    const bool staged = parse_fed(s, gfed, len, f, in_range);
+    const uint32_t total = s.scal[S_TOTAL];
     if (tid == 0) {
       if (s.scal[S_FLAGS]) atomicOr(&status[e].flags, s.scal[S_FLAGS]);
       if (s.scal[S_NBAD]) atomicAdd(&status[e].n_bad_channels, s.scal[S_NBAD]);
-      if (s.scal[S_TOTAL]) atomicAdd(&status[e].n_digi, s.scal[S_TOTAL]);
+      if (total) atomicAdd(&status[e].n_digi, total);
     }
-    const bool single = s.scal[S_TOTAL] <= (uint32_t)tile;
+    const bool single = total <= (uint32_t)TILE;
+    const bool slots = single && s.scal[S_SLOTS] != 0;
     // multi-chunk FEDs re-read their records from global memory: the staging
-    // buffer is reused for cluster records after the first chunk
-    const uint8_t* esrc = (single || src != s.fedbuf) ? src : raw + fo;
-    auto fill = [&](int c0, int c1) { emit_tile(s, esrc, c0, c1, lanes); };
+    // buffer holds cluster results after the first chunk
+    auto fill = [&](int c0, int c1) {
+      if (slots) {
+        if (staged) emit_slots(s, s.u.fedbuf); else emit_slots(s, gfed);
+      } else if (single && staged) {
+        emit_channels(s, s.u.fedbuf, c0, c1, lanes);
+      } else {
+        emit_channels(s, gfed, c0, c1, lanes);
+      }
+    };
     const uint64_t off = clu_off[e];
     const uint64_t cap = clu_off[e + 1] - off;
     cluster_fed(s, kp, f, fill, out, off, cap, lb, (long long)item, (long long)e * n_feds, &status[e]);
@@ -835,23 +973,73 @@ __global__ void k_badmask(const uint8_t* __restrict__ bad, uint32_t* __restrict_
   mask[w] = m;
 }
 
+// ---------------------------------------------------------------- launch helpers
+
+template <int TILE>
+cudaError_t launch_unpack_t(const uint8_t* raw, const uint32_t* fed_len, uint32_t n_feds, const sst_digis& out,
+                            const Scratch& s, const Shape& sh, cudaStream_t st) {
+  const size_t sm = sizeof(Shm<TILE>);
+  cudaError_t e = cudaFuncSetAttribute((const void*)k_unpack<TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e) return e;
+  k_unpack<TILE><<<n_feds, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_feds, out, s.lb, s.tickets, sh.lanes);
+  return cudaGetLastError();
+}
+
+template <int TILE>
+cudaError_t launch_cluster_t(const sst_digis& in, uint32_t n_feds, const sst_clusters& out, const KParams& kp,
+                             const Scratch& s, const Shape& sh, cudaStream_t st) {
+  const size_t sm = sizeof(Shm<TILE>);
+  cudaError_t e = cudaFuncSetAttribute((const void*)k_cluster<TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e) return e;
+  k_cluster<TILE><<<n_feds, sh.block, sm, st>>>(in, n_feds, out, kp, s.lb, s.tickets);
+  return cudaGetLastError();
+}
+
+template <int TILE>
+cudaError_t launch_batch_t(const uint8_t* raw, const uint32_t* fed_len, uint32_t n_events, uint32_t n_feds,
+                           const uint64_t* clu_off, const sst_clusters& out, sst_event_status* status,
+                           const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st,
+                           cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+  const size_t sm = sizeof(Shm<TILE>);
+  const size_t items = (size_t)n_events * n_feds;
+  cudaError_t e = cudaFuncSetAttribute((const void*)k_batch<TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e) return e;
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<TILE>, sh.block, sm))) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int ctas = n_sm * (sh.ctas_per_sm < per_sm ? sh.ctas_per_sm : per_sm);
+  const int grid = (size_t)ctas < items ? ctas : (int)items;
+  if (ev_begin && (e = cudaEventRecord(ev_begin, st))) return e;
+  k_batch<TILE><<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out, status, kp,
+                                            s.lb, s.tickets, sh.lanes);
+  if ((e = cudaGetLastError())) return e;
+  if (ev_end && (e = cudaEventRecord(ev_end, st))) return e;
+  return cudaSuccess;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- host side
 
-size_t smem_bytes(int tile) { return make_layout(tile).total; }
+size_t smem_bytes(int tile) {
+  switch (tile) {
+    case 1024: return sizeof(Shm<1024>);
+    case 2048: return sizeof(Shm<2048>);
+    case 4096: return sizeof(Shm<4096>);
+    default: return 0;
+  }
+}
 
-Shape default_shape() { return Shape{256, 2048, 2, 3}; }
+Shape default_shape() { return Shape{256, 2048, 2, 4}; }
 
 bool shape_valid(const Shape& s) {
   const bool blk = s.block == 128 || s.block == 256 || s.block == 512;
   const bool til = s.tile == 1024 || s.tile == 2048 || s.tile == 4096;
   const bool ln = s.lanes == 1 || s.lanes == 2 || s.lanes == 4 || s.lanes == 8 || s.lanes == 16 || s.lanes == 32;
   return blk && til && ln && s.ctas_per_sm >= 1 && s.ctas_per_sm <= 8;
-}
-
-static cudaError_t set_smem(const void* fn, size_t bytes) {
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 cudaError_t launch_unpack(const uint8_t* raw, uint64_t raw_bytes, const uint32_t* fed_len, uint32_t n_feds,
@@ -861,10 +1049,12 @@ cudaError_t launch_unpack(const uint8_t* raw, uint64_t raw_bytes, const uint32_t
   if ((e = cudaMemsetAsync(s.lb, 0, sizeof(unsigned long long) * n_feds, st))) return e;
   if ((e = cudaMemsetAsync(s.tickets, 0, sizeof(uint32_t) * 4, st))) return e;
   k_fed_scan<<<1, 256, 0, st>>>(nullptr, raw_bytes, fed_len, n_feds, s.fed_off, out.status);
-  const size_t sm = smem_bytes(sh.tile);
-  if ((e = set_smem((const void*)k_unpack, sm))) return e;
-  k_unpack<<<n_feds, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_feds, out, s.lb, s.tickets, sh.tile, sh.lanes);
-  return cudaGetLastError();
+  switch (sh.tile) {
+    case 1024: return launch_unpack_t<1024>(raw, fed_len, n_feds, out, s, sh, st);
+    case 2048: return launch_unpack_t<2048>(raw, fed_len, n_feds, out, s, sh, st);
+    case 4096: return launch_unpack_t<4096>(raw, fed_len, n_feds, out, s, sh, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_cluster(const sst_digis& in, uint32_t n_feds, const sst_clusters& out, const KParams& kp,
@@ -873,31 +1063,36 @@ cudaError_t launch_cluster(const sst_digis& in, uint32_t n_feds, const sst_clust
   if ((e = cudaMemsetAsync(&in.status->n_clusters, 0, sizeof(uint32_t), st))) return e;
   if ((e = cudaMemsetAsync(s.lb, 0, sizeof(unsigned long long) * n_feds, st))) return e;
   if ((e = cudaMemsetAsync(s.tickets, 0, sizeof(uint32_t) * 4, st))) return e;
-  const size_t sm = smem_bytes(sh.tile);
-  if ((e = set_smem((const void*)k_cluster, sm))) return e;
-  k_cluster<<<n_feds, sh.block, sm, st>>>(in, n_feds, out, kp, s.lb, s.tickets, sh.tile);
-  return cudaGetLastError();
+  switch (sh.tile) {
+    case 1024: return launch_cluster_t<1024>(in, n_feds, out, kp, s, sh, st);
+    case 2048: return launch_cluster_t<2048>(in, n_feds, out, kp, s, sh, st);
+    case 4096: return launch_cluster_t<4096>(in, n_feds, out, kp, s, sh, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len, uint32_t n_events,
                          uint32_t n_feds, const uint64_t* clu_off, const sst_clusters& out, sst_event_status* status,
-                         const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st) {
+                         const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st,
+                         cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   cudaError_t e;
   const size_t items = (size_t)n_events * n_feds;
   if ((e = cudaMemsetAsync(status, 0, sizeof(sst_event_status) * n_events, st))) return e;
   if ((e = cudaMemsetAsync(s.lb, 0, sizeof(unsigned long long) * items, st))) return e;
   if ((e = cudaMemsetAsync(s.tickets, 0, sizeof(uint32_t) * 4, st))) return e;
   k_fed_scan<<<n_events, 256, 0, st>>>(event_off, 0, fed_len, n_feds, s.fed_off, status);
-  const size_t sm = smem_bytes(sh.tile);
-  if ((e = set_smem((const void*)k_batch, sm))) return e;
-  int per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, sh.block, sm))) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int ctas = n_sm * (sh.ctas_per_sm < per_sm ? sh.ctas_per_sm : per_sm);
-  const int grid = (size_t)ctas < items ? ctas : (int)items;
-  k_batch<<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out, status, kp, s.lb,
-                                      s.tickets, sh.tile, sh.lanes);
-  return cudaGetLastError();
+  switch (sh.tile) {
+    case 1024:
+      return launch_batch_t<1024>(raw, fed_len, n_events, n_feds, clu_off, out, status, kp, s, sh, n_sm, st,
+                                  ev_begin, ev_end);
+    case 2048:
+      return launch_batch_t<2048>(raw, fed_len, n_events, n_feds, clu_off, out, status, kp, s, sh, n_sm, st,
+                                  ev_begin, ev_end);
+    case 4096:
+      return launch_batch_t<4096>(raw, fed_len, n_events, n_feds, clu_off, out, status, kp, s, sh, n_sm, st,
+                                  ev_begin, ev_end);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st) {
