@@ -389,10 +389,10 @@ def main():
             "e2e": {"value": round(total_events / e2e_s, 1), "unit": "events/s",
                     "h2d_bytes_per_step": int(h2d_bytes), "d2h_bytes_per_step": int(d2h_total / e2e_steps),
                     "steps": e2e_steps},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": 4 * args.steps,
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "kernel": "k_batch", "kernel_ms": round(k_ms, 4), "algorithmic_bytes": int(b_alg),
+                         "kernel": "k_batch", "kernels_per_step": 4, "kernel_ms": round(k_ms, 4), "algorithmic_bytes": int(b_alg),
                          "peak_kind": peak_kind},
             "cpu_baseline": cpu,
             "clocks": clk,

@@ -152,7 +152,7 @@ typedef struct {
   uint16_t* width;
   uint32_t* charge;
   float* barycenter;
-  uint64_t capacity; /* per-event path: elements of each array */
+  uint64_t capacity; /* elements of each array; also sizes the context's staging scratch */
 } sst_clusters;
 
 /* ---- context ------------------------------------------------------------------ */
@@ -197,21 +197,26 @@ sst_status sst_unpack(sst_ctx* ctx, const uint8_t* raw, uint64_t raw_bytes, cons
 
 /* Clusters one event's digis (as sst_unpack wrote them, for n_feds FEDs) with the
  * three-threshold algorithm (section 2).  Writes the cluster SoA and sets
- * in->status->n_clusters; ORs SST_EV_CLUSTER_CAPACITY / SST_EV_TIMEOUT into
- * in->status->flags.  NO_CALIB before sst_calib_upload. */
+ * in->status->n_clusters.  When the event has more clusters than out->capacity,
+ * SST_EV_CLUSTER_CAPACITY is ORed into in->status->flags and the arrays hold a
+ * sorted subset of the event's clusters (whole FEDs first, in allocation order).
+ * NO_CALIB before sst_calib_upload. */
 sst_status sst_cluster(sst_ctx* ctx, const sst_digis* in, uint32_t n_feds, const sst_clusters* out,
                        void* stream);
 
 /* ---- batched path (section 3: many events concurrently on one GPU) -------------- */
 
 /* Unpacks and clusters n_events events in one persistent launch; digis stay on
- * chip.  All pointers are device memory:
+ * chip.  Every FED's clusters are staged (context scratch of out->capacity
+ * records), then ordered per event by a scan and a copy kernel.  All pointers are
+ * device memory:
  *   raw        events back to back; event e occupies [event_off[e], event_off[e+1]),
  *              every event_off[e] a multiple of 16
  *   event_off  [n_events + 1] uint64
  *   fed_len    [n_events * n_feds] uint32, event-major
  *   clu_off    [n_events + 1] uint64: event e's clusters go to
- *              [clu_off[e], clu_off[e+1]) of out's arrays (capacity per event)
+ *              [clu_off[e], clu_off[e+1]) of out's arrays (capacity per event);
+ *              clu_off[n_events] <= out->capacity
  *   status     [n_events] per-event status records
  * Output is identical, event by event, to sst_unpack + sst_cluster on each event
  * alone.  NO_CALIB before sst_calib_upload. */

@@ -33,29 +33,40 @@ KParams kparams(const sst_ctx* c) {
   return k;
 }
 
-cudaError_t ensure_scratch(Scratch& s, size_t lb_needed, size_t fed_off_needed) {
+template <typename T>
+static cudaError_t grow(T*& p, size_t& cap, size_t need) {
+  if (need <= cap) return cudaSuccess;
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  cudaError_t e = cudaMalloc(&p, need * sizeof(T));
+  if (e == cudaSuccess) cap = need;
+  return e;
+}
+
+cudaError_t ensure_scratch(Scratch& s, size_t items, size_t events, size_t stage_records) {
   cudaError_t e = cudaSuccess;
   if (!s.tickets) {
     if ((e = cudaMalloc(&s.tickets, 16 * sizeof(uint32_t)))) return e;
     if ((e = cudaMemset(s.tickets, 0, 16 * sizeof(uint32_t)))) return e;
   }
-  if (lb_needed > s.lb_cap || fed_off_needed > s.fed_off_cap) {
+  items = items ? items : 1;
+  events = events ? events : 1;
+  stage_records = stage_records ? stage_records : 1;
+  if (items > s.items_cap || events > s.ev_cap || stage_records > s.stage_cap) {
     // growing: wait for all work that may still use the old buffers
     if ((e = cudaDeviceSynchronize())) return e;
-    if (lb_needed > s.lb_cap) {
-      if (s.lb) cudaFree(s.lb);
-      s.lb = nullptr;
-      s.lb_cap = 0;
-      if ((e = cudaMalloc(&s.lb, lb_needed * sizeof(unsigned long long)))) return e;
-      s.lb_cap = lb_needed;
+    if (items > s.items_cap) {
+      size_t cap = s.items_cap, c2 = s.items_cap, c3 = s.items_cap, c4 = s.items_cap, c5 = s.items_cap;
+      if ((e = grow(s.lb, cap, items))) return e;
+      if ((e = grow(s.fed_off, c2, items))) return e;
+      if ((e = grow(s.fed_cnt, c3, items))) return e;
+      if ((e = grow(s.fed_start, c4, items))) return e;
+      if ((e = grow(s.fed_dest, c5, items))) return e;
+      s.items_cap = items;
     }
-    if (fed_off_needed > s.fed_off_cap) {
-      if (s.fed_off) cudaFree(s.fed_off);
-      s.fed_off = nullptr;
-      s.fed_off_cap = 0;
-      if ((e = cudaMalloc(&s.fed_off, fed_off_needed * sizeof(uint64_t)))) return e;
-      s.fed_off_cap = fed_off_needed;
-    }
+    if ((e = grow(s.ev_alloc, s.ev_cap, events))) return e;
+    if ((e = grow(s.stage, s.stage_cap, stage_records))) return e;
   }
   return cudaSuccess;
 }
@@ -63,6 +74,11 @@ cudaError_t ensure_scratch(Scratch& s, size_t lb_needed, size_t fed_off_needed) 
 void free_scratch(Scratch& s) {
   if (s.lb) cudaFree(s.lb);
   if (s.fed_off) cudaFree(s.fed_off);
+  if (s.fed_cnt) cudaFree(s.fed_cnt);
+  if (s.fed_start) cudaFree(s.fed_start);
+  if (s.fed_dest) cudaFree(s.fed_dest);
+  if (s.ev_alloc) cudaFree(s.ev_alloc);
+  if (s.stage) cudaFree(s.stage);
   if (s.tickets) cudaFree(s.tickets);
   s = Scratch{};
 }
@@ -106,7 +122,7 @@ sst_status sst_create(sst_ctx** out, int device, uint32_t n_feds) {
   c->shape = default_shape();
   DeviceGuard g(device);
   cudaError_t e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
-  if (e == cudaSuccess) e = ensure_scratch(c->scratch, (size_t)n_feds, (size_t)n_feds);
+  if (e == cudaSuccess) e = ensure_scratch(c->scratch, (size_t)n_feds, 1, 1);
   if (e != cudaSuccess) {
     free_scratch(c->scratch);
     delete c;
@@ -189,7 +205,7 @@ sst_status sst_unpack(sst_ctx* ctx, const uint8_t* raw, uint64_t raw_bytes, cons
   if (n_feds == 0 || n_feds > ctx->n_feds)
     return set_err(ctx, SST_ERR_INVALID_ARG, "sst_unpack: n_feds outside 1..context FEDs");
   DeviceGuard g(ctx->device);
-  cudaError_t e = ensure_scratch(ctx->scratch, n_feds, n_feds);
+  cudaError_t e = ensure_scratch(ctx->scratch, n_feds, 1, 1);
   if (e) return cuda_err(ctx, e, "sst_unpack scratch");
   e = launch_unpack(raw, raw_bytes, fed_len, n_feds, *out, ctx->scratch, ctx->shape, (cudaStream_t)stream);
   return cuda_err(ctx, e, "sst_unpack");
@@ -204,7 +220,7 @@ sst_status sst_cluster(sst_ctx* ctx, const sst_digis* in, uint32_t n_feds, const
   if (n_feds == 0 || n_feds > ctx->n_feds)
     return set_err(ctx, SST_ERR_INVALID_ARG, "sst_cluster: n_feds outside 1..context FEDs");
   DeviceGuard g(ctx->device);
-  cudaError_t e = ensure_scratch(ctx->scratch, n_feds, n_feds);
+  cudaError_t e = ensure_scratch(ctx->scratch, n_feds, 1, out->capacity);
   if (e) return cuda_err(ctx, e, "sst_cluster scratch");
   e = launch_cluster(*in, n_feds, *out, kparams(ctx), ctx->scratch, ctx->shape, (cudaStream_t)stream);
   return cuda_err(ctx, e, "sst_cluster");
@@ -225,7 +241,7 @@ sst_status sst_batch(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off
     return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch: too many FED records in one batch");
   DeviceGuard g(ctx->device);
   const size_t items = (size_t)n_events * n_feds;
-  cudaError_t e = ensure_scratch(ctx->scratch, items, items);
+  cudaError_t e = ensure_scratch(ctx->scratch, items, n_events, out->capacity);
   if (e) return cuda_err(ctx, e, "sst_batch scratch");
   cudaEvent_t eb = nullptr, ee = nullptr;
   if (ctx->profiling) {

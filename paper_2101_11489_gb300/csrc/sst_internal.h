@@ -39,14 +39,21 @@ struct Shape {
   int ctas_per_sm;  // persistent CTAs per SM (batched kernel)
 };
 
-// Device scratch for one stream of work: look-back states, work tickets and
-// per-FED byte offsets.  Owned by a context (or by one server stream).
+// Device scratch for one stream of work, owned by a context (or by one server
+// stream): look-back states of the per-event unpack, work tickets, per-(event,
+// FED) byte offsets and cluster bookkeeping, and the cluster staging buffer.
 struct Scratch {
-  unsigned long long* lb = nullptr;  // look-back states
-  size_t lb_cap = 0;
+  unsigned long long* lb = nullptr;  // look-back states, one per FED (per-event unpack)
   uint64_t* fed_off = nullptr;       // absolute byte offset per (event, FED)
-  size_t fed_off_cap = 0;
-  uint32_t* tickets = nullptr;       // [4] work counters
+  uint32_t* fed_cnt = nullptr;       // clusters found per (event, FED)
+  uint32_t* fed_start = nullptr;     // staging offset per (event, FED), within its event's slice
+  uint32_t* fed_dest = nullptr;      // output offset per (event, FED), within its event's slice
+  size_t items_cap = 0;
+  uint32_t* ev_alloc = nullptr;      // staging allocation counter per event
+  size_t ev_cap = 0;
+  uint4* stage = nullptr;            // staged cluster records (16 bytes each)
+  size_t stage_cap = 0;
+  uint32_t* tickets = nullptr;       // [16] work counters
 };
 
 size_t smem_bytes(int tile);
@@ -58,6 +65,8 @@ cudaError_t launch_unpack(const uint8_t* raw, uint64_t raw_bytes, const uint32_t
                           const sst_digis& out, const Scratch& s, const Shape& sh, cudaStream_t st);
 cudaError_t launch_cluster(const sst_digis& in, uint32_t n_feds, const sst_clusters& out, const KParams& kp,
                            const Scratch& s, const Shape& sh, cudaStream_t st);
+// Kernels launched per batch step (for launch counting): scan, batch, cluster scan, compaction.
+constexpr int kBatchKernels = 4;
 cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len, uint32_t n_events,
                          uint32_t n_feds, const uint64_t* clu_off, const sst_clusters& out, sst_event_status* status,
                          const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st,
@@ -91,6 +100,6 @@ namespace sst {
 sst_status set_err(sst_ctx* c, sst_status code, const std::string& msg);
 sst_status cuda_err(sst_ctx* c, cudaError_t e, const char* where);
 KParams kparams(const sst_ctx* c);
-cudaError_t ensure_scratch(Scratch& s, size_t lb_needed, size_t fed_off_needed);
+cudaError_t ensure_scratch(Scratch& s, size_t items, size_t events, size_t stage_records);
 void free_scratch(Scratch& s);
 }  // namespace sst

@@ -69,12 +69,12 @@ struct __align__(16) Shm {
   uint8_t chan_st[kCh];
   uint16_t t_key[TILE];  // (channel << 8) | strip, sorted
   uint8_t t_adc[TILE];
-  uint8_t t_flag[TILE];  // 1 active, 2 seed, 4 first strip of a candidate
+  uint8_t t_flag[TILE];  // 1 active, 2 seed
   union __align__(16) {
     uint2 runs[TILE];  // run records, during the copy into the tile
     struct {
       float nsq[TILE];     // noise^2 of active digis; later the output rank of owners
-      uint16_t own[TILE];  // first digi of every candidate that holds a seed
+      uint16_t own[TILE];  // first digi of every candidate that holds a seed, in strip order
       uint8_t q[TILE];     // gain-corrected charge of active digis
     } c;
   } r;
@@ -86,6 +86,7 @@ struct __align__(16) Shm {
       uint16_t first[TILE];
       uint16_t width[TILE];  // 0: rejected by the cluster threshold
     } st;
+    uint16_t aux[TILE];  // per seed: first digi of its candidate | 0x8000 when it owns it
   } u;
 };
 
@@ -507,91 +508,76 @@ __device__ void flag_tile(Shm<TILE>& s, const KParams& kp, uint32_t fed, int c0,
   __syncthreads();
 }
 
-// Candidate first strips: an active digi not linked to the previous active strip
-// of its channel (found by walking back over the tile, which is sorted by strip).
+// Previous / next active digi of the same channel in the (strip-sorted) tile, or -1.
 template <int TILE>
-__device__ void start_tile(Shm<TILE>& s, const KParams& kp, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    if (!(s.t_flag[i] & 1)) continue;
-    const uint32_t key = s.t_key[i];
-    const uint32_t c = key >> 8;
-    int a = -1;
-    for (int j = i - 1; j >= 0; --j) {
-      const uint32_t kj = s.t_key[j];
-      if ((kj >> 8) != c) break;
-      if (s.t_flag[j] & 1) {
-        a = (int)(kj & 255u);
-        break;
-      }
-    }
-    if (a < 0 || !linked_gap(s.bad + c * kMaskWords, a, (int)(key & 255u), kp.max_holes, kp.max_bad))
-      s.t_flag[i] |= 4;
+__device__ __forceinline__ int prev_active(const Shm<TILE>& s, int i, uint32_t c) {
+  for (int j = i - 1; j >= 0; --j) {
+    if ((s.t_key[j] >> 8) != c) return -1;
+    if (s.t_flag[j] & 1) return j;
   }
-  __syncthreads();
+  return -1;
+}
+template <int TILE>
+__device__ __forceinline__ int next_active(const Shm<TILE>& s, int i, int n, uint32_t c) {
+  for (int j = i + 1; j < n; ++j) {
+    if ((s.t_key[j] >> 8) != c) return -1;
+    if (s.t_flag[j] & 1) return j;
+  }
+  return -1;
 }
 
-// a4: a seed owns its candidate when no other seed lies between the candidate's
-// first strip and it (the leftmost seed).  The first digis of owned candidates are
-// compacted in strip order with a block scan; returns their number.
+// a4 (boundary search, left): from every seed, walk back over the active strips
+// of its candidate (successive active strips linked by the hole / bad-strip
+// rules).  Meeting another seed means an earlier seed owns the candidate; reaching
+// the candidate's first strip without one makes this seed the owner.  The first
+// digis of owned candidates are compacted in strip order with a block scan (the
+// array of seed strips the clusters are formed from); returns their number.
 template <int TILE>
-__device__ int owners_tile(Shm<TILE>& s, int n) {
+__device__ int owners_tile(Shm<TILE>& s, const KParams& kp, int n) {
   const int T = blockDim.x;
   const int k = (n + T - 1) / T;
   const int b0 = threadIdx.x * k;
   const int b1 = min(n, b0 + k);
   uint32_t cnt = 0;
   for (int i = b0; i < b1; i++) {
-    const uint8_t f = s.t_flag[i];
-    if (!(f & 2)) continue;
-    if (f & 4) {
-      cnt++;
-      continue;
-    }
+    if (!(s.t_flag[i] & 2)) continue;
     const uint32_t c = s.t_key[i] >> 8;
-    for (int j = i - 1; j >= 0 && (s.t_key[j] >> 8) == c; --j) {
-      const uint8_t g = s.t_flag[j];
-      if (!(g & 1)) continue;
-      if (g & 2) break;  // an earlier seed owns the candidate
-      if (g & 4) {
-        cnt++;
+    const uint32_t* B = s.bad + c * kMaskWords;
+    int cur = i;
+    bool owner = true;
+    for (;;) {
+      const int j = prev_active(s, cur, c);
+      if (j < 0 || !linked_gap(B, s.t_key[j] & 255, s.t_key[cur] & 255, kp.max_holes, kp.max_bad)) break;
+      if (s.t_flag[j] & 2) {
+        owner = false;
         break;
       }
+      cur = j;
     }
+    s.u.aux[i] = (uint16_t)(cur | (owner ? 0x8000 : 0));
+    cnt += owner ? 1u : 0u;
   }
   uint32_t total;
   uint32_t r = block_excl_scan(cnt, s.wsum, &total);
   for (int i = b0; i < b1; i++) {
-    const uint8_t f = s.t_flag[i];
-    if (!(f & 2)) continue;
-    if (f & 4) {
-      s.r.c.own[r++] = (uint16_t)i;
-      continue;
-    }
-    const uint32_t c = s.t_key[i] >> 8;
-    for (int j = i - 1; j >= 0 && (s.t_key[j] >> 8) == c; --j) {
-      const uint8_t g = s.t_flag[j];
-      if (!(g & 1)) continue;
-      if (g & 2) break;
-      if (g & 4) {
-        s.r.c.own[r++] = (uint16_t)j;
-        break;
-      }
-    }
+    if (!(s.t_flag[i] & 2)) continue;
+    const uint32_t a = s.u.aux[i];
+    if (a & 0x8000) s.r.c.own[r++] = (uint16_t)(a & 0x7FFF);
   }
   __syncthreads();
   return (int)total;
 }
 
-// a5 + a6: one thread per owned candidate: the candidate runs from its first digi
-// to the digi before the next candidate start; it is widened over up to max_adj
-// adjacent bad strips; its active strips are summed in strip order (raw ADC,
-// noise^2 left to right in binary32, gain-corrected charge, first moment); then
-// the cluster threshold and the centroid.  Results are staged per owner.
+// a5 + a6: one thread per owned candidate walks forward from its first digi over
+// linked active strips to the right boundary, summing in strip order (raw ADC,
+// noise^2 left to right in binary32, gain-corrected charge, first moment); the
+// candidate is widened over up to max_adj adjacent bad strips; then the cluster
+// threshold and the centroid.  Results are staged per owner.
 template <int TILE>
 __device__ void form_owners(Shm<TILE>& s, const KParams& kp, int n, int n_own) {
   for (int k = threadIdx.x; k < n_own; k += blockDim.x) {
-    const int i0 = s.r.c.own[k];
-    const uint32_t key0 = s.t_key[i0];
+    int j = s.r.c.own[k];
+    const uint32_t key0 = s.t_key[j];
     const uint32_t c = key0 >> 8;
     const int l = (int)(key0 & 255u);
     const uint32_t* B = s.bad + c * kMaskWords;
@@ -600,33 +586,32 @@ __device__ void form_owners(Shm<TILE>& s, const KParams& kp, int n, int n_own) {
     uint32_t s_raw = 0, q_sum = 0, moment = 0;
     float n2 = 0.f;
     int r = l;
-    int j = i0;
-    do {
-      if (s.t_flag[j] & 1) {
-        const int st = s.t_key[j] & 255;
-        const uint32_t q = s.r.c.q[j];
-        s_raw += s.t_adc[j];
-        n2 = __fadd_rn(n2, s.r.c.nsq[j]);
-        q_sum += q;
-        moment += (uint32_t)(st - lo) * q;
-        r = st;
-      }
-      ++j;
-    } while (j < n && (s.t_key[j] >> 8) == c && !(s.t_flag[j] & 4));
+    for (;;) {
+      const int st = s.t_key[j] & 255;
+      const uint32_t q = s.r.c.q[j];
+      s_raw += s.t_adc[j];
+      n2 = __fadd_rn(n2, s.r.c.nsq[j]);
+      q_sum += q;
+      moment += (uint32_t)(st - lo) * q;
+      r = st;
+      const int nx = next_active(s, j, n, c);
+      if (nx < 0 || !linked_gap(B, st, s.t_key[nx] & 255, kp.max_holes, kp.max_bad)) break;
+      j = nx;
+    }
     int hi = r;
     for (int m = 0; m < kp.max_adj && hi + 1 < kStrips && bit(B, hi + 1); m++) hi++;
     const bool pass = __uint2float_rn(s_raw) > __fmul_rn(kp.t_cluster, __fsqrt_rn(n2));
     const int w = hi - lo + 1;
+    float bary = 0.f;
     if (pass) {
-      float bary;
       if (q_sum == 0)
         bary = __fadd_rn((float)lo, __fmul_rn(0.5f, (float)w));
       else
         bary = __fadd_rn(__fadd_rn((float)lo, 0.5f), __fdiv_rn(__uint2float_rn(moment), __uint2float_rn(q_sum)));
-      s.u.st.first[k] = (uint16_t)lo;
-      s.u.st.charge[k] = q_sum;
-      s.u.st.bary[k] = bary;
     }
+    s.u.st.first[k] = (uint16_t)lo;
+    s.u.st.charge[k] = q_sum;
+    s.u.st.bary[k] = bary;
     s.u.st.width[k] = pass ? (uint16_t)w : (uint16_t)0;
   }
   __syncthreads();
@@ -650,21 +635,22 @@ __device__ uint32_t rank_owners(Shm<TILE>& s, int n_own) {
   return total;
 }
 
-// Writes the kept clusters to out[off + base + rank] (dropping those past cap).
+// Staged cluster record (16 bytes): det | first, width | charge | barycenter.
+__device__ __forceinline__ uint4 pack_cluster(uint32_t det, uint32_t first, uint32_t width, uint32_t charge,
+                                              float bary) {
+  return make_uint4(det, first | (width << 16), charge, __float_as_uint(bary));
+}
+
+// Writes the kept clusters of the tile to stage[base + rank], base + rank < cap.
 template <int TILE>
-__device__ void write_owners(Shm<TILE>& s, const sst_clusters& out, uint64_t off, uint64_t cap, uint32_t base,
-                             uint32_t fed, int n_own) {
+__device__ void stage_owners(Shm<TILE>& s, uint4* stage, uint64_t cap, uint64_t base, uint32_t fed, int n_own) {
   const uint32_t* rank = reinterpret_cast<const uint32_t*>(s.r.c.nsq);
   for (int k = threadIdx.x; k < n_own; k += blockDim.x) {
     if (!s.u.st.width[k]) continue;
-    const uint64_t pos = (uint64_t)base + rank[k];
+    const uint64_t pos = base + rank[k];
     if (pos >= cap) continue;
-    const uint64_t o = off + pos;
-    out.det[o] = fed * kCh + (s.t_key[s.r.c.own[k]] >> 8);
-    out.first[o] = s.u.st.first[k];
-    out.width[o] = s.u.st.width[k];
-    out.charge[o] = s.u.st.charge[k];
-    out.barycenter[o] = s.u.st.bary[k];
+    stage[pos] = pack_cluster(fed * kCh + (s.t_key[s.r.c.own[k]] >> 8), s.u.st.first[k], s.u.st.width[k],
+                              s.u.st.charge[k], s.u.st.bary[k]);
   }
 }
 
@@ -676,68 +662,79 @@ __device__ int chunk_end(Shm<TILE>& s, int c0) {
   return c1;
 }
 
-// Clusters the digis of one FED and writes them to out[off ...] (per-event
-// capacity `cap`); the FED's cluster offset in its event comes from the look-back
-// over lb[lo .. idx-1].  `fill(c0, c1)` puts the digis of channels [c0, c1) into
-// the tile (single chunk: c0 = 0, c1 = 96).
+// Where one FED's clusters go: the event's staging slice (clusters of the event
+// are allocated FED by FED with one atomic each) and the per-FED bookkeeping.
+struct StageOut {
+  uint4* stage;         // the event's slice of the staging buffer
+  uint64_t cap;         // records in that slice
+  uint32_t* ev_alloc;   // the event's allocation counter
+  uint32_t* fed_cnt;    // this FED's cluster count
+  uint32_t* fed_start;  // this FED's offset in the slice
+};
+
+// Clusters one chunk of channels [c0, c1) that `fill` has put in the tile;
+// returns the number of kept clusters (ranked in the tile).
 template <int TILE, typename Fill>
-__device__ void cluster_fed(Shm<TILE>& s, const KParams& kp, uint32_t fed, Fill fill, const sst_clusters& out,
-                            uint64_t off, uint64_t cap, unsigned long long* lb, long long idx, long long lo,
+__device__ uint32_t cluster_chunk(Shm<TILE>& s, const KParams& kp, uint32_t fed, Fill& fill, int c0, int c1,
+                                  int n, int* n_own_out) {
+  int n_own = 0;
+  uint32_t emits = 0;
+  if (n > 0) {
+    fill(c0, c1);
+    __syncthreads();
+    flag_tile(s, kp, fed, c0, c1, n);
+    n_own = owners_tile(s, kp, n);
+    form_owners(s, kp, n, n_own);
+    if (n_own > 0) emits = rank_owners(s, n_own);
+  }
+  *n_own_out = n_own;
+  return emits;
+}
+
+// Clusters the digis of one FED and stages them.  A FED that fits one tile is
+// processed once; a larger one is processed chunk by chunk twice, first to count
+// its clusters (so that its staging region can be allocated in one piece), then
+// to stage them.  `fill(c0, c1)` puts the digis of channels [c0, c1) in the tile.
+template <int TILE, typename Fill>
+__device__ void cluster_fed(Shm<TILE>& s, const KParams& kp, uint32_t fed, Fill fill, const StageOut& so,
                             sst_event_status* status) {
   const int tid = threadIdx.x;
   const uint32_t total_digis = s.chan_cnt[kCh];
   const bool single = total_digis <= (uint32_t)TILE;
-  uint32_t base = 0, found = 0, written = 0;
-  bool first_chunk = true;
-  int c0 = 0;
-  while (c0 < kCh) {
+  uint32_t found = 0;
+  if (!single) {
+    for (int c0 = 0; c0 < kCh;) {
+      const int c1 = chunk_end(s, c0);
+      int n_own;
+      found += cluster_chunk(s, kp, fed, fill, c0, c1, (int)(s.chan_cnt[c1] - s.chan_cnt[c0]), &n_own);
+      __syncthreads();
+      c0 = c1;
+    }
+  }
+  uint32_t base = 0;
+  for (int c0 = 0; c0 < kCh;) {
     const int c1 = single ? kCh : chunk_end(s, c0);
     const int n = (int)(s.chan_cnt[c1] - s.chan_cnt[c0]);
     int n_own = 0;
-    if (n > 0) {
-      fill(c0, c1);
-      __syncthreads();
-      flag_tile(s, kp, fed, c0, c1, n);
-      start_tile(s, kp, n);
-      n_own = owners_tile(s, n);
-      form_owners(s, kp, n, n_own);
-    }
-    const uint32_t emits = n_own > 0 ? rank_owners(s, n_own) : 0u;
-    if (first_chunk) {
-      if (tid < 32) {
-        bool to = false;
-        uint32_t excl = 0;
-        if (idx > lo) {
-          if (single && tid == 0) st_release(lb + idx, kLbAgg | emits);
-          excl = lookback_warp(lb, idx, lo, &to);
-        }
-        if (tid == 0) {
-          if (single) st_release(lb + idx, kLbPre | (uint32_t)(excl + emits));
-          s.scal[S_BASE] = excl;
-          s.scal[S_TIMEOUT] = to ? 1u : 0u;
-        }
+    const uint32_t emits = cluster_chunk(s, kp, fed, fill, c0, c1, n, &n_own);
+    if (c0 == 0) {
+      if (tid == 0) {
+        const uint32_t total = single ? emits : found;
+        const uint32_t start = total ? atomicAdd(so.ev_alloc, total) : 0u;
+        uint32_t kept = 0;
+        if ((uint64_t)start < so.cap) kept = (uint64_t)start + total <= so.cap ? total : (uint32_t)(so.cap - start);
+        if (kept < total) atomicOr(&status->flags, SST_EV_CLUSTER_CAPACITY);
+        *so.fed_cnt = kept;
+        *so.fed_start = start;
+        s.scal[S_BASE] = start;
       }
       __syncthreads();
       base = s.scal[S_BASE];
-      first_chunk = false;
     }
-    if (emits > 0) {
-      write_owners(s, out, off, cap, base + found, fed, n_own);
-      const uint64_t start = (uint64_t)base + found;
-      const uint64_t end = start + emits;
-      written += (uint32_t)(end <= cap ? emits : (start < cap ? cap - start : 0));
-      found += emits;
-    }
+    if (emits > 0) stage_owners(s, so.stage, so.cap, base, fed, n_own);
+    base += emits;
     __syncthreads();
     c0 = c1;
-  }
-  if (tid == 0) {
-    if (!single) st_release(lb + idx, kLbPre | (uint32_t)(base + found));
-    uint32_t fl = 0;
-    if ((uint64_t)base + found > cap) fl |= SST_EV_CLUSTER_CAPACITY;
-    if (s.scal[S_TIMEOUT]) fl |= SST_EV_TIMEOUT;
-    if (fl) atomicOr(&status->flags, fl);
-    if (written) atomicAdd(&status->n_clusters, written);
   }
 }
 
@@ -771,6 +768,59 @@ __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_
     __syncthreads();
   }
   if (threadIdx.x == 0 && ev0 + carry_s != ev1) atomicOr(&status[e].flags, SST_EV_SIZE);
+}
+
+// a6, ordering: per event, the exclusive scan of its FEDs' cluster counts gives
+// every FED's position in the event's sorted cluster SoA; the event's total is its
+// cluster count.  One CTA per event.
+__global__ void k_clu_scan(const uint32_t* __restrict__ fed_cnt, uint32_t n_feds, uint32_t* __restrict__ fed_dest,
+                           sst_event_status* status) {
+  __shared__ uint32_t wsum[32];
+  __shared__ uint32_t carry_s;
+  const uint32_t e = blockIdx.x;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (uint32_t b = 0; b < n_feds; b += blockDim.x) {
+    const uint32_t f = b + threadIdx.x;
+    const uint32_t n = f < n_feds ? fed_cnt[(size_t)e * n_feds + f] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan(n, wsum, &tot);
+    const uint32_t carry = carry_s;
+    if (f < n_feds) fed_dest[(size_t)e * n_feds + f] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s = carry + tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) status[e].n_clusters = carry_s;
+}
+
+// a6, output: copies every FED's staged clusters to its place in the event's
+// sorted cluster SoA (16-byte loads, coalesced stores).  One CTA per group of
+// `per_cta` consecutive (event, FED) items.
+__global__ void __launch_bounds__(256) k_compact(const uint4* __restrict__ stage, const uint64_t* __restrict__ clu_off,
+                                                 const uint32_t* __restrict__ fed_cnt,
+                                                 const uint32_t* __restrict__ fed_start,
+                                                 const uint32_t* __restrict__ fed_dest, uint32_t n_events,
+                                                 uint32_t n_feds, uint32_t per_cta, sst_clusters out) {
+  const uint64_t items = (uint64_t)n_events * n_feds;
+  const uint64_t it0 = (uint64_t)blockIdx.x * per_cta;
+  for (uint64_t it = it0; it < it0 + per_cta && it < items; ++it) {
+    const uint32_t n = fed_cnt[it];
+    if (n == 0) continue;
+    const uint32_t e = (uint32_t)(it / n_feds);
+    const uint64_t off = clu_off ? clu_off[e] : 0;
+    const uint4* src = stage + off + fed_start[it];
+    const uint64_t dst = off + fed_dest[it];
+    for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) {
+      const uint4 r = __ldg(src + k);
+      const uint64_t o = dst + k;
+      out.det[o] = r.x;
+      out.first[o] = (uint16_t)(r.y & 0xFFFFu);
+      out.width[o] = (uint16_t)(r.y >> 16);
+      out.charge[o] = r.z;
+      out.barycenter[o] = __uint_as_float(r.w);
+    }
+  }
 }
 
 // a1 + a2 per event: one CTA per FED (ticket order), digis written to the global
@@ -850,16 +900,15 @@ __global__ void __launch_bounds__(512) k_unpack(const uint8_t* __restrict__ raw,
   }
 }
 
-// a3 - a6 per event: one CTA per FED (ticket order) over the global digi SoA.
+// a3 - a6 per event: one CTA per FED over the global digi SoA; clusters staged.
 template <int TILE>
-__global__ void __launch_bounds__(512) k_cluster(sst_digis in, uint32_t n_feds, sst_clusters out, KParams kp,
-                                                 unsigned long long* lb, uint32_t* ticket) {
+__global__ void __launch_bounds__(512) k_cluster(sst_digis in, uint32_t n_feds, KParams kp, uint4* stage,
+                                                 uint64_t cap, uint32_t* ev_alloc, uint32_t* fed_cnt,
+                                                 uint32_t* fed_start) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Shm<TILE>& s = *reinterpret_cast<Shm<TILE>*>(smem_raw);
   const int tid = threadIdx.x;
-  if (tid == 0) s.scal[S_TICKET] = atomicAdd(ticket, 1u);
-  __syncthreads();
-  const uint32_t f = s.scal[S_TICKET];
+  const uint32_t f = blockIdx.x;
   if (f >= n_feds) return;
   // Channel digi ranges from the CSR row pointers, clamped to the input capacity
   // and to 256 digis per channel, so that malformed input cannot leave the tile.
@@ -891,7 +940,8 @@ __global__ void __launch_bounds__(512) k_cluster(sst_digis in, uint32_t n_feds, 
       }
     }
   };
-  cluster_fed(s, kp, f, fill, out, 0, out.capacity, lb, f, 0, in.status);
+  const StageOut so{stage, cap, ev_alloc, fed_cnt + f, fed_start + f};
+  cluster_fed(s, kp, f, fill, so, in.status);
 }
 
 // a7: every FED of every event of a batch, unpacked and clustered on chip.  A
@@ -903,8 +953,9 @@ __global__ void __launch_bounds__(512) k_batch(const uint8_t* __restrict__ raw,
                                                const uint32_t* __restrict__ fed_len,
                                                const uint64_t* __restrict__ fed_off, uint32_t n_events,
                                                uint32_t n_feds, const uint64_t* __restrict__ clu_off,
-                                               sst_clusters out, sst_event_status* status, KParams kp,
-                                               unsigned long long* lb, uint32_t* ticket, int lanes) {
+                                               uint64_t out_cap, sst_event_status* status, KParams kp,
+                                               uint4* stage, uint32_t* ev_alloc, uint32_t* fed_cnt,
+                                               uint32_t* fed_start, uint32_t* ticket, int lanes) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Shm<TILE>& s = *reinterpret_cast<Shm<TILE>*>(smem_raw);
   const int tid = threadIdx.x;
@@ -959,8 +1010,10 @@ __global__ void __launch_bounds__(512) k_batch(const uint8_t* __restrict__ raw,
       }
     };
     const uint64_t off = clu_off[e];
-    const uint64_t cap = clu_off[e + 1] - off;
-    cluster_fed(s, kp, f, fill, out, off, cap, lb, (long long)item, (long long)e * n_feds, &status[e]);
+    const uint64_t end = clu_off[e + 1] < out_cap ? clu_off[e + 1] : out_cap;
+    const uint64_t cap = end > off ? end - off : 0;
+    const StageOut so{stage + (off < out_cap ? off : 0), cap, ev_alloc + e, fed_cnt + item, fed_start + item};
+    cluster_fed(s, kp, f, fill, so, &status[e]);
     __syncthreads();
   }
 }
@@ -987,21 +1040,21 @@ cudaError_t launch_unpack_t(const uint8_t* raw, const uint32_t* fed_len, uint32_
 }
 
 template <int TILE>
-cudaError_t launch_cluster_t(const sst_digis& in, uint32_t n_feds, const sst_clusters& out, const KParams& kp,
-                             const Scratch& s, const Shape& sh, cudaStream_t st) {
+cudaError_t launch_cluster_t(const sst_digis& in, uint32_t n_feds, const KParams& kp, const Scratch& s,
+                             uint64_t cap, const Shape& sh, cudaStream_t st) {
   const size_t sm = sizeof(Shm<TILE>);
   cudaError_t e = cudaFuncSetAttribute((const void*)k_cluster<TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sm);
   if (e) return e;
-  k_cluster<TILE><<<n_feds, sh.block, sm, st>>>(in, n_feds, out, kp, s.lb, s.tickets);
+  k_cluster<TILE><<<n_feds, sh.block, sm, st>>>(in, n_feds, kp, s.stage, cap, s.ev_alloc, s.fed_cnt, s.fed_start);
   return cudaGetLastError();
 }
 
 template <int TILE>
 cudaError_t launch_batch_t(const uint8_t* raw, const uint32_t* fed_len, uint32_t n_events, uint32_t n_feds,
-                           const uint64_t* clu_off, const sst_clusters& out, sst_event_status* status,
-                           const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st,
-                           cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+                           const uint64_t* clu_off, uint64_t out_cap, sst_event_status* status, const KParams& kp,
+                           const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st, cudaEvent_t ev_begin,
+                           cudaEvent_t ev_end) {
   const size_t sm = sizeof(Shm<TILE>);
   const size_t items = (size_t)n_events * n_feds;
   cudaError_t e = cudaFuncSetAttribute((const void*)k_batch<TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1013,11 +1066,24 @@ cudaError_t launch_batch_t(const uint8_t* raw, const uint32_t* fed_len, uint32_t
   const int ctas = n_sm * (sh.ctas_per_sm < per_sm ? sh.ctas_per_sm : per_sm);
   const int grid = (size_t)ctas < items ? ctas : (int)items;
   if (ev_begin && (e = cudaEventRecord(ev_begin, st))) return e;
-  k_batch<TILE><<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out, status, kp,
-                                            s.lb, s.tickets, sh.lanes);
+  k_batch<TILE><<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out_cap, status, kp,
+                                            s.stage, s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets, sh.lanes);
   if ((e = cudaGetLastError())) return e;
   if (ev_end && (e = cudaEventRecord(ev_end, st))) return e;
   return cudaSuccess;
+}
+
+// Per-event cluster order and the copy into the caller's SoA.
+cudaError_t launch_order(const uint64_t* clu_off, uint32_t n_events, uint32_t n_feds, const sst_clusters& out,
+                         sst_event_status* status, const Scratch& s, cudaStream_t st) {
+  k_clu_scan<<<n_events, 256, 0, st>>>(s.fed_cnt, n_feds, s.fed_dest, status);
+  cudaError_t e = cudaGetLastError();
+  if (e) return e;
+  const uint64_t items = (uint64_t)n_events * n_feds;
+  const uint32_t per_cta = 2;
+  k_compact<<<(unsigned)((items + per_cta - 1) / per_cta), 256, 0, st>>>(
+      s.stage, clu_off, s.fed_cnt, s.fed_start, s.fed_dest, n_events, n_feds, per_cta, out);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -1060,15 +1126,15 @@ cudaError_t launch_unpack(const uint8_t* raw, uint64_t raw_bytes, const uint32_t
 cudaError_t launch_cluster(const sst_digis& in, uint32_t n_feds, const sst_clusters& out, const KParams& kp,
                            const Scratch& s, const Shape& sh, cudaStream_t st) {
   cudaError_t e;
-  if ((e = cudaMemsetAsync(&in.status->n_clusters, 0, sizeof(uint32_t), st))) return e;
-  if ((e = cudaMemsetAsync(s.lb, 0, sizeof(unsigned long long) * n_feds, st))) return e;
-  if ((e = cudaMemsetAsync(s.tickets, 0, sizeof(uint32_t) * 4, st))) return e;
+  if ((e = cudaMemsetAsync(s.ev_alloc, 0, sizeof(uint32_t), st))) return e;
   switch (sh.tile) {
-    case 1024: return launch_cluster_t<1024>(in, n_feds, out, kp, s, sh, st);
-    case 2048: return launch_cluster_t<2048>(in, n_feds, out, kp, s, sh, st);
-    case 4096: return launch_cluster_t<4096>(in, n_feds, out, kp, s, sh, st);
+    case 1024: e = launch_cluster_t<1024>(in, n_feds, kp, s, out.capacity, sh, st); break;
+    case 2048: e = launch_cluster_t<2048>(in, n_feds, kp, s, out.capacity, sh, st); break;
+    case 4096: e = launch_cluster_t<4096>(in, n_feds, kp, s, out.capacity, sh, st); break;
     default: return cudaErrorInvalidValue;
   }
+  if (e) return e;
+  return launch_order(nullptr, 1, n_feds, out, in.status, s, st);  // one event at offset 0
 }
 
 cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len, uint32_t n_events,
@@ -1076,23 +1142,27 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
                          const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st,
                          cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   cudaError_t e;
-  const size_t items = (size_t)n_events * n_feds;
   if ((e = cudaMemsetAsync(status, 0, sizeof(sst_event_status) * n_events, st))) return e;
-  if ((e = cudaMemsetAsync(s.lb, 0, sizeof(unsigned long long) * items, st))) return e;
+  if ((e = cudaMemsetAsync(s.ev_alloc, 0, sizeof(uint32_t) * n_events, st))) return e;
   if ((e = cudaMemsetAsync(s.tickets, 0, sizeof(uint32_t) * 4, st))) return e;
   k_fed_scan<<<n_events, 256, 0, st>>>(event_off, 0, fed_len, n_feds, s.fed_off, status);
   switch (sh.tile) {
     case 1024:
-      return launch_batch_t<1024>(raw, fed_len, n_events, n_feds, clu_off, out, status, kp, s, sh, n_sm, st,
-                                  ev_begin, ev_end);
+      e = launch_batch_t<1024>(raw, fed_len, n_events, n_feds, clu_off, out.capacity, status, kp, s, sh, n_sm, st,
+                               ev_begin, ev_end);
+      break;
     case 2048:
-      return launch_batch_t<2048>(raw, fed_len, n_events, n_feds, clu_off, out, status, kp, s, sh, n_sm, st,
-                                  ev_begin, ev_end);
+      e = launch_batch_t<2048>(raw, fed_len, n_events, n_feds, clu_off, out.capacity, status, kp, s, sh, n_sm, st,
+                               ev_begin, ev_end);
+      break;
     case 4096:
-      return launch_batch_t<4096>(raw, fed_len, n_events, n_feds, clu_off, out, status, kp, s, sh, n_sm, st,
-                                  ev_begin, ev_end);
+      e = launch_batch_t<4096>(raw, fed_len, n_events, n_feds, clu_off, out.capacity, status, kp, s, sh, n_sm, st,
+                               ev_begin, ev_end);
+      break;
     default: return cudaErrorInvalidValue;
   }
+  if (e) return e;
+  return launch_order(clu_off, n_events, n_feds, out, status, s, st);
 }
 
 cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st) {

@@ -148,3 +148,37 @@ def test_batch_launch_shapes_give_identical_results(w0):
             for k in c0:
                 assert np.array_equal(c0[k], c1[k])
     sst.sst_set_tune(g.ctx, 256, 3, 2048, 2)
+
+
+def _as_set(c):
+    return set(zip(c["det"].tolist(), c["first"].tolist(), c["width"].tolist(), c["charge"].tolist()))
+
+
+def test_cluster_capacity_overflow_is_flagged_and_bounded(w0):
+    w, calib, g = w0
+    e = eg.make_event(w, calib, 3)
+    od, oc, ost = g.oracle(e.raw, e.fed_len, w.n_feds)
+    cap = oc["det"].size // 3
+    dh, ch = g.event(e.raw, e.fed_len, w.n_feds, clu_cap=cap)
+    assert dh["flags"] & sst.SST_EV_CLUSTER_CAPACITY
+    assert dh["n_clusters"] <= cap and ch["det"].size == dh["n_clusters"]
+    key = ch["det"].astype(np.int64) * 256 + ch["first"]
+    assert np.all(np.diff(key) > 0)  # still sorted
+    assert _as_set(ch) <= _as_set(oc)  # a subset of the true clusters
+    # the batched path flags the same event the same way
+    out = g.batch([(e.raw, e.fed_len)], clu_caps=[cap])
+    st, cl = out[0]
+    assert st["flags"] & sst.SST_EV_CLUSTER_CAPACITY and st["n_clusters"] <= cap
+    assert _as_set(cl) <= _as_set(oc)
+
+
+def test_digi_capacity_overflow_is_flagged_and_bounded(w0):
+    w, calib, g = w0
+    e = eg.make_event(w, calib, 4)
+    od, oc, ost = g.oracle(e.raw, e.fed_len, w.n_feds)
+    cap = od["strip"].size // 2
+    dh, ch = g.event(e.raw, e.fed_len, w.n_feds, digi_cap=cap)
+    assert dh["flags"] & sst.SST_EV_DIGI_CAPACITY
+    assert dh["n_digi"] == cap
+    assert np.array_equal(dh["strip"], od["strip"][:cap])
+    assert np.all(dh["chan_off"] <= cap)
