@@ -226,7 +226,7 @@ sst_status sst_batch(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off
 
 /* Launch-shape knobs of the batched kernel (picked by sst_autotune). */
 typedef struct {
-  uint32_t block;       /* threads per CTA: 128, 256 or 512 */
+  uint32_t block;       /* threads per CTA: 128 or 256 */
   uint32_t ctas_per_sm; /* persistent CTAs per SM: 1..8 (clamped to what fits) */
   uint32_t tile_digis;  /* digis per on-chip tile: 1024, 2048 or 4096 */
   uint32_t lanes_per_channel; /* lanes that copy one channel's runs: 1, 2, 4, 8, 16 or 32 */

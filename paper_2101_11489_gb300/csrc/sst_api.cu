@@ -220,7 +220,7 @@ sst_status sst_cluster(sst_ctx* ctx, const sst_digis* in, uint32_t n_feds, const
   if (n_feds == 0 || n_feds > ctx->n_feds)
     return set_err(ctx, SST_ERR_INVALID_ARG, "sst_cluster: n_feds outside 1..context FEDs");
   DeviceGuard g(ctx->device);
-  cudaError_t e = ensure_scratch(ctx->scratch, n_feds, 1, out->capacity);
+  cudaError_t e = ensure_scratch(ctx->scratch, (size_t)n_feds * kFe, 1, out->capacity);
   if (e) return cuda_err(ctx, e, "sst_cluster scratch");
   e = launch_cluster(*in, n_feds, *out, kparams(ctx), ctx->scratch, ctx->shape, (cudaStream_t)stream);
   return cuda_err(ctx, e, "sst_cluster");
@@ -241,7 +241,7 @@ sst_status sst_batch(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off
     return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch: too many FED records in one batch");
   DeviceGuard g(ctx->device);
   const size_t items = (size_t)n_events * n_feds;
-  cudaError_t e = ensure_scratch(ctx->scratch, items, n_events, out->capacity);
+  cudaError_t e = ensure_scratch(ctx->scratch, items * kFe, n_events, out->capacity);
   if (e) return cuda_err(ctx, e, "sst_batch scratch");
   cudaEvent_t eb = nullptr, ee = nullptr;
   if (ctx->profiling) {
@@ -327,7 +327,7 @@ sst_status sst_autotune(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_
     cudaEventDestroy(e0);
     return cuda_err(ctx, cudaGetLastError(), "autotune event");
   }
-  const int blocks[] = {128, 256, 512};
+  const int blocks[] = {128, 256};
   const int tiles[] = {1024, 2048, 4096};
   const int lanes[] = {1, 2, 4, 8};
   const int per_sm[] = {2, 3, 4, 6, 8};

@@ -1,0 +1,474 @@
+// sst_fe.cuh -- warp-level unpacking and clustering of one FE unit (12 channels of
+// one FED), the work unit of the batched and per-event cluster kernels.
+//
+// A FE unit is independent of every other: its channel records sit back to back in
+// the FED record, and clusters never cross a channel (arXiv 2101.11489, section 2:
+// channel = module of 256 strips).  One warp handles one FE unit from the raw bytes
+// to staged clusters with no block-wide barrier, so that a GB300 SM keeps dozens of
+// independent units in flight and hides the latency of each unit's serial steps
+// (the FE length chain, the run chains, the L2 gathers of noise).
+//
+// Included by sst_kernels.cu only, inside its namespace, after the mask and
+// gap helpers it uses (bit, count_range, linked_gap).
+#pragma once
+
+namespace fe {
+
+constexpr int kTile = 384;    // digis per warp tile (a chunk of whole channels)
+constexpr int kBuf = 1024;    // FE-unit bytes staged per warp (larger units are read in place)
+constexpr int kFeStrips = kChPerFe * kStrips;  // 3,072
+
+// Per-warp shared memory.
+struct __align__(16) Warp {
+  uint8_t fe[kBuf];                      // staged FE-unit bytes
+  uint32_t bad[kChPerFe * kMaskWords];   // bad-strip masks of the 12 channels
+  float gain[kChPerFe * 2];              // APV gains of the 12 channels
+  float nsq[kTile];                      // noise^2 of active digis
+  uint32_t chan_pos[kChPerFe];           // channel record offset within the FE unit
+  uint32_t chan_cnt[kChPerFe + 1];       // digis per channel, then exclusive prefix
+  uint16_t chan_len[kChPerFe];
+  uint8_t chan_st[kChPerFe];
+  uint16_t key[kTile];                   // (channel in FE unit << 8) | strip, sorted
+  uint16_t own[kTile];                   // first digi of every seeded candidate
+  uint8_t adc[kTile];
+  uint8_t flag[kTile];                   // 1 active, 2 seed, 4 first strip of a candidate
+  uint8_t q[kTile];                      // gain-corrected charge of active digis
+};
+
+__device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
+
+// Byte b (0..31) of a 32-byte block held one byte per lane.
+__device__ __forceinline__ uint32_t byte_at(uint32_t v, int b) { return __shfl_sync(0xffffffffu, v, b) & 0xFFu; }
+__device__ __forceinline__ uint32_t u16_at(uint32_t v, int b) { return byte_at(v, b) | (byte_at(v, b + 1) << 8); }
+__device__ __forceinline__ uint32_t u32_at(uint32_t v, int b) { return u16_at(v, b) | (u16_at(v, b + 2) << 16); }
+
+// Where the FE unit is and what the FED header says about it.
+struct Unit {
+  uint32_t fed, u;         // FED index, FE unit (0..7)
+  const uint8_t* src;      // first byte of the FE unit's records (shared or global), or null
+  uint32_t len;            // bytes of channel records in the FE unit
+  uint8_t fed_status;      // SST_CH_FED_HDR when the FED record is corrupt or out of range, else 0
+};
+
+// Reads and checks the FED header (every unit of a FED checks it alike), locates
+// FE unit u and stages its bytes.  `g` is the FED record (len bytes) or null
+// when the record lies outside its event.
+__device__ Unit locate(Warp& w, const uint8_t* g, uint32_t len, uint32_t fed, uint32_t u, bool in_range) {
+  const int lane = threadIdx.x & 31;
+  Unit r{fed, u, nullptr, 0, 0};
+  const bool present = in_range && len > 0;
+  if (!in_range) r.fed_status = SST_CH_FED_HDR;
+  if (!present) return r;
+  if (len < (uint32_t)kHdr) {
+    r.fed_status = SST_CH_FED_HDR;
+    return r;
+  }
+  const uint32_t hb = __ldg(g + lane);  // the 32-byte header, one byte per lane
+  uint32_t fe_len[kFe];
+#pragma unroll
+  for (int v = 0; v < kFe; v++) fe_len[v] = u16_at(hb, 16 + 2 * v);
+  uint32_t body = 0, start = kHdr;
+#pragma unroll
+  for (int v = 0; v < kFe; v++) {
+    const uint32_t p = (fe_len[v] + 7u) & ~7u;
+    if ((uint32_t)v < u) start += p;
+    body += p;
+  }
+  const uint32_t total = (kHdr + body + 15u) & ~15u;
+  const bool ok = u32_at(hb, 0) == SST_FED_MAGIC && u16_at(hb, 4) == fed && byte_at(hb, 6) == (uint32_t)kCh &&
+                  byte_at(hb, 7) == (uint32_t)kFe && u32_at(hb, 8) == len && total == len;
+  if (!ok) {
+    r.fed_status = SST_CH_FED_HDR;
+    return r;
+  }
+  r.len = u16_at(hb, 16 + 2 * (int)u);  // shuffle, not a dynamically indexed local array
+  const uint8_t* a = g + start;
+  if (r.len <= (uint32_t)kBuf) {
+    if ((((uintptr_t)a) & 7u) == 0) {
+      const uint32_t nv = (r.len + 7u) >> 3;  // whole 8-byte words; padding bytes exist up to the next 8
+      for (uint32_t i = lane; i < nv; i += 32)
+        *reinterpret_cast<uint2*>(w.fe + 8 * i) = __ldg(reinterpret_cast<const uint2*>(a) + i);
+    } else {
+      for (uint32_t i = lane; i < r.len; i += 32) w.fe[i] = __ldg(a + i);
+    }
+    r.src = w.fe;
+  } else {
+    r.src = a;
+  }
+  __syncwarp();
+  return r;
+}
+
+// a1 + a2 for one FE unit: lane 0 walks the 12 channel lengths (the location
+// map); lanes 0..11 then validate their channel's runs and count its digis; the
+// counts are prefix-summed.  A broken length chain invalidates all 12 channels.
+// Returns the unit's digi count; *flags / *nbad receive the OR of the channel
+// statuses and the number of bad channels.
+__device__ uint32_t parse_unit(Warp& w, const Unit& un, uint32_t* flags, uint32_t* nbad) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
+    bool good = un.src != nullptr;
+    uint32_t p = 0;
+    const uint32_t end = un.len;
+    for (int k = 0; k < kChPerFe; k++) {
+      uint32_t l = 0;
+      if (good) {
+        if (p + 2 > end) {
+          good = false;
+        } else {
+          l = (uint32_t)un.src[p] | ((uint32_t)un.src[p + 1] << 8);
+          if (l < 3 || p + l > end) good = false;
+        }
+      }
+      w.chan_pos[k] = good ? p : 0u;
+      w.chan_len[k] = good ? (uint16_t)l : (uint16_t)0;
+      if (good) p += l;
+    }
+    if (good && p != end) good = false;
+    uint8_t st = 0;
+    if (un.src == nullptr)
+      st = un.fed_status;
+    else if (!good)
+      st = SST_CH_FRAMING;
+    for (int k = 0; k < kChPerFe; k++) {
+      w.chan_st[k] = st;
+      if (st) w.chan_len[k] = 0;
+    }
+  }
+  __syncwarp();
+  uint32_t cnt = 0;
+  uint8_t st = 0;
+  if (lane < kChPerFe) {
+    st = w.chan_st[lane];
+    const uint32_t len_c = w.chan_len[lane];
+    if (st == 0 && len_c >= 3) {
+      const uint8_t* r = un.src + w.chan_pos[lane];
+      if (r[2] != SST_ZS_CODE) {
+        st = SST_CH_BAD_CODE;
+      } else {
+        uint32_t p = 3, prev_end = 0;
+        while (p < len_c) {
+          if (p + 2 > len_c) { st = SST_CH_TRUNC; break; }
+          const uint32_t first = r[p], wd = r[p + 1];
+          if (wd == 0 || first + wd > (uint32_t)kStrips) { st = SST_CH_RUN_RANGE; break; }
+          if (first < prev_end) { st = SST_CH_RUN_ORDER; break; }
+          if (p + 2 + wd > len_c) { st = SST_CH_TRUNC; break; }
+          prev_end = first + wd;
+          cnt += wd;
+          p += 2 + wd;
+        }
+      }
+      if (st) cnt = 0;
+      w.chan_st[lane] = st;
+    }
+  }
+  uint32_t x = cnt;
+#pragma unroll
+  for (int d = 1; d < 16; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane < kChPerFe) w.chan_cnt[lane] = x - cnt;
+  const uint32_t total = __shfl_sync(0xffffffffu, x, kChPerFe - 1);
+  if (lane == 0) w.chan_cnt[kChPerFe] = total;
+  *flags = __reduce_or_sync(0xffffffffu, lane < kChPerFe ? (uint32_t)st : 0u);
+  *nbad = __popc(__ballot_sync(0xffffffffu, lane < kChPerFe && st != 0));
+  __syncwarp();
+  return total;
+}
+
+// Greedy chunk of whole channels [c0, c1) with at most kTile digis.
+__device__ __forceinline__ int chunk_end(const Warp& w, int c0) {
+  int c1 = c0 + 1;
+  while (c1 < kChPerFe && w.chan_cnt[c1 + 1] - w.chan_cnt[c0] <= (uint32_t)kTile) ++c1;
+  return c1;
+}
+
+// a2: copies the runs of channels [c0, c1) into the tile, one lane per channel
+// (the runs were validated by parse_unit; the copy stays within the counted digis).
+__device__ void copy_runs(Warp& w, const Unit& un, int c0, int c1) {
+  const int lane = threadIdx.x & 31;
+  const int c = c0 + lane;
+  if (c < c1) {
+    const uint32_t n = w.chan_cnt[c + 1] - w.chan_cnt[c];
+    const uint32_t o0 = w.chan_cnt[c] - w.chan_cnt[c0];
+    const uint8_t* r = un.src + w.chan_pos[c];
+    const uint32_t len_c = w.chan_len[c];
+    uint32_t p = 3, o = 0;
+    while (p + 2 <= len_c && o < n) {
+      const uint32_t first = r[p];
+      uint32_t wd = r[p + 1];
+      if (wd > n - o) wd = n - o;
+      for (uint32_t k = 0; k < wd; k++) {
+        w.key[o0 + o + k] = (uint16_t)(((uint32_t)c << 8) | ((first + k) & 255u));
+        w.adc[o0 + o + k] = r[p + 2 + k];
+      }
+      o += wd;
+      p += 2 + wd;
+    }
+  }
+  __syncwarp();
+}
+
+
+// a3 for the n digis of the tile, one lane per digi, two noise loads in flight:
+// the channel and seed thresholds (binary32 product threshold x noise, strict
+// "larger than"), the gain-corrected charge and noise^2 of active digis.
+__device__ __forceinline__ void flag_one(Warp& w, const KParams& kp, int i, float nz) {
+  const uint32_t key = w.key[i];
+  const uint32_t c = key >> 8, st = key & 255u;
+  if (c >= (uint32_t)kChPerFe) {  // a digi that takes no part in clustering
+    w.flag[i] = 0;
+    w.q[i] = 0;
+    w.nsq[i] = 0.f;
+    return;
+  }
+  const bool isbad = (w.bad[c * kMaskWords + (st >> 5)] >> (st & 31u)) & 1u;
+  const uint32_t adc = w.adc[i];
+  const float a = __uint2float_rn(adc);
+  const bool act = !isbad && a > __fmul_rn(kp.t_channel, nz);
+  const bool sd = !isbad && a > __fmul_rn(kp.t_seed, nz);
+  uint32_t q = 0;
+  float nsq = 0.f;
+  if (act) {
+    if (adc >= 254u) {
+      q = adc;  // saturation codes are kept
+    } else {
+      const float x = __fdiv_rn(a, w.gain[c * 2 + (st >> 7)]);
+      const int ci = __float2int_rz(__fadd_rn(x, 0.5f));
+      q = ci > 253 ? 254u : (uint32_t)ci;
+    }
+    nsq = __fmul_rn(nz, nz);
+  }
+  w.flag[i] = (uint8_t)((act ? 1 : 0) | (sd ? 2 : 0));
+  w.q[i] = (uint8_t)q;
+  w.nsq[i] = nsq;
+}
+
+__device__ void flag_unit(Warp& w, const KParams& kp, const float* noise, int n) {
+  const int lane = threadIdx.x & 31;
+  for (int i0 = lane; i0 < n; i0 += 64) {
+    const int i1 = i0 + 32;
+    const uint32_t k0 = w.key[i0], k1 = i1 < n ? w.key[i1] : k0;
+    const float nz0 = __ldg(noise + (k0 >> 8 < (uint32_t)kChPerFe ? k0 : 0u));
+    const float nz1 = __ldg(noise + (k1 >> 8 < (uint32_t)kChPerFe ? k1 : 0u));
+    flag_one(w, kp, i0, nz0);
+    if (i1 < n) flag_one(w, kp, i1, nz1);
+  }
+  __syncwarp();
+}
+
+// a4, candidate boundaries: an active digi not linked (hole / bad-strip rules) to
+// the previous active strip of its channel is the first strip of a candidate.
+__device__ void starts_unit(Warp& w, const KParams& kp, int n) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < n; i += 32) {
+    if (!(w.flag[i] & 1)) continue;
+    const uint32_t key = w.key[i];
+    const uint32_t c = key >> 8;
+    int a = -1;
+    for (int j = i - 1; j >= 0; --j) {
+      const uint32_t kj = w.key[j];
+      if ((kj >> 8) != c) break;
+      if (w.flag[j] & 1) {
+        a = (int)(kj & 255u);
+        break;
+      }
+    }
+    if (a < 0 || !linked_gap(w.bad + c * kMaskWords, a, (int)(key & 255u), kp.max_holes, kp.max_bad))
+      w.flag[i] |= 4;
+  }
+  __syncwarp();
+}
+
+// a4, seed array: the leftmost seed of every candidate owns it.  The digis are
+// scanned 32 at a time in strip order; two ballots (seeds, candidate starts) and
+// a carry across windows decide, for every seed, whether another seed lies
+// between its candidate's first strip and it.  The first digis of owned
+// candidates are compacted in strip order into own[]; returns their number.
+__device__ int owners_unit(Warp& w, int n) {
+  const int lane = threadIdx.x & 31;
+  int n_own = 0, carry_start = -1;
+  bool carry_seen = false;
+  for (int base = 0; base < n; base += 32) {
+    const int i = base + lane;
+    const uint8_t f = i < n ? w.flag[i] : 0;
+    const unsigned S = __ballot_sync(0xffffffffu, (f & 2) != 0);
+    const unsigned B = __ballot_sync(0xffffffffu, (f & 4) != 0);
+    const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    const unsigned mb = B & upto;
+    bool seen;
+    int start;
+    if (mb) {
+      const int ls = 31 - __clz(mb);
+      seen = (S & lanemask_lt(lane) & ~lanemask_lt(ls)) != 0;
+      start = base + ls;
+    } else {
+      seen = carry_seen || (S & lanemask_lt(lane)) != 0;
+      start = carry_start;
+    }
+    const bool owner = (f & 2) && !seen;
+    const unsigned O = __ballot_sync(0xffffffffu, owner);
+    if (owner) w.own[n_own + __popc(O & lanemask_lt(lane))] = (uint16_t)start;
+    n_own += __popc(O);
+    if (B) {
+      const int lw = 31 - __clz(B);
+      carry_start = base + lw;
+      carry_seen = (S >> lw) != 0;
+    } else {
+      carry_seen = carry_seen || S != 0;
+    }
+  }
+  __syncwarp();
+  return n_own;
+}
+
+// Staged cluster record (16 bytes): det | first, width | charge | barycenter.
+__device__ __forceinline__ uint4 pack_cluster(uint32_t det, uint32_t first, uint32_t width, uint32_t charge,
+                                              float bary) {
+  return make_uint4(det, first | (width << 16), charge, __float_as_uint(bary));
+}
+
+// a5 + a6: one lane per owned candidate walks it from its first strip to the
+// digi before the next candidate start (the right boundary is its last active
+// strip), summing in strip order raw ADC, noise^2 (binary32, left to right),
+// gain-corrected charge and first moment; the candidate is widened over up to
+// max_adj adjacent bad strips; the cluster threshold decides.  Returns the number
+// kept; when `stage` is given the kept clusters are written, in strip order, to
+// stage[base + rank] for base + rank < cap.
+__device__ uint32_t form_unit(Warp& w, const KParams& kp, int n, int n_own, uint32_t det0, uint4* stage,
+                              uint64_t cap, uint64_t base) {
+  const int lane = threadIdx.x & 31;
+  uint32_t kept = 0;
+  for (int k0 = 0; k0 < n_own; k0 += 32) {
+    const int k = k0 + lane;
+    bool pass = false;
+    uint32_t c = 0, lo = 0, wd = 0, q_sum = 0;
+    float bary = 0.f;
+    if (k < n_own) {
+      int j = w.own[k];
+      const uint32_t key0 = w.key[j];
+      c = key0 >> 8;
+      const int l = (int)(key0 & 255u);
+      const uint32_t* B = w.bad + c * kMaskWords;
+      int lo_i = l;
+      for (int m = 0; m < kp.max_adj && lo_i - 1 >= 0 && bit(B, lo_i - 1); m++) lo_i--;
+      uint32_t s_raw = 0, moment = 0;
+      float n2 = 0.f;
+      int r = l;
+      do {
+        const uint32_t kj = w.key[j];
+        if (w.flag[j] & 1) {
+          const uint32_t q = w.q[j];
+          const int st = (int)(kj & 255u);
+          s_raw += w.adc[j];
+          n2 = __fadd_rn(n2, w.nsq[j]);
+          q_sum += q;
+          moment += (uint32_t)(st - lo_i) * q;
+          r = st;
+        }
+        ++j;
+      } while (j < n && (w.key[j] >> 8) == c && !(w.flag[j] & 4));
+      pass = __uint2float_rn(s_raw) > __fmul_rn(kp.t_cluster, __fsqrt_rn(n2));
+      int hi = r;
+      for (int m = 0; m < kp.max_adj && hi + 1 < kStrips && bit(B, hi + 1); m++) hi++;
+      lo = (uint32_t)lo_i;
+      wd = (uint32_t)(hi - lo_i + 1);
+      if (pass && stage)
+        bary = q_sum == 0 ? __fadd_rn((float)lo_i, __fmul_rn(0.5f, (float)wd))
+                          : __fadd_rn(__fadd_rn((float)lo_i, 0.5f),
+                                      __fdiv_rn(__uint2float_rn(moment), __uint2float_rn(q_sum)));
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, pass);
+    if (pass && stage) {
+      const uint64_t pos = base + kept + __popc(b & lanemask_lt(lane));
+      if (pos < cap) stage[pos] = pack_cluster(det0 + c, lo, wd, q_sum, bary);
+    }
+    kept += __popc(b);
+  }
+  return kept;
+}
+
+// Where one unit's clusters go: its event's staging slice (records allocated unit
+// by unit with one atomic each) and the unit's segment bookkeeping.
+struct SegOut {
+  uint4* stage;         // the event's slice of the staging buffer
+  uint64_t cap;         // records in that slice
+  uint32_t* ev_alloc;   // the event's allocation counter
+  uint32_t* seg_cnt;    // this unit's cluster count
+  uint32_t* seg_start;  // this unit's offset in the slice
+};
+
+// Clusters the `total` digis of one unit (placed in the tile by `fill(c0, c1)`,
+// channel chunk [c0, c1)) and stages its clusters.  The kept clusters are first
+// counted, then their region is allocated in one piece, then they are written; a
+// unit whose digis exceed the tile goes through its channel chunks twice.
+template <typename Fill>
+__device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uint32_t det0, uint32_t total,
+                             Fill& fill, const SegOut& so, sst_event_status* status) {
+  const int lane = threadIdx.x & 31;
+  const bool single = total <= (uint32_t)kTile;
+  uint32_t found = 0;
+  int n = 0, n_own = 0;
+  if (single) {
+    n = (int)total;
+    if (n > 0) {
+      fill(0, kChPerFe);
+      flag_unit(w, kp, noise, n);
+      starts_unit(w, kp, n);
+      n_own = owners_unit(w, n);
+      if (n_own > 0) found = form_unit(w, kp, n, n_own, det0, nullptr, 0, 0);
+    }
+  } else {
+    for (int c0 = 0; c0 < kChPerFe;) {
+      const int c1 = chunk_end(w, c0);
+      const int nn = (int)(w.chan_cnt[c1] - w.chan_cnt[c0]);
+      if (nn > 0) {
+        fill(c0, c1);
+        flag_unit(w, kp, noise, nn);
+        starts_unit(w, kp, nn);
+        const int no = owners_unit(w, nn);
+        if (no > 0) found += form_unit(w, kp, nn, no, det0, nullptr, 0, 0);
+      }
+      c0 = c1;
+    }
+  }
+  uint32_t start = 0;
+  if (lane == 0) {
+    start = found ? atomicAdd(so.ev_alloc, found) : 0u;
+    uint32_t fits = 0;
+    if ((uint64_t)start < so.cap) fits = (uint64_t)start + found <= so.cap ? found : (uint32_t)(so.cap - start);
+    if (fits < found) atomicOr(&status->flags, SST_EV_CLUSTER_CAPACITY);
+    *so.seg_cnt = fits;
+    *so.seg_start = start;
+  }
+  start = __shfl_sync(0xffffffffu, start, 0);
+  if (found == 0) return;
+  if (single) {
+    form_unit(w, kp, n, n_own, det0, so.stage, so.cap, start);
+  } else {
+    uint64_t base = start;
+    for (int c0 = 0; c0 < kChPerFe;) {
+      const int c1 = chunk_end(w, c0);
+      const int nn = (int)(w.chan_cnt[c1] - w.chan_cnt[c0]);
+      if (nn > 0) {
+        fill(c0, c1);
+        flag_unit(w, kp, noise, nn);
+        starts_unit(w, kp, nn);
+        const int no = owners_unit(w, nn);
+        if (no > 0) base += form_unit(w, kp, nn, no, det0, so.stage, so.cap, base);
+      }
+      c0 = c1;
+    }
+  }
+}
+
+// Loads the bad-strip masks and APV gains of channels ch0 .. ch0 + 11.
+__device__ __forceinline__ void load_calib(Warp& w, const KParams& kp, uint32_t ch0) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t* bm = kp.badmask + (size_t)ch0 * kMaskWords;
+  for (int i = lane; i < kChPerFe * kMaskWords; i += 32) w.bad[i] = __ldg(bm + i);
+  if (lane < kChPerFe * 2) w.gain[lane] = __ldg(kp.gain + (size_t)ch0 * 2 + lane);
+}
+
+}  // namespace fe

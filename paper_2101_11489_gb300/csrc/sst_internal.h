@@ -45,9 +45,9 @@ struct Shape {
 struct Scratch {
   unsigned long long* lb = nullptr;  // look-back states, one per FED (per-event unpack)
   uint64_t* fed_off = nullptr;       // absolute byte offset per (event, FED)
-  uint32_t* fed_cnt = nullptr;       // clusters found per (event, FED)
-  uint32_t* fed_start = nullptr;     // staging offset per (event, FED), within its event's slice
-  uint32_t* fed_dest = nullptr;      // output offset per (event, FED), within its event's slice
+  uint32_t* fed_cnt = nullptr;       // clusters found per (event, FED, FE unit)
+  uint32_t* fed_start = nullptr;     // staging offset per (event, FED, FE unit), within its event's slice
+  uint32_t* fed_dest = nullptr;      // output offset per (event, FED, FE unit), within its event's slice
   size_t items_cap = 0;
   uint32_t* ev_alloc = nullptr;      // staging allocation counter per event
   size_t ev_cap = 0;

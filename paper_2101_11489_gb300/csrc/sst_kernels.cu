@@ -2,25 +2,22 @@
 // three-threshold clustering (arXiv 2101.11489, section 2), per event and batched
 // (section 3).
 //
-// Work unit: one FED (96 channels x 256 strips) of one event, handled by one CTA.
-//   * The FED's bytes are staged in shared memory with 16-byte loads.
-//   * Warp 0 checks the header and walks the 8 FE units' length chains (one lane
-//     per FE unit) to locate the 96 channel records: the "map of channel
-//     locations" of the paper, here on the device.
-//   * One thread per channel validates the channel's runs, counts its digis and
-//     records every run header; a warp scan turns the counts into tile offsets.
-//   * The runs are copied into an on-chip digi tile sorted by strip, one thread
-//     per run (or, for FEDs that do not fit, groups of `lanes` threads per
-//     channel over channel-aligned chunks).
-//   * Clustering on the tile, one thread per digi: channel / seed thresholds,
-//     gain-corrected charge and noise^2; candidate first strips from the tile-order
-//     neighbour and the hole / bad-strip rules; the leftmost seed of each candidate
-//     found by a short backward walk and compacted with a block scan (the paper's
-//     array of seed strips); one thread per kept candidate sums its strips in strip
-//     order and applies the cluster threshold and centroid.
-//   * The FED's offset in its event's cluster (or digi) array comes from a
-//     warp-parallel decoupled look-back over the FEDs before it, so the output is
-//     sorted without a second pass.
+// Clustering work unit: one FE unit (12 channels) of one FED of one event, handled
+// by one warp end to end (sst_fe.cuh): FED header check, the FE unit's channel
+// length chain (the paper's "map of channel locations", here on the device), run
+// validation and counts (one lane per channel), copy into an on-chip digi tile
+// sorted by strip, thresholds (one lane per digi), candidate boundaries, the
+// leftmost seed of each candidate (warp ballots; the paper's array of seed
+// strips), and cluster forming (one lane per kept candidate).  No block-wide
+// barrier: a GB300 SM keeps some thirty independent units in flight.
+//
+// Output order without device-side waits: every unit allocates an exact-size
+// staging region with one atomic per event; k_clu_scan prefix-sums the units'
+// counts per event and k_compact copies the staged records into each event's
+// sorted cluster SoA.
+//
+// Per-event unpacking (k_unpack) keeps one CTA per FED and places the FED's digis
+// with a warp-parallel decoupled look-back over the FEDs before it.
 //
 // Floating point in the threshold tests and sums uses explicit round-to-nearest
 // intrinsics (__fmul_rn, __fadd_rn, __fdiv_rn, __fsqrt_rn): no multiply-add is
@@ -53,48 +50,30 @@ enum {
 
 // ---------------------------------------------------------------- shared memory
 
-// Everything one CTA keeps on chip for one FED.  TILE = digis per tile.
+// What one CTA of the per-event unpack kernel keeps on chip for one FED.
+// TILE = digis per tile.
 template <int TILE>
 struct __align__(16) Shm {
-  static constexpr int kRegion = (12 * TILE > kFedBufMin) ? 12 * TILE : kFedBufMin;
+  static constexpr int kRegion = (8 * TILE > kFedBufMin) ? 8 * TILE : kFedBufMin;
   uint32_t scal[S_SCAL_N];
   uint32_t wsum[32];
   uint32_t chan_pos[kCh];       // byte offset of the channel record within the FED
   uint32_t chan_cnt[kCh + 1];   // digis per channel, then exclusive prefix (in place)
   uint32_t chan_slot[kCh + 1];  // first run slot of each channel
   uint32_t fe_len[kFe];
-  alignas(16) uint32_t bad[kCh * kMaskWords];  // 256-bit bad-strip mask per channel (16-byte stores)
-  float gain[kCh * 2];                         // two APV gains per channel
   uint16_t chan_len[kCh];
   uint8_t chan_st[kCh];
   uint16_t t_key[TILE];  // (channel << 8) | strip, sorted
   uint8_t t_adc[TILE];
-  uint8_t t_flag[TILE];  // 1 active, 2 seed
-  union __align__(16) {
-    uint2 runs[TILE];  // run records, during the copy into the tile
-    struct {
-      float nsq[TILE];     // noise^2 of active digis; later the output rank of owners
-      uint16_t own[TILE];  // first digi of every candidate that holds a seed, in strip order
-      uint8_t q[TILE];     // gain-corrected charge of active digis
-    } c;
-  } r;
-  union __align__(16) {
-    uint8_t fedbuf[kRegion];  // the staged FED record
-    struct {                  // results per owner, after the copy into the tile
-      uint32_t charge[TILE];
-      float bary[TILE];
-      uint16_t first[TILE];
-      uint16_t width[TILE];  // 0: rejected by the cluster threshold
-    } st;
-    uint16_t aux[TILE];  // per seed: first digi of its candidate | 0x8000 when it owns it
-  } u;
+  alignas(16) uint2 runs[TILE];  // run records
+  alignas(16) uint8_t fedbuf[kRegion];  // the staged FED record
 };
 
 // Fields written with 8- or 16-byte accesses must be aligned to that width.
 template <int TILE>
 constexpr bool shm_aligned() {
-  return offsetof(Shm<TILE>, bad) % 16 == 0 && offsetof(Shm<TILE>, r) % 16 == 0 &&
-         offsetof(Shm<TILE>, u) % 16 == 0 && sizeof(Shm<TILE>) % 16 == 0;
+  return offsetof(Shm<TILE>, runs) % 16 == 0 && offsetof(Shm<TILE>, fedbuf) % 16 == 0 &&
+         sizeof(Shm<TILE>) % 16 == 0;
 }
 static_assert(shm_aligned<1024>() && shm_aligned<2048>() && shm_aligned<4096>(), "shared layout misaligned");
 
@@ -216,16 +195,6 @@ __device__ void stage_fed(const uint8_t* g, uint32_t len, uint8_t* dst) {
   }
 }
 
-// Loads bad-strip masks and APV gains of the FED's 96 channels.
-template <int TILE>
-__device__ void load_fed_calib(Shm<TILE>& s, const KParams& kp, uint32_t fed) {
-  const uint4* bm = reinterpret_cast<const uint4*>(kp.badmask + (size_t)fed * kCh * kMaskWords);
-  uint4* bd = reinterpret_cast<uint4*>(s.bad);
-  for (int i = threadIdx.x; i < kCh * kMaskWords / 4; i += blockDim.x) bd[i] = __ldg(bm + i);
-  const float* gp = kp.gain + (size_t)fed * kCh * 2;
-  for (int i = threadIdx.x; i < kCh * 2; i += blockDim.x) s.gain[i] = __ldg(gp + i);
-}
-
 // Header, FE-unit walk, per-channel validation and digi counts (a1 + a2).  `src`
 // points at the record (shared or global memory).  On return (after a barrier):
 // chan_* describe each channel, chan_cnt holds the exclusive prefix of the digi
@@ -329,7 +298,7 @@ __device__ void parse_body(Shm<TILE>& s, const uint8_t* src, uint32_t len, uint3
           if (first < prev_end) { st = SST_CH_RUN_ORDER; break; }
           if (p + 2 + w > len_c) { st = SST_CH_TRUNC; break; }
           if (use_slots && slot0 + nrun < slot1)
-            s.r.runs[slot0 + nrun] = make_uint2(pos + p + 2, run_y(cnt, first, w, c));
+            s.runs[slot0 + nrun] = make_uint2(pos + p + 2, run_y(cnt, first, w, c));
           prev_end = first + w;
           cnt += w;
           nrun++;
@@ -343,7 +312,7 @@ __device__ void parse_body(Shm<TILE>& s, const uint8_t* src, uint32_t len, uint3
       s.chan_st[c] = st;
     }
     if (use_slots)
-      for (uint32_t k = slot0 + nrun; k < slot1; k++) s.r.runs[k] = make_uint2(0u, 0u);
+      for (uint32_t k = slot0 + nrun; k < slot1; k++) s.runs[k] = make_uint2(0u, 0u);
     s.chan_cnt[c] = cnt;
   }
   __syncthreads();
@@ -375,9 +344,9 @@ template <int TILE>
 __device__ bool parse_fed(Shm<TILE>& s, const uint8_t* gfed, uint32_t len, uint32_t fed_id, bool in_range) {
   const bool staged = in_range && len > 0 && len <= (uint32_t)Shm<TILE>::kRegion;
   if (staged) {
-    stage_fed(gfed, len, s.u.fedbuf);
+    stage_fed(gfed, len, s.fedbuf);
     __syncthreads();
-    parse_body(s, s.u.fedbuf, len, fed_id, in_range);
+    parse_body(s, s.fedbuf, len, fed_id, in_range);
   } else {
     parse_body(s, gfed, len, fed_id, in_range);
   }
@@ -390,7 +359,7 @@ template <int TILE>
 __device__ void emit_slots(Shm<TILE>& s, const uint8_t* src) {
   const uint32_t nslots = s.chan_slot[kCh];
   for (uint32_t k = threadIdx.x; k < nslots; k += blockDim.x) {
-    const uint2 rr = s.r.runs[k];
+    const uint2 rr = s.runs[k];
     const uint32_t w = (rr.y >> 17) & 0xFFu;
     if (w == 0) continue;
     const uint32_t c = rr.y >> 25, first = (rr.y >> 9) & 0xFFu;
@@ -472,187 +441,7 @@ __device__ bool linked_gap(const uint32_t* B, int a, int t, int max_holes, int m
   return true;
 }
 
-// a3: per digi, the channel and seed thresholds (binary32 product threshold x
-// noise, strict comparison), the gain-corrected charge and noise^2 of active digis.
-template <int TILE>
-__device__ void flag_tile(Shm<TILE>& s, const KParams& kp, uint32_t fed, int c0, int c1, int n) {
-  const float* noise = kp.noise + (size_t)fed * kFedStrips;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const uint32_t key = s.t_key[i];
-    const uint32_t c = key >> 8, st = key & 255u;
-    uint8_t fl = 0, q = 0;
-    float nsq = 0.f;
-    if ((int)c >= c0 && (int)c < c1) {
-      const float nz = __ldg(noise + key);
-      const bool isbad = (s.bad[c * kMaskWords + (st >> 5)] >> (st & 31u)) & 1u;
-      const uint32_t adc = s.t_adc[i];
-      const float a = __uint2float_rn(adc);
-      const bool act = !isbad && a > __fmul_rn(kp.t_channel, nz);
-      const bool sd = !isbad && a > __fmul_rn(kp.t_seed, nz);
-      if (act) {
-        if (adc >= 254u) {
-          q = (uint8_t)adc;  // saturation codes are kept
-        } else {
-          const float x = __fdiv_rn(a, s.gain[c * 2 + (st >> 7)]);
-          const int ci = __float2int_rz(__fadd_rn(x, 0.5f));
-          q = ci > 253 ? (uint8_t)254 : (uint8_t)ci;
-        }
-        nsq = __fmul_rn(nz, nz);
-      }
-      fl = (act ? 1 : 0) | (sd ? 2 : 0);
-    }
-    s.t_flag[i] = fl;
-    s.r.c.q[i] = q;
-    s.r.c.nsq[i] = nsq;
-  }
-  __syncthreads();
-}
-
-// Previous / next active digi of the same channel in the (strip-sorted) tile, or -1.
-template <int TILE>
-__device__ __forceinline__ int prev_active(const Shm<TILE>& s, int i, uint32_t c) {
-  for (int j = i - 1; j >= 0; --j) {
-    if ((s.t_key[j] >> 8) != c) return -1;
-    if (s.t_flag[j] & 1) return j;
-  }
-  return -1;
-}
-template <int TILE>
-__device__ __forceinline__ int next_active(const Shm<TILE>& s, int i, int n, uint32_t c) {
-  for (int j = i + 1; j < n; ++j) {
-    if ((s.t_key[j] >> 8) != c) return -1;
-    if (s.t_flag[j] & 1) return j;
-  }
-  return -1;
-}
-
-// a4 (boundary search, left): from every seed, walk back over the active strips
-// of its candidate (successive active strips linked by the hole / bad-strip
-// rules).  Meeting another seed means an earlier seed owns the candidate; reaching
-// the candidate's first strip without one makes this seed the owner.  The first
-// digis of owned candidates are compacted in strip order with a block scan (the
-// array of seed strips the clusters are formed from); returns their number.
-template <int TILE>
-__device__ int owners_tile(Shm<TILE>& s, const KParams& kp, int n) {
-  const int T = blockDim.x;
-  const int k = (n + T - 1) / T;
-  const int b0 = threadIdx.x * k;
-  const int b1 = min(n, b0 + k);
-  uint32_t cnt = 0;
-  for (int i = b0; i < b1; i++) {
-    if (!(s.t_flag[i] & 2)) continue;
-    const uint32_t c = s.t_key[i] >> 8;
-    const uint32_t* B = s.bad + c * kMaskWords;
-    int cur = i;
-    bool owner = true;
-    for (;;) {
-      const int j = prev_active(s, cur, c);
-      if (j < 0 || !linked_gap(B, s.t_key[j] & 255, s.t_key[cur] & 255, kp.max_holes, kp.max_bad)) break;
-      if (s.t_flag[j] & 2) {
-        owner = false;
-        break;
-      }
-      cur = j;
-    }
-    s.u.aux[i] = (uint16_t)(cur | (owner ? 0x8000 : 0));
-    cnt += owner ? 1u : 0u;
-  }
-  uint32_t total;
-  uint32_t r = block_excl_scan(cnt, s.wsum, &total);
-  for (int i = b0; i < b1; i++) {
-    if (!(s.t_flag[i] & 2)) continue;
-    const uint32_t a = s.u.aux[i];
-    if (a & 0x8000) s.r.c.own[r++] = (uint16_t)(a & 0x7FFF);
-  }
-  __syncthreads();
-  return (int)total;
-}
-
-// a5 + a6: one thread per owned candidate walks forward from its first digi over
-// linked active strips to the right boundary, summing in strip order (raw ADC,
-// noise^2 left to right in binary32, gain-corrected charge, first moment); the
-// candidate is widened over up to max_adj adjacent bad strips; then the cluster
-// threshold and the centroid.  Results are staged per owner.
-template <int TILE>
-__device__ void form_owners(Shm<TILE>& s, const KParams& kp, int n, int n_own) {
-  for (int k = threadIdx.x; k < n_own; k += blockDim.x) {
-    int j = s.r.c.own[k];
-    const uint32_t key0 = s.t_key[j];
-    const uint32_t c = key0 >> 8;
-    const int l = (int)(key0 & 255u);
-    const uint32_t* B = s.bad + c * kMaskWords;
-    int lo = l;
-    for (int m = 0; m < kp.max_adj && lo - 1 >= 0 && bit(B, lo - 1); m++) lo--;
-    uint32_t s_raw = 0, q_sum = 0, moment = 0;
-    float n2 = 0.f;
-    int r = l;
-    for (;;) {
-      const int st = s.t_key[j] & 255;
-      const uint32_t q = s.r.c.q[j];
-      s_raw += s.t_adc[j];
-      n2 = __fadd_rn(n2, s.r.c.nsq[j]);
-      q_sum += q;
-      moment += (uint32_t)(st - lo) * q;
-      r = st;
-      const int nx = next_active(s, j, n, c);
-      if (nx < 0 || !linked_gap(B, st, s.t_key[nx] & 255, kp.max_holes, kp.max_bad)) break;
-      j = nx;
-    }
-    int hi = r;
-    for (int m = 0; m < kp.max_adj && hi + 1 < kStrips && bit(B, hi + 1); m++) hi++;
-    const bool pass = __uint2float_rn(s_raw) > __fmul_rn(kp.t_cluster, __fsqrt_rn(n2));
-    const int w = hi - lo + 1;
-    float bary = 0.f;
-    if (pass) {
-      if (q_sum == 0)
-        bary = __fadd_rn((float)lo, __fmul_rn(0.5f, (float)w));
-      else
-        bary = __fadd_rn(__fadd_rn((float)lo, 0.5f), __fdiv_rn(__uint2float_rn(moment), __uint2float_rn(q_sum)));
-    }
-    s.u.st.first[k] = (uint16_t)lo;
-    s.u.st.charge[k] = q_sum;
-    s.u.st.bary[k] = bary;
-    s.u.st.width[k] = pass ? (uint16_t)w : (uint16_t)0;
-  }
-  __syncthreads();
-}
-
-// Output rank of every kept cluster among the owners; returns the number kept.
-template <int TILE>
-__device__ uint32_t rank_owners(Shm<TILE>& s, int n_own) {
-  const int T = blockDim.x;
-  const int k = (n_own + T - 1) / T;
-  const int b0 = threadIdx.x * k;
-  const int b1 = min(n_own, b0 + k);
-  uint32_t cnt = 0;
-  for (int i = b0; i < b1; i++) cnt += s.u.st.width[i] != 0;
-  uint32_t total;
-  uint32_t r = block_excl_scan(cnt, s.wsum, &total);
-  uint32_t* rank = reinterpret_cast<uint32_t*>(s.r.c.nsq);
-  for (int i = b0; i < b1; i++)
-    if (s.u.st.width[i]) rank[i] = r++;
-  __syncthreads();
-  return total;
-}
-
-// Staged cluster record (16 bytes): det | first, width | charge | barycenter.
-__device__ __forceinline__ uint4 pack_cluster(uint32_t det, uint32_t first, uint32_t width, uint32_t charge,
-                                              float bary) {
-  return make_uint4(det, first | (width << 16), charge, __float_as_uint(bary));
-}
-
-// Writes the kept clusters of the tile to stage[base + rank], base + rank < cap.
-template <int TILE>
-__device__ void stage_owners(Shm<TILE>& s, uint4* stage, uint64_t cap, uint64_t base, uint32_t fed, int n_own) {
-  const uint32_t* rank = reinterpret_cast<const uint32_t*>(s.r.c.nsq);
-  for (int k = threadIdx.x; k < n_own; k += blockDim.x) {
-    if (!s.u.st.width[k]) continue;
-    const uint64_t pos = base + rank[k];
-    if (pos >= cap) continue;
-    stage[pos] = pack_cluster(fed * kCh + (s.t_key[s.r.c.own[k]] >> 8), s.u.st.first[k], s.u.st.width[k],
-                              s.u.st.charge[k], s.u.st.bary[k]);
-  }
-}
+#include "sst_fe.cuh"
 
 // Greedy channel-aligned chunk [c0, c1) holding at most TILE digis.
 template <int TILE>
@@ -660,82 +449,6 @@ __device__ int chunk_end(Shm<TILE>& s, int c0) {
   int c1 = c0 + 1;
   while (c1 < kCh && s.chan_cnt[c1 + 1] - s.chan_cnt[c0] <= (uint32_t)TILE) ++c1;
   return c1;
-}
-
-// Where one FED's clusters go: the event's staging slice (clusters of the event
-// are allocated FED by FED with one atomic each) and the per-FED bookkeeping.
-struct StageOut {
-  uint4* stage;         // the event's slice of the staging buffer
-  uint64_t cap;         // records in that slice
-  uint32_t* ev_alloc;   // the event's allocation counter
-  uint32_t* fed_cnt;    // this FED's cluster count
-  uint32_t* fed_start;  // this FED's offset in the slice
-};
-
-// Clusters one chunk of channels [c0, c1) that `fill` has put in the tile;
-// returns the number of kept clusters (ranked in the tile).
-template <int TILE, typename Fill>
-__device__ uint32_t cluster_chunk(Shm<TILE>& s, const KParams& kp, uint32_t fed, Fill& fill, int c0, int c1,
-                                  int n, int* n_own_out) {
-  int n_own = 0;
-  uint32_t emits = 0;
-  if (n > 0) {
-    fill(c0, c1);
-    __syncthreads();
-    flag_tile(s, kp, fed, c0, c1, n);
-    n_own = owners_tile(s, kp, n);
-    form_owners(s, kp, n, n_own);
-    if (n_own > 0) emits = rank_owners(s, n_own);
-  }
-  *n_own_out = n_own;
-  return emits;
-}
-
-// Clusters the digis of one FED and stages them.  A FED that fits one tile is
-// processed once; a larger one is processed chunk by chunk twice, first to count
-// its clusters (so that its staging region can be allocated in one piece), then
-// to stage them.  `fill(c0, c1)` puts the digis of channels [c0, c1) in the tile.
-template <int TILE, typename Fill>
-__device__ void cluster_fed(Shm<TILE>& s, const KParams& kp, uint32_t fed, Fill fill, const StageOut& so,
-                            sst_event_status* status) {
-  const int tid = threadIdx.x;
-  const uint32_t total_digis = s.chan_cnt[kCh];
-  const bool single = total_digis <= (uint32_t)TILE;
-  uint32_t found = 0;
-  if (!single) {
-    for (int c0 = 0; c0 < kCh;) {
-      const int c1 = chunk_end(s, c0);
-      int n_own;
-      found += cluster_chunk(s, kp, fed, fill, c0, c1, (int)(s.chan_cnt[c1] - s.chan_cnt[c0]), &n_own);
-      __syncthreads();
-      c0 = c1;
-    }
-  }
-  uint32_t base = 0;
-  for (int c0 = 0; c0 < kCh;) {
-    const int c1 = single ? kCh : chunk_end(s, c0);
-    const int n = (int)(s.chan_cnt[c1] - s.chan_cnt[c0]);
-    int n_own = 0;
-    const uint32_t emits = cluster_chunk(s, kp, fed, fill, c0, c1, n, &n_own);
-    if (c0 == 0) {
-      if (tid == 0) {
-        const uint32_t total = single ? emits : found;
-        const uint32_t start = total ? atomicAdd(so.ev_alloc, total) : 0u;
-        uint32_t kept = 0;
-        if ((uint64_t)start < so.cap) kept = (uint64_t)start + total <= so.cap ? total : (uint32_t)(so.cap - start);
-        if (kept < total) atomicOr(&status->flags, SST_EV_CLUSTER_CAPACITY);
-        *so.fed_cnt = kept;
-        *so.fed_start = start;
-        s.scal[S_BASE] = start;
-      }
-      __syncthreads();
-      base = s.scal[S_BASE];
-    }
-    if (emits > 0) stage_owners(s, so.stage, so.cap, base, fed, n_own);
-    base += emits;
-    __syncthreads();
-    c0 = c1;
-  }
 }
 
 // ---------------------------------------------------------------- kernels
@@ -794,39 +507,38 @@ __global__ void k_clu_scan(const uint32_t* __restrict__ fed_cnt, uint32_t n_feds
   if (threadIdx.x == 0) status[e].n_clusters = carry_s;
 }
 
-// a6, output: copies every FED's staged clusters to its place in the event's
-// sorted cluster SoA (16-byte loads, coalesced stores).  One CTA per group of
-// `per_cta` consecutive (event, FED) items.
+// a6, output: copies every segment's staged clusters (one segment per FE unit)
+// to its place in the event's sorted cluster SoA, one warp per segment (16-byte
+// loads, coalesced stores).
 __global__ void __launch_bounds__(256) k_compact(const uint4* __restrict__ stage, const uint64_t* __restrict__ clu_off,
-                                                 const uint32_t* __restrict__ fed_cnt,
-                                                 const uint32_t* __restrict__ fed_start,
-                                                 const uint32_t* __restrict__ fed_dest, uint32_t n_events,
-                                                 uint32_t n_feds, uint32_t per_cta, sst_clusters out) {
-  const uint64_t items = (uint64_t)n_events * n_feds;
-  const uint64_t it0 = (uint64_t)blockIdx.x * per_cta;
-  for (uint64_t it = it0; it < it0 + per_cta && it < items; ++it) {
-    const uint32_t n = fed_cnt[it];
-    if (n == 0) continue;
-    const uint32_t e = (uint32_t)(it / n_feds);
-    const uint64_t off = clu_off ? clu_off[e] : 0;
-    const uint4* src = stage + off + fed_start[it];
-    const uint64_t dst = off + fed_dest[it];
-    for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) {
-      const uint4 r = __ldg(src + k);
-      const uint64_t o = dst + k;
-      out.det[o] = r.x;
-      out.first[o] = (uint16_t)(r.y & 0xFFFFu);
-      out.width[o] = (uint16_t)(r.y >> 16);
-      out.charge[o] = r.z;
-      out.barycenter[o] = __uint_as_float(r.w);
-    }
+                                                 const uint32_t* __restrict__ seg_cnt,
+                                                 const uint32_t* __restrict__ seg_start,
+                                                 const uint32_t* __restrict__ seg_dest, uint32_t n_events,
+                                                 uint32_t n_segs, sst_clusters out) {
+  const uint64_t items = (uint64_t)n_events * n_segs;
+  const uint64_t it = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (it >= items) return;
+  const uint32_t n = seg_cnt[it];
+  if (n == 0) return;
+  const uint32_t e = (uint32_t)(it / n_segs);
+  const uint64_t off = clu_off ? clu_off[e] : 0;
+  const uint4* src = stage + off + seg_start[it];
+  const uint64_t dst = off + seg_dest[it];
+  for (uint32_t k = threadIdx.x & 31; k < n; k += 32) {
+    const uint4 r = __ldg(src + k);
+    const uint64_t o = dst + k;
+    out.det[o] = r.x;
+    out.first[o] = (uint16_t)(r.y & 0xFFFFu);
+    out.width[o] = (uint16_t)(r.y >> 16);
+    out.charge[o] = r.z;
+    out.barycenter[o] = __uint_as_float(r.w);
   }
 }
 
 // a1 + a2 per event: one CTA per FED (ticket order), digis written to the global
 // digi SoA at the FED's offset from the look-back over FED digi counts.
 template <int TILE>
-__global__ void __launch_bounds__(512) k_unpack(const uint8_t* __restrict__ raw,
+__global__ void __launch_bounds__(256, 4) k_unpack(const uint8_t* __restrict__ raw,
                                                 const uint32_t* __restrict__ fed_len,
                                                 const uint64_t* __restrict__ fed_off, uint32_t n_feds,
                                                 sst_digis out, unsigned long long* lb, uint32_t* ticket, int lanes) {
@@ -881,9 +593,9 @@ __global__ void __launch_bounds__(512) k_unpack(const uint8_t* __restrict__ raw,
     const int n = (int)(s.chan_cnt[c1] - s.chan_cnt[c0]);
     if (n > 0) {
       if (slots) {
-        if (staged) emit_slots(s, s.u.fedbuf); else emit_slots(s, gfed);
+        if (staged) emit_slots(s, s.fedbuf); else emit_slots(s, gfed);
       } else {
-        if (staged) emit_channels(s, s.u.fedbuf, c0, c1, lanes); else emit_channels(s, gfed, c0, c1, lanes);
+        if (staged) emit_channels(s, s.fedbuf, c0, c1, lanes); else emit_channels(s, gfed, c0, c1, lanes);
       }
       __syncthreads();
       const uint64_t o = (uint64_t)base + s.chan_cnt[c0];
@@ -900,121 +612,103 @@ __global__ void __launch_bounds__(512) k_unpack(const uint8_t* __restrict__ raw,
   }
 }
 
-// a3 - a6 per event: one CTA per FED over the global digi SoA; clusters staged.
-template <int TILE>
-__global__ void __launch_bounds__(512) k_cluster(sst_digis in, uint32_t n_feds, KParams kp, uint4* stage,
-                                                 uint64_t cap, uint32_t* ev_alloc, uint32_t* fed_cnt,
-                                                 uint32_t* fed_start) {
+// a3 - a6 per event: one warp per FE unit over the global digi SoA; clusters
+// staged per unit.
+__global__ void __launch_bounds__(256, 4) k_cluster(sst_digis in, uint32_t n_feds, KParams kp, uint4* stage,
+                                                    uint64_t cap, uint32_t* ev_alloc, uint32_t* seg_cnt,
+                                                    uint32_t* seg_start) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Shm<TILE>& s = *reinterpret_cast<Shm<TILE>*>(smem_raw);
-  const int tid = threadIdx.x;
-  const uint32_t f = blockIdx.x;
-  if (f >= n_feds) return;
-  // Channel digi ranges from the CSR row pointers, clamped to the input capacity
-  // and to 256 digis per channel, so that malformed input cannot leave the tile.
-  if (tid < kCh) {
-    const size_t c = (size_t)f * kCh + tid;
-    uint64_t a = in.chan_off[c], b = in.chan_off[c + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  fe::Warp& w = reinterpret_cast<fe::Warp*>(smem_raw)[warp];
+  const uint32_t unit = blockIdx.x * nw + warp;
+  if (unit >= n_feds * kFe) return;
+  const uint32_t f = unit / kFe, u = unit % kFe;
+  const uint32_t ch0 = f * kCh + u * kChPerFe;
+  fe::load_calib(w, kp, ch0);
+  // channel digi ranges from the CSR row pointers, clamped to the input capacity
+  // and to 256 digis per channel, so that malformed input cannot leave the tile
+  uint32_t cnt = 0;
+  if (lane < kChPerFe) {
+    uint64_t a = in.chan_off[ch0 + lane], b = in.chan_off[ch0 + lane + 1];
     if (a > in.capacity) a = in.capacity;
     if (b > in.capacity) b = in.capacity;
     const uint32_t n = b > a ? (uint32_t)(b - a) : 0u;
-    s.chan_pos[tid] = (uint32_t)a;
-    s.chan_cnt[tid] = n < (uint32_t)kStrips ? n : (uint32_t)kStrips;
+    cnt = n < (uint32_t)kStrips ? n : (uint32_t)kStrips;
+    w.chan_pos[lane] = (uint32_t)a;
   }
-  load_fed_calib(s, kp, f);
-  __syncthreads();
-  if (tid < 32) warp_scan96(s.chan_cnt, tid);
-  __syncthreads();
+  uint32_t x = cnt;
+#pragma unroll
+  for (int d = 1; d < 16; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane < kChPerFe) w.chan_cnt[lane] = x - cnt;
+  const uint32_t total = __shfl_sync(0xffffffffu, x, kChPerFe - 1);
+  if (lane == 0) w.chan_cnt[kChPerFe] = total;
+  __syncwarp();
+  const uint32_t g0 = ch0 * (uint32_t)kStrips;
   auto fill = [&](int c0, int c1) {
-    const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const uint32_t g0 = f * (uint32_t)kFedStrips;
-    for (int c = c0 + warp; c < c1; c += nw) {
-      const uint32_t o = s.chan_cnt[c] - s.chan_cnt[c0];
-      const uint32_t n = s.chan_cnt[c + 1] - s.chan_cnt[c];
-      const size_t a = s.chan_pos[c];
+    for (int c = c0; c < c1; c++) {
+      const uint32_t o = w.chan_cnt[c] - w.chan_cnt[c0];
+      const uint32_t n = w.chan_cnt[c + 1] - w.chan_cnt[c];
+      const size_t a = w.chan_pos[c];
       for (uint32_t k = lane; k < n; k += 32) {
         const uint32_t key = in.strip[a + k] - g0;
-        // a digi that does not belong to channel c is ignored by flag_tile
-        s.t_key[o + k] = (key >> 8) == (uint32_t)c ? (uint16_t)key : (uint16_t)0xFFFFu;
-        s.t_adc[o + k] = in.adc[a + k];
+        // a digi that does not belong to channel c takes no part in clustering
+        w.key[o + k] = (key >> 8) == (uint32_t)c ? (uint16_t)key : (uint16_t)0xFFFFu;
+        w.adc[o + k] = in.adc[a + k];
       }
     }
+    __syncwarp();
   };
-  const StageOut so{stage, cap, ev_alloc, fed_cnt + f, fed_start + f};
-  cluster_fed(s, kp, f, fill, so, in.status);
+  const fe::SegOut so{stage, cap, ev_alloc, seg_cnt + unit, seg_start + unit};
+  fe::cluster_unit(w, kp, kp.noise + (size_t)g0, ch0, total, fill, so, in.status);
 }
 
-// a7: every FED of every event of a batch, unpacked and clustered on chip.  A
-// persistent grid takes (FED, event) tickets FED-major, so that the CTAs working
-// at any moment share the same FED's calibration in L2.  Thread 0 fetches the
-// next ticket and its FED's offset and length while the current FED is processed.
-template <int TILE>
-__global__ void __launch_bounds__(512) k_batch(const uint8_t* __restrict__ raw,
-                                               const uint32_t* __restrict__ fed_len,
-                                               const uint64_t* __restrict__ fed_off, uint32_t n_events,
-                                               uint32_t n_feds, const uint64_t* __restrict__ clu_off,
-                                               uint64_t out_cap, sst_event_status* status, KParams kp,
-                                               uint4* stage, uint32_t* ev_alloc, uint32_t* fed_cnt,
-                                               uint32_t* fed_start, uint32_t* ticket, int lanes) {
+// a7: every FE unit of every FED of every event of a batch, unpacked and
+// clustered on chip, one warp per unit.  Persistent warps take tickets
+// FED-major (FED, then event, then FE unit), so that the warps working at any
+// moment share the same FED's calibration in L2.
+__global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ raw,
+                                                  const uint32_t* __restrict__ fed_len,
+                                                  const uint64_t* __restrict__ fed_off, uint32_t n_events,
+                                                  uint32_t n_feds, const uint64_t* __restrict__ clu_off,
+                                                  uint64_t out_cap, sst_event_status* status, KParams kp,
+                                                  uint4* stage, uint32_t* ev_alloc, uint32_t* seg_cnt,
+                                                  uint32_t* seg_start, uint32_t* ticket) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Shm<TILE>& s = *reinterpret_cast<Shm<TILE>*>(smem_raw);
-  const int tid = threadIdx.x;
-  const uint32_t n_items = n_events * n_feds;
-  auto fetch = [&]() {
-    const uint32_t t = atomicAdd(ticket, 1u);
-    uint32_t len = 0;
-    uint64_t fo = kBadOff;
-    if (t < n_items) {
-      const uint32_t f = t / n_events, e = t % n_events;
-      const size_t item = (size_t)e * n_feds + f;
-      fo = fed_off[item];
-      len = fed_len[item];
-    }
-    s.scal[S_NEXT_T] = t;
-    s.scal[S_NEXT_LEN] = len;
-    s.scal[S_NEXT_OFF_LO] = (uint32_t)fo;
-    s.scal[S_NEXT_OFF_HI] = (uint32_t)(fo >> 32);
-  };
-  if (tid == 0) fetch();
-  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  fe::Warp& w = reinterpret_cast<fe::Warp*>(smem_raw)[warp];
+  const uint32_t per_fed = n_events * kFe;
+  const uint32_t n_units = n_feds * per_fed;
   for (;;) {
-    const uint32_t t = s.scal[S_NEXT_T];
-    if (t >= n_items) break;
-    const uint64_t fo = ((uint64_t)s.scal[S_NEXT_OFF_HI] << 32) | s.scal[S_NEXT_OFF_LO];
-    const bool in_range = fo != kBadOff;
-    const uint32_t len = in_range ? s.scal[S_NEXT_LEN] : 0u;
-    __syncthreads();
-    if (tid == 0) fetch();
-    const uint32_t f = t / n_events, e = t % n_events;
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(ticket, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= n_units) break;
+    const uint32_t f = t / per_fed, r = t % per_fed, e = r / kFe, u = r % kFe;
     const size_t item = (size_t)e * n_feds + f;
-    load_fed_calib(s, kp, f);
-    const uint8_t* gfed = in_range ? raw + fo : raw;
-    const bool staged = parse_fed(s, gfed, len, f, in_range);
-    const uint32_t total = s.scal[S_TOTAL];
-    if (tid == 0) {
-      if (s.scal[S_FLAGS]) atomicOr(&status[e].flags, s.scal[S_FLAGS]);
-      if (s.scal[S_NBAD]) atomicAdd(&status[e].n_bad_channels, s.scal[S_NBAD]);
+    const uint64_t fo = fed_off[item];
+    const bool in_range = fo != kBadOff;
+    const uint32_t len = in_range ? fed_len[item] : 0u;
+    const uint32_t ch0 = f * kCh + u * kChPerFe;
+    fe::load_calib(w, kp, ch0);
+    const fe::Unit un = fe::locate(w, in_range ? raw + fo : nullptr, len, f, u, in_range);
+    uint32_t flags, nbad;
+    const uint32_t total = fe::parse_unit(w, un, &flags, &nbad);
+    if (lane == 0) {
+      if (flags) atomicOr(&status[e].flags, flags);
+      if (nbad) atomicAdd(&status[e].n_bad_channels, nbad);
       if (total) atomicAdd(&status[e].n_digi, total);
     }
-    const bool single = total <= (uint32_t)TILE;
-    const bool slots = single && s.scal[S_SLOTS] != 0;
-    // multi-chunk FEDs re-read their records from global memory: the staging
-    // buffer holds cluster results after the first chunk
-    auto fill = [&](int c0, int c1) {
-      if (slots) {
-        if (staged) emit_slots(s, s.u.fedbuf); else emit_slots(s, gfed);
-      } else if (single && staged) {
-        emit_channels(s, s.u.fedbuf, c0, c1, lanes);
-      } else {
-        emit_channels(s, gfed, c0, c1, lanes);
-      }
-    };
     const uint64_t off = clu_off[e];
     const uint64_t end = clu_off[e + 1] < out_cap ? clu_off[e + 1] : out_cap;
     const uint64_t cap = end > off ? end - off : 0;
-    const StageOut so{stage + (off < out_cap ? off : 0), cap, ev_alloc + e, fed_cnt + item, fed_start + item};
-    cluster_fed(s, kp, f, fill, so, &status[e]);
-    __syncthreads();
+    const fe::SegOut so{stage + (off < out_cap ? off : 0), cap, ev_alloc + e, seg_cnt + item * kFe + u,
+                        seg_start + item * kFe + u};
+    auto fill = [&](int c0, int c1) { fe::copy_runs(w, un, c0, c1); };
+    fe::cluster_unit(w, kp, kp.noise + (size_t)ch0 * kStrips, ch0, total, fill, so, &status[e]);
+    __syncwarp();
   }
 }
 
@@ -1039,50 +733,50 @@ cudaError_t launch_unpack_t(const uint8_t* raw, const uint32_t* fed_len, uint32_
   return cudaGetLastError();
 }
 
-template <int TILE>
-cudaError_t launch_cluster_t(const sst_digis& in, uint32_t n_feds, const KParams& kp, const Scratch& s,
-                             uint64_t cap, const Shape& sh, cudaStream_t st) {
-  const size_t sm = sizeof(Shm<TILE>);
-  cudaError_t e = cudaFuncSetAttribute((const void*)k_cluster<TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
+cudaError_t launch_cluster_fe(const sst_digis& in, uint32_t n_feds, const KParams& kp, const Scratch& s,
+                              uint64_t cap, const Shape& sh, cudaStream_t st) {
+  const int nw = sh.block / 32;
+  const size_t sm = sizeof(fe::Warp) * nw;
+  cudaError_t e = cudaFuncSetAttribute((const void*)k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e) return e;
-  k_cluster<TILE><<<n_feds, sh.block, sm, st>>>(in, n_feds, kp, s.stage, cap, s.ev_alloc, s.fed_cnt, s.fed_start);
+  const uint32_t units = n_feds * kFe;
+  k_cluster<<<(units + nw - 1) / nw, sh.block, sm, st>>>(in, n_feds, kp, s.stage, cap, s.ev_alloc, s.fed_cnt,
+                                                       s.fed_start);
   return cudaGetLastError();
 }
 
-template <int TILE>
-cudaError_t launch_batch_t(const uint8_t* raw, const uint32_t* fed_len, uint32_t n_events, uint32_t n_feds,
-                           const uint64_t* clu_off, uint64_t out_cap, sst_event_status* status, const KParams& kp,
-                           const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st, cudaEvent_t ev_begin,
-                           cudaEvent_t ev_end) {
-  const size_t sm = sizeof(Shm<TILE>);
-  const size_t items = (size_t)n_events * n_feds;
-  cudaError_t e = cudaFuncSetAttribute((const void*)k_batch<TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
+cudaError_t launch_batch_fe(const uint8_t* raw, const uint32_t* fed_len, uint32_t n_events, uint32_t n_feds,
+                            const uint64_t* clu_off, uint64_t out_cap, sst_event_status* status, const KParams& kp,
+                            const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st, cudaEvent_t ev_begin,
+                            cudaEvent_t ev_end) {
+  const int nw = sh.block / 32;
+  const size_t sm = sizeof(fe::Warp) * nw;
+  const size_t units = (size_t)n_events * n_feds * kFe;
+  cudaError_t e = cudaFuncSetAttribute((const void*)k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e) return e;
   int per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<TILE>, sh.block, sm))) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, sh.block, sm))) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int ctas = n_sm * (sh.ctas_per_sm < per_sm ? sh.ctas_per_sm : per_sm);
-  const int grid = (size_t)ctas < items ? ctas : (int)items;
+  const size_t ctas = (size_t)n_sm * (sh.ctas_per_sm < per_sm ? sh.ctas_per_sm : per_sm);
+  const size_t need = (units + nw - 1) / nw;
+  const int grid = (int)(ctas < need ? ctas : need);
   if (ev_begin && (e = cudaEventRecord(ev_begin, st))) return e;
-  k_batch<TILE><<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out_cap, status, kp,
-                                            s.stage, s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets, sh.lanes);
+  k_batch<<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out_cap, status, kp,
+                                      s.stage, s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets);
   if ((e = cudaGetLastError())) return e;
   if (ev_end && (e = cudaEventRecord(ev_end, st))) return e;
   return cudaSuccess;
 }
 
 // Per-event cluster order and the copy into the caller's SoA.
-cudaError_t launch_order(const uint64_t* clu_off, uint32_t n_events, uint32_t n_feds, const sst_clusters& out,
+cudaError_t launch_order(const uint64_t* clu_off, uint32_t n_events, uint32_t n_segs, const sst_clusters& out,
                          sst_event_status* status, const Scratch& s, cudaStream_t st) {
-  k_clu_scan<<<n_events, 256, 0, st>>>(s.fed_cnt, n_feds, s.fed_dest, status);
+  k_clu_scan<<<n_events, 256, 0, st>>>(s.fed_cnt, n_segs, s.fed_dest, status);
   cudaError_t e = cudaGetLastError();
   if (e) return e;
-  const uint64_t items = (uint64_t)n_events * n_feds;
-  const uint32_t per_cta = 2;
-  k_compact<<<(unsigned)((items + per_cta - 1) / per_cta), 256, 0, st>>>(
-      s.stage, clu_off, s.fed_cnt, s.fed_start, s.fed_dest, n_events, n_feds, per_cta, out);
+  const uint64_t items = (uint64_t)n_events * n_segs;
+  k_compact<<<(unsigned)((items + 7) / 8), 256, 0, st>>>(s.stage, clu_off, s.fed_cnt, s.fed_start, s.fed_dest,
+                                                        n_events, n_segs, out);
   return cudaGetLastError();
 }
 
@@ -1102,7 +796,7 @@ size_t smem_bytes(int tile) {
 Shape default_shape() { return Shape{256, 2048, 2, 4}; }
 
 bool shape_valid(const Shape& s) {
-  const bool blk = s.block == 128 || s.block == 256 || s.block == 512;
+  const bool blk = s.block == 128 || s.block == 256;
   const bool til = s.tile == 1024 || s.tile == 2048 || s.tile == 4096;
   const bool ln = s.lanes == 1 || s.lanes == 2 || s.lanes == 4 || s.lanes == 8 || s.lanes == 16 || s.lanes == 32;
   return blk && til && ln && s.ctas_per_sm >= 1 && s.ctas_per_sm <= 8;
@@ -1127,14 +821,8 @@ cudaError_t launch_cluster(const sst_digis& in, uint32_t n_feds, const sst_clust
                            const Scratch& s, const Shape& sh, cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(s.ev_alloc, 0, sizeof(uint32_t), st))) return e;
-  switch (sh.tile) {
-    case 1024: e = launch_cluster_t<1024>(in, n_feds, kp, s, out.capacity, sh, st); break;
-    case 2048: e = launch_cluster_t<2048>(in, n_feds, kp, s, out.capacity, sh, st); break;
-    case 4096: e = launch_cluster_t<4096>(in, n_feds, kp, s, out.capacity, sh, st); break;
-    default: return cudaErrorInvalidValue;
-  }
-  if (e) return e;
-  return launch_order(nullptr, 1, n_feds, out, in.status, s, st);  // one event at offset 0
+  if ((e = launch_cluster_fe(in, n_feds, kp, s, out.capacity, sh, st))) return e;
+  return launch_order(nullptr, 1, n_feds * kFe, out, in.status, s, st);  // one event at offset 0
 }
 
 cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len, uint32_t n_events,
@@ -1146,23 +834,10 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
   if ((e = cudaMemsetAsync(s.ev_alloc, 0, sizeof(uint32_t) * n_events, st))) return e;
   if ((e = cudaMemsetAsync(s.tickets, 0, sizeof(uint32_t) * 4, st))) return e;
   k_fed_scan<<<n_events, 256, 0, st>>>(event_off, 0, fed_len, n_feds, s.fed_off, status);
-  switch (sh.tile) {
-    case 1024:
-      e = launch_batch_t<1024>(raw, fed_len, n_events, n_feds, clu_off, out.capacity, status, kp, s, sh, n_sm, st,
-                               ev_begin, ev_end);
-      break;
-    case 2048:
-      e = launch_batch_t<2048>(raw, fed_len, n_events, n_feds, clu_off, out.capacity, status, kp, s, sh, n_sm, st,
-                               ev_begin, ev_end);
-      break;
-    case 4096:
-      e = launch_batch_t<4096>(raw, fed_len, n_events, n_feds, clu_off, out.capacity, status, kp, s, sh, n_sm, st,
-                               ev_begin, ev_end);
-      break;
-    default: return cudaErrorInvalidValue;
-  }
+  e = launch_batch_fe(raw, fed_len, n_events, n_feds, clu_off, out.capacity, status, kp, s, sh, n_sm, st, ev_begin,
+                      ev_end);
   if (e) return e;
-  return launch_order(clu_off, n_events, n_feds, out, status, s, st);
+  return launch_order(clu_off, n_events, n_feds * kFe, out, status, s, st);
 }
 
 cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st) {

@@ -140,7 +140,7 @@ def test_batch_launch_shapes_give_identical_results(w0):
     w, calib, g = w0
     evs = [eg.make_event(w, calib, 40 + i, occupancy=0.01 * (i + 1)) for i in range(3)]
     ref = g.batch([(e.raw, e.fed_len) for e in evs])
-    for block, cps, tile, lanes in [(128, 4, 1024, 1), (512, 2, 4096, 8), (256, 3, 2048, 32), (256, 8, 1024, 4)]:
+    for block, cps, tile, lanes in [(128, 4, 1024, 1), (128, 2, 4096, 8), (256, 3, 2048, 32), (256, 8, 1024, 4)]:
         sst.sst_set_tune(g.ctx, block, cps, tile, lanes)
         got = g.batch([(e.raw, e.fed_len) for e in evs])
         for (s0, c0), (s1, c1) in zip(ref, got):
