@@ -204,6 +204,29 @@ sst_status sst_unpack(sst_ctx* ctx, const uint8_t* raw, uint64_t raw_bytes, cons
 sst_status sst_cluster(sst_ctx* ctx, const sst_digis* in, uint32_t n_feds, const sst_clusters* out,
                        void* stream);
 
+/* ---- per-event unpacking without allocation ------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that may not
+ * allocate device memory once they run (a trigger or DAQ process whose device
+ * memory is reserved up front by its own allocator; code that must not let
+ * cudaMalloc synchronise the device under a real-time pipeline).  It needs no
+ * context: it unpacks exactly as sst_unpack does (same arguments, same outputs,
+ * same status semantics), on the current CUDA device, with its scratch in a fixed
+ * device array of the library (SST_NOALLOC_MAX_FEDS look-back states and FED
+ * offsets, about 16 KiB per device, held until the process exits).  It calls no
+ * cudaMalloc, cudaFree or allocating routine.
+ *   - n_feds > SST_NOALLOC_MAX_FEDS returns SST_ERR_TOO_LARGE; a null pointer, a
+ *     misaligned raw buffer or n_feds == 0 returns SST_ERR_INVALID_ARG; a CUDA
+ *     error returns SST_ERR_CUDA.
+ *   - The first call on a device looks up the array's device address on that
+ *     device (cudaGetSymbolAddress); make that first call before capturing any
+ *     stream.
+ *   - All calls on a device share the one array: calls whose work overlaps on the
+ *     GPU (different streams, not ordered) race and give wrong results.  Every call
+ *     clears what must start at zero on its own stream before its kernels run. */
+#define SST_NOALLOC_MAX_FEDS 1024u
+sst_status sst_unpack_noalloc(const uint8_t* raw, uint64_t raw_bytes, const uint32_t* fed_len, uint32_t n_feds,
+                              const sst_digis* out, void* stream);
+
 /* ---- batched path (section 3: many events concurrently on one GPU) -------------- */
 
 /* Unpacks and clusters n_events events in one persistent launch; digis stay on

@@ -108,6 +108,7 @@ def load_library():
         "sst_last_error": ([vp], ctypes.c_char_p),
         "sst_calib_upload": ([vp, vp, vp, vp, P(sst_params), vp], i32),
         "sst_unpack": ([vp, vp, u64, vp, u32, P(sst_digis), vp], i32),
+        "sst_unpack_noalloc": ([vp, u64, vp, u32, P(sst_digis), vp], i32),
         "sst_cluster": ([vp, P(sst_digis), u32, P(sst_clusters), vp], i32),
         "sst_batch": ([vp, vp, vp, vp, u32, u32, vp, P(sst_clusters), vp, vp], i32),
         "sst_set_tune": ([vp, P(sst_tune)], i32),
@@ -129,7 +130,8 @@ def load_library():
 
 
 def exported_symbols() -> list[str]:
-    return ["sst_create", "sst_destroy", "sst_last_error", "sst_calib_upload", "sst_unpack", "sst_cluster",
+    return ["sst_create", "sst_destroy", "sst_last_error", "sst_calib_upload", "sst_unpack", "sst_unpack_noalloc",
+            "sst_cluster",
             "sst_batch", "sst_set_tune", "sst_get_tune", "sst_autotune", "sst_profile_enable", "sst_profile_read",
             "sst_server_start", "sst_server_stop",
             "sst_submit", "sst_poll"]
@@ -194,6 +196,16 @@ def sst_unpack(ctx: int, raw, fed_len, n_feds: int, digis: sst_digis, stream=Non
     code = load_library().sst_unpack(ctx, _dp(raw), raw.numel(), _dp(fed_len), n_feds, ctypes.byref(digis),
                                      _stream(stream))
     _check(ctx, code, "sst_unpack")
+
+
+def sst_unpack_noalloc(raw, fed_len, n_feds: int, digis: sst_digis, stream=None) -> int:
+    """Unpacks like sst_unpack without a context and without allocating; returns
+    the status code (SST_OK, SST_ERR_TOO_LARGE, ...) instead of raising."""
+    return load_library().sst_unpack_noalloc(_dp(raw), raw.numel(), _dp(fed_len), n_feds, ctypes.byref(digis),
+                                             _stream(stream))
+
+
+NOALLOC_MAX_FEDS = 1024
 
 
 def sst_cluster(ctx: int, digis: sst_digis, n_feds: int, clusters: sst_clusters, stream=None) -> None:
