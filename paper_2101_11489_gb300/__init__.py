@@ -268,12 +268,13 @@ def sst_server_stop(ctx: int) -> None:
 
 
 def sst_submit(ctx: int, raw: np.ndarray, fed_len: np.ndarray) -> tuple[int, int]:
-    """Returns (status code, ticket); BUSY / BUDGET are returned, not raised."""
+    """Returns (status code, ticket); the admission outcomes BUSY, BUDGET and
+    TOO_LARGE are returned, not raised."""
     raw = np.ascontiguousarray(raw, dtype=np.uint8)
     fed_len = np.ascontiguousarray(fed_len, dtype=np.uint32)
     t = ctypes.c_uint64()
     code = load_library().sst_submit(ctx, _hp(raw), raw.size, _hp(fed_len), ctypes.byref(t))
-    if code not in (SST_OK, SST_ERR_BUSY, SST_ERR_BUDGET):
+    if code not in (SST_OK, SST_ERR_BUSY, SST_ERR_BUDGET, SST_ERR_TOO_LARGE):
         _check(ctx, code, "sst_submit")
     return code, t.value
 

@@ -72,6 +72,9 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
                          const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st,
                          cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st);
+// Served path: packs each event's clusters back to back; pack_off[n_events + 1].
+cudaError_t launch_pack(const uint64_t* clu_off, const sst_event_status* status, uint32_t n_events,
+                        const sst_clusters& in, const sst_clusters& out, uint64_t* pack_off, cudaStream_t st);
 
 }  // namespace sst
 

@@ -712,6 +712,44 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
   }
 }
 
+// Served path: packs the clusters of every event of a batch back to back
+// (event order) so that the host reads them with one copy per array.  One CTA:
+// pack_off[e] = sum of the events' cluster counts before e (n_events + 1 values).
+__global__ void __launch_bounds__(1024) k_pack(const uint64_t* __restrict__ clu_off,
+                                               const sst_event_status* __restrict__ status, uint32_t n_events,
+                                               sst_clusters in, sst_clusters out, uint64_t* pack_off) {
+  __shared__ uint32_t wsum[32];
+  __shared__ uint64_t carry_s;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (uint32_t b = 0; b < n_events; b += blockDim.x) {
+    const uint32_t e = b + threadIdx.x;
+    const uint32_t n = e < n_events ? status[e].n_clusters : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan(n, wsum, &tot);
+    const uint64_t carry = carry_s;
+    if (e < n_events) pack_off[e] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s = carry + tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) pack_off[n_events] = carry_s;
+  __syncthreads();
+  // copy, one warp per event
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (uint32_t e = warp; e < n_events; e += nw) {
+    const uint32_t n = status[e].n_clusters;
+    const uint64_t a = clu_off[e], d = pack_off[e];
+    for (uint32_t k = lane; k < n; k += 32) {
+      out.det[d + k] = in.det[a + k];
+      out.first[d + k] = in.first[a + k];
+      out.width[d + k] = in.width[a + k];
+      out.charge[d + k] = in.charge[a + k];
+      out.barycenter[d + k] = in.barycenter[a + k];
+    }
+  }
+}
+
 __global__ void k_badmask(const uint8_t* __restrict__ bad, uint32_t* __restrict__ mask, uint64_t n_words) {
   const uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= n_words) return;
@@ -838,6 +876,12 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
                       ev_end);
   if (e) return e;
   return launch_order(clu_off, n_events, n_feds * kFe, out, status, s, st);
+}
+
+cudaError_t launch_pack(const uint64_t* clu_off, const sst_event_status* status, uint32_t n_events,
+                        const sst_clusters& in, const sst_clusters& out, uint64_t* pack_off, cudaStream_t st) {
+  k_pack<<<1, 1024, 0, st>>>(clu_off, status, n_events, in, out, pack_off);
+  return cudaGetLastError();
 }
 
 cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st) {

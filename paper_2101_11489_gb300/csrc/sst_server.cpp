@@ -1,17 +1,533 @@
-// sst_server.cpp -- served path (continuous batching).  Placeholder until the
-// request loop lands: every entry point reports SST_ERR_STATE.
+// sst_server.cpp -- the served path: continuous batching of events submitted one at
+// a time (arXiv 2101.11489, section 3: many events processed concurrently on one
+// GPU, with transfers overlapped with computation and a caching allocator for
+// device memory).
+//
+// Memory: at start the server carves `max_inflight` batch slots out of the device
+// budget.  A slot owns a stream, the batched kernels' scratch, a device raw arena,
+// device cluster arrays and pinned host mirrors for its results; events waiting for
+// a slot sit in a pinned host pool.  Nothing is allocated per event.
+//
+// Admission (sst_submit): an event is taken when a request slot is free (else
+// BUSY) and its bytes fit in the host pool (else BUDGET, retry after polling);
+// an event larger than a slot's raw arena is never admissible (TOO_LARGE).
+//
+// The loop thread launches a batch as soon as a slot is free and events are
+// pending (FIFO, up to max_batch_events and the slot's raw arena): it copies the
+// events into the slot's arena, runs the batched unpack + cluster kernels, packs
+// the events' clusters back to back and reads back the statuses; when those are
+// in, it reads back exactly the packed clusters into a pinned results pool and
+// frees the slot.  Batches on different slots overlap on the GPU.  sst_poll
+// copies an event's results out of the pool.  The pool is sized for the worst
+// case of every admitted event (a cluster needs at least two payload bytes, so at
+// most 8 bytes of results per raw byte), so a batch never waits for the client to
+// poll, whatever order the client polls in.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <thread>
+#include <vector>
+
 #include "sst_internal.h"
 
+namespace {
+
+double now_us() {
+  using namespace std::chrono;
+  return duration_cast<duration<double, std::micro>>(steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator of byte ranges (host pool), 256-byte granules.
+class RangeAlloc {
+ public:
+  void reset(size_t cap) {
+    free_.clear();
+    cap_ = cap;
+    if (cap) free_[0] = cap;
+  }
+  bool alloc(size_t n, size_t* off) {
+    n = (n + 255) & ~size_t(255);
+    if (n == 0) n = 256;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        *off = it->first;
+        const size_t rest = it->second - n, at = it->first + n;
+        free_.erase(it);
+        if (rest) free_[at] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t n) {
+    n = (n + 255) & ~size_t(255);
+    if (n == 0) n = 256;
+    auto next = free_.lower_bound(off);
+    if (next != free_.end() && off + n == next->first) {
+      n += next->second;
+      free_.erase(next);
+    }
+    auto it = free_.lower_bound(off);
+    if (it != free_.begin()) {
+      auto prev = std::prev(it);
+      if (prev->first + prev->second == off) {
+        prev->second += n;
+        return;
+      }
+    }
+    free_[off] = n;
+  }
+
+ private:
+  std::map<size_t, size_t> free_;
+  size_t cap_ = 0;
+};
+
+enum class ReqState { kFree, kPending, kLaunched, kDone };
+enum class SlotState { kFree, kRunning, kReading };
+
+struct Req {
+  ReqState state = ReqState::kFree;
+  uint64_t ticket = 0;
+  size_t host_off = 0;   // raw bytes in the host pool
+  uint64_t bytes = 0;
+  std::vector<uint32_t> fed_len;
+  double t_submit = 0, t_done = 0;
+  int slot = -1;
+  uint32_t index = 0;    // position in its batch
+  sst_event_status status{};
+  size_t res_off = 0;    // its batch's results region in the results pool
+  uint64_t res_total = 0;  // records in that region
+  uint64_t first = 0;    // its first record in the region
+};
+
+struct Slot {
+  SlotState state = SlotState::kFree;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev_status = nullptr, ev_done = nullptr;
+  sst::Scratch scratch;
+  uint8_t* d_raw = nullptr;
+  size_t raw_cap = 0;
+  uint64_t* d_event_off = nullptr;
+  uint32_t* d_fed_len = nullptr;
+  uint64_t* d_clu_off = nullptr;
+  sst_event_status* d_status = nullptr;
+  uint64_t* d_pack_off = nullptr;
+  sst_clusters d_out{}, d_pack{};  // per-event slices, then packed
+  size_t clu_cap = 0;
+  uint64_t* h_event_off = nullptr;
+  uint32_t* h_fed_len = nullptr;
+  uint64_t* h_clu_off = nullptr;
+  sst_event_status* h_status = nullptr;
+  uint64_t* h_pack_off = nullptr;
+  std::vector<int> reqs;   // requests of the current batch, in batch order
+  size_t res_off = 0;      // results region of the current batch
+  uint64_t res_total = 0;
+};
+
+}  // namespace
+
+struct sst_server {
+  sst_ctx* ctx = nullptr;
+  sst_server_opts opts{};
+  std::mutex mu;
+  std::condition_variable cv_loop, cv_done;
+  std::thread loop;
+  bool stop = false;
+  std::string fatal;  // CUDA error seen by the loop; every later call reports it
+  std::vector<Slot> slots;
+  std::vector<Req> reqs;
+  std::deque<int> pending;
+  uint64_t next_ticket = 1;
+  uint8_t* host_pool = nullptr;
+  size_t host_cap = 0;
+  RangeAlloc host_alloc;
+  uint8_t* res_pool = nullptr;  // results of finished batches (pinned)
+  size_t res_cap = 0;
+  RangeAlloc res_alloc;
+  std::map<size_t, std::pair<size_t, int>> regions;  // results region -> (bytes, events not yet polled)
+  size_t max_event_bytes = 0;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+  return cudaMalloc(reinterpret_cast<void**>(p), (n ? n : 1) * sizeof(T));
+}
+template <typename T>
+cudaError_t halloc(T** p, size_t n) {
+  return cudaHostAlloc(reinterpret_cast<void**>(p), (n ? n : 1) * sizeof(T), cudaHostAllocDefault);
+}
+
+void free_slot(Slot& s) {
+  if (s.st) cudaStreamSynchronize(s.st);
+  sst::free_scratch(s.scratch);
+  cudaFree(s.d_raw);
+  cudaFree(s.d_event_off);
+  cudaFree(s.d_fed_len);
+  cudaFree(s.d_clu_off);
+  cudaFree(s.d_status);
+  cudaFree(s.d_pack_off);
+  for (sst_clusters* c : {&s.d_out, &s.d_pack}) {
+    cudaFree(c->det);
+    cudaFree(c->first);
+    cudaFree(c->width);
+    cudaFree(c->charge);
+    cudaFree(c->barycenter);
+  }
+  cudaFreeHost(s.h_event_off);
+  cudaFreeHost(s.h_fed_len);
+  cudaFreeHost(s.h_clu_off);
+  cudaFreeHost(s.h_status);
+  cudaFreeHost(s.h_pack_off);
+  if (s.ev_status) cudaEventDestroy(s.ev_status);
+  if (s.ev_done) cudaEventDestroy(s.ev_done);
+  if (s.st) cudaStreamDestroy(s.st);
+  s = Slot{};
+}
+
+cudaError_t alloc_clusters(sst_clusters* c, size_t n, bool /*host*/) {
+  cudaError_t e;
+  c->capacity = n;
+  if ((e = dalloc(&c->det, n)) || (e = dalloc(&c->first, n)) || (e = dalloc(&c->width, n)) ||
+      (e = dalloc(&c->charge, n)) || (e = dalloc(&c->barycenter, n)))
+    return e;
+  return cudaSuccess;
+}
+
+// The five arrays of `n` packed records of a results region, in the pool.
+struct HostClusters {
+  uint32_t* det;
+  uint16_t* first;
+  uint16_t* width;
+  uint32_t* charge;
+  float* bary;
+};
+HostClusters region_arrays(uint8_t* base, uint64_t n) {
+  HostClusters h;
+  h.det = reinterpret_cast<uint32_t*>(base);
+  h.charge = reinterpret_cast<uint32_t*>(base + 4 * n);
+  h.bary = reinterpret_cast<float*>(base + 8 * n);
+  h.first = reinterpret_cast<uint16_t*>(base + 12 * n);
+  h.width = reinterpret_cast<uint16_t*>(base + 14 * n);
+  return h;
+}
+
+cudaError_t init_slot(Slot& s, const sst_server_opts& o, size_t raw_cap, uint32_t n_feds) {
+  cudaError_t e;
+  const uint32_t E = o.max_batch_events;
+  s.raw_cap = raw_cap;
+  s.clu_cap = raw_cap / 2 + E;
+  if ((e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking))) return e;
+  if ((e = cudaEventCreateWithFlags(&s.ev_status, cudaEventDisableTiming))) return e;
+  if ((e = cudaEventCreateWithFlags(&s.ev_done, cudaEventDisableTiming))) return e;
+  if ((e = sst::ensure_scratch(s.scratch, (size_t)E * n_feds * sst::kFe, E, s.clu_cap))) return e;
+  if ((e = dalloc(&s.d_raw, raw_cap))) return e;
+  if ((e = dalloc(&s.d_event_off, E + 1)) || (e = dalloc(&s.d_fed_len, (size_t)E * n_feds)) ||
+      (e = dalloc(&s.d_clu_off, E + 1)) || (e = dalloc(&s.d_status, E)) || (e = dalloc(&s.d_pack_off, E + 1)))
+    return e;
+  if ((e = alloc_clusters(&s.d_out, s.clu_cap, false)) || (e = alloc_clusters(&s.d_pack, s.clu_cap, false)))
+    return e;
+  if ((e = halloc(&s.h_event_off, E + 1)) || (e = halloc(&s.h_fed_len, (size_t)E * n_feds)) ||
+      (e = halloc(&s.h_clu_off, E + 1)) || (e = halloc(&s.h_status, E)) || (e = halloc(&s.h_pack_off, E + 1)))
+    return e;
+  return cudaSuccess;
+}
+
+void loop_main(sst_server* sv);
+
+}  // namespace
+
+namespace {
+
+// Forms the next batch from the pending queue and launches it on slot si.
+// Called with the lock held.  Returns false when nothing was pending.
+bool launch_on(sst_server* sv, int si) {
+  Slot& s = sv->slots[si];
+  const uint32_t nf = sv->opts.n_feds;
+  s.reqs.clear();
+  uint64_t bytes = 0;
+  while (!sv->pending.empty() && s.reqs.size() < sv->opts.max_batch_events) {
+    const Req& r = sv->reqs[sv->pending.front()];
+    if (bytes + r.bytes > s.raw_cap) break;
+    bytes += r.bytes;
+    s.reqs.push_back(sv->pending.front());
+    sv->pending.pop_front();
+  }
+  if (s.reqs.empty()) return false;
+  const uint32_t E = (uint32_t)s.reqs.size();
+  uint64_t off = 0, coff = 0;
+  cudaError_t e = cudaSuccess;
+  for (uint32_t i = 0; i < E; i++) {
+    Req& r = sv->reqs[s.reqs[i]];
+    s.h_event_off[i] = off;
+    s.h_clu_off[i] = coff;
+    std::memcpy(s.h_fed_len + (size_t)i * nf, r.fed_len.data(), nf * sizeof(uint32_t));
+    if (!e) e = cudaMemcpyAsync(s.d_raw + off, sv->host_pool + r.host_off, r.bytes, cudaMemcpyHostToDevice, s.st);
+    off += r.bytes;
+    coff += r.bytes / 2 + 1;
+    r.state = ReqState::kLaunched;
+    r.slot = si;
+    r.index = i;
+  }
+  s.h_event_off[E] = off;
+  s.h_clu_off[E] = coff;
+  if (!e) e = cudaMemcpyAsync(s.d_event_off, s.h_event_off, (E + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, s.st);
+  if (!e) e = cudaMemcpyAsync(s.d_fed_len, s.h_fed_len, (size_t)E * nf * sizeof(uint32_t), cudaMemcpyHostToDevice, s.st);
+  if (!e) e = cudaMemcpyAsync(s.d_clu_off, s.h_clu_off, (E + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, s.st);
+  sst_clusters out = s.d_out;
+  out.capacity = s.clu_cap;
+  if (!e) e = sst::launch_batch(s.d_raw, s.d_event_off, s.d_fed_len, E, nf, s.d_clu_off, out, s.d_status,
+                                sst::kparams(sv->ctx), s.scratch, sv->ctx->shape, sv->ctx->n_sm, s.st);
+  if (!e) e = sst::launch_pack(s.d_clu_off, s.d_status, E, s.d_out, s.d_pack, s.d_pack_off, s.st);
+  if (!e) e = cudaMemcpyAsync(s.h_status, s.d_status, E * sizeof(sst_event_status), cudaMemcpyDeviceToHost, s.st);
+  if (!e) e = cudaMemcpyAsync(s.h_pack_off, s.d_pack_off, (E + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s.st);
+  if (!e) e = cudaEventRecord(s.ev_status, s.st);
+  if (e) sv->fatal = std::string("served batch launch: ") + cudaGetErrorString(e);
+  s.state = SlotState::kRunning;
+  return true;
+}
+
+// Advances running slots; called with the lock held.  Returns true on progress.
+bool advance(sst_server* sv) {
+  bool progress = false;
+  for (Slot& s : sv->slots) {
+    if (s.state == SlotState::kRunning) {
+      const cudaError_t q = cudaEventQuery(s.ev_status);
+      if (q == cudaErrorNotReady) continue;
+      cudaError_t e = q;
+      const uint64_t total = s.h_pack_off[s.reqs.size()];
+      size_t off = 0;
+      if (!e && !sv->res_alloc.alloc(16 * total, &off)) {
+        sv->fatal = "served batch: results pool exhausted";  // excluded by its sizing
+        e = cudaErrorMemoryAllocation;
+      }
+      s.res_off = off;
+      s.res_total = total;
+      const sst_clusters& d = s.d_pack;
+      const HostClusters h = region_arrays(sv->res_pool + off, total);
+      if (!e && total) {
+        e = cudaMemcpyAsync(h.det, d.det, total * 4, cudaMemcpyDeviceToHost, s.st);
+        if (!e) e = cudaMemcpyAsync(h.first, d.first, total * 2, cudaMemcpyDeviceToHost, s.st);
+        if (!e) e = cudaMemcpyAsync(h.width, d.width, total * 2, cudaMemcpyDeviceToHost, s.st);
+        if (!e) e = cudaMemcpyAsync(h.charge, d.charge, total * 4, cudaMemcpyDeviceToHost, s.st);
+        if (!e) e = cudaMemcpyAsync(h.bary, d.barycenter, total * 4, cudaMemcpyDeviceToHost, s.st);
+      }
+      if (!e) e = cudaEventRecord(s.ev_done, s.st);
+      if (e && sv->fatal.empty()) sv->fatal = std::string("served batch: ") + cudaGetErrorString(e);
+      s.state = SlotState::kReading;
+      progress = true;
+    }
+    if (s.state == SlotState::kReading) {
+      const cudaError_t q = cudaEventQuery(s.ev_done);
+      if (q == cudaErrorNotReady) continue;
+      if (q && sv->fatal.empty()) sv->fatal = std::string("served batch: ") + cudaGetErrorString(q);
+      const double t = now_us();
+      sv->regions[s.res_off] = std::make_pair((size_t)(16 * s.res_total), (int)s.reqs.size());
+      for (size_t i = 0; i < s.reqs.size(); i++) {
+        Req& r = sv->reqs[s.reqs[i]];
+        r.state = ReqState::kDone;
+        r.t_done = t;
+        r.status = s.h_status[i];
+        r.res_off = s.res_off;
+        r.res_total = s.res_total;
+        r.first = s.h_pack_off[i];
+      }
+      s.reqs.clear();
+      s.state = SlotState::kFree;
+      progress = true;
+      sv->cv_done.notify_all();
+    }
+  }
+  return progress;
+}
+
+void loop_main(sst_server* sv) {
+  cudaSetDevice(sv->ctx->device);
+  std::unique_lock<std::mutex> lock(sv->mu);
+  while (!sv->stop) {
+    bool progress = advance(sv);
+    for (size_t si = 0; si < sv->slots.size() && !sv->pending.empty(); si++)
+      if (sv->slots[si].state == SlotState::kFree && launch_on(sv, (int)si)) progress = true;
+    if (progress) continue;
+    bool busy = false;
+    for (const Slot& s : sv->slots)
+      busy |= s.state == SlotState::kRunning || s.state == SlotState::kReading;
+    if (busy)
+      sv->cv_loop.wait_for(lock, std::chrono::microseconds(20));
+    else
+      sv->cv_loop.wait_for(lock, std::chrono::milliseconds(5));
+  }
+}
+
+// Releases a finished request: its raw bytes and its share of its results region.
+// Lock held.
+void release(sst_server* sv, int ri) {
+  Req& r = sv->reqs[ri];
+  sv->host_alloc.release(r.host_off, r.bytes);
+  auto it = sv->regions.find(r.res_off);
+  if (r.state == ReqState::kDone && it != sv->regions.end() && --it->second.second == 0) {
+    sv->res_alloc.release(it->first, it->second.first);
+    sv->regions.erase(it);
+  }
+  r = Req{};
+}
+
+}  // namespace
+
 extern "C" {
-sst_status sst_server_start(sst_ctx* ctx, const sst_server_opts*) {
-  return sst::set_err(ctx, SST_ERR_STATE, "server not available");
+
+sst_status sst_server_stop(sst_ctx* ctx);
+
+sst_status sst_server_start(sst_ctx* ctx, const sst_server_opts* opts) {
+  if (!ctx || !opts) return SST_ERR_INVALID_ARG;
+  if (ctx->server) return sst::set_err(ctx, SST_ERR_STATE, "sst_server_start: already running");
+  if (!ctx->has_calib) return sst::set_err(ctx, SST_ERR_NO_CALIB, "sst_server_start: no calibration");
+  const sst_server_opts& o = *opts;
+  if (o.mem_budget_bytes < (64ull << 20) || o.max_batch_events == 0 || o.max_batch_events > 4096 ||
+      o.max_inflight == 0 || o.max_inflight > 8 || o.max_requests == 0 || o.max_requests > (1u << 20) ||
+      o.n_feds == 0 || o.n_feds > ctx->n_feds)
+    return sst::set_err(ctx, SST_ERR_INVALID_ARG,
+                        "sst_server_start: need budget >= 64 MiB, 1..4096 events per batch, 1..8 in flight, "
+                        "1..2^20 requests and 1..context FEDs per event");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  auto* sv = new sst_server();
+  sv->ctx = ctx;
+  sv->opts = o;
+  // per slot: raw arena r, cluster records r/2 three times over (per-event
+  // output, packed output, staging) at 16 bytes each, pinned host results: ~25 r
+  const size_t raw_cap = (size_t)(o.mem_budget_bytes / (25ull * o.max_inflight)) & ~size_t(255);
+  sv->max_event_bytes = raw_cap;
+  sv->host_cap = raw_cap * (o.max_inflight + 1);
+  if (sv->host_cap > (size_t(2) << 30)) sv->host_cap = size_t(2) << 30;
+  cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&sv->host_pool), sv->host_cap, cudaHostAllocDefault);
+  sv->host_alloc.reset(sv->host_cap);
+  // every admitted event's results fit at once: at most raw/2 + 1 records of 16
+  // bytes per event, plus one 256-byte granule of rounding per batch
+  sv->res_cap = 8 * sv->host_cap + (size_t)(16 + 256) * o.max_requests + 256 * o.max_inflight;
+  if (!e) e = cudaHostAlloc(reinterpret_cast<void**>(&sv->res_pool), sv->res_cap, cudaHostAllocDefault);
+  sv->res_alloc.reset(sv->res_cap);
+  sv->slots.resize(o.max_inflight);
+  for (uint32_t i = 0; i < o.max_inflight && !e; i++) e = init_slot(sv->slots[i], o, raw_cap, o.n_feds);
+  if (e) {
+    for (Slot& s : sv->slots) free_slot(s);
+    if (sv->host_pool) cudaFreeHost(sv->host_pool);
+    if (sv->res_pool) cudaFreeHost(sv->res_pool);
+    delete sv;
+    if (prev >= 0) cudaSetDevice(prev);
+    return sst::cuda_err(ctx, e, "sst_server_start");
+  }
+  sv->reqs.resize(o.max_requests);
+  ctx->server = sv;
+  sv->loop = std::thread(loop_main, sv);
+  if (prev >= 0) cudaSetDevice(prev);
+  return SST_OK;
 }
-sst_status sst_server_stop(sst_ctx* ctx) { return ctx ? SST_OK : SST_ERR_INVALID_ARG; }
-sst_status sst_submit(sst_ctx* ctx, const uint8_t*, uint64_t, const uint32_t*, uint64_t*) {
-  return sst::set_err(ctx, SST_ERR_STATE, "server not running");
+
+sst_status sst_server_stop(sst_ctx* ctx) {
+  if (!ctx) return SST_ERR_INVALID_ARG;
+  sst_server* sv = ctx->server;
+  if (!sv) return SST_OK;
+  {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    sv->stop = true;
+  }
+  sv->cv_loop.notify_all();
+  sv->cv_done.notify_all();
+  sv->loop.join();
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  for (Slot& s : sv->slots) free_slot(s);
+  if (sv->host_pool) cudaFreeHost(sv->host_pool);
+  if (sv->res_pool) cudaFreeHost(sv->res_pool);
+  if (prev >= 0) cudaSetDevice(prev);
+  ctx->server = nullptr;
+  delete sv;
+  return SST_OK;
 }
-sst_status sst_poll(sst_ctx* ctx, uint64_t, int64_t, sst_result_info*, uint32_t*, uint16_t*, uint16_t*, uint32_t*,
-                    float*, uint64_t) {
-  return sst::set_err(ctx, SST_ERR_STATE, "server not running");
+
+sst_status sst_submit(sst_ctx* ctx, const uint8_t* raw, uint64_t raw_bytes, const uint32_t* fed_len,
+                      uint64_t* ticket) {
+  if (!ctx || !raw || !fed_len || !ticket) return SST_ERR_INVALID_ARG;
+  sst_server* sv = ctx->server;
+  if (!sv) return sst::set_err(ctx, SST_ERR_STATE, "sst_submit: server not running");
+  if (raw_bytes > sv->max_event_bytes) return SST_ERR_TOO_LARGE;
+  int ri = -1;
+  size_t off = 0;
+  {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    if (!sv->fatal.empty()) return sst::set_err(ctx, SST_ERR_CUDA, sv->fatal);
+    for (size_t i = 0; i < sv->reqs.size(); i++)
+      if (sv->reqs[i].state == ReqState::kFree) {
+        ri = (int)i;
+        break;
+      }
+    if (ri < 0) return SST_ERR_BUSY;
+    if (!sv->host_alloc.alloc(raw_bytes, &off)) return SST_ERR_BUDGET;
+    Req& r = sv->reqs[ri];
+    r.state = ReqState::kPending;  // reserved; not yet queued
+    r.host_off = off;
+    r.bytes = raw_bytes;
+    r.ticket = sv->next_ticket++;
+    *ticket = r.ticket;
+  }
+  // copy outside the lock, then queue
+  std::memcpy(sv->host_pool + off, raw, raw_bytes);
+  std::vector<uint32_t> fl(fed_len, fed_len + sv->opts.n_feds);
+  {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    Req& r = sv->reqs[ri];
+    r.fed_len.swap(fl);
+    r.t_submit = now_us();
+    sv->pending.push_back(ri);
+  }
+  sv->cv_loop.notify_one();
+  return SST_OK;
 }
+
+sst_status sst_poll(sst_ctx* ctx, uint64_t ticket, int64_t timeout_us, sst_result_info* info, uint32_t* det,
+                    uint16_t* first, uint16_t* width, uint32_t* charge, float* barycenter, uint64_t capacity) {
+  if (!ctx) return SST_ERR_INVALID_ARG;
+  sst_server* sv = ctx->server;
+  if (!sv) return sst::set_err(ctx, SST_ERR_STATE, "sst_poll: server not running");
+  std::unique_lock<std::mutex> lock(sv->mu);
+  int ri = -1;
+  for (size_t i = 0; i < sv->reqs.size(); i++)
+    if (sv->reqs[i].state != ReqState::kFree && sv->reqs[i].ticket == ticket) {
+      ri = (int)i;
+      break;
+    }
+  if (ri < 0) return sst::set_err(ctx, SST_ERR_INVALID_ARG, "sst_poll: unknown ticket");
+  auto done = [&] { return sv->reqs[ri].state == ReqState::kDone || !sv->fatal.empty() || sv->stop; };
+  if (timeout_us < 0)
+    sv->cv_done.wait(lock, done);
+  else if (timeout_us > 0)
+    sv->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), done);
+  if (!sv->fatal.empty()) return sst::set_err(ctx, SST_ERR_CUDA, sv->fatal);
+  Req& r = sv->reqs[ri];
+  if (r.state != ReqState::kDone) return SST_ERR_NOT_READY;
+  const sst_event_status st = r.status;
+  const uint64_t a = r.first;
+  const uint64_t n = st.n_clusters < capacity ? st.n_clusters : capacity;
+  const HostClusters h = region_arrays(sv->res_pool + r.res_off, r.res_total);
+  if (det) std::memcpy(det, h.det + a, n * sizeof(uint32_t));
+  if (first) std::memcpy(first, h.first + a, n * sizeof(uint16_t));
+  if (width) std::memcpy(width, h.width + a, n * sizeof(uint16_t));
+  if (charge) std::memcpy(charge, h.charge + a, n * sizeof(uint32_t));
+  if (barycenter) std::memcpy(barycenter, h.bary + a, n * sizeof(float));
+  if (info) {
+    info->status = st;
+    info->t_submit_us = r.t_submit;
+    info->t_done_us = r.t_done;
+  }
+  release(sv, ri);
+  return SST_OK;
 }
+
+}  // extern "C"
