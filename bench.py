@@ -68,6 +68,13 @@ def _gen_event(args):
     return e.raw, e.fed_len, e.n_digi
 
 
+def _gen_served_event(ev):
+    # the served stream's occupancy mix (lognormal, median 1.5%, clipped to
+    # [0.5%, 5%]) on the same detector and calibration
+    e = eg.make_event(eg.WORKLOADS[4], _W_CALIB, ev)
+    return e.raw, e.fed_len
+
+
 def _oracle_event(args):
     raw, fed_len = args
     import oracle as orc
@@ -87,6 +94,58 @@ def time_oracle(pool, cores, events, n_sample):
     wall = time.perf_counter() - t0
     cpu = sum(r[0] for r in res)
     return n_sample / wall, wall, cpu
+
+
+# ---------------------------------------------------------------- served stream
+
+def run_served(sst, ctx, events, n_feds, n_requests, rate):
+    """Submits n_requests events (cycling over `events`) with Poisson arrivals at
+    `rate` events/s (0 = as fast as possible) from one thread while another polls
+    them in order.  Returns throughput and latency percentiles (submit to done,
+    host clock, microseconds)."""
+    import threading
+    rng = np.random.default_rng(12345)
+    gaps = rng.exponential(1.0 / rate, n_requests) if rate > 0 else np.zeros(n_requests)
+    tickets = [None] * n_requests
+    ready = threading.Semaphore(0)
+    lat, done_t = [], []
+    retries = [0]
+
+    def submitter():
+        t = time.perf_counter()
+        for i in range(n_requests):
+            t += gaps[i]
+            while rate > 0 and time.perf_counter() < t:
+                pass
+            raw, fl = events[i % len(events)]
+            while True:
+                code, tk = sst.sst_submit(ctx, raw, fl)
+                if code == sst.SST_OK:
+                    break
+                retries[0] += 1
+                time.sleep(20e-6)
+            tickets[i] = tk
+            ready.release()
+
+    def poller():
+        for i in range(n_requests):
+            ready.acquire()
+            code, info, _ = sst.sst_poll(ctx, tickets[i], -1, 0)
+            assert code == sst.SST_OK
+            lat.append(info.t_done_us - info.t_submit_us)
+            done_t.append(time.perf_counter())
+
+    t0 = time.perf_counter()
+    th = [threading.Thread(target=submitter), threading.Thread(target=poller)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    wall = max(done_t) - t0
+    lat = np.array(lat)
+    return {"offered_rate": round(rate, 1) if rate > 0 else "saturating", "events": n_requests,
+            "throughput": round(n_requests / wall, 1), "p50_us": round(float(np.percentile(lat, 50)), 1),
+            "p99_us": round(float(np.percentile(lat, 99)), 1), "submit_retries": retries[0]}
 
 
 # ---------------------------------------------------------------- clocks
@@ -151,10 +210,17 @@ def kernel_traffic():
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    src = open(os.path.join(ROOT, "paper_2101_11489_gb300", "csrc", "sst_kernels.cu"), "rb").read()
-    if hashlib.sha256(src).hexdigest() != d.get("kernel_source_sha256"):
+    if kernel_source_sha256() != d.get("kernel_source_sha256"):
         return None
     return d
+
+
+def kernel_source_sha256():
+    """SHA-256 over the sources the batched kernel is compiled from, in this order."""
+    h = hashlib.sha256()
+    for f in ("sst_kernels.cu", "sst_fe.cuh", "sst_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2101_11489_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
 
 
 def algorithmic_bytes(events, n_digi, n_clusters):
@@ -178,6 +244,7 @@ def main():
     ap.add_argument("--workload", default="batch64", choices=sorted(WORKLOADS))
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--served-events", type=int, default=10000, help="events per served-stream point (0: skip)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     wid, n_events = WORKLOADS[args.workload]
@@ -194,6 +261,8 @@ def main():
     base_event = rank * n_events
     gen = pool.map(_gen_event, [(wid, base_event + i) for i in range(n_events)], chunksize=1)
     events = [(r, f) for r, f, _ in gen]
+    served_pool = pool.map(_gen_served_event, range(base_event, base_event + 64), chunksize=1) \
+        if args.served_events > 0 and wid == 2 else []
     calib = eg.make_calibration(w.n_feds, w.seed, w.p_bad)
 
     import torch
@@ -342,6 +411,22 @@ def main():
         e2e_s = float(t[0])
     h2d_bytes = raw_h.nbytes + fl_h.nbytes + eoff.nbytes
 
+    # ---- served stream: continuous batching behind sst_submit / sst_poll
+    served = None
+    if served_pool:
+        sst.sst_server_start(ctx, 8 << 30, 64, 3, 4096, w.n_feds)
+        try:
+            run_served(sst, ctx, served_pool, w.n_feds, 500, 0.0)  # warm-up
+            cap = run_served(sst, ctx, served_pool, w.n_feds, args.served_events, 0.0)
+            pts = [run_served(sst, ctx, served_pool, w.n_feds, args.served_events, f * cap["throughput"])
+                   for f in (0.5, 0.9)]
+            served = {"workload": "served-440fed-lognormal: occupancy lognormal median 1.5%, clip [0.5%, 5%], "
+                                  "64 distinct events cycled, Poisson arrivals, one Python submitter thread",
+                      "budget_bytes": 8 << 30, "max_batch_events": 64, "max_inflight": 3,
+                      "saturation": cap, "points": pts}
+        finally:
+            sst.sst_server_stop(ctx)
+
     # ---- roofline of the dominant kernel (the batched kernel)
     peak, peak_kind = measured_peaks()
     b_alg = algorithmic_bytes(events, n_digi, n_clu)
@@ -394,6 +479,7 @@ def main():
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "kernel": "k_batch", "kernels_per_step": 4, "kernel_ms": round(k_ms, 4), "algorithmic_bytes": int(b_alg),
                          "peak_kind": peak_kind},
+            "served": served,
             "cpu_baseline": cpu,
             "clocks": clk,
             "wall_s_timed_region": round(t_wall, 4),
