@@ -13,8 +13,8 @@ strips.  --workload batch256 selects 256 events at 5% occupancy, widths 1-12,
 
 Prints one JSON line (rank 0).  `value` is events/s of the batched path (device
 time, CUDA events, L2 flushed between steps); `e2e` is the same through the C ABI
-with host-resident events (pinned H2D of the raw bytes, D2H of statuses and
-clusters inside the timed region).  `per_event` times the plain per-event launches
+call for host-resident events, sst_batch_host (pinned H2D of the raw bytes, D2H of
+statuses and clusters inside the timed region, overlapped over chunks of events).  `per_event` times the plain per-event launches
 (sst_unpack + sst_cluster) on the same events.  --impl reference times the CPU
 oracle on the host cores instead.
 
@@ -370,36 +370,27 @@ def main():
         pe_ms.append(a.elapsed_time(b))
     pe_value = n_events / (statistics.median(pe_ms) / 1e3)
 
-    # ---- end to end through the C ABI with host-resident events
-    raw_pin = torch.from_numpy(raw_h).pin_memory()
-    fl_pin = torch.from_numpy(fl_h.view(np.int32)).pin_memory()
-    eoff_pin = torch.from_numpy(eoff).pin_memory()
-    st_pin = torch.zeros(n_events * 4, dtype=torch.int32).pin_memory()
-    out_pin = {k: torch.empty(int(coff[-1]), dtype=getattr(cb, k).dtype).pin_memory()
-               for k in ("det", "first", "width", "charge", "barycenter")}
+    # ---- end to end through the C ABI with host-resident events (sst_batch_host:
+    # H2D of every step's events, the kernels, D2H of every cluster and status,
+    # chunks of events overlapped on the library's streams)
+    keep = [torch.from_numpy(a).pin_memory() for a in (raw_h, eoff.view(np.int64), fl_h.view(np.int32))]
+    raw_pin, eoff_pin, fl_pin = keep[0].numpy(), keep[1].numpy().view(np.uint64), keep[2].numpy().view(np.uint32)
+    host_out = sst.HostClusters.alloc(int(coff[-1]), pinned=True)
+    keep += [torch.zeros(n_events + 1, dtype=torch.int64).pin_memory(),
+             torch.zeros(n_events * 4, dtype=torch.int32).pin_memory()]
+    ev_first = keep[3].numpy().view(np.uint64)
+    st_host = keep[4].numpy().view(np.uint32).reshape(n_events, 4)
 
     def e2e_step():
-        raw.copy_(raw_pin, non_blocking=True)
-        fl_d.copy_(fl_pin, non_blocking=True)
-        eoff_d.copy_(eoff_pin, non_blocking=True)
-        step()
-        st_pin.copy_(st_d, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        nc = st_pin.numpy().view(np.uint32).reshape(n_events, 4)[:, 1]
-        d2h = st_pin.numel() * 4
-        for e in range(n_events):
-            a, n = int(coff[e]), int(min(nc[e], caps[e]))
-            for k, dst in out_pin.items():
-                dst[a:a + n].copy_(getattr(cb, k)[a:a + n], non_blocking=True)
-                d2h += n * dst.element_size()
-        torch.cuda.current_stream().synchronize()
-        return d2h
+        sst.sst_batch_host(ctx, raw_pin, eoff_pin, fl_pin, n_events, w.n_feds, host_out, ev_first, st_host)
+        return 16 * int(ev_first[-1]) + st_host.nbytes + ev_first.nbytes
 
     e2e_step()
+    assert np.array_equal(st_host, st_h), "sst_batch_host statuses differ from sst_batch"
     barrier()
     t0 = time.perf_counter()
     d2h_total = 0
-    e2e_steps = max(3, min(args.steps, 100))
+    e2e_steps = max(3, min(args.steps, 200))
     for i in range(e2e_steps):
         d2h_total += e2e_step()
     barrier()
@@ -409,7 +400,7 @@ def main():
         t = torch.tensor([e2e_s], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t[0])
-    h2d_bytes = raw_h.nbytes + fl_h.nbytes + eoff.nbytes
+    h2d_bytes = raw_h.nbytes + fl_h.nbytes + 2 * eoff.nbytes  # raw, FED lengths, event and cluster offsets
 
     # ---- served stream: continuous batching behind sst_submit / sst_poll
     served = None
@@ -473,7 +464,7 @@ def main():
             "batched_over_per_event": round((total_events / (ms_per_step / 1e3)) / (pe_value * world), 2),
             "e2e": {"value": round(total_events / e2e_s, 1), "unit": "events/s",
                     "h2d_bytes_per_step": int(h2d_bytes), "d2h_bytes_per_step": int(d2h_total / e2e_steps),
-                    "steps": e2e_steps},
+                    "steps": e2e_steps, "api": "sst_batch_host, pinned host buffers"},
             "gpu_launches": 4 * args.steps,
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,

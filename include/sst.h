@@ -247,12 +247,42 @@ sst_status sst_batch(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off
                      uint32_t n_events, uint32_t n_feds, const uint64_t* clu_off, const sst_clusters* out,
                      sst_event_status* status, void* stream);
 
+/* The batched path for events in HOST memory (section 3: transfers overlapped
+ * with computation on CUDA streams).  Same computation as sst_batch, but every
+ * pointer is host memory and the call is synchronous: it returns when all
+ * results are in the caller's arrays.  The batch is cut into chunks of
+ * consecutive events; the host->device copy, the kernels and the device->host
+ * copy of successive chunks overlap on three streams of the context.
+ *   raw, event_off, fed_len  as for sst_batch, in host memory; event_off need
+ *              not start at 0 (only [event_off[0], event_off[n_events]) is read)
+ *   out        host arrays of out->capacity records; the events' clusters are
+ *              stored back to back in event order, each event's sorted as in
+ *              sst_batch
+ *   event_first [n_events + 1] uint64, written: event e's clusters are records
+ *              [event_first[e], event_first[e] + status[e].n_clusters);
+ *              event_first[n_events] = records stored
+ *   status     [n_events], written (host)
+ * Clusters beyond out->capacity are not stored: the events cut set
+ * SST_EV_CLUSTER_CAPACITY and their n_clusters counts what was stored.
+ * Pinned host memory (cudaHostAlloc, cudaHostRegister) gives full copy speed;
+ * pageable memory works, with copies staged by the CUDA driver.  Device arenas
+ * grow on demand (cudaMalloc only when a call needs more than any call before it
+ * on the context) and are freed by sst_destroy.  A context runs one
+ * sst_batch_host call at a time (calls from several threads are serialised).
+ * Errors: INVALID_ARG (null pointer, n_events == 0, n_feds outside 1..context
+ * FEDs, decreasing event_off), NO_CALIB, CUDA. */
+sst_status sst_batch_host(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len,
+                          uint32_t n_events, uint32_t n_feds, const sst_clusters* out, uint64_t* event_first,
+                          sst_event_status* status);
+
 /* Launch-shape knobs of the batched kernel (picked by sst_autotune). */
 typedef struct {
   uint32_t block;       /* threads per CTA: 128 or 256 */
   uint32_t ctas_per_sm; /* persistent CTAs per SM: 1..8 (clamped to what fits) */
   uint32_t tile_digis;  /* digis per on-chip tile: 1024, 2048 or 4096 */
   uint32_t lanes_per_channel; /* lanes that copy one channel's runs: 1, 2, 4, 8, 16 or 32 */
+  uint32_t host_chunk_events; /* events per pipeline chunk of sst_batch_host, 0..4096;
+                                 0 = automatic (a quarter of the batch, at most 32) */
 } sst_tune;
 
 sst_status sst_set_tune(sst_ctx* ctx, const sst_tune* t);

@@ -77,7 +77,7 @@ class sst_clusters(ctypes.Structure):
 
 class sst_tune(ctypes.Structure):
     _fields_ = [("block", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("tile_digis", ctypes.c_uint32),
-                ("lanes_per_channel", ctypes.c_uint32)]
+                ("lanes_per_channel", ctypes.c_uint32), ("host_chunk_events", ctypes.c_uint32)]
 
 
 class sst_server_opts(ctypes.Structure):
@@ -111,6 +111,7 @@ def load_library():
         "sst_unpack_noalloc": ([vp, u64, vp, u32, P(sst_digis), vp], i32),
         "sst_cluster": ([vp, P(sst_digis), u32, P(sst_clusters), vp], i32),
         "sst_batch": ([vp, vp, vp, vp, u32, u32, vp, P(sst_clusters), vp, vp], i32),
+        "sst_batch_host": ([vp, vp, vp, vp, u32, u32, P(sst_clusters), vp, vp], i32),
         "sst_set_tune": ([vp, P(sst_tune)], i32),
         "sst_get_tune": ([vp, P(sst_tune)], i32),
         "sst_autotune": ([vp, vp, vp, vp, u32, u32, vp, P(sst_clusters), vp, vp, P(sst_tune), P(ctypes.c_float)], i32),
@@ -132,7 +133,7 @@ def load_library():
 def exported_symbols() -> list[str]:
     return ["sst_create", "sst_destroy", "sst_last_error", "sst_calib_upload", "sst_unpack", "sst_unpack_noalloc",
             "sst_cluster",
-            "sst_batch", "sst_set_tune", "sst_get_tune", "sst_autotune", "sst_profile_enable", "sst_profile_read",
+            "sst_batch", "sst_batch_host", "sst_set_tune", "sst_get_tune", "sst_autotune", "sst_profile_enable", "sst_profile_read",
             "sst_server_start", "sst_server_stop",
             "sst_submit", "sst_poll"]
 
@@ -220,8 +221,24 @@ def sst_batch(ctx: int, raw, event_off, fed_len, n_events: int, n_feds: int, clu
     _check(ctx, code, "sst_batch")
 
 
-def sst_set_tune(ctx: int, block: int, ctas_per_sm: int, tile_digis: int, lanes_per_channel: int) -> None:
-    t = sst_tune(block, ctas_per_sm, tile_digis, lanes_per_channel)
+def sst_batch_host(ctx: int, raw: np.ndarray, event_off: np.ndarray, fed_len: np.ndarray, n_events: int,
+                   n_feds: int, out: "HostClusters", event_first: np.ndarray, status: np.ndarray) -> None:
+    """Host-memory batch: raw (uint8), event_off (uint64, n_events + 1), fed_len
+    (uint32, n_events x n_feds) are read; out, event_first (uint64, n_events + 1)
+    and status (uint32, n_events x 4) are written.  Synchronous."""
+    for a, dt in ((raw, np.uint8), (event_off, np.uint64), (fed_len, np.uint32), (event_first, np.uint64),
+                  (status, np.uint32)):
+        assert a.dtype == dt and a.flags["C_CONTIGUOUS"], "sst_batch_host: wrong dtype or layout"
+    assert event_off.size >= n_events + 1 and event_first.size >= n_events + 1 and status.size >= 4 * n_events
+    assert fed_len.size >= n_events * n_feds and raw.size >= int(event_off[n_events])
+    code = load_library().sst_batch_host(ctx, _hp(raw), _hp(event_off), _hp(fed_len), n_events, n_feds,
+                                         ctypes.byref(out.record()), _hp(event_first), _hp(status))
+    _check(ctx, code, "sst_batch_host")
+
+
+def sst_set_tune(ctx: int, block: int, ctas_per_sm: int, tile_digis: int, lanes_per_channel: int,
+                 host_chunk_events: int = 0) -> None:
+    t = sst_tune(block, ctas_per_sm, tile_digis, lanes_per_channel, host_chunk_events)
     _check(ctx, load_library().sst_set_tune(ctx, ctypes.byref(t)), "sst_set_tune")
 
 
@@ -229,7 +246,7 @@ def sst_get_tune(ctx: int) -> dict:
     t = sst_tune()
     _check(ctx, load_library().sst_get_tune(ctx, ctypes.byref(t)), "sst_get_tune")
     return {"block": t.block, "ctas_per_sm": t.ctas_per_sm, "tile_digis": t.tile_digis,
-            "lanes_per_channel": t.lanes_per_channel}
+            "lanes_per_channel": t.lanes_per_channel, "host_chunk_events": t.host_chunk_events}
 
 
 def sst_autotune(ctx: int, raw, event_off, fed_len, n_events: int, n_feds: int, clu_off, clusters: sst_clusters,
@@ -241,7 +258,7 @@ def sst_autotune(ctx: int, raw, event_off, fed_len, n_events: int, n_feds: int, 
                                        ctypes.byref(t), ctypes.byref(us))
     _check(ctx, code, "sst_autotune")
     return {"block": t.block, "ctas_per_sm": t.ctas_per_sm, "tile_digis": t.tile_digis,
-            "lanes_per_channel": t.lanes_per_channel}, us.value
+            "lanes_per_channel": t.lanes_per_channel, "host_chunk_events": t.host_chunk_events}, us.value
 
 
 def sst_profile_enable(ctx: int, enable: bool = True) -> None:
@@ -357,6 +374,34 @@ class ClusterBuffers:
                 "width": self.width[start:end].cpu().numpy().view(np.uint16).copy(),
                 "charge": self.charge[start:end].cpu().numpy().view(np.uint32).copy(),
                 "barycenter": self.barycenter[start:end].cpu().numpy().copy()}
+
+
+@dataclass
+class HostClusters:
+    """Host arrays behind an sst_clusters record, optionally in pinned memory."""
+    det: np.ndarray
+    first: np.ndarray
+    width: np.ndarray
+    charge: np.ndarray
+    barycenter: np.ndarray
+    _keep: object = None  # pinned tensors that own the memory
+
+    @classmethod
+    def alloc(cls, capacity: int, pinned: bool = False):
+        c = max(capacity, 1)
+        dts = (np.uint32, np.uint16, np.uint16, np.uint32, np.float32)
+        if not pinned:
+            return cls(*[np.zeros(c, d) for d in dts])
+        import torch
+        ts = [torch.empty(c * np.dtype(d).itemsize, dtype=torch.uint8, pin_memory=True) for d in dts]
+        return cls(*[t.numpy().view(d) for t, d in zip(ts, dts)], _keep=ts)
+
+    def record(self) -> sst_clusters:
+        return sst_clusters(_hp(self.det), _hp(self.first), _hp(self.width), _hp(self.charge), _hp(self.barycenter),
+                            self.det.size)
+
+    def view(self, start: int, n: int) -> dict:
+        return {k: getattr(self, k)[start:start + n] for k in ("det", "first", "width", "charge", "barycenter")}
 
 
 def params(t_channel=2.0, t_seed=3.0, t_cluster=5.0, max_seq_holes=0, max_seq_bad=1, max_adj_bad=0) -> sst_params:

@@ -94,20 +94,6 @@ static bool params_ok(const sst_params* p) {
 
 using namespace sst;
 
-namespace {
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-}  // namespace
-
 extern "C" {
 
 sst_status sst_create(sst_ctx** out, int device, uint32_t n_feds) {
@@ -139,6 +125,7 @@ sst_status sst_destroy(sst_ctx* ctx) {
   if (ctx->server) sst_server_stop(ctx);
   DeviceGuard g(ctx->device);
   cudaDeviceSynchronize();
+  free_host_pipe(ctx);
   for (auto& pr : ctx->prof_events) ctx->prof_free.push_back(pr);
   for (auto& pr : ctx->prof_free) {
     cudaEventDestroy(pr.first);
@@ -258,7 +245,7 @@ sst_status sst_batch(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off
     }
   }
   e = launch_batch(raw, event_off, fed_len, n_events, n_feds, clu_off, *out, status, kparams(ctx), ctx->scratch,
-                   ctx->shape, ctx->n_sm, (cudaStream_t)stream, eb, ee);
+                   ctx->shape, ctx->n_sm, (cudaStream_t)stream, nullptr, eb, ee);
   if (eb) {
     if (e == cudaSuccess)
       ctx->prof_events.emplace_back(eb, ee);
@@ -296,7 +283,9 @@ sst_status sst_profile_read(sst_ctx* ctx, uint64_t* launches, double* total_ms, 
 
 sst_status sst_set_tune(sst_ctx* ctx, const sst_tune* t) {
   if (!ctx || !t) return SST_ERR_INVALID_ARG;
-  Shape s{(int)t->block, (int)t->tile_digis, (int)t->lanes_per_channel, (int)t->ctas_per_sm};
+  if (t->host_chunk_events > 4096u) return set_err(ctx, SST_ERR_INVALID_ARG, "sst_set_tune: host_chunk_events > 4096");
+  Shape s{(int)t->block, (int)t->tile_digis, (int)t->lanes_per_channel, (int)t->ctas_per_sm,
+          (int)t->host_chunk_events};
   if (!shape_valid(s)) return set_err(ctx, SST_ERR_INVALID_ARG, "sst_set_tune: unsupported launch shape");
   ctx->shape = s;
   return SST_OK;
@@ -308,6 +297,7 @@ sst_status sst_get_tune(const sst_ctx* ctx, sst_tune* t) {
   t->tile_digis = (uint32_t)ctx->shape.tile;
   t->lanes_per_channel = (uint32_t)ctx->shape.lanes;
   t->ctas_per_sm = (uint32_t)ctx->shape.ctas_per_sm;
+  t->host_chunk_events = (uint32_t)ctx->shape.host_chunk;
   return SST_OK;
 }
 
@@ -338,7 +328,7 @@ sst_status sst_autotune(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_
     for (int t : tiles)
       for (int l : lanes)
         for (int p : per_sm) {
-          Shape s{b, t, l, p};
+          Shape s{b, t, l, p, ctx->shape.host_chunk};
           if (!shape_valid(s) || smem_bytes(t) * (size_t)p > 227u * 1024u) continue;
           ctx->shape = s;
           float ms_total = 0.f;

@@ -37,6 +37,7 @@ struct Shape {
   int tile;         // digis per on-chip tile
   int lanes;        // lanes per channel when copying runs
   int ctas_per_sm;  // persistent CTAs per SM (batched kernel)
+  int host_chunk = 0;  // events per chunk of sst_batch_host (0: automatic)
 };
 
 // Device scratch for one stream of work, owned by a context (or by one server
@@ -65,20 +66,24 @@ cudaError_t launch_unpack(const uint8_t* raw, uint64_t raw_bytes, const uint32_t
                           const sst_digis& out, const Scratch& s, const Shape& sh, cudaStream_t st);
 cudaError_t launch_cluster(const sst_digis& in, uint32_t n_feds, const sst_clusters& out, const KParams& kp,
                            const Scratch& s, const Shape& sh, cudaStream_t st);
-// Kernels launched per batch step (for launch counting): scan, batch, cluster scan, compaction.
+// Kernels launched per batch step (for launch counting): scan, batch, cluster scan, compaction
+// (one more, the event scan, in packed mode).
 constexpr int kBatchKernels = 4;
+// Batched unpack + cluster.  Event e's clusters are staged in, and by default
+// written to, the slice [clu_off[e], clu_off[e+1]) of `out` (bounded by
+// out.capacity).  With pack_off (device, n_events + 1 values) the events' clusters
+// are written back to back instead, event e from pack_off[e], which the launch
+// computes.
 cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len, uint32_t n_events,
                          uint32_t n_feds, const uint64_t* clu_off, const sst_clusters& out, sst_event_status* status,
                          const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st,
-                         cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
+                         uint64_t* pack_off = nullptr, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st);
-// Served path: packs each event's clusters back to back; pack_off[n_events + 1].
-cudaError_t launch_pack(const uint64_t* clu_off, const sst_event_status* status, uint32_t n_events,
-                        const sst_clusters& in, const sst_clusters& out, uint64_t* pack_off, cudaStream_t st);
 
 }  // namespace sst
 
 struct sst_server;
+struct sst_host_pipe;
 
 struct sst_ctx {
   int device = 0;
@@ -94,6 +99,7 @@ struct sst_ctx {
   std::string err;
   std::mutex mu;
   sst_server* server = nullptr;
+  sst_host_pipe* pipe = nullptr;  // streams and arenas of sst_batch_host, made on first use
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;  // recorded launches
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_free;    // reusable pairs
@@ -105,4 +111,18 @@ sst_status cuda_err(sst_ctx* c, cudaError_t e, const char* where);
 KParams kparams(const sst_ctx* c);
 cudaError_t ensure_scratch(Scratch& s, size_t items, size_t events, size_t stage_records);
 void free_scratch(Scratch& s);
+void free_host_pipe(sst_ctx* ctx);
+
+// Makes `dev` current for the guard's lifetime.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
 }  // namespace sst

@@ -509,8 +509,10 @@ __global__ void k_clu_scan(const uint32_t* __restrict__ fed_cnt, uint32_t n_feds
 
 // a6, output: copies every segment's staged clusters (one segment per FE unit)
 // to its place in the event's sorted cluster SoA, one warp per segment (16-byte
-// loads, coalesced stores).
+// loads, coalesced stores).  The event's clusters start at clu_off[e] (its slice),
+// or at pack_off[e] when pack_off is given (events packed back to back).
 __global__ void __launch_bounds__(256) k_compact(const uint4* __restrict__ stage, const uint64_t* __restrict__ clu_off,
+                                                 const uint64_t* __restrict__ pack_off,
                                                  const uint32_t* __restrict__ seg_cnt,
                                                  const uint32_t* __restrict__ seg_start,
                                                  const uint32_t* __restrict__ seg_dest, uint32_t n_events,
@@ -523,7 +525,7 @@ __global__ void __launch_bounds__(256) k_compact(const uint4* __restrict__ stage
   const uint32_t e = (uint32_t)(it / n_segs);
   const uint64_t off = clu_off ? clu_off[e] : 0;
   const uint4* src = stage + off + seg_start[it];
-  const uint64_t dst = off + seg_dest[it];
+  const uint64_t dst = (pack_off ? pack_off[e] : off) + seg_dest[it];
   for (uint32_t k = threadIdx.x & 31; k < n; k += 32) {
     const uint4 r = __ldg(src + k);
     const uint64_t o = dst + k;
@@ -712,12 +714,11 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
   }
 }
 
-// Served path: packs the clusters of every event of a batch back to back
-// (event order) so that the host reads them with one copy per array.  One CTA:
-// pack_off[e] = sum of the events' cluster counts before e (n_events + 1 values).
-__global__ void __launch_bounds__(1024) k_pack(const uint64_t* __restrict__ clu_off,
-                                               const sst_event_status* __restrict__ status, uint32_t n_events,
-                                               sst_clusters in, sst_clusters out, uint64_t* pack_off) {
+// Packed output: pack_off[e] = sum of the cluster counts of the events before e
+// (n_events + 1 values), so that k_compact can write the events back to back.
+// One CTA.
+__global__ void __launch_bounds__(1024) k_pack_scan(const sst_event_status* __restrict__ status, uint32_t n_events,
+                                                    uint64_t* pack_off) {
   __shared__ uint32_t wsum[32];
   __shared__ uint64_t carry_s;
   if (threadIdx.x == 0) carry_s = 0;
@@ -734,20 +735,6 @@ __global__ void __launch_bounds__(1024) k_pack(const uint64_t* __restrict__ clu_
     __syncthreads();
   }
   if (threadIdx.x == 0) pack_off[n_events] = carry_s;
-  __syncthreads();
-  // copy, one warp per event
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (uint32_t e = warp; e < n_events; e += nw) {
-    const uint32_t n = status[e].n_clusters;
-    const uint64_t a = clu_off[e], d = pack_off[e];
-    for (uint32_t k = lane; k < n; k += 32) {
-      out.det[d + k] = in.det[a + k];
-      out.first[d + k] = in.first[a + k];
-      out.width[d + k] = in.width[a + k];
-      out.charge[d + k] = in.charge[a + k];
-      out.barycenter[d + k] = in.barycenter[a + k];
-    }
-  }
 }
 
 __global__ void k_badmask(const uint8_t* __restrict__ bad, uint32_t* __restrict__ mask, uint64_t n_words) {
@@ -760,12 +747,60 @@ __global__ void k_badmask(const uint8_t* __restrict__ bad, uint32_t* __restrict_
 
 // ---------------------------------------------------------------- launch helpers
 
+// Raises a kernel's dynamic shared memory limit to what a launch needs and
+// returns its CTAs per SM.  The limit only grows (per device and kernel), and the
+// occupancy is looked up once per device, kernel, block size and shared memory
+// size, so that repeated launches make no driver calls for either.
+struct Prep {
+  int dev;
+  const void* fn;
+  int block;
+  size_t smem;
+  int per_sm;
+};
+struct Limit {
+  int dev;
+  const void* fn;
+  size_t smem;
+};
+std::mutex g_prep_mu;
+std::vector<Prep> g_prep;
+std::vector<Limit> g_limit;
+
+cudaError_t prepare(const void* fn, int block, size_t smem, int* per_sm) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return e;
+  std::lock_guard<std::mutex> lock(g_prep_mu);
+  Limit* lim = nullptr;
+  for (Limit& l : g_limit)
+    if (l.dev == dev && l.fn == fn) lim = &l;
+  if (!lim) {
+    g_limit.push_back(Limit{dev, fn, 0});
+    lim = &g_limit.back();
+  }
+  if (smem > lim->smem) {
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    lim->smem = smem;
+  }
+  for (const Prep& p : g_prep)
+    if (p.dev == dev && p.fn == fn && p.block == block && p.smem == smem) {
+      *per_sm = p.per_sm;
+      return cudaSuccess;
+    }
+  int n = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem))) return e;
+  g_prep.push_back(Prep{dev, fn, block, smem, n});
+  *per_sm = n;
+  return cudaSuccess;
+}
+
 template <int TILE>
 cudaError_t launch_unpack_t(const uint8_t* raw, const uint32_t* fed_len, uint32_t n_feds, const sst_digis& out,
                             const Scratch& s, const Shape& sh, cudaStream_t st) {
   const size_t sm = sizeof(Shm<TILE>);
-  cudaError_t e = cudaFuncSetAttribute((const void*)k_unpack<TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
+  int per_sm = 0;
+  cudaError_t e = prepare((const void*)k_unpack<TILE>, sh.block, sm, &per_sm);
   if (e) return e;
   k_unpack<TILE><<<n_feds, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_feds, out, s.lb, s.tickets, sh.lanes);
   return cudaGetLastError();
@@ -775,7 +810,8 @@ cudaError_t launch_cluster_fe(const sst_digis& in, uint32_t n_feds, const KParam
                               uint64_t cap, const Shape& sh, cudaStream_t st) {
   const int nw = sh.block / 32;
   const size_t sm = sizeof(fe::Warp) * nw;
-  cudaError_t e = cudaFuncSetAttribute((const void*)k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int per_sm = 0;
+  cudaError_t e = prepare((const void*)k_cluster, sh.block, sm, &per_sm);
   if (e) return e;
   const uint32_t units = n_feds * kFe;
   k_cluster<<<(units + nw - 1) / nw, sh.block, sm, st>>>(in, n_feds, kp, s.stage, cap, s.ev_alloc, s.fed_cnt,
@@ -790,10 +826,9 @@ cudaError_t launch_batch_fe(const uint8_t* raw, const uint32_t* fed_len, uint32_
   const int nw = sh.block / 32;
   const size_t sm = sizeof(fe::Warp) * nw;
   const size_t units = (size_t)n_events * n_feds * kFe;
-  cudaError_t e = cudaFuncSetAttribute((const void*)k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e) return e;
   int per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, sh.block, sm))) return e;
+  cudaError_t e = prepare((const void*)k_batch, sh.block, sm, &per_sm);
+  if (e) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const size_t ctas = (size_t)n_sm * (sh.ctas_per_sm < per_sm ? sh.ctas_per_sm : per_sm);
   const size_t need = (units + nw - 1) / nw;
@@ -808,13 +843,17 @@ cudaError_t launch_batch_fe(const uint8_t* raw, const uint32_t* fed_len, uint32_
 
 // Per-event cluster order and the copy into the caller's SoA.
 cudaError_t launch_order(const uint64_t* clu_off, uint32_t n_events, uint32_t n_segs, const sst_clusters& out,
-                         sst_event_status* status, const Scratch& s, cudaStream_t st) {
+                         sst_event_status* status, const Scratch& s, uint64_t* pack_off, cudaStream_t st) {
   k_clu_scan<<<n_events, 256, 0, st>>>(s.fed_cnt, n_segs, s.fed_dest, status);
   cudaError_t e = cudaGetLastError();
   if (e) return e;
+  if (pack_off) {
+    k_pack_scan<<<1, 1024, 0, st>>>(status, n_events, pack_off);
+    if ((e = cudaGetLastError())) return e;
+  }
   const uint64_t items = (uint64_t)n_events * n_segs;
-  k_compact<<<(unsigned)((items + 7) / 8), 256, 0, st>>>(s.stage, clu_off, s.fed_cnt, s.fed_start, s.fed_dest,
-                                                        n_events, n_segs, out);
+  k_compact<<<(unsigned)((items + 7) / 8), 256, 0, st>>>(s.stage, clu_off, pack_off, s.fed_cnt, s.fed_start,
+                                                        s.fed_dest, n_events, n_segs, out);
   return cudaGetLastError();
 }
 
@@ -837,7 +876,7 @@ bool shape_valid(const Shape& s) {
   const bool blk = s.block == 128 || s.block == 256;
   const bool til = s.tile == 1024 || s.tile == 2048 || s.tile == 4096;
   const bool ln = s.lanes == 1 || s.lanes == 2 || s.lanes == 4 || s.lanes == 8 || s.lanes == 16 || s.lanes == 32;
-  return blk && til && ln && s.ctas_per_sm >= 1 && s.ctas_per_sm <= 8;
+  return blk && til && ln && s.ctas_per_sm >= 1 && s.ctas_per_sm <= 8 && s.host_chunk >= 0 && s.host_chunk <= 4096;
 }
 
 cudaError_t launch_unpack(const uint8_t* raw, uint64_t raw_bytes, const uint32_t* fed_len, uint32_t n_feds,
@@ -860,13 +899,13 @@ cudaError_t launch_cluster(const sst_digis& in, uint32_t n_feds, const sst_clust
   cudaError_t e;
   if ((e = cudaMemsetAsync(s.ev_alloc, 0, sizeof(uint32_t), st))) return e;
   if ((e = launch_cluster_fe(in, n_feds, kp, s, out.capacity, sh, st))) return e;
-  return launch_order(nullptr, 1, n_feds * kFe, out, in.status, s, st);  // one event at offset 0
+  return launch_order(nullptr, 1, n_feds * kFe, out, in.status, s, nullptr, st);  // one event at offset 0
 }
 
 cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len, uint32_t n_events,
                          uint32_t n_feds, const uint64_t* clu_off, const sst_clusters& out, sst_event_status* status,
                          const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st,
-                         cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+                         uint64_t* pack_off, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(status, 0, sizeof(sst_event_status) * n_events, st))) return e;
   if ((e = cudaMemsetAsync(s.ev_alloc, 0, sizeof(uint32_t) * n_events, st))) return e;
@@ -875,13 +914,7 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
   e = launch_batch_fe(raw, fed_len, n_events, n_feds, clu_off, out.capacity, status, kp, s, sh, n_sm, st, ev_begin,
                       ev_end);
   if (e) return e;
-  return launch_order(clu_off, n_events, n_feds * kFe, out, status, s, st);
-}
-
-cudaError_t launch_pack(const uint64_t* clu_off, const sst_event_status* status, uint32_t n_events,
-                        const sst_clusters& in, const sst_clusters& out, uint64_t* pack_off, cudaStream_t st) {
-  k_pack<<<1, 1024, 0, st>>>(clu_off, status, n_events, in, out, pack_off);
-  return cudaGetLastError();
+  return launch_order(clu_off, n_events, n_feds * kFe, out, status, s, pack_off, st);
 }
 
 cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st) {

@@ -115,7 +115,7 @@ struct Slot {
   uint64_t* d_clu_off = nullptr;
   sst_event_status* d_status = nullptr;
   uint64_t* d_pack_off = nullptr;
-  sst_clusters d_out{}, d_pack{};  // per-event slices, then packed
+  sst_clusters d_out{};  // the batch's clusters, events back to back (d_pack_off)
   size_t clu_cap = 0;
   uint64_t* h_event_off = nullptr;
   uint32_t* h_fed_len = nullptr;
@@ -171,13 +171,11 @@ void free_slot(Slot& s) {
   cudaFree(s.d_clu_off);
   cudaFree(s.d_status);
   cudaFree(s.d_pack_off);
-  for (sst_clusters* c : {&s.d_out, &s.d_pack}) {
-    cudaFree(c->det);
-    cudaFree(c->first);
-    cudaFree(c->width);
-    cudaFree(c->charge);
-    cudaFree(c->barycenter);
-  }
+  cudaFree(s.d_out.det);
+  cudaFree(s.d_out.first);
+  cudaFree(s.d_out.width);
+  cudaFree(s.d_out.charge);
+  cudaFree(s.d_out.barycenter);
   cudaFreeHost(s.h_event_off);
   cudaFreeHost(s.h_fed_len);
   cudaFreeHost(s.h_clu_off);
@@ -229,8 +227,7 @@ cudaError_t init_slot(Slot& s, const sst_server_opts& o, size_t raw_cap, uint32_
   if ((e = dalloc(&s.d_event_off, E + 1)) || (e = dalloc(&s.d_fed_len, (size_t)E * n_feds)) ||
       (e = dalloc(&s.d_clu_off, E + 1)) || (e = dalloc(&s.d_status, E)) || (e = dalloc(&s.d_pack_off, E + 1)))
     return e;
-  if ((e = alloc_clusters(&s.d_out, s.clu_cap, false)) || (e = alloc_clusters(&s.d_pack, s.clu_cap, false)))
-    return e;
+  if ((e = alloc_clusters(&s.d_out, s.clu_cap, false))) return e;
   if ((e = halloc(&s.h_event_off, E + 1)) || (e = halloc(&s.h_fed_len, (size_t)E * n_feds)) ||
       (e = halloc(&s.h_clu_off, E + 1)) || (e = halloc(&s.h_status, E)) || (e = halloc(&s.h_pack_off, E + 1)))
     return e;
@@ -281,8 +278,7 @@ bool launch_on(sst_server* sv, int si) {
   sst_clusters out = s.d_out;
   out.capacity = s.clu_cap;
   if (!e) e = sst::launch_batch(s.d_raw, s.d_event_off, s.d_fed_len, E, nf, s.d_clu_off, out, s.d_status,
-                                sst::kparams(sv->ctx), s.scratch, sv->ctx->shape, sv->ctx->n_sm, s.st);
-  if (!e) e = sst::launch_pack(s.d_clu_off, s.d_status, E, s.d_out, s.d_pack, s.d_pack_off, s.st);
+                                sst::kparams(sv->ctx), s.scratch, sv->ctx->shape, sv->ctx->n_sm, s.st, s.d_pack_off);
   if (!e) e = cudaMemcpyAsync(s.h_status, s.d_status, E * sizeof(sst_event_status), cudaMemcpyDeviceToHost, s.st);
   if (!e) e = cudaMemcpyAsync(s.h_pack_off, s.d_pack_off, (E + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s.st);
   if (!e) e = cudaEventRecord(s.ev_status, s.st);
@@ -307,7 +303,7 @@ bool advance(sst_server* sv) {
       }
       s.res_off = off;
       s.res_total = total;
-      const sst_clusters& d = s.d_pack;
+      const sst_clusters& d = s.d_out;
       const HostClusters h = region_arrays(sv->res_pool + off, total);
       if (!e && total) {
         e = cudaMemcpyAsync(h.det, d.det, total * 4, cudaMemcpyDeviceToHost, s.st);
