@@ -50,55 +50,6 @@ struct Unit {
   uint8_t fed_status;      // SST_CH_FED_HDR when the FED record is corrupt or out of range, else 0
 };
 
-// Reads and checks the FED header (every unit of a FED checks it alike), locates
-// FE unit u and stages its bytes.  `g` is the FED record (len bytes) or null
-// when the record lies outside its event.
-__device__ Unit locate(Warp& w, const uint8_t* g, uint32_t len, uint32_t fed, uint32_t u, bool in_range) {
-  const int lane = threadIdx.x & 31;
-  Unit r{fed, u, nullptr, 0, 0};
-  const bool present = in_range && len > 0;
-  if (!in_range) r.fed_status = SST_CH_FED_HDR;
-  if (!present) return r;
-  if (len < (uint32_t)kHdr) {
-    r.fed_status = SST_CH_FED_HDR;
-    return r;
-  }
-  const uint32_t hb = __ldg(g + lane);  // the 32-byte header, one byte per lane
-  uint32_t fe_len[kFe];
-#pragma unroll
-  for (int v = 0; v < kFe; v++) fe_len[v] = u16_at(hb, 16 + 2 * v);
-  uint32_t body = 0, start = kHdr;
-#pragma unroll
-  for (int v = 0; v < kFe; v++) {
-    const uint32_t p = (fe_len[v] + 7u) & ~7u;
-    if ((uint32_t)v < u) start += p;
-    body += p;
-  }
-  const uint32_t total = (kHdr + body + 15u) & ~15u;
-  const bool ok = u32_at(hb, 0) == SST_FED_MAGIC && u16_at(hb, 4) == fed && byte_at(hb, 6) == (uint32_t)kCh &&
-                  byte_at(hb, 7) == (uint32_t)kFe && u32_at(hb, 8) == len && total == len;
-  if (!ok) {
-    r.fed_status = SST_CH_FED_HDR;
-    return r;
-  }
-  r.len = u16_at(hb, 16 + 2 * (int)u);  // shuffle, not a dynamically indexed local array
-  const uint8_t* a = g + start;
-  if (r.len <= (uint32_t)kBuf) {
-    if ((((uintptr_t)a) & 7u) == 0) {
-      const uint32_t nv = (r.len + 7u) >> 3;  // whole 8-byte words; padding bytes exist up to the next 8
-      for (uint32_t i = lane; i < nv; i += 32)
-        *reinterpret_cast<uint2*>(w.fe + 8 * i) = __ldg(reinterpret_cast<const uint2*>(a) + i);
-    } else {
-      for (uint32_t i = lane; i < r.len; i += 32) w.fe[i] = __ldg(a + i);
-    }
-    r.src = w.fe;
-  } else {
-    r.src = a;
-  }
-  __syncwarp();
-  return r;
-}
-
 // a1 + a2 for one FE unit: lane 0 walks the 12 channel lengths (the location
 // map); lanes 0..11 then validate their channel's runs and count its digis; the
 // counts are prefix-summed.  A broken length chain invalidates all 12 channels.
@@ -184,32 +135,59 @@ __device__ __forceinline__ int chunk_end(const Warp& w, int c0) {
   return c1;
 }
 
-// a2: copies the runs of channels [c0, c1) into the tile, one lane per channel
-// (the runs were validated by parse_unit; the copy stays within the counted digis).
+// a2: the digis of channels [c0, c1) into the tile, all lanes at once.  Lanes
+// c0 .. c1-1 walk their channel's runs (validated by parse_unit) and leave, at the
+// tile position of each run's first digi, a descriptor (byte position of its ADCs,
+// first strip, channel) and a run-start flag.  Then every lane takes one digi at a
+// time and finds its run as the last run start at or before it: the highest set
+// bit at or below the lane in the ballot of its 32-digi window, or the last run
+// start of the windows before.  Descriptors and flags live in nsq[] and flag[],
+// which flag_unit overwrites afterwards.
 __device__ void copy_runs(Warp& w, const Unit& un, int c0, int c1) {
   const int lane = threadIdx.x & 31;
+  uint32_t* desc = reinterpret_cast<uint32_t*>(w.nsq);
+  const int n = (int)(w.chan_cnt[c1] - w.chan_cnt[c0]);
+  uint32_t* fl32 = reinterpret_cast<uint32_t*>(w.flag);
+  for (int i = lane; i < (n + 3) / 4; i += 32) fl32[i] = 0;
+  __syncwarp();
   const int c = c0 + lane;
   if (c < c1) {
-    const uint32_t n = w.chan_cnt[c + 1] - w.chan_cnt[c];
-    const uint32_t o0 = w.chan_cnt[c] - w.chan_cnt[c0];
-    const uint8_t* r = un.src + w.chan_pos[c];
+    const uint32_t cnt = w.chan_cnt[c + 1] - w.chan_cnt[c];
+    uint32_t o = w.chan_cnt[c] - w.chan_cnt[c0];
+    const uint32_t pos = w.chan_pos[c];
+    const uint8_t* r = un.src + pos;
     const uint32_t len_c = w.chan_len[c];
-    uint32_t p = 3, o = 0;
-    while (p + 2 <= len_c && o < n) {
-      const uint32_t first = r[p];
-      uint32_t wd = r[p + 1];
-      if (wd > n - o) wd = n - o;
-      for (uint32_t k = 0; k < wd; k++) {
-        w.key[o0 + o + k] = (uint16_t)(((uint32_t)c << 8) | ((first + k) & 255u));
-        w.adc[o0 + o + k] = r[p + 2 + k];
+    uint32_t p = 3, left = cnt;
+    while (p + 2 <= len_c && left > 0) {
+      const uint32_t first = r[p], wd0 = r[p + 1];
+      const uint32_t wd = wd0 < left ? wd0 : left;
+      if (wd > 0) {
+        desc[o] = ((pos + p + 2) << 12) | (first << 4) | (uint32_t)c;
+        w.flag[o] = 1;
       }
       o += wd;
-      p += 2 + wd;
+      left -= wd;
+      p += 2 + wd0;
     }
   }
   __syncwarp();
+  int carry = 0;
+  for (int base = 0; base < n; base += 32) {
+    const int i = base + lane;
+    const uint32_t m = __ballot_sync(0xffffffffu, i < n && w.flag[i] != 0);
+    const uint32_t le = m & (lane == 31 ? 0xffffffffu : ((2u << lane) - 1u));
+    const int s = le ? base + 31 - __clz(le) : carry;
+    if (i < n) {
+      const uint32_t d = desc[s];
+      const uint32_t k = (uint32_t)(i - s);
+      w.key[i] = (uint16_t)(((d & 15u) << 8) | ((((d >> 4) & 255u) + k) & 255u));
+      const uint32_t b = (d >> 12) + k;
+      w.adc[i] = b < un.len ? un.src[b] : (uint8_t)0;
+    }
+    if (m) carry = base + 31 - __clz(m);
+  }
+  __syncwarp();
 }
-
 
 // a3 for the n digis of the tile, one lane per digi, two noise loads in flight:
 // the channel and seed thresholds (binary32 product threshold x noise, strict
@@ -336,11 +314,11 @@ __device__ __forceinline__ uint4 pack_cluster(uint32_t det, uint32_t first, uint
 // max_adj adjacent bad strips; the cluster threshold decides.  Returns the number
 // kept; when `stage` is given the kept clusters are written, in strip order, to
 // stage[base + rank] for base + rank < cap.
-__device__ uint32_t form_unit(Warp& w, const KParams& kp, int n, int n_own, uint32_t det0, uint4* stage,
-                              uint64_t cap, uint64_t base) {
+__device__ uint32_t form_unit(Warp& w, const KParams& kp, int n, int k_begin, int n_own, uint32_t det0, uint4* stage,
+                              uint64_t cap, uint64_t base, uint4* keep = nullptr, bool* keep_pass = nullptr) {
   const int lane = threadIdx.x & 31;
   uint32_t kept = 0;
-  for (int k0 = 0; k0 < n_own; k0 += 32) {
+  for (int k0 = k_begin; k0 < n_own; k0 += 32) {
     const int k = k0 + lane;
     bool pass = false;
     uint32_t c = 0, lo = 0, wd = 0, q_sum = 0;
@@ -374,13 +352,16 @@ __device__ uint32_t form_unit(Warp& w, const KParams& kp, int n, int n_own, uint
       for (int m = 0; m < kp.max_adj && hi + 1 < kStrips && bit(B, hi + 1); m++) hi++;
       lo = (uint32_t)lo_i;
       wd = (uint32_t)(hi - lo_i + 1);
-      if (pass && stage)
+      if (pass && (stage || keep))
         bary = q_sum == 0 ? __fadd_rn((float)lo_i, __fmul_rn(0.5f, (float)wd))
                           : __fadd_rn(__fadd_rn((float)lo_i, 0.5f),
                                       __fdiv_rn(__uint2float_rn(moment), __uint2float_rn(q_sum)));
     }
     const unsigned b = __ballot_sync(0xffffffffu, pass);
-    if (pass && stage) {
+    if (keep && k0 == k_begin) {
+      *keep = pack_cluster(det0 + c, lo, wd, q_sum, bary);
+      *keep_pass = pass;
+    } else if (pass && stage) {
       const uint64_t pos = base + kept + __popc(b & lanemask_lt(lane));
       if (pos < cap) stage[pos] = pack_cluster(det0 + c, lo, wd, q_sum, bary);
     }
@@ -408,8 +389,10 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uin
                              Fill& fill, const SegOut& so, sst_event_status* status) {
   const int lane = threadIdx.x & 31;
   const bool single = total <= (uint32_t)kTile;
-  uint32_t found = 0;
+  uint32_t found = 0, found0 = 0;
   int n = 0, n_own = 0;
+  uint4 rec0 = make_uint4(0u, 0u, 0u, 0u);  // this lane's record of the first 32 candidates
+  bool pass0 = false;
   if (single) {
     n = (int)total;
     if (n > 0) {
@@ -417,7 +400,11 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uin
       flag_unit(w, kp, noise, n);
       starts_unit(w, kp, n);
       n_own = owners_unit(w, n);
-      if (n_own > 0) found = form_unit(w, kp, n, n_own, det0, nullptr, 0, 0);
+      if (n_own > 0) {
+        found0 = form_unit(w, kp, n, 0, n_own < 32 ? n_own : 32, det0, nullptr, 0, 0, &rec0, &pass0);
+        found = found0;
+        if (n_own > 32) found += form_unit(w, kp, n, 32, n_own, det0, nullptr, 0, 0);
+      }
     }
   } else {
     for (int c0 = 0; c0 < kChPerFe;) {
@@ -428,7 +415,7 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uin
         flag_unit(w, kp, noise, nn);
         starts_unit(w, kp, nn);
         const int no = owners_unit(w, nn);
-        if (no > 0) found += form_unit(w, kp, nn, no, det0, nullptr, 0, 0);
+        if (no > 0) found += form_unit(w, kp, nn, 0, no, det0, nullptr, 0, 0);
       }
       c0 = c1;
     }
@@ -445,7 +432,12 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uin
   start = __shfl_sync(0xffffffffu, start, 0);
   if (found == 0) return;
   if (single) {
-    form_unit(w, kp, n, n_own, det0, so.stage, so.cap, start);
+    const unsigned b = __ballot_sync(0xffffffffu, pass0);
+    if (pass0) {
+      const uint64_t pos = (uint64_t)start + __popc(b & lanemask_lt(lane));
+      if (pos < so.cap) so.stage[pos] = rec0;
+    }
+    if (n_own > 32) form_unit(w, kp, n, 32, n_own, det0, so.stage, so.cap, (uint64_t)start + found0);
   } else {
     uint64_t base = start;
     for (int c0 = 0; c0 < kChPerFe;) {
@@ -456,19 +448,53 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uin
         flag_unit(w, kp, noise, nn);
         starts_unit(w, kp, nn);
         const int no = owners_unit(w, nn);
-        if (no > 0) base += form_unit(w, kp, nn, no, det0, so.stage, so.cap, base);
+        if (no > 0) base += form_unit(w, kp, nn, 0, no, det0, so.stage, so.cap, base);
       }
       c0 = c1;
     }
   }
 }
 
-// Loads the bad-strip masks and APV gains of channels ch0 .. ch0 + 11.
+// Loads the bad-strip masks (96 words) and APV gains (24 floats) of channels
+// ch0 .. ch0 + 11: one 16-byte load per lane (both tables start on a 16-byte
+// boundary: ch0 is a multiple of 12).
 __device__ __forceinline__ void load_calib(Warp& w, const KParams& kp, uint32_t ch0) {
   const int lane = threadIdx.x & 31;
-  const uint32_t* bm = kp.badmask + (size_t)ch0 * kMaskWords;
-  for (int i = lane; i < kChPerFe * kMaskWords; i += 32) w.bad[i] = __ldg(bm + i);
-  if (lane < kChPerFe * 2) w.gain[lane] = __ldg(kp.gain + (size_t)ch0 * 2 + lane);
+  if (lane < 24)
+    reinterpret_cast<uint4*>(w.bad)[lane] =
+        __ldg(reinterpret_cast<const uint4*>(kp.badmask + (size_t)ch0 * kMaskWords) + lane);
+  else if (lane < 30)
+    reinterpret_cast<uint4*>(w.gain)[lane - 24] =
+        __ldg(reinterpret_cast<const uint4*>(kp.gain + (size_t)ch0 * 2) + (lane - 24));
 }
+
+// FE unit u of FED `fed` as described by d (k_fed_scan checked the FED header and
+// wrote, per FE unit, its byte offset in the FED record, its length, the FED's
+// status and whether the record holds data).  The unit's bytes are staged in the
+// warp's buffer when they fit, else read in place.  g is the FED record.
+__device__ Unit locate(Warp& w, const uint8_t* g, uint2 d, uint32_t fed, uint32_t u) {
+  const int lane = threadIdx.x & 31;
+  Unit r{fed, u, nullptr, 0, (uint8_t)((d.y >> 16) & 255u)};
+  if (!(d.y >> 24)) return r;
+  r.len = d.y & 0xFFFFu;
+  const uint8_t* a = g + d.x;
+  if (r.len <= (uint32_t)kBuf) {
+    if ((((uintptr_t)a) & 7u) == 0) {
+      const uint32_t nv = (r.len + 7u) >> 3;
+      for (uint32_t i = lane; i < nv; i += 32)
+        *reinterpret_cast<uint2*>(w.fe + 8 * i) = __ldg(reinterpret_cast<const uint2*>(a) + i);
+    } else {
+      for (uint32_t i = lane; i < r.len; i += 32) w.fe[i] = __ldg(a + i);
+    }
+    r.src = w.fe;
+  } else {
+    r.src = a;
+  }
+  __syncwarp();
+  return r;
+}
+
+static_assert(offsetof(Warp, bad) % 16 == 0 && offsetof(Warp, gain) % 16 == 0 && sizeof(Warp) % 16 == 0,
+              "vector calibration loads need 16-byte aligned tables");
 
 }  // namespace fe

@@ -49,6 +49,7 @@ struct Scratch {
   uint32_t* fed_cnt = nullptr;       // clusters found per (event, FED, FE unit)
   uint32_t* fed_start = nullptr;     // staging offset per (event, FED, FE unit), within its event's slice
   uint32_t* fed_dest = nullptr;      // output offset per (event, FED, FE unit), within its event's slice
+  uint2* unit_desc = nullptr;        // per (event, FED, FE unit): offset in the FED record, length | status
   size_t items_cap = 0;
   uint32_t* ev_alloc = nullptr;      // staging allocation counter per event
   size_t ev_cap = 0;

@@ -3,13 +3,15 @@
 // (section 3).
 //
 // Clustering work unit: one FE unit (12 channels) of one FED of one event, handled
-// by one warp end to end (sst_fe.cuh): FED header check, the FE unit's channel
-// length chain (the paper's "map of channel locations", here on the device), run
-// validation and counts (one lane per channel), copy into an on-chip digi tile
-// sorted by strip, thresholds (one lane per digi), candidate boundaries, the
-// leftmost seed of each candidate (warp ballots; the paper's array of seed
-// strips), and cluster forming (one lane per kept candidate).  No block-wide
-// barrier: a GB300 SM keeps some thirty independent units in flight.
+// by one warp end to end (sst_fe.cuh): the FE unit's channel length chain (the
+// paper's "map of channel locations", here on the device), run validation and
+// counts (one lane per channel), expansion of the runs into an on-chip digi tile
+// sorted by strip (one lane per digi), thresholds (one lane per digi), candidate
+// boundaries, the leftmost seed of each candidate (warp ballots; the paper's array
+// of seed strips), and cluster forming (one lane per kept candidate).  No
+// block-wide barrier: a GB300 SM keeps some thirty independent units in flight.
+// The FED headers are checked once per FED by the prologue kernel (k_fed_scan),
+// which hands every unit its byte range.
 //
 // Output order without device-side waits: every unit allocates an exact-size
 // staging region with one atomic per event; k_clu_scan prefix-sums the units'
@@ -453,18 +455,75 @@ __device__ int chunk_end(Shm<TILE>& s, int c0) {
 
 // ---------------------------------------------------------------- kernels
 
+// a1, FED level: checks FED `fed`'s header (record at raw + fo, len bytes;
+// fo == kBadOff when the record lies outside its event) and describes its 8 FE
+// units for the batched kernel: d[v] = (byte offset of FE unit v in the record,
+// its length | FED status << 16 | has data << 24).  A header is valid when the
+// magic, FED id, channel and FE-unit counts and fed_bytes match and the padded FE
+// lengths add up to the record length; otherwise every channel of the FED gets
+// SST_CH_FED_HDR.  An absent FED (len 0) has no data and no error.
+__device__ void describe_fed(const uint8_t* __restrict__ raw, uint64_t fo, uint32_t len, uint32_t fed, uint2* d) {
+  uint32_t st = 0, data = 0;
+  uint32_t fe_len[kFe], start[kFe];
+#pragma unroll
+  for (int v = 0; v < kFe; v++) fe_len[v] = start[v] = 0;
+  if (fo == kBadOff) {
+    st = SST_CH_FED_HDR;
+  } else if (len > 0 && len < (uint32_t)kHdr) {
+    st = SST_CH_FED_HDR;
+  } else if (len > 0) {
+    const uint8_t* g = raw + fo;
+    uint32_t h[8];
+    if ((fo & 15u) == 0) {
+      const uint4 a = __ldg(reinterpret_cast<const uint4*>(g)), b = __ldg(reinterpret_cast<const uint4*>(g) + 1);
+      h[0] = a.x; h[1] = a.y; h[2] = a.z; h[3] = a.w; h[4] = b.x; h[5] = b.y; h[6] = b.z; h[7] = b.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; i++) h[i] = rd32(g + 4 * i);
+    }
+    uint32_t body = 0;
+#pragma unroll
+    for (int v = 0; v < kFe; v++) {
+      fe_len[v] = (h[4 + v / 2] >> (16 * (v & 1))) & 0xFFFFu;
+      start[v] = kHdr + body;
+      body += (fe_len[v] + 7u) & ~7u;
+    }
+    const uint32_t total = (kHdr + body + 15u) & ~15u;
+    const bool ok = h[0] == SST_FED_MAGIC && (h[1] & 0xFFFFu) == fed && ((h[1] >> 16) & 0xFFu) == (uint32_t)kCh &&
+                    (h[1] >> 24) == (uint32_t)kFe && h[2] == len && total == len;
+    if (ok) data = 1;
+    else st = SST_CH_FED_HDR;
+  }
+#pragma unroll
+  for (int v = 0; v < kFe; v++)
+    d[v] = make_uint2(data ? start[v] : 0u, (data ? fe_len[v] : 0u) | (st << 16) | (data << 24));
+}
+
 // a1, outer level: byte offset of every FED record (exclusive scan of fed_len per
 // event, plus the event's start).  A record that would end past its event is
-// marked kBadOff; a size mismatch sets SST_EV_SIZE.  One CTA per event.
+// marked kBadOff; a size mismatch sets SST_EV_SIZE.  One CTA per event.  With
+// unit_desc (batched path) every FED's header is checked and its FE units
+// described (describe_fed).  It is also the launch sequence's prologue: it clears
+// the event's status and staging counter (ev_alloc, when given), CTA 0 clears the
+// work tickets, and the look-back states lb[0 .. n_lb) are cleared (per-event
+// unpacking, one CTA).
 __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_bytes,
                            const uint32_t* __restrict__ fed_len, uint32_t n_feds, uint64_t* __restrict__ fed_off,
-                           sst_event_status* status) {
+                           sst_event_status* status, uint32_t* ev_alloc, uint32_t* tickets, unsigned long long* lb,
+                           uint32_t n_lb, const uint8_t* __restrict__ raw, uint2* unit_desc) {
   __shared__ uint32_t wsum[32];
   __shared__ uint64_t carry_s;
   const uint32_t e = blockIdx.x;
   const uint64_t ev0 = event_off ? event_off[e] : 0;
   const uint64_t ev1 = event_off ? event_off[e + 1] : raw_bytes;
-  if (threadIdx.x == 0) carry_s = 0;
+  if (threadIdx.x == 0) {
+    carry_s = 0;
+    status[e] = sst_event_status{0u, 0u, 0u, 0u};
+    if (ev_alloc) ev_alloc[e] = 0;
+  }
+  if (e == 0 && threadIdx.x < 16) tickets[threadIdx.x] = 0;
+  if (lb)
+    for (uint32_t i = threadIdx.x; i < n_lb; i += blockDim.x) lb[i] = 0;
   __syncthreads();
   for (uint32_t b = 0; b < n_feds; b += blockDim.x) {
     const uint32_t f = b + threadIdx.x;
@@ -474,7 +533,9 @@ __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_
     const uint64_t carry = carry_s;
     if (f < n_feds) {
       const uint64_t o = ev0 + carry + ex;
-      fed_off[(size_t)e * n_feds + f] = (ev1 >= ev0 && o + len <= ev1) ? o : kBadOff;
+      const uint64_t fo = (ev1 >= ev0 && o + len <= ev1) ? o : kBadOff;
+      fed_off[(size_t)e * n_feds + f] = fo;
+      if (unit_desc) describe_fed(raw, fo, len, f, unit_desc + ((size_t)e * n_feds + f) * kFe);
     }
     __syncthreads();
     if (threadIdx.x == 0) carry_s = carry + tot;
@@ -485,11 +546,16 @@ __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_
 
 // a6, ordering: per event, the exclusive scan of its FEDs' cluster counts gives
 // every FED's position in the event's sorted cluster SoA; the event's total is its
-// cluster count.  One CTA per event.
+// cluster count.  One CTA per event.  With pack_off (events packed back to back),
+// the CTA that finishes last (counted in *done, which the prologue cleared; no
+// CTA waits for another) also scans the events' counts: pack_off[e] = clusters
+// of the events before e, pack_off[n_events] = all clusters.
 __global__ void k_clu_scan(const uint32_t* __restrict__ fed_cnt, uint32_t n_feds, uint32_t* __restrict__ fed_dest,
-                           sst_event_status* status) {
+                           sst_event_status* status, uint64_t* pack_off, uint32_t* done) {
   __shared__ uint32_t wsum[32];
   __shared__ uint32_t carry_s;
+  __shared__ uint64_t pcarry_s;
+  __shared__ bool last_s;
   const uint32_t e = blockIdx.x;
   if (threadIdx.x == 0) carry_s = 0;
   __syncthreads();
@@ -505,6 +571,31 @@ __global__ void k_clu_scan(const uint32_t* __restrict__ fed_cnt, uint32_t n_feds
     __syncthreads();
   }
   if (threadIdx.x == 0) status[e].n_clusters = carry_s;
+  if (!pack_off) return;
+  if (threadIdx.x == 0) {
+    __threadfence();  // this event's count is visible before it is counted as done
+    last_s = atomicAdd(done, 1u) == gridDim.x - 1;
+    pcarry_s = 0;
+  }
+  __syncthreads();
+  if (!last_s) return;
+  __threadfence();
+  const uint32_t n_events = gridDim.x;
+  for (uint32_t b = 0; b < n_events; b += blockDim.x) {
+    const uint32_t i = b + threadIdx.x;
+    const uint32_t n = i < n_events ? __ldcg(&status[i].n_clusters) : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan(n, wsum, &tot);
+    const uint64_t carry = pcarry_s;
+    if (i < n_events) pack_off[i] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) pcarry_s = carry + tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    pack_off[n_events] = pcarry_s;
+    *done = 0;
+  }
 }
 
 // a6, output: copies every segment's staged clusters (one segment per FE unit)
@@ -677,7 +768,8 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
                                                   uint32_t n_feds, const uint64_t* __restrict__ clu_off,
                                                   uint64_t out_cap, sst_event_status* status, KParams kp,
                                                   uint4* stage, uint32_t* ev_alloc, uint32_t* seg_cnt,
-                                                  uint32_t* seg_start, uint32_t* ticket) {
+                                                  uint32_t* seg_start, uint32_t* ticket,
+                                                  const uint2* __restrict__ unit_desc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   fe::Warp& w = reinterpret_cast<fe::Warp*>(smem_raw)[warp];
@@ -692,10 +784,9 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
     const size_t item = (size_t)e * n_feds + f;
     const uint64_t fo = fed_off[item];
     const bool in_range = fo != kBadOff;
-    const uint32_t len = in_range ? fed_len[item] : 0u;
     const uint32_t ch0 = f * kCh + u * kChPerFe;
     fe::load_calib(w, kp, ch0);
-    const fe::Unit un = fe::locate(w, in_range ? raw + fo : nullptr, len, f, u, in_range);
+    const fe::Unit un = fe::locate(w, raw + (in_range ? fo : 0), unit_desc[item * kFe + u], f, u);
     uint32_t flags, nbad;
     const uint32_t total = fe::parse_unit(w, un, &flags, &nbad);
     if (lane == 0) {
@@ -712,29 +803,6 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
     fe::cluster_unit(w, kp, kp.noise + (size_t)ch0 * kStrips, ch0, total, fill, so, &status[e]);
     __syncwarp();
   }
-}
-
-// Packed output: pack_off[e] = sum of the cluster counts of the events before e
-// (n_events + 1 values), so that k_compact can write the events back to back.
-// One CTA.
-__global__ void __launch_bounds__(1024) k_pack_scan(const sst_event_status* __restrict__ status, uint32_t n_events,
-                                                    uint64_t* pack_off) {
-  __shared__ uint32_t wsum[32];
-  __shared__ uint64_t carry_s;
-  if (threadIdx.x == 0) carry_s = 0;
-  __syncthreads();
-  for (uint32_t b = 0; b < n_events; b += blockDim.x) {
-    const uint32_t e = b + threadIdx.x;
-    const uint32_t n = e < n_events ? status[e].n_clusters : 0u;
-    uint32_t tot;
-    const uint32_t ex = block_excl_scan(n, wsum, &tot);
-    const uint64_t carry = carry_s;
-    if (e < n_events) pack_off[e] = carry + ex;
-    __syncthreads();
-    if (threadIdx.x == 0) carry_s = carry + tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) pack_off[n_events] = carry_s;
 }
 
 __global__ void k_badmask(const uint8_t* __restrict__ bad, uint32_t* __restrict__ mask, uint64_t n_words) {
@@ -835,7 +903,8 @@ cudaError_t launch_batch_fe(const uint8_t* raw, const uint32_t* fed_len, uint32_
   const int grid = (int)(ctas < need ? ctas : need);
   if (ev_begin && (e = cudaEventRecord(ev_begin, st))) return e;
   k_batch<<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out_cap, status, kp,
-                                      s.stage, s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets);
+                                      s.stage, s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets,
+                                      s.unit_desc);
   if ((e = cudaGetLastError())) return e;
   if (ev_end && (e = cudaEventRecord(ev_end, st))) return e;
   return cudaSuccess;
@@ -844,13 +913,9 @@ cudaError_t launch_batch_fe(const uint8_t* raw, const uint32_t* fed_len, uint32_
 // Per-event cluster order and the copy into the caller's SoA.
 cudaError_t launch_order(const uint64_t* clu_off, uint32_t n_events, uint32_t n_segs, const sst_clusters& out,
                          sst_event_status* status, const Scratch& s, uint64_t* pack_off, cudaStream_t st) {
-  k_clu_scan<<<n_events, 256, 0, st>>>(s.fed_cnt, n_segs, s.fed_dest, status);
+  k_clu_scan<<<n_events, 256, 0, st>>>(s.fed_cnt, n_segs, s.fed_dest, status, pack_off, s.tickets + 1);
   cudaError_t e = cudaGetLastError();
   if (e) return e;
-  if (pack_off) {
-    k_pack_scan<<<1, 1024, 0, st>>>(status, n_events, pack_off);
-    if ((e = cudaGetLastError())) return e;
-  }
   const uint64_t items = (uint64_t)n_events * n_segs;
   k_compact<<<(unsigned)((items + 7) / 8), 256, 0, st>>>(s.stage, clu_off, pack_off, s.fed_cnt, s.fed_start,
                                                         s.fed_dest, n_events, n_segs, out);
@@ -882,10 +947,9 @@ bool shape_valid(const Shape& s) {
 cudaError_t launch_unpack(const uint8_t* raw, uint64_t raw_bytes, const uint32_t* fed_len, uint32_t n_feds,
                           const sst_digis& out, const Scratch& s, const Shape& sh, cudaStream_t st) {
   cudaError_t e;
-  if ((e = cudaMemsetAsync(out.status, 0, sizeof(sst_event_status), st))) return e;
-  if ((e = cudaMemsetAsync(s.lb, 0, sizeof(unsigned long long) * n_feds, st))) return e;
-  if ((e = cudaMemsetAsync(s.tickets, 0, sizeof(uint32_t) * 4, st))) return e;
-  k_fed_scan<<<1, 256, 0, st>>>(nullptr, raw_bytes, fed_len, n_feds, s.fed_off, out.status);
+  k_fed_scan<<<1, 256, 0, st>>>(nullptr, raw_bytes, fed_len, n_feds, s.fed_off, out.status, nullptr, s.tickets, s.lb,
+                                n_feds, nullptr, nullptr);
+  if ((e = cudaGetLastError())) return e;
   switch (sh.tile) {
     case 1024: return launch_unpack_t<1024>(raw, fed_len, n_feds, out, s, sh, st);
     case 2048: return launch_unpack_t<2048>(raw, fed_len, n_feds, out, s, sh, st);
@@ -907,10 +971,9 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
                          const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st,
                          uint64_t* pack_off, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   cudaError_t e;
-  if ((e = cudaMemsetAsync(status, 0, sizeof(sst_event_status) * n_events, st))) return e;
-  if ((e = cudaMemsetAsync(s.ev_alloc, 0, sizeof(uint32_t) * n_events, st))) return e;
-  if ((e = cudaMemsetAsync(s.tickets, 0, sizeof(uint32_t) * 4, st))) return e;
-  k_fed_scan<<<n_events, 256, 0, st>>>(event_off, 0, fed_len, n_feds, s.fed_off, status);
+  k_fed_scan<<<n_events, 256, 0, st>>>(event_off, 0, fed_len, n_feds, s.fed_off, status, s.ev_alloc, s.tickets,
+                                       nullptr, 0, raw, s.unit_desc);
+  if ((e = cudaGetLastError())) return e;
   e = launch_batch_fe(raw, fed_len, n_events, n_feds, clu_off, out.capacity, status, kp, s, sh, n_sm, st, ev_begin,
                       ev_end);
   if (e) return e;
