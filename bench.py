@@ -188,6 +188,24 @@ class Clocks:
 
 # ---------------------------------------------------------------- helpers
 
+def shard(rank: int, n_events: int) -> range:
+    """Event ids a rank processes: every rank is an independent replica with its own
+    n_events events (rank r takes ids r * n_events ... r * n_events + n_events - 1),
+    so no data moves between ranks."""
+    return range(rank * n_events, (rank + 1) * n_events)
+
+
+def max_over_ranks(values, world: int) -> list:
+    """Element-wise maximum of per-rank timings over all ranks (identity at N = 1)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -258,10 +276,10 @@ def main():
     cores = os.cpu_count() or 1
     # the process pool is started (spawn) before the first CUDA call
     pool = mp.get_context("spawn").Pool(cores, initializer=_worker_init, initargs=(wid,))
-    base_event = rank * n_events
-    gen = pool.map(_gen_event, [(wid, base_event + i) for i in range(n_events)], chunksize=1)
+    ids = shard(rank, n_events)
+    gen = pool.map(_gen_event, [(wid, i) for i in ids], chunksize=1)
     events = [(r, f) for r, f, _ in gen]
-    served_pool = pool.map(_gen_served_event, range(base_event, base_event + 64), chunksize=1) \
+    served_pool = pool.map(_gen_served_event, range(ids.start, ids.start + 64), chunksize=1) \
         if args.served_events > 0 and wid == 2 else []
     calib = eg.make_calibration(w.n_feds, w.seed, w.p_bad)
 
@@ -330,13 +348,7 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     n_launch, kernel_ms = sst.sst_profile_read(ctx, reset=True)
     ms_per_step = sum(step_ms) / len(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_per_step, kernel_ms / max(n_launch, 1)], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_per_step, k_ms = float(t[0]), float(t[1])
-    else:
-        k_ms = kernel_ms / max(n_launch, 1)
+    ms_per_step, k_ms = max_over_ranks([ms_per_step, kernel_ms / max(n_launch, 1)], world)
 
     st_h = st_d.cpu().numpy().view(np.uint32).reshape(n_events, 4)
     n_digi = int(st_h[:, 0].sum())
@@ -368,7 +380,8 @@ def main():
         b.record(stream)
         torch.cuda.synchronize()
         pe_ms.append(a.elapsed_time(b))
-    pe_value = n_events / (statistics.median(pe_ms) / 1e3)
+    pe_med = max_over_ranks([statistics.median(pe_ms)], world)[0]
+    pe_value = n_events / (pe_med / 1e3)
 
     # ---- end to end through the C ABI with host-resident events (sst_batch_host:
     # H2D of every step's events, the kernels, D2H of every cluster and status,
@@ -394,12 +407,7 @@ def main():
     for i in range(e2e_steps):
         d2h_total += e2e_step()
     barrier()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t[0])
+    e2e_s = max_over_ranks([(time.perf_counter() - t0) / e2e_steps], world)[0]
     h2d_bytes = raw_h.nbytes + fl_h.nbytes + 2 * eoff.nbytes  # raw, FED lengths, event and cluster offsets
 
     # ---- served stream: continuous batching behind sst_submit / sst_poll
@@ -459,7 +467,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "strips_per_s": round(total_events * w.n_feds * 96 * 256 / (ms_per_step / 1e3), 1),
             "per_event": {"value": round(pe_value * world, 1), "unit": "events/s",
-                          "ms_per_event": round(statistics.median(pe_ms) / n_events, 4),
+                          "ms_per_event": round(pe_med / n_events, 4),
                           "what": "sst_unpack + sst_cluster, one event per launch pair, same events"},
             "batched_over_per_event": round((total_events / (ms_per_step / 1e3)) / (pe_value * world), 2),
             "e2e": {"value": round(total_events / e2e_s, 1), "unit": "events/s",
