@@ -98,49 +98,72 @@ def time_oracle(pool, cores, events, n_sample):
 
 # ---------------------------------------------------------------- served stream
 
-def run_served(sst, ctx, events, n_feds, n_requests, rate):
+def run_served(sst, ctx, events, n_feds, n_requests, rate, submitters=8):
     """Submits n_requests events (cycling over `events`) with Poisson arrivals at
-    `rate` events/s (0 = as fast as possible) from one thread while another polls
-    them in order.  Returns throughput and latency percentiles (submit to done,
-    host clock, microseconds)."""
+    `rate` events/s (0 = as fast as possible) from `submitters` threads (arrival i
+    goes to thread i mod submitters; each sst_submit copies the event into the
+    server's pinned pool with the GIL released) while another thread polls the
+    admitted events in admission order, which frees their space.  Returns
+    throughput and latency percentiles (submit to done, host clock, microseconds).
+    A thread that makes no progress for a minute ends the run with an error."""
+    import queue
+    import sys
     import threading
     rng = np.random.default_rng(12345)
     gaps = rng.exponential(1.0 / rate, n_requests) if rate > 0 else np.zeros(n_requests)
-    tickets = [None] * n_requests
-    ready = threading.Semaphore(0)
-    lat, done_t = [], []
+    due = np.cumsum(gaps)
+    admitted = queue.SimpleQueue()
+    lat, done_t, errors = [], [], []
     retries = [0]
+    limit_s = 60.0
+    old_switch = sys.getswitchinterval()
+    sys.setswitchinterval(5e-5)  # a waiting thread takes the GIL within 50 us
 
-    def submitter():
-        t = time.perf_counter()
-        for i in range(n_requests):
-            t += gaps[i]
-            while rate > 0 and time.perf_counter() < t:
-                pass
-            raw, fl = events[i % len(events)]
-            while True:
-                code, tk = sst.sst_submit(ctx, raw, fl)
-                if code == sst.SST_OK:
-                    break
-                retries[0] += 1
-                time.sleep(20e-6)
-            tickets[i] = tk
-            ready.release()
+    def submitter(k, t0):
+        try:
+            for i in range(k, n_requests, submitters):
+                if rate > 0:
+                    while True:
+                        left = t0 + due[i] - time.perf_counter()
+                        if left <= 0:
+                            break
+                        time.sleep(left if left > 2e-4 else 0)
+                raw, fl = events[i % len(events)]
+                t_try = time.perf_counter()
+                while True:
+                    code, tk = sst.sst_submit(ctx, raw, fl)
+                    if code == sst.SST_OK:
+                        break
+                    if time.perf_counter() - t_try > limit_s:
+                        raise RuntimeError(f"sst_submit refused for {limit_s} s (code {code})")
+                    retries[0] += 1
+                    time.sleep(20e-6)
+                admitted.put(tk)
+        except Exception as ex:  # reported by the caller
+            errors.append(repr(ex))
 
     def poller():
-        for i in range(n_requests):
-            ready.acquire()
-            code, info, _ = sst.sst_poll(ctx, tickets[i], -1, 0)
-            assert code == sst.SST_OK
-            lat.append(info.t_done_us - info.t_submit_us)
-            done_t.append(time.perf_counter())
+        try:
+            for _ in range(n_requests):
+                tk = admitted.get(timeout=limit_s)
+                code, info, _ = sst.sst_poll(ctx, tk, -1, 0)
+                if code != sst.SST_OK:
+                    raise RuntimeError(f"sst_poll returned {code}")
+                lat.append(info.t_done_us - info.t_submit_us)
+                done_t.append(time.perf_counter())
+        except Exception as ex:
+            errors.append(repr(ex))
 
     t0 = time.perf_counter()
-    th = [threading.Thread(target=submitter), threading.Thread(target=poller)]
+    th = [threading.Thread(target=submitter, args=(k, t0)) for k in range(submitters)]
+    th.append(threading.Thread(target=poller))
     for x in th:
         x.start()
     for x in th:
         x.join()
+    sys.setswitchinterval(old_switch)
+    if errors or len(lat) != n_requests:
+        raise RuntimeError(f"served run incomplete: {len(lat)} of {n_requests} events; {errors[:3]}")
     wall = max(done_t) - t0
     lat = np.array(lat)
     return {"offered_rate": round(rate, 1) if rate > 0 else "saturating", "events": n_requests,
@@ -420,7 +443,7 @@ def main():
             pts = [run_served(sst, ctx, served_pool, w.n_feds, args.served_events, f * cap["throughput"])
                    for f in (0.5, 0.9)]
             served = {"workload": "served-440fed-lognormal: occupancy lognormal median 1.5%, clip [0.5%, 5%], "
-                                  "64 distinct events cycled, Poisson arrivals, one Python submitter thread",
+                                  "64 distinct events cycled, Poisson arrivals, 8 Python submitter threads",
                       "budget_bytes": 8 << 30, "max_batch_events": 64, "max_inflight": 3,
                       "saturation": cap, "points": pts}
         finally:

@@ -50,3 +50,16 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     assert L.sst_create(ctypes.byref(h), 0, 0) == sst.SST_ERR_INVALID_ARG
     assert L.sst_destroy(None) == sst.SST_ERR_INVALID_ARG
     assert L.sst_last_error(None) == b"null context"
+
+
+def test_status_bits_agree_between_header_binding_and_oracle():
+    """The data-error bits are an interface: the header, the binding and the
+    independently written oracle must report the same values."""
+    import re
+    import oracle as orc
+    import paper_2101_11489_gb300 as sst
+    hdr = open(os.path.join(ROOT, "include", "sst.h")).read()
+    for name in ("FED_HDR", "FRAMING", "BAD_CODE", "RUN_RANGE", "RUN_ORDER", "TRUNC"):
+        m = re.search(r"#define SST_CH_%s (0x[0-9A-Fa-f]+)u" % name, hdr)
+        assert m, name
+        assert int(m.group(1), 16) == getattr(sst, "SST_CH_" + name) == getattr(orc, "ST_" + name)
