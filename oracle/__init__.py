@@ -95,6 +95,10 @@ def _load():
             lib.orc_cluster_event.argtypes = [u32p, u8p, u32p, ctypes.c_uint32, f32p, f32p, u8p, _P(_Params),
                                               u32p, u16p, u16p, u32p, f32p, ctypes.c_uint64]
             lib.orc_is_active.restype = ctypes.c_int
+            lib.orc_cluster_amplitudes.argtypes = [u32p, u8p, u32p, f32p, f32p, u8p, _P(_Params), u32p,
+                                                   ctypes.POINTER(ctypes.c_uint16), ctypes.POINTER(ctypes.c_uint16),
+                                                   ctypes.c_uint64, u32p, u8p, ctypes.c_uint64]
+            lib.orc_cluster_amplitudes.restype = ctypes.c_int64
             lib.orc_is_active.argtypes = [ctypes.c_uint8, ctypes.c_float, ctypes.c_uint8, _P(_Params)]
             lib.orc_is_seed.restype = ctypes.c_int
             lib.orc_is_seed.argtypes = [ctypes.c_uint8, ctypes.c_float, ctypes.c_uint8, _P(_Params)]
@@ -225,6 +229,33 @@ def cluster_event(digis: dict, n_feds: int, noise, gain, bad, p: Params) -> dict
         raise RuntimeError("oracle event clusterizer: capacity too small")
     return {"det": det[:k].copy(), "first": first[:k].copy(), "width": width[:k].copy(),
             "charge": charge[:k].copy(), "barycenter": bary[:k].copy()}
+
+
+def cluster_amplitudes(digis: dict, clusters: dict, noise, gain, bad, p: Params) -> tuple[np.ndarray, np.ndarray]:
+    """Per-strip amplitudes of the clusters (gain-corrected charge of active
+    strips, 0 elsewhere), back to back: returns (amp_first per cluster, amp)."""
+    strip = np.ascontiguousarray(digis["strip"], dtype=np.uint32)
+    adc = np.ascontiguousarray(digis["adc"], dtype=np.uint8)
+    chan_off = np.ascontiguousarray(digis["chan_off"], dtype=np.uint32)
+    det = np.ascontiguousarray(clusters["det"], dtype=np.uint32)
+    first = np.ascontiguousarray(clusters["first"], dtype=np.uint16)
+    width = np.ascontiguousarray(clusters["width"], dtype=np.uint16)
+    noise = np.ascontiguousarray(noise, dtype=np.float32)
+    gain = np.ascontiguousarray(gain, dtype=np.float32)
+    bad = np.ascontiguousarray(bad, dtype=np.uint8)
+    n = det.size
+    cap = max(int(width.astype(np.int64).sum()), 1)
+    amp_first = np.zeros(max(n, 1), np.uint32)
+    amp = np.zeros(cap, np.uint8)
+    k = _load().orc_cluster_amplitudes(_ptr(strip, ctypes.c_uint32), _ptr(adc, ctypes.c_uint8),
+                                       _ptr(chan_off, ctypes.c_uint32), _ptr(noise, ctypes.c_float),
+                                       _ptr(gain, ctypes.c_float), _ptr(bad, ctypes.c_uint8), ctypes.byref(p._c()),
+                                       _ptr(det, ctypes.c_uint32), _ptr(first, ctypes.c_uint16),
+                                       _ptr(width, ctypes.c_uint16), n, _ptr(amp_first, ctypes.c_uint32),
+                                       _ptr(amp, ctypes.c_uint8), cap)
+    if k < 0:
+        raise RuntimeError("oracle amplitudes failed")
+    return amp_first[:n].copy(), amp[:k].copy()
 
 
 def process_event(raw, fed_len, n_feds: int, noise, gain, bad, p: Params) -> tuple[dict, dict]:

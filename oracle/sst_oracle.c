@@ -456,3 +456,31 @@ int64_t orc_cluster_event(const uint32_t* strip, const uint8_t* adc, const uint3
   }
   return (int64_t)out;
 }
+
+/* ---- per-strip amplitudes of clusters --------------------------------------- */
+
+int64_t orc_cluster_amplitudes(const uint32_t* strip, const uint8_t* adc, const uint32_t* chan_off,
+                               const float* noise, const float* gain, const uint8_t* bad,
+                               const orc_params* p, const uint32_t* det, const uint16_t* first,
+                               const uint16_t* width, uint64_t n_clusters, uint32_t* amp_first,
+                               uint8_t* amp, uint64_t cap) {
+  uint64_t out = 0;
+  uint8_t row_adc[ORC_STRIPS_PER_CH];
+  for (uint64_t k = 0; k < n_clusters; k++) {
+    uint32_t c = det[k];
+    uint64_t g0 = (uint64_t)c * ORC_STRIPS_PER_CH;
+    /* the module's ADC row: recorded strips from the digis, 0 elsewhere */
+    memset(row_adc, 0, sizeof row_adc);
+    for (uint32_t d = chan_off[c]; d < chan_off[c + 1]; d++) row_adc[strip[d] - g0] = adc[d];
+    if (first[k] + width[k] > ORC_STRIPS_PER_CH) return -1;
+    if (out + width[k] > cap) return -1;
+    amp_first[k] = (uint32_t)out;
+    for (int i = 0; i < width[k]; i++) {
+      int s = first[k] + i;
+      uint64_t g = g0 + (uint64_t)s;
+      int act = orc_is_active(row_adc[s], noise[g], bad[g], p);
+      amp[out++] = act ? (uint8_t)orc_corrected_charge(row_adc[s], gain[g / ORC_STRIPS_PER_APV]) : 0;
+    }
+  }
+  return (int64_t)out;
+}

@@ -85,6 +85,21 @@ int64_t orc_cluster_event(const uint32_t* strip, const uint8_t* adc, const uint3
                           float* barycenter, uint64_t cap);
 
 /* The three threshold predicates, exposed for the pins (section 2). */
+/* Optional per-strip amplitudes of clusters (section 2: a kept cluster reports
+ * its boundaries, centroid "and optionally ADC values").  For cluster k (module
+ * det[k], strips first[k] .. first[k] + width[k] - 1), the amplitude of a strip
+ * is its gain-corrected charge (orc_corrected_charge) when the strip is active,
+ * and 0 otherwise (a hole, a bad strip inside the cluster or a bad strip it was
+ * widened over).  Clusters' amplitudes are written back to back:
+ * amp_first[k] = sum of width[j] for j < k.  The digis and calibration are those
+ * given to orc_cluster_event.  Returns the number of amplitudes written, or -1
+ * when `cap` is too small. */
+int64_t orc_cluster_amplitudes(const uint32_t* strip, const uint8_t* adc, const uint32_t* chan_off,
+                               const float* noise, const float* gain, const uint8_t* bad,
+                               const orc_params* p, const uint32_t* det, const uint16_t* first,
+                               const uint16_t* width, uint64_t n_clusters, uint32_t* amp_first,
+                               uint8_t* amp, uint64_t cap);
+
 int orc_is_active(uint8_t adc, float noise, uint8_t bad, const orc_params* p);
 int orc_is_seed(uint8_t adc, float noise, uint8_t bad, const orc_params* p);
 int orc_passes_cluster(uint32_t s_raw, float n2, const orc_params* p);
