@@ -96,6 +96,7 @@ typedef int32_t sst_status;
 #define SST_EV_CLUSTER_CAPACITY 0x200u /* cluster output capacity exceeded; clusters dropped */
 #define SST_EV_TIMEOUT 0x400u          /* a device wait gave up; the event's output is invalid */
 #define SST_EV_SIZE 0x800u             /* batch: sum of fed_len != event_off[e+1] - event_off[e] */
+#define SST_EV_AMP_CAPACITY 0x1000u    /* amplitude capacity exceeded; some clusters have no amplitudes */
 
 /* Per-event status record, in device memory. */
 typedef struct {
@@ -153,6 +154,22 @@ typedef struct {
   uint32_t* charge;
   float* barycenter;
   uint64_t capacity; /* elements of each array; also sizes the context's staging scratch */
+  /* Optional per-strip amplitudes (section 2: a cluster reports its boundaries,
+   * centroid "and optionally ADC values"); amp == NULL: none are produced.  Only
+   * sst_cluster and sst_batch produce them (sst_batch_host and the served path
+   * take amp == NULL).  The amplitude of each strip of a cluster is its
+   * gain-corrected charge when the strip is active, else 0 (a hole, a bad strip
+   * inside, a bad strip the cluster was widened over): cluster k's width[k]
+   * amplitudes are amp[amp_first[k] ..].  Within an event they follow the
+   * cluster order.  When an FE unit's amplitudes do not fit, none of them is
+   * stored, its clusters get amp_first = 0xFFFFFFFF and the event
+   * SST_EV_AMP_CAPACITY (the clusters themselves are unaffected). */
+  uint8_t* amp;            /* [amp_capacity] */
+  uint32_t* amp_first;     /* [capacity], absolute index into amp */
+  const uint64_t* amp_off; /* sst_batch: [n_events + 1] device; event e's amplitudes lie in
+                              [amp_off[e], amp_off[e+1]) (bounded by amp_capacity);
+                              sst_cluster: unused, the event has [0, amp_capacity) */
+  uint64_t amp_capacity;   /* bytes of amp; also sizes the context's amplitude staging */
 } sst_clusters;
 
 /* ---- context ------------------------------------------------------------------ */
@@ -270,7 +287,8 @@ sst_status sst_batch(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off
  * on the context) and are freed by sst_destroy.  A context runs one
  * sst_batch_host call at a time (calls from several threads are serialised).
  * Errors: INVALID_ARG (null pointer, n_events == 0, n_feds outside 1..context
- * FEDs, decreasing event_off), NO_CALIB, CUDA. */
+ * FEDs, decreasing event_off, out->amp set: amplitudes are not produced here),
+ * NO_CALIB, CUDA. */
 sst_status sst_batch_host(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len,
                           uint32_t n_events, uint32_t n_feds, const sst_clusters* out, uint64_t* event_first,
                           sst_event_status* status);

@@ -46,6 +46,8 @@ SST_EV_DIGI_CAPACITY = 0x100
 SST_EV_CLUSTER_CAPACITY = 0x200
 SST_EV_TIMEOUT = 0x400
 SST_EV_SIZE = 0x800
+SST_EV_AMP_CAPACITY = 0x1000
+NO_AMP = 0xFFFFFFFF  # amp_first of a cluster whose amplitudes did not fit
 
 
 class SstError(RuntimeError):
@@ -72,7 +74,9 @@ class sst_digis(ctypes.Structure):
 
 class sst_clusters(ctypes.Structure):
     _fields_ = [("det", ctypes.c_void_p), ("first", ctypes.c_void_p), ("width", ctypes.c_void_p),
-                ("charge", ctypes.c_void_p), ("barycenter", ctypes.c_void_p), ("capacity", ctypes.c_uint64)]
+                ("charge", ctypes.c_void_p), ("barycenter", ctypes.c_void_p), ("capacity", ctypes.c_uint64),
+                ("amp", ctypes.c_void_p), ("amp_first", ctypes.c_void_p), ("amp_off", ctypes.c_void_p),
+                ("amp_capacity", ctypes.c_uint64)]
 
 
 class sst_tune(ctypes.Structure):
@@ -348,32 +352,49 @@ class DigiBuffers:
 @dataclass
 class ClusterBuffers:
     """Device tensors behind an sst_clusters record (int32 / int16 tensors hold the
-    unsigned fields bit for bit)."""
+    unsigned fields bit for bit), with optional amplitude arrays (amp u8,
+    amp_first u32 per cluster; amp_off, device u64 per event + 1, for sst_batch)."""
     det: object
     first: object
     width: object
     charge: object
     barycenter: object
+    amp: object = None
+    amp_first: object = None
+    amp_off: object = None
 
     @classmethod
-    def alloc(cls, capacity: int, device="cuda"):
+    def alloc(cls, capacity: int, device="cuda", amp_capacity: int = 0):
         import torch
         c = max(capacity, 1)
-        return cls(torch.empty(c, dtype=torch.int32, device=device), torch.empty(c, dtype=torch.int16, device=device),
-                   torch.empty(c, dtype=torch.int16, device=device), torch.empty(c, dtype=torch.int32, device=device),
-                   torch.empty(c, dtype=torch.float32, device=device))
+        b = cls(torch.empty(c, dtype=torch.int32, device=device), torch.empty(c, dtype=torch.int16, device=device),
+                torch.empty(c, dtype=torch.int16, device=device), torch.empty(c, dtype=torch.int32, device=device),
+                torch.empty(c, dtype=torch.float32, device=device))
+        if amp_capacity > 0:
+            b.amp = torch.empty(amp_capacity, dtype=torch.uint8, device=device)
+            b.amp_first = torch.empty(c, dtype=torch.int32, device=device)
+        return b
 
     def record(self) -> sst_clusters:
+        amp = self.amp is not None
         return sst_clusters(_dp(self.det), _dp(self.first), _dp(self.width), _dp(self.charge), _dp(self.barycenter),
-                            self.det.numel())
+                            self.det.numel(), _dp(self.amp) if amp else None, _dp(self.amp_first) if amp else None,
+                            _dp(self.amp_off) if amp and self.amp_off is not None else None,
+                            self.amp.numel() if amp else 0)
 
     def to_host(self, start: int = 0, n: int | None = None) -> dict:
         end = self.det.numel() if n is None else start + n
-        return {"det": self.det[start:end].cpu().numpy().view(np.uint32).copy(),
-                "first": self.first[start:end].cpu().numpy().view(np.uint16).copy(),
-                "width": self.width[start:end].cpu().numpy().view(np.uint16).copy(),
-                "charge": self.charge[start:end].cpu().numpy().view(np.uint32).copy(),
-                "barycenter": self.barycenter[start:end].cpu().numpy().copy()}
+        h = {"det": self.det[start:end].cpu().numpy().view(np.uint32).copy(),
+             "first": self.first[start:end].cpu().numpy().view(np.uint16).copy(),
+             "width": self.width[start:end].cpu().numpy().view(np.uint16).copy(),
+             "charge": self.charge[start:end].cpu().numpy().view(np.uint32).copy(),
+             "barycenter": self.barycenter[start:end].cpu().numpy().copy()}
+        if self.amp is not None:
+            h["amp_first"] = self.amp_first[start:end].cpu().numpy().view(np.uint32).copy()
+        return h
+
+    def amplitudes(self) -> np.ndarray:
+        return self.amp.cpu().numpy().copy()
 
 
 @dataclass
@@ -398,7 +419,7 @@ class HostClusters:
 
     def record(self) -> sst_clusters:
         return sst_clusters(_hp(self.det), _hp(self.first), _hp(self.width), _hp(self.charge), _hp(self.barycenter),
-                            self.det.size)
+                            self.det.size, None, None, None, 0)
 
     def view(self, start: int, n: int) -> dict:
         return {k: getattr(self, k)[start:start + n] for k in ("det", "first", "width", "charge", "barycenter")}

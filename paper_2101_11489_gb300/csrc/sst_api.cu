@@ -73,6 +73,24 @@ cudaError_t ensure_scratch(Scratch& s, size_t items, size_t events, size_t stage
   return cudaSuccess;
 }
 
+cudaError_t ensure_amp_scratch(Scratch& s, size_t items, size_t events, size_t amp_bytes) {
+  items = items ? items : 1;
+  events = events ? events : 1;
+  amp_bytes = amp_bytes ? amp_bytes : 1;
+  if (items <= s.amp_items_cap && events <= s.amp_ev_cap && amp_bytes <= s.amp_stage_cap) return cudaSuccess;
+  cudaError_t e = cudaDeviceSynchronize();  // growing: wait for all work that may still use the old buffers
+  if (e) return e;
+  if (items > s.amp_items_cap) {
+    size_t c1 = s.amp_items_cap, c2 = s.amp_items_cap, c3 = s.amp_items_cap;
+    if ((e = grow(s.seg_amp_cnt, c1, items))) return e;
+    if ((e = grow(s.seg_amp_start, c2, items))) return e;
+    if ((e = grow(s.seg_amp_dest, c3, items))) return e;
+    s.amp_items_cap = items;
+  }
+  if ((e = grow(s.amp_alloc, s.amp_ev_cap, events))) return e;
+  return grow(s.amp_stage, s.amp_stage_cap, amp_bytes);
+}
+
 void free_scratch(Scratch& s) {
   if (s.lb) cudaFree(s.lb);
   if (s.fed_off) cudaFree(s.fed_off);
@@ -83,6 +101,9 @@ void free_scratch(Scratch& s) {
   if (s.ev_alloc) cudaFree(s.ev_alloc);
   if (s.stage) cudaFree(s.stage);
   if (s.tickets) cudaFree(s.tickets);
+  for (void* p : {(void*)s.amp_stage, (void*)s.amp_alloc, (void*)s.seg_amp_cnt, (void*)s.seg_amp_start,
+                  (void*)s.seg_amp_dest})
+    if (p) cudaFree(p);
   s = Scratch{};
 }
 
@@ -209,8 +230,11 @@ sst_status sst_cluster(sst_ctx* ctx, const sst_digis* in, uint32_t n_feds, const
     return set_err(ctx, SST_ERR_INVALID_ARG, "sst_cluster: null pointer");
   if (n_feds == 0 || n_feds > ctx->n_feds)
     return set_err(ctx, SST_ERR_INVALID_ARG, "sst_cluster: n_feds outside 1..context FEDs");
+  if (out->amp && (!out->amp_first || out->amp_capacity == 0 || out->amp_capacity >= kNoAmp))
+    return set_err(ctx, SST_ERR_INVALID_ARG, "sst_cluster: amp needs amp_first and 1 <= amp_capacity < 2^32 - 1");
   DeviceGuard g(ctx->device);
   cudaError_t e = ensure_scratch(ctx->scratch, (size_t)n_feds * kFe, 1, out->capacity);
+  if (!e && out->amp) e = ensure_amp_scratch(ctx->scratch, (size_t)n_feds * kFe, 1, out->amp_capacity);
   if (e) return cuda_err(ctx, e, "sst_cluster scratch");
   e = launch_cluster(*in, n_feds, *out, kparams(ctx), ctx->scratch, ctx->shape, (cudaStream_t)stream);
   return cuda_err(ctx, e, "sst_cluster");
@@ -229,9 +253,13 @@ sst_status sst_batch(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off
     return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch: bad n_events / n_feds");
   if ((uint64_t)n_events * n_feds >= (1ull << 31))
     return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch: too many FED records in one batch");
+  if (out->amp && (!out->amp_first || !out->amp_off || out->amp_capacity == 0 || out->amp_capacity >= kNoAmp))
+    return set_err(ctx, SST_ERR_INVALID_ARG,
+                   "sst_batch: amp needs amp_first, amp_off and 1 <= amp_capacity < 2^32 - 1");
   DeviceGuard g(ctx->device);
   const size_t items = (size_t)n_events * n_feds;
   cudaError_t e = ensure_scratch(ctx->scratch, items * kFe, n_events, out->capacity);
+  if (!e && out->amp) e = ensure_amp_scratch(ctx->scratch, items * kFe, n_events, out->amp_capacity);
   if (e) return cuda_err(ctx, e, "sst_batch scratch");
   cudaEvent_t eb = nullptr, ee = nullptr;
   if (ctx->profiling) {

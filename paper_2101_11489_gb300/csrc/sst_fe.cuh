@@ -307,15 +307,30 @@ __device__ __forceinline__ uint4 pack_cluster(uint32_t det, uint32_t first, uint
   return make_uint4(det, first | (width << 16), charge, __float_as_uint(bary));
 }
 
+// Where a kept cluster's amplitudes go during the write pass: the unit's region of
+// the amplitude staging buffer (null: no amplitudes) and the running position in
+// it (clusters' amplitudes follow each other in strip order).
+struct AmpPos {
+  uint8_t* amp;   // staging slice of the event, or null
+  uint64_t cap;   // bytes in that slice
+  uint64_t pos;   // next free byte of the unit's region
+};
+
 // a5 + a6: one lane per owned candidate walks it from its first strip to the
 // digi before the next candidate start (the right boundary is its last active
 // strip), summing in strip order raw ADC, noise^2 (binary32, left to right),
 // gain-corrected charge and first moment; the candidate is widened over up to
 // max_adj adjacent bad strips; the cluster threshold decides.  Returns the number
-// kept; when `stage` is given the kept clusters are written, in strip order, to
-// stage[base + rank] for base + rank < cap.
+// kept among owners [k_begin, n_own); when `stage` is given the kept clusters are
+// written, in strip order, to stage[base + rank] for base + rank < cap.  With
+// `keep`, the first window's records are returned to the caller instead; with
+// `wsum`, the kept clusters' widths are added to it; with `ap` (write pass), the
+// kept clusters' amplitudes are written at ap->pos onwards: 0 for every strip of
+// the cluster, then the gain-corrected charge of its active strips.
+template <bool AMP>
 __device__ uint32_t form_unit(Warp& w, const KParams& kp, int n, int k_begin, int n_own, uint32_t det0, uint4* stage,
-                              uint64_t cap, uint64_t base, uint4* keep = nullptr, bool* keep_pass = nullptr) {
+                              uint64_t cap, uint64_t base, uint4* keep = nullptr, bool* keep_pass = nullptr,
+                              uint32_t* wsum = nullptr, AmpPos* ap = nullptr) {
   const int lane = threadIdx.x & 31;
   uint32_t kept = 0;
   for (int k0 = k_begin; k0 < n_own; k0 += 32) {
@@ -365,31 +380,62 @@ __device__ uint32_t form_unit(Warp& w, const KParams& kp, int n, int k_begin, in
       const uint64_t pos = base + kept + __popc(b & lanemask_lt(lane));
       if (pos < cap) stage[pos] = pack_cluster(det0 + c, lo, wd, q_sum, bary);
     }
+    if (AMP && wsum) *wsum += __reduce_add_sync(0xffffffffu, pass ? wd : 0u);
+    if (AMP && ap) {
+      // this lane's place among the window's kept clusters' amplitudes
+      const uint32_t x = pass ? wd : 0u;
+      uint32_t incl = x;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+      }
+      const uint64_t a = ap->pos + incl - x;
+      if (pass && ap->amp && a + wd <= ap->cap) {
+        uint8_t* dst = ap->amp + a;
+        for (uint32_t i = 0; i < wd; i++) dst[i] = 0;
+        int j = w.own[k];
+        do {
+          if (w.flag[j] & 1) dst[(w.key[j] & 255u) - lo] = w.q[j];
+          ++j;
+        } while (j < n && (w.key[j] >> 8) == c && !(w.flag[j] & 4));
+      }
+      ap->pos += __shfl_sync(0xffffffffu, incl, 31);
+    }
     kept += __popc(b);
   }
   return kept;
 }
 
 // Where one unit's clusters go: its event's staging slice (records allocated unit
-// by unit with one atomic each) and the unit's segment bookkeeping.
+// by unit with one atomic each) and the unit's segment bookkeeping; the same for
+// its amplitudes when they are wanted (amp non-null).
 struct SegOut {
   uint4* stage;         // the event's slice of the staging buffer
   uint64_t cap;         // records in that slice
   uint32_t* ev_alloc;   // the event's allocation counter
   uint32_t* seg_cnt;    // this unit's cluster count
   uint32_t* seg_start;  // this unit's offset in the slice
+  uint8_t* amp = nullptr;           // the event's slice of the amplitude staging buffer
+  uint64_t amp_cap = 0;             // bytes in that slice
+  uint32_t* amp_alloc = nullptr;    // the event's amplitude allocation counter
+  uint32_t* seg_amp_cnt = nullptr;  // this unit's amplitude count (0 when they did not fit)
+  uint32_t* seg_amp_start = nullptr;  // their offset in the slice, or kNoAmp
 };
 
 // Clusters the `total` digis of one unit (placed in the tile by `fill(c0, c1)`,
 // channel chunk [c0, c1)) and stages its clusters.  The kept clusters are first
 // counted, then their region is allocated in one piece, then they are written; a
-// unit whose digis exceed the tile goes through its channel chunks twice.
-template <typename Fill>
+// unit whose digis exceed the tile goes through its channel chunks twice.  Without
+// amplitudes, the records of the first 32 candidates are kept in registers from
+// the counting pass.  AMP: amplitudes are wanted (so.amp is then non-null).
+template <bool AMP, typename Fill>
 __device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uint32_t det0, uint32_t total,
                              Fill& fill, const SegOut& so, sst_event_status* status) {
   const int lane = threadIdx.x & 31;
   const bool single = total <= (uint32_t)kTile;
-  uint32_t found = 0, found0 = 0;
+  constexpr bool amps = AMP;
+  uint32_t found = 0, found0 = 0, wsum = 0;
   int n = 0, n_own = 0;
   uint4 rec0 = make_uint4(0u, 0u, 0u, 0u);  // this lane's record of the first 32 candidates
   bool pass0 = false;
@@ -401,9 +447,13 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uin
       starts_unit(w, kp, n);
       n_own = owners_unit(w, n);
       if (n_own > 0) {
-        found0 = form_unit(w, kp, n, 0, n_own < 32 ? n_own : 32, det0, nullptr, 0, 0, &rec0, &pass0);
-        found = found0;
-        if (n_own > 32) found += form_unit(w, kp, n, 32, n_own, det0, nullptr, 0, 0);
+        if (amps) {
+          found = form_unit<AMP>(w, kp, n, 0, n_own, det0, nullptr, 0, 0, nullptr, nullptr, &wsum);
+        } else {
+          found0 = form_unit<AMP>(w, kp, n, 0, n_own < 32 ? n_own : 32, det0, nullptr, 0, 0, &rec0, &pass0);
+          found = found0;
+          if (n_own > 32) found += form_unit<AMP>(w, kp, n, 32, n_own, det0, nullptr, 0, 0);
+        }
       }
     }
   } else {
@@ -415,12 +465,12 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uin
         flag_unit(w, kp, noise, nn);
         starts_unit(w, kp, nn);
         const int no = owners_unit(w, nn);
-        if (no > 0) found += form_unit(w, kp, nn, 0, no, det0, nullptr, 0, 0);
+        if (no > 0) found += form_unit<AMP>(w, kp, nn, 0, no, det0, nullptr, 0, 0, nullptr, nullptr, amps ? &wsum : nullptr);
       }
       c0 = c1;
     }
   }
-  uint32_t start = 0;
+  uint32_t start = 0, astart = kNoAmp;
   if (lane == 0) {
     start = found ? atomicAdd(so.ev_alloc, found) : 0u;
     uint32_t fits = 0;
@@ -428,16 +478,34 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uin
     if (fits < found) atomicOr(&status->flags, SST_EV_CLUSTER_CAPACITY);
     *so.seg_cnt = fits;
     *so.seg_start = start;
+    if (amps) {
+      uint32_t acnt = 0;
+      if (wsum) {
+        const uint32_t a = atomicAdd(so.amp_alloc, wsum);
+        if ((uint64_t)a + wsum <= so.amp_cap) {
+          astart = a;
+          acnt = wsum;
+        } else {
+          atomicOr(&status->flags, SST_EV_AMP_CAPACITY);
+        }
+      }
+      *so.seg_amp_cnt = acnt;
+      *so.seg_amp_start = astart;
+    }
   }
   start = __shfl_sync(0xffffffffu, start, 0);
+  astart = __shfl_sync(0xffffffffu, astart, 0);
   if (found == 0) return;
-  if (single) {
+  AmpPos ap{astart != kNoAmp ? so.amp : nullptr, so.amp_cap, astart != kNoAmp ? (uint64_t)astart : 0u};
+  if (single && !amps) {
     const unsigned b = __ballot_sync(0xffffffffu, pass0);
     if (pass0) {
       const uint64_t pos = (uint64_t)start + __popc(b & lanemask_lt(lane));
       if (pos < so.cap) so.stage[pos] = rec0;
     }
-    if (n_own > 32) form_unit(w, kp, n, 32, n_own, det0, so.stage, so.cap, (uint64_t)start + found0);
+    if (n_own > 32) form_unit<AMP>(w, kp, n, 32, n_own, det0, so.stage, so.cap, (uint64_t)start + found0);
+  } else if (single) {
+    form_unit<AMP>(w, kp, n, 0, n_own, det0, so.stage, so.cap, start, nullptr, nullptr, nullptr, &ap);
   } else {
     uint64_t base = start;
     for (int c0 = 0; c0 < kChPerFe;) {
@@ -448,7 +516,9 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uin
         flag_unit(w, kp, noise, nn);
         starts_unit(w, kp, nn);
         const int no = owners_unit(w, nn);
-        if (no > 0) base += form_unit(w, kp, nn, 0, no, det0, so.stage, so.cap, base);
+        if (no > 0)
+          base += form_unit<AMP>(w, kp, nn, 0, no, det0, so.stage, so.cap, base, nullptr, nullptr, nullptr,
+                            amps ? &ap : nullptr);
       }
       c0 = c1;
     }

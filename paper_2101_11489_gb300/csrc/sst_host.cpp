@@ -298,6 +298,8 @@ extern "C" sst_status sst_batch_host(sst_ctx* ctx, const uint8_t* raw, const uin
     return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch_host: null pointer");
   if (n_events == 0 || n_feds == 0 || n_feds > ctx->n_feds)
     return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch_host: bad n_events / n_feds");
+  if (out->amp)
+    return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch_host: amplitudes are produced by sst_batch and sst_cluster");
   for (uint32_t i = 0; i < n_events; i++)
     if (event_off[i + 1] < event_off[i])
       return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch_host: event_off decreases");

@@ -56,7 +56,16 @@ struct Scratch {
   uint4* stage = nullptr;            // staged cluster records (16 bytes each)
   size_t stage_cap = 0;
   uint32_t* tickets = nullptr;       // [16] work counters
+  // optional cluster amplitudes
+  uint8_t* amp_stage = nullptr;      // staged amplitudes, sliced per event like the output
+  size_t amp_stage_cap = 0;
+  uint32_t* amp_alloc = nullptr;     // amplitude allocation counter per event
+  uint32_t* seg_amp_cnt = nullptr;   // amplitudes per (event, FED, FE unit); 0 when they did not fit
+  uint32_t* seg_amp_start = nullptr; // their offset in the event's slice, or kNoAmp
+  uint32_t* seg_amp_dest = nullptr;  // their offset in the event's output slice
+  size_t amp_items_cap = 0, amp_ev_cap = 0;
 };
+constexpr uint32_t kNoAmp = 0xFFFFFFFFu;
 
 size_t smem_bytes(int tile);
 Shape default_shape();
@@ -111,6 +120,7 @@ sst_status set_err(sst_ctx* c, sst_status code, const std::string& msg);
 sst_status cuda_err(sst_ctx* c, cudaError_t e, const char* where);
 KParams kparams(const sst_ctx* c);
 cudaError_t ensure_scratch(Scratch& s, size_t items, size_t events, size_t stage_records);
+cudaError_t ensure_amp_scratch(Scratch& s, size_t items, size_t events, size_t amp_bytes);
 void free_scratch(Scratch& s);
 void free_host_pipe(sst_ctx* ctx);
 

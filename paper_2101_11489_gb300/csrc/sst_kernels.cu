@@ -455,6 +455,29 @@ __device__ int chunk_end(Shm<TILE>& s, int c0) {
 
 // ---------------------------------------------------------------- kernels
 
+// Optional cluster amplitudes: the staging buffer and per-unit bookkeeping
+// (context scratch) and the caller's output arrays; stage == nullptr: none.
+struct AmpArgs {
+  uint8_t* stage = nullptr;       // staged amplitudes, sliced per event like the output
+  const uint64_t* off = nullptr;  // [n_events + 1] event slices (batch), or null (one event at 0)
+  uint64_t cap = 0;               // bytes of staging and of output
+  uint32_t* alloc = nullptr;      // allocation counter per event
+  uint32_t* cnt = nullptr;        // per unit: amplitudes stored (0 when they did not fit)
+  uint32_t* start = nullptr;      // per unit: offset in the event's staging slice, or kNoAmp
+  uint32_t* dest = nullptr;       // per unit: offset in the event's output slice
+  uint8_t* out = nullptr;         // caller's amp
+  uint32_t* first = nullptr;      // caller's amp_first
+};
+
+// The event's slice [a, b) of the amplitude arrays.
+__device__ __forceinline__ void amp_slice(const AmpArgs& am, uint32_t e, uint64_t* a, uint64_t* b) {
+  uint64_t lo = am.off ? am.off[e] : 0, hi = am.off ? am.off[e + 1] : am.cap;
+  if (hi > am.cap) hi = am.cap;
+  if (lo > hi) lo = hi;
+  *a = lo;
+  *b = hi;
+}
+
 // a1, FED level: checks FED `fed`'s header (record at raw + fo, len bytes;
 // fo == kBadOff when the record lies outside its event) and describes its 8 FE
 // units for the batched kernel: d[v] = (byte offset of FE unit v in the record,
@@ -510,7 +533,7 @@ __device__ void describe_fed(const uint8_t* __restrict__ raw, uint64_t fo, uint3
 __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_bytes,
                            const uint32_t* __restrict__ fed_len, uint32_t n_feds, uint64_t* __restrict__ fed_off,
                            sst_event_status* status, uint32_t* ev_alloc, uint32_t* tickets, unsigned long long* lb,
-                           uint32_t n_lb, const uint8_t* __restrict__ raw, uint2* unit_desc) {
+                           uint32_t n_lb, const uint8_t* __restrict__ raw, uint2* unit_desc, uint32_t* amp_alloc) {
   __shared__ uint32_t wsum[32];
   __shared__ uint64_t carry_s;
   const uint32_t e = blockIdx.x;
@@ -520,6 +543,7 @@ __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_
     carry_s = 0;
     status[e] = sst_event_status{0u, 0u, 0u, 0u};
     if (ev_alloc) ev_alloc[e] = 0;
+    if (amp_alloc) amp_alloc[e] = 0;
   }
   if (e == 0 && threadIdx.x < 16) tickets[threadIdx.x] = 0;
   if (lb)
@@ -551,13 +575,13 @@ __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_
 // CTA waits for another) also scans the events' counts: pack_off[e] = clusters
 // of the events before e, pack_off[n_events] = all clusters.
 __global__ void k_clu_scan(const uint32_t* __restrict__ fed_cnt, uint32_t n_feds, uint32_t* __restrict__ fed_dest,
-                           sst_event_status* status, uint64_t* pack_off, uint32_t* done) {
+                           sst_event_status* status, uint64_t* pack_off, uint32_t* done, AmpArgs am) {
   __shared__ uint32_t wsum[32];
-  __shared__ uint32_t carry_s;
+  __shared__ uint32_t carry_s, acarry_s;
   __shared__ uint64_t pcarry_s;
   __shared__ bool last_s;
   const uint32_t e = blockIdx.x;
-  if (threadIdx.x == 0) carry_s = 0;
+  if (threadIdx.x == 0) carry_s = acarry_s = 0;
   __syncthreads();
   for (uint32_t b = 0; b < n_feds; b += blockDim.x) {
     const uint32_t f = b + threadIdx.x;
@@ -569,6 +593,16 @@ __global__ void k_clu_scan(const uint32_t* __restrict__ fed_cnt, uint32_t n_feds
     __syncthreads();
     if (threadIdx.x == 0) carry_s = carry + tot;
     __syncthreads();
+    if (am.stage) {  // the units' amplitude counts, the same way
+      const uint32_t na = f < n_feds ? am.cnt[(size_t)e * n_feds + f] : 0u;
+      uint32_t atot;
+      const uint32_t aex = block_excl_scan(na, wsum, &atot);
+      const uint32_t acarry = acarry_s;
+      if (f < n_feds) am.dest[(size_t)e * n_feds + f] = acarry + aex;
+      __syncthreads();
+      if (threadIdx.x == 0) acarry_s = acarry + atot;
+      __syncthreads();
+    }
   }
   if (threadIdx.x == 0) status[e].n_clusters = carry_s;
   if (!pack_off) return;
@@ -601,30 +635,75 @@ __global__ void k_clu_scan(const uint32_t* __restrict__ fed_cnt, uint32_t n_feds
 // a6, output: copies every segment's staged clusters (one segment per FE unit)
 // to its place in the event's sorted cluster SoA, one warp per segment (16-byte
 // loads, coalesced stores).  The event's clusters start at clu_off[e] (its slice),
-// or at pack_off[e] when pack_off is given (events packed back to back).
+// or at pack_off[e] when pack_off is given (events packed back to back).  With
+// amplitudes, each cluster's amp_first is the segment's output offset plus the
+// widths of the segment's clusters before it, and the segment's amplitude bytes
+// are copied after its clusters.
+template <bool AMP>
 __global__ void __launch_bounds__(256) k_compact(const uint4* __restrict__ stage, const uint64_t* __restrict__ clu_off,
                                                  const uint64_t* __restrict__ pack_off,
                                                  const uint32_t* __restrict__ seg_cnt,
                                                  const uint32_t* __restrict__ seg_start,
                                                  const uint32_t* __restrict__ seg_dest, uint32_t n_events,
-                                                 uint32_t n_segs, sst_clusters out) {
+                                                 uint32_t n_segs, sst_clusters out, AmpArgs am) {
   const uint64_t items = (uint64_t)n_events * n_segs;
   const uint64_t it = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (it >= items) return;
   const uint32_t n = seg_cnt[it];
   if (n == 0) return;
+  const int lane = threadIdx.x & 31;
   const uint32_t e = (uint32_t)(it / n_segs);
   const uint64_t off = clu_off ? clu_off[e] : 0;
   const uint4* src = stage + off + seg_start[it];
   const uint64_t dst = (pack_off ? pack_off[e] : off) + seg_dest[it];
-  for (uint32_t k = threadIdx.x & 31; k < n; k += 32) {
-    const uint4 r = __ldg(src + k);
-    const uint64_t o = dst + k;
-    out.det[o] = r.x;
-    out.first[o] = (uint16_t)(r.y & 0xFFFFu);
-    out.width[o] = (uint16_t)(r.y >> 16);
-    out.charge[o] = r.z;
-    out.barycenter[o] = __uint_as_float(r.w);
+  if (!AMP) {
+    for (uint32_t k = lane; k < n; k += 32) {
+      const uint4 r = __ldg(src + k);
+      const uint64_t o = dst + k;
+      out.det[o] = r.x;
+      out.first[o] = (uint16_t)(r.y & 0xFFFFu);
+      out.width[o] = (uint16_t)(r.y >> 16);
+      out.charge[o] = r.z;
+      out.barycenter[o] = __uint_as_float(r.w);
+    }
+    return;
+  }
+  uint64_t a0 = 0, a1 = 0, acarry = 0;
+  bool amps = false;
+  {
+    amp_slice(am, e, &a0, &a1);
+    amps = am.start[it] != kNoAmp;
+    acarry = a0 + am.dest[it];
+  }
+  for (uint32_t k0 = 0; k0 < n; k0 += 32) {
+    const uint32_t k = k0 + lane;
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
+    if (k < n) {
+      r = __ldg(src + k);
+      const uint64_t o = dst + k;
+      out.det[o] = r.x;
+      out.first[o] = (uint16_t)(r.y & 0xFFFFu);
+      out.width[o] = (uint16_t)(r.y >> 16);
+      out.charge[o] = r.z;
+      out.barycenter[o] = __uint_as_float(r.w);
+    }
+    {
+      const uint32_t x = k < n ? (r.y >> 16) : 0u;
+      uint32_t incl = x;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+      }
+      if (k < n) am.first[dst + k] = amps ? (uint32_t)(acarry + incl - x) : kNoAmp;
+      acarry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+  if (amps) {
+    const uint32_t na = am.cnt[it];
+    const uint8_t* as = am.stage + a0 + am.start[it];
+    uint8_t* ad = am.out + a0 + am.dest[it];
+    for (uint32_t i = lane; i < na; i += 32) ad[i] = as[i];
   }
 }
 
@@ -707,9 +786,10 @@ __global__ void __launch_bounds__(256, 4) k_unpack(const uint8_t* __restrict__ r
 
 // a3 - a6 per event: one warp per FE unit over the global digi SoA; clusters
 // staged per unit.
+template <bool AMP>
 __global__ void __launch_bounds__(256, 4) k_cluster(sst_digis in, uint32_t n_feds, KParams kp, uint4* stage,
                                                     uint64_t cap, uint32_t* ev_alloc, uint32_t* seg_cnt,
-                                                    uint32_t* seg_start) {
+                                                    uint32_t* seg_start, AmpArgs am) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   fe::Warp& w = reinterpret_cast<fe::Warp*>(smem_raw)[warp];
@@ -754,14 +834,22 @@ __global__ void __launch_bounds__(256, 4) k_cluster(sst_digis in, uint32_t n_fed
     }
     __syncwarp();
   };
-  const fe::SegOut so{stage, cap, ev_alloc, seg_cnt + unit, seg_start + unit};
-  fe::cluster_unit(w, kp, kp.noise + (size_t)g0, ch0, total, fill, so, in.status);
+  fe::SegOut so{stage, cap, ev_alloc, seg_cnt + unit, seg_start + unit};
+  if (AMP) {
+    so.amp = am.stage;
+    so.amp_cap = am.cap;
+    so.amp_alloc = am.alloc;
+    so.seg_amp_cnt = am.cnt + unit;
+    so.seg_amp_start = am.start + unit;
+  }
+  fe::cluster_unit<AMP>(w, kp, kp.noise + (size_t)g0, ch0, total, fill, so, in.status);
 }
 
 // a7: every FE unit of every FED of every event of a batch, unpacked and
 // clustered on chip, one warp per unit.  Persistent warps take tickets
 // FED-major (FED, then event, then FE unit), so that the warps working at any
 // moment share the same FED's calibration in L2.
+template <bool AMP>
 __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ raw,
                                                   const uint32_t* __restrict__ fed_len,
                                                   const uint64_t* __restrict__ fed_off, uint32_t n_events,
@@ -769,7 +857,7 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
                                                   uint64_t out_cap, sst_event_status* status, KParams kp,
                                                   uint4* stage, uint32_t* ev_alloc, uint32_t* seg_cnt,
                                                   uint32_t* seg_start, uint32_t* ticket,
-                                                  const uint2* __restrict__ unit_desc) {
+                                                  const uint2* __restrict__ unit_desc, AmpArgs am) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   fe::Warp& w = reinterpret_cast<fe::Warp*>(smem_raw)[warp];
@@ -797,10 +885,19 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
     const uint64_t off = clu_off[e];
     const uint64_t end = clu_off[e + 1] < out_cap ? clu_off[e + 1] : out_cap;
     const uint64_t cap = end > off ? end - off : 0;
-    const fe::SegOut so{stage + (off < out_cap ? off : 0), cap, ev_alloc + e, seg_cnt + item * kFe + u,
-                        seg_start + item * kFe + u};
+    fe::SegOut so{stage + (off < out_cap ? off : 0), cap, ev_alloc + e, seg_cnt + item * kFe + u,
+                  seg_start + item * kFe + u};
+    if (AMP) {
+      uint64_t a0, a1;
+      amp_slice(am, e, &a0, &a1);
+      so.amp = am.stage + a0;
+      so.amp_cap = a1 - a0;
+      so.amp_alloc = am.alloc + e;
+      so.seg_amp_cnt = am.cnt + item * kFe + u;
+      so.seg_amp_start = am.start + item * kFe + u;
+    }
     auto fill = [&](int c0, int c1) { fe::copy_runs(w, un, c0, c1); };
-    fe::cluster_unit(w, kp, kp.noise + (size_t)ch0 * kStrips, ch0, total, fill, so, &status[e]);
+    fe::cluster_unit<AMP>(w, kp, kp.noise + (size_t)ch0 * kStrips, ch0, total, fill, so, &status[e]);
     __syncwarp();
   }
 }
@@ -874,37 +971,64 @@ cudaError_t launch_unpack_t(const uint8_t* raw, const uint32_t* fed_len, uint32_
   return cudaGetLastError();
 }
 
+// The amplitude arguments of a launch: none unless the caller asked for them.
+AmpArgs amp_args(const sst_clusters& out, const Scratch& s) {
+  AmpArgs a;
+  if (!out.amp) return a;
+  a.stage = s.amp_stage;
+  a.off = out.amp_off;
+  a.cap = out.amp_capacity;
+  a.alloc = s.amp_alloc;
+  a.cnt = s.seg_amp_cnt;
+  a.start = s.seg_amp_start;
+  a.dest = s.seg_amp_dest;
+  a.out = out.amp;
+  a.first = out.amp_first;
+  return a;
+}
+
 cudaError_t launch_cluster_fe(const sst_digis& in, uint32_t n_feds, const KParams& kp, const Scratch& s,
-                              uint64_t cap, const Shape& sh, cudaStream_t st) {
+                              uint64_t cap, const Shape& sh, const AmpArgs& am, cudaStream_t st) {
   const int nw = sh.block / 32;
   const size_t sm = sizeof(fe::Warp) * nw;
   int per_sm = 0;
-  cudaError_t e = prepare((const void*)k_cluster, sh.block, sm, &per_sm);
+  const void* fn = am.stage ? (const void*)k_cluster<true> : (const void*)k_cluster<false>;
+  cudaError_t e = prepare(fn, sh.block, sm, &per_sm);
   if (e) return e;
   const uint32_t units = n_feds * kFe;
-  k_cluster<<<(units + nw - 1) / nw, sh.block, sm, st>>>(in, n_feds, kp, s.stage, cap, s.ev_alloc, s.fed_cnt,
-                                                       s.fed_start);
+  if (am.stage)
+    k_cluster<true><<<(units + nw - 1) / nw, sh.block, sm, st>>>(in, n_feds, kp, s.stage, cap, s.ev_alloc, s.fed_cnt,
+                                                               s.fed_start, am);
+  else
+    k_cluster<false><<<(units + nw - 1) / nw, sh.block, sm, st>>>(in, n_feds, kp, s.stage, cap, s.ev_alloc,
+                                                                s.fed_cnt, s.fed_start, am);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batch_fe(const uint8_t* raw, const uint32_t* fed_len, uint32_t n_events, uint32_t n_feds,
                             const uint64_t* clu_off, uint64_t out_cap, sst_event_status* status, const KParams& kp,
-                            const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st, cudaEvent_t ev_begin,
-                            cudaEvent_t ev_end) {
+                            const Scratch& s, const Shape& sh, int n_sm, const AmpArgs& am, cudaStream_t st,
+                            cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   const int nw = sh.block / 32;
   const size_t sm = sizeof(fe::Warp) * nw;
   const size_t units = (size_t)n_events * n_feds * kFe;
   int per_sm = 0;
-  cudaError_t e = prepare((const void*)k_batch, sh.block, sm, &per_sm);
+  const void* fn = am.stage ? (const void*)k_batch<true> : (const void*)k_batch<false>;
+  cudaError_t e = prepare(fn, sh.block, sm, &per_sm);
   if (e) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const size_t ctas = (size_t)n_sm * (sh.ctas_per_sm < per_sm ? sh.ctas_per_sm : per_sm);
   const size_t need = (units + nw - 1) / nw;
   const int grid = (int)(ctas < need ? ctas : need);
   if (ev_begin && (e = cudaEventRecord(ev_begin, st))) return e;
-  k_batch<<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out_cap, status, kp,
-                                      s.stage, s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets,
-                                      s.unit_desc);
+  if (am.stage)
+    k_batch<true><<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out_cap, status, kp,
+                                              s.stage, s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets, s.unit_desc,
+                                              am);
+  else
+    k_batch<false><<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out_cap, status,
+                                               kp, s.stage, s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets,
+                                               s.unit_desc, am);
   if ((e = cudaGetLastError())) return e;
   if (ev_end && (e = cudaEventRecord(ev_end, st))) return e;
   return cudaSuccess;
@@ -912,13 +1036,18 @@ cudaError_t launch_batch_fe(const uint8_t* raw, const uint32_t* fed_len, uint32_
 
 // Per-event cluster order and the copy into the caller's SoA.
 cudaError_t launch_order(const uint64_t* clu_off, uint32_t n_events, uint32_t n_segs, const sst_clusters& out,
-                         sst_event_status* status, const Scratch& s, uint64_t* pack_off, cudaStream_t st) {
-  k_clu_scan<<<n_events, 256, 0, st>>>(s.fed_cnt, n_segs, s.fed_dest, status, pack_off, s.tickets + 1);
+                         sst_event_status* status, const Scratch& s, uint64_t* pack_off, const AmpArgs& am,
+                         cudaStream_t st) {
+  k_clu_scan<<<n_events, 256, 0, st>>>(s.fed_cnt, n_segs, s.fed_dest, status, pack_off, s.tickets + 1, am);
   cudaError_t e = cudaGetLastError();
   if (e) return e;
   const uint64_t items = (uint64_t)n_events * n_segs;
-  k_compact<<<(unsigned)((items + 7) / 8), 256, 0, st>>>(s.stage, clu_off, pack_off, s.fed_cnt, s.fed_start,
-                                                        s.fed_dest, n_events, n_segs, out);
+  if (am.stage)
+    k_compact<true><<<(unsigned)((items + 7) / 8), 256, 0, st>>>(s.stage, clu_off, pack_off, s.fed_cnt, s.fed_start,
+                                                                s.fed_dest, n_events, n_segs, out, am);
+  else
+    k_compact<false><<<(unsigned)((items + 7) / 8), 256, 0, st>>>(s.stage, clu_off, pack_off, s.fed_cnt,
+                                                                 s.fed_start, s.fed_dest, n_events, n_segs, out, am);
   return cudaGetLastError();
 }
 
@@ -948,7 +1077,7 @@ cudaError_t launch_unpack(const uint8_t* raw, uint64_t raw_bytes, const uint32_t
                           const sst_digis& out, const Scratch& s, const Shape& sh, cudaStream_t st) {
   cudaError_t e;
   k_fed_scan<<<1, 256, 0, st>>>(nullptr, raw_bytes, fed_len, n_feds, s.fed_off, out.status, nullptr, s.tickets, s.lb,
-                                n_feds, nullptr, nullptr);
+                                n_feds, nullptr, nullptr, nullptr);
   if ((e = cudaGetLastError())) return e;
   switch (sh.tile) {
     case 1024: return launch_unpack_t<1024>(raw, fed_len, n_feds, out, s, sh, st);
@@ -961,9 +1090,11 @@ cudaError_t launch_unpack(const uint8_t* raw, uint64_t raw_bytes, const uint32_t
 cudaError_t launch_cluster(const sst_digis& in, uint32_t n_feds, const sst_clusters& out, const KParams& kp,
                            const Scratch& s, const Shape& sh, cudaStream_t st) {
   cudaError_t e;
+  const AmpArgs am = amp_args(out, s);
   if ((e = cudaMemsetAsync(s.ev_alloc, 0, sizeof(uint32_t), st))) return e;
-  if ((e = launch_cluster_fe(in, n_feds, kp, s, out.capacity, sh, st))) return e;
-  return launch_order(nullptr, 1, n_feds * kFe, out, in.status, s, nullptr, st);  // one event at offset 0
+  if (am.stage && (e = cudaMemsetAsync(s.amp_alloc, 0, sizeof(uint32_t), st))) return e;
+  if ((e = launch_cluster_fe(in, n_feds, kp, s, out.capacity, sh, am, st))) return e;
+  return launch_order(nullptr, 1, n_feds * kFe, out, in.status, s, nullptr, am, st);  // one event at offset 0
 }
 
 cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len, uint32_t n_events,
@@ -971,13 +1102,14 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
                          const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st,
                          uint64_t* pack_off, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   cudaError_t e;
+  const AmpArgs am = amp_args(out, s);
   k_fed_scan<<<n_events, 256, 0, st>>>(event_off, 0, fed_len, n_feds, s.fed_off, status, s.ev_alloc, s.tickets,
-                                       nullptr, 0, raw, s.unit_desc);
+                                       nullptr, 0, raw, s.unit_desc, am.stage ? s.amp_alloc : nullptr);
   if ((e = cudaGetLastError())) return e;
-  e = launch_batch_fe(raw, fed_len, n_events, n_feds, clu_off, out.capacity, status, kp, s, sh, n_sm, st, ev_begin,
-                      ev_end);
+  e = launch_batch_fe(raw, fed_len, n_events, n_feds, clu_off, out.capacity, status, kp, s, sh, n_sm, am, st,
+                      ev_begin, ev_end);
   if (e) return e;
-  return launch_order(clu_off, n_events, n_feds * kFe, out, status, s, pack_off, st);
+  return launch_order(clu_off, n_events, n_feds * kFe, out, status, s, pack_off, am, st);
 }
 
 cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st) {
