@@ -568,14 +568,16 @@ __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_
   if (threadIdx.x == 0 && ev0 + carry_s != ev1) atomicOr(&status[e].flags, SST_EV_SIZE);
 }
 
-// a6, ordering: per event, the exclusive scan of its FEDs' cluster counts gives
-// every FED's position in the event's sorted cluster SoA; the event's total is its
-// cluster count.  One CTA per event.  With pack_off (events packed back to back),
+// a6, ordering: per event, the exclusive scan of its FE units' cluster counts
+// gives every unit's position in the event's sorted cluster SoA; the event's total
+// is its cluster count.  One CTA of 1024 threads per event (3,520 units of a full
+// event in four block scans).  With pack_off (events packed back to back),
 // the CTA that finishes last (counted in *done, which the prologue cleared; no
 // CTA waits for another) also scans the events' counts: pack_off[e] = clusters
 // of the events before e, pack_off[n_events] = all clusters.
-__global__ void k_clu_scan(const uint32_t* __restrict__ fed_cnt, uint32_t n_feds, uint32_t* __restrict__ fed_dest,
-                           sst_event_status* status, uint64_t* pack_off, uint32_t* done, AmpArgs am) {
+__global__ void __launch_bounds__(1024) k_clu_scan(const uint32_t* __restrict__ fed_cnt, uint32_t n_feds,
+                                                   uint32_t* __restrict__ fed_dest, sst_event_status* status,
+                                                   uint64_t* pack_off, uint32_t* done, AmpArgs am) {
   __shared__ uint32_t wsum[32];
   __shared__ uint32_t carry_s, acarry_s;
   __shared__ uint64_t pcarry_s;
@@ -1038,7 +1040,7 @@ cudaError_t launch_batch_fe(const uint8_t* raw, const uint32_t* fed_len, uint32_
 cudaError_t launch_order(const uint64_t* clu_off, uint32_t n_events, uint32_t n_segs, const sst_clusters& out,
                          sst_event_status* status, const Scratch& s, uint64_t* pack_off, const AmpArgs& am,
                          cudaStream_t st) {
-  k_clu_scan<<<n_events, 256, 0, st>>>(s.fed_cnt, n_segs, s.fed_dest, status, pack_off, s.tickets + 1, am);
+  k_clu_scan<<<n_events, 1024, 0, st>>>(s.fed_cnt, n_segs, s.fed_dest, status, pack_off, s.tickets + 1, am);
   cudaError_t e = cudaGetLastError();
   if (e) return e;
   const uint64_t items = (uint64_t)n_events * n_segs;
