@@ -1,12 +1,16 @@
-// sst_fe.cuh -- warp-level unpacking and clustering of one FE unit (12 channels of
-// one FED), the work unit of the batched and per-event cluster kernels.
+// sst_fe.cuh -- warp-level unpacking and clustering of two adjacent FE units (24
+// consecutive channels of one FED), the work item of the batched and per-event
+// cluster kernels.
 //
-// A FE unit is independent of every other: its channel records sit back to back in
-// the FED record, and clusters never cross a channel (arXiv 2101.11489, section 2:
-// channel = module of 256 strips).  One warp handles one FE unit from the raw bytes
-// to staged clusters with no block-wide barrier, so that a GB300 SM keeps dozens of
-// independent units in flight and hides the latency of each unit's serial steps
-// (the FE length chain, the run chains, the L2 gathers of noise).
+// FE units are independent of one another: their channel records sit back to back
+// in the FED record, and clusters never cross a channel (arXiv 2101.11489, section
+// 2: channel = module of 256 strips).  One warp handles one work item from the raw
+// bytes to staged clusters with no block-wide barrier, so that a GB300 SM keeps
+// dozens of independent items in flight and hides the latency of each item's
+// serial steps (the FE length chains, the run chains, the L2 gathers of noise).
+// Two FE units per warp rather than one: the serial per-channel steps (length
+// chains, run walks) then occupy 24 lanes instead of 12, and the fixed cost of an
+// item is paid once per pair.
 //
 // Included by sst_kernels.cu only, inside its namespace, after the mask and
 // gap helpers it uses (bit, count_range, linked_gap).
@@ -15,20 +19,21 @@
 namespace fe {
 
 constexpr int kTile = 384;    // digis per warp tile (a chunk of whole channels)
-constexpr int kBuf = 1024;    // FE-unit bytes staged per warp (larger units are read in place)
-constexpr int kFeStrips = kChPerFe * kStrips;  // 3,072
+constexpr int kBuf = 1536;    // bytes of the two FE units staged per warp (larger pairs are read in place)
+constexpr int kUnits = 2;     // FE units per work item: two adjacent units of one FED
+constexpr int kChW = kUnits * kChPerFe;  // 24 consecutive channels per work item
 
 // Per-warp shared memory.
 struct __align__(16) Warp {
-  uint8_t fe[kBuf];                      // staged FE-unit bytes
-  uint32_t bad[kChPerFe * kMaskWords];   // bad-strip masks of the 12 channels
-  float gain[kChPerFe * 2];              // APV gains of the 12 channels
+  uint8_t fe[kBuf];                      // staged bytes of the two FE units
+  uint32_t bad[kChW * kMaskWords];       // bad-strip masks of the 24 channels
+  float gain[kChW * 2];                  // APV gains of the 24 channels
   float nsq[kTile];                      // noise^2 of active digis
-  uint32_t chan_pos[kChPerFe];           // channel record offset within the FE unit
-  uint32_t chan_cnt[kChPerFe + 1];       // digis per channel, then exclusive prefix
-  uint16_t chan_len[kChPerFe];
-  uint8_t chan_st[kChPerFe];
-  uint16_t key[kTile];                   // (channel in FE unit << 8) | strip, sorted
+  uint32_t chan_pos[kChW];               // channel record offset from the first unit's start
+  uint32_t chan_cnt[kChW + 1];           // digis per channel, then exclusive prefix
+  uint16_t chan_len[kChW];
+  uint8_t chan_st[kChW];
+  uint16_t key[kTile];                   // (channel in the work item << 8) | strip, sorted
   uint16_t own[kTile];                   // first digi of every seeded candidate
   uint8_t adc[kTile];
   uint8_t flag[kTile];                   // 1 active, 2 seed, 4 first strip of a candidate
@@ -42,37 +47,41 @@ __device__ __forceinline__ uint32_t byte_at(uint32_t v, int b) { return __shfl_s
 __device__ __forceinline__ uint32_t u16_at(uint32_t v, int b) { return byte_at(v, b) | (byte_at(v, b + 1) << 8); }
 __device__ __forceinline__ uint32_t u32_at(uint32_t v, int b) { return u16_at(v, b) | (u16_at(v, b + 2) << 16); }
 
-// Where the FE unit is and what the FED header says about it.
+// Where the work item's two FE units are and what the FED header says about them.
 struct Unit {
-  uint32_t fed, u;         // FED index, FE unit (0..7)
-  const uint8_t* src;      // first byte of the FE unit's records (shared or global), or null
-  uint32_t len;            // bytes of channel records in the FE unit
+  uint32_t fed, u;         // FED index, first FE unit (0, 2, 4, 6)
+  const uint8_t* src;      // first byte of the first unit's records (shared or global), or null
+  uint32_t off1;           // byte offset of the second unit's records from src
+  uint32_t len;            // bytes of the first unit's records
+  uint32_t len1;           // bytes of the second unit's records
   uint8_t fed_status;      // SST_CH_FED_HDR when the FED record is corrupt or out of range, else 0
 };
 
-// a1 + a2 for one FE unit: lane 0 walks the 12 channel lengths (the location
-// map); lanes 0..11 then validate their channel's runs and count its digis; the
-// counts are prefix-summed.  A broken length chain invalidates all 12 channels.
-// Returns the unit's digi count; *flags / *nbad receive the OR of the channel
-// statuses and the number of bad channels.
+// a1 + a2 for the two FE units: lanes 0 and 16 each walk one unit's 12 channel
+// lengths (the location map); lanes 0..23 then validate their channel's runs and
+// count its digis; the counts are prefix-summed.  A broken length chain
+// invalidates the 12 channels of its unit.  Returns the digi count; *flags /
+// *nbad receive the OR of the channel statuses and the number of bad channels.
 __device__ uint32_t parse_unit(Warp& w, const Unit& un, uint32_t* flags, uint32_t* nbad) {
   const int lane = threadIdx.x & 31;
-  if (lane == 0) {
+  if ((lane & 15) == 0) {
+    const int h = lane >> 4;
+    const uint32_t base = h ? un.off1 : 0u;
+    const uint32_t end = h ? un.len1 : un.len;
     bool good = un.src != nullptr;
     uint32_t p = 0;
-    const uint32_t end = un.len;
     for (int k = 0; k < kChPerFe; k++) {
       uint32_t l = 0;
       if (good) {
         if (p + 2 > end) {
           good = false;
         } else {
-          l = (uint32_t)un.src[p] | ((uint32_t)un.src[p + 1] << 8);
+          l = (uint32_t)un.src[base + p] | ((uint32_t)un.src[base + p + 1] << 8);
           if (l < 3 || p + l > end) good = false;
         }
       }
-      w.chan_pos[k] = good ? p : 0u;
-      w.chan_len[k] = good ? (uint16_t)l : (uint16_t)0;
+      w.chan_pos[h * kChPerFe + k] = good ? base + p : 0u;
+      w.chan_len[h * kChPerFe + k] = good ? (uint16_t)l : (uint16_t)0;
       if (good) p += l;
     }
     if (good && p != end) good = false;
@@ -82,14 +91,14 @@ __device__ uint32_t parse_unit(Warp& w, const Unit& un, uint32_t* flags, uint32_
     else if (!good)
       st = SST_CH_FRAMING;
     for (int k = 0; k < kChPerFe; k++) {
-      w.chan_st[k] = st;
-      if (st) w.chan_len[k] = 0;
+      w.chan_st[h * kChPerFe + k] = st;
+      if (st) w.chan_len[h * kChPerFe + k] = 0;
     }
   }
   __syncwarp();
   uint32_t cnt = 0;
   uint8_t st = 0;
-  if (lane < kChPerFe) {
+  if (lane < kChW) {
     st = w.chan_st[lane];
     const uint32_t len_c = w.chan_len[lane];
     if (st == 0 && len_c >= 3) {
@@ -115,23 +124,24 @@ __device__ uint32_t parse_unit(Warp& w, const Unit& un, uint32_t* flags, uint32_
   }
   uint32_t x = cnt;
 #pragma unroll
-  for (int d = 1; d < 16; d <<= 1) {
+  for (int d = 1; d < 32; d <<= 1) {
     const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
     if (lane >= d) x += y;
   }
-  if (lane < kChPerFe) w.chan_cnt[lane] = x - cnt;
-  const uint32_t total = __shfl_sync(0xffffffffu, x, kChPerFe - 1);
-  if (lane == 0) w.chan_cnt[kChPerFe] = total;
-  *flags = __reduce_or_sync(0xffffffffu, lane < kChPerFe ? (uint32_t)st : 0u);
-  *nbad = __popc(__ballot_sync(0xffffffffu, lane < kChPerFe && st != 0));
+  if (lane < kChW) w.chan_cnt[lane] = x - cnt;
+  const uint32_t total = __shfl_sync(0xffffffffu, x, kChW - 1);
+  if (lane == 0) w.chan_cnt[kChW] = total;
+  *flags = __reduce_or_sync(0xffffffffu, lane < kChW ? (uint32_t)st : 0u);
+  *nbad = __popc(__ballot_sync(0xffffffffu, lane < kChW && st != 0));
   __syncwarp();
   return total;
 }
 
 // Greedy chunk of whole channels [c0, c1) with at most kTile digis.
+template <int NCH>
 __device__ __forceinline__ int chunk_end(const Warp& w, int c0) {
   int c1 = c0 + 1;
-  while (c1 < kChPerFe && w.chan_cnt[c1 + 1] - w.chan_cnt[c0] <= (uint32_t)kTile) ++c1;
+  while (c1 < NCH && w.chan_cnt[c1 + 1] - w.chan_cnt[c0] <= (uint32_t)kTile) ++c1;
   return c1;
 }
 
@@ -162,7 +172,7 @@ __device__ void copy_runs(Warp& w, const Unit& un, int c0, int c1) {
       const uint32_t first = r[p], wd0 = r[p + 1];
       const uint32_t wd = wd0 < left ? wd0 : left;
       if (wd > 0) {
-        desc[o] = ((pos + p + 2) << 12) | (first << 4) | (uint32_t)c;
+        desc[o] = ((pos + p + 2) << 13) | (first << 5) | (uint32_t)c;
         w.flag[o] = 1;
       }
       o += wd;
@@ -180,9 +190,9 @@ __device__ void copy_runs(Warp& w, const Unit& un, int c0, int c1) {
     if (i < n) {
       const uint32_t d = desc[s];
       const uint32_t k = (uint32_t)(i - s);
-      w.key[i] = (uint16_t)(((d & 15u) << 8) | ((((d >> 4) & 255u) + k) & 255u));
-      const uint32_t b = (d >> 12) + k;
-      w.adc[i] = b < un.len ? un.src[b] : (uint8_t)0;
+      w.key[i] = (uint16_t)(((d & 31u) << 8) | ((((d >> 5) & 255u) + k) & 255u));
+      const uint32_t b = (d >> 13) + k;
+      w.adc[i] = b < un.off1 + un.len1 ? un.src[b] : (uint8_t)0;
     }
     if (m) carry = base + 31 - __clz(m);
   }
@@ -192,10 +202,11 @@ __device__ void copy_runs(Warp& w, const Unit& un, int c0, int c1) {
 // a3 for the n digis of the tile, one lane per digi, two noise loads in flight:
 // the channel and seed thresholds (binary32 product threshold x noise, strict
 // "larger than"), the gain-corrected charge and noise^2 of active digis.
+template <int NCH>
 __device__ __forceinline__ void flag_one(Warp& w, const KParams& kp, int i, float nz) {
   const uint32_t key = w.key[i];
   const uint32_t c = key >> 8, st = key & 255u;
-  if (c >= (uint32_t)kChPerFe) {  // a digi that takes no part in clustering
+  if (c >= (uint32_t)NCH) {  // a digi that takes no part in clustering
     w.flag[i] = 0;
     w.q[i] = 0;
     w.nsq[i] = 0.f;
@@ -223,15 +234,16 @@ __device__ __forceinline__ void flag_one(Warp& w, const KParams& kp, int i, floa
   w.nsq[i] = nsq;
 }
 
+template <int NCH>
 __device__ void flag_unit(Warp& w, const KParams& kp, const float* noise, int n) {
   const int lane = threadIdx.x & 31;
   for (int i0 = lane; i0 < n; i0 += 64) {
     const int i1 = i0 + 32;
     const uint32_t k0 = w.key[i0], k1 = i1 < n ? w.key[i1] : k0;
-    const float nz0 = __ldg(noise + (k0 >> 8 < (uint32_t)kChPerFe ? k0 : 0u));
-    const float nz1 = __ldg(noise + (k1 >> 8 < (uint32_t)kChPerFe ? k1 : 0u));
-    flag_one(w, kp, i0, nz0);
-    if (i1 < n) flag_one(w, kp, i1, nz1);
+    const float nz0 = __ldg(noise + (k0 >> 8 < (uint32_t)NCH ? k0 : 0u));
+    const float nz1 = __ldg(noise + (k1 >> 8 < (uint32_t)NCH ? k1 : 0u));
+    flag_one<NCH>(w, kp, i0, nz0);
+    if (i1 < n) flag_one<NCH>(w, kp, i1, nz1);
   }
   __syncwarp();
 }
@@ -428,8 +440,9 @@ struct SegOut {
 // counted, then their region is allocated in one piece, then they are written; a
 // unit whose digis exceed the tile goes through its channel chunks twice.  Without
 // amplitudes, the records of the first 32 candidates are kept in registers from
-// the counting pass.  AMP: amplitudes are wanted (so.amp is then non-null).
-template <bool AMP, typename Fill>
+// the counting pass.  NCH: channels of the work item (12 or 24); AMP: amplitudes
+// are wanted (so.amp is then non-null).
+template <int NCH, bool AMP, typename Fill>
 __device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uint32_t det0, uint32_t total,
                              Fill& fill, const SegOut& so, sst_event_status* status) {
   const int lane = threadIdx.x & 31;
@@ -442,8 +455,8 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uin
   if (single) {
     n = (int)total;
     if (n > 0) {
-      fill(0, kChPerFe);
-      flag_unit(w, kp, noise, n);
+      fill(0, NCH);
+      flag_unit<NCH>(w, kp, noise, n);
       starts_unit(w, kp, n);
       n_own = owners_unit(w, n);
       if (n_own > 0) {
@@ -457,12 +470,12 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uin
       }
     }
   } else {
-    for (int c0 = 0; c0 < kChPerFe;) {
-      const int c1 = chunk_end(w, c0);
+    for (int c0 = 0; c0 < NCH;) {
+      const int c1 = chunk_end<NCH>(w, c0);
       const int nn = (int)(w.chan_cnt[c1] - w.chan_cnt[c0]);
       if (nn > 0) {
         fill(c0, c1);
-        flag_unit(w, kp, noise, nn);
+        flag_unit<NCH>(w, kp, noise, nn);
         starts_unit(w, kp, nn);
         const int no = owners_unit(w, nn);
         if (no > 0) found += form_unit<AMP>(w, kp, nn, 0, no, det0, nullptr, 0, 0, nullptr, nullptr, amps ? &wsum : nullptr);
@@ -508,12 +521,12 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uin
     form_unit<AMP>(w, kp, n, 0, n_own, det0, so.stage, so.cap, start, nullptr, nullptr, nullptr, &ap);
   } else {
     uint64_t base = start;
-    for (int c0 = 0; c0 < kChPerFe;) {
-      const int c1 = chunk_end(w, c0);
+    for (int c0 = 0; c0 < NCH;) {
+      const int c1 = chunk_end<NCH>(w, c0);
       const int nn = (int)(w.chan_cnt[c1] - w.chan_cnt[c0]);
       if (nn > 0) {
         fill(c0, c1);
-        flag_unit(w, kp, noise, nn);
+        flag_unit<NCH>(w, kp, noise, nn);
         starts_unit(w, kp, nn);
         const int no = owners_unit(w, nn);
         if (no > 0)
@@ -525,36 +538,42 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uin
   }
 }
 
-// Loads the bad-strip masks (96 words) and APV gains (24 floats) of channels
-// ch0 .. ch0 + 11: one 16-byte load per lane (both tables start on a 16-byte
-// boundary: ch0 is a multiple of 12).
+// Loads the bad-strip masks (8 words per channel) and APV gains (2 per channel)
+// of channels ch0 .. ch0 + NCH - 1 with 16-byte loads (both tables start on a
+// 16-byte boundary: ch0 is a multiple of 12).
+template <int NCH>
 __device__ __forceinline__ void load_calib(Warp& w, const KParams& kp, uint32_t ch0) {
   const int lane = threadIdx.x & 31;
-  if (lane < 24)
-    reinterpret_cast<uint4*>(w.bad)[lane] =
-        __ldg(reinterpret_cast<const uint4*>(kp.badmask + (size_t)ch0 * kMaskWords) + lane);
-  else if (lane < 30)
-    reinterpret_cast<uint4*>(w.gain)[lane - 24] =
-        __ldg(reinterpret_cast<const uint4*>(kp.gain + (size_t)ch0 * 2) + (lane - 24));
+  constexpr int kB = NCH * kMaskWords / 4, kG = NCH * 2 / 4;  // vectors of masks, of gains
+  for (int i = lane; i < kB + kG; i += 32) {
+    if (i < kB)
+      reinterpret_cast<uint4*>(w.bad)[i] = __ldg(reinterpret_cast<const uint4*>(kp.badmask + (size_t)ch0 * kMaskWords) + i);
+    else
+      reinterpret_cast<uint4*>(w.gain)[i - kB] = __ldg(reinterpret_cast<const uint4*>(kp.gain + (size_t)ch0 * 2) + (i - kB));
+  }
 }
 
-// FE unit u of FED `fed` as described by d (k_fed_scan checked the FED header and
-// wrote, per FE unit, its byte offset in the FED record, its length, the FED's
-// status and whether the record holds data).  The unit's bytes are staged in the
-// warp's buffer when they fit, else read in place.  g is the FED record.
-__device__ Unit locate(Warp& w, const uint8_t* g, uint2 d, uint32_t fed, uint32_t u) {
+// FE units u and u + 1 of FED `fed` as described by dA and dB (k_fed_scan checked
+// the FED header and wrote, per FE unit, its byte offset in the FED record, its
+// length, the FED's status and whether the record holds data).  The units' bytes
+// (the first unit, its padding, the second unit) are staged in the warp's buffer
+// when they fit, else read in place.  g is the FED record.
+__device__ Unit locate(Warp& w, const uint8_t* g, uint2 dA, uint2 dB, uint32_t fed, uint32_t u) {
   const int lane = threadIdx.x & 31;
-  Unit r{fed, u, nullptr, 0, (uint8_t)((d.y >> 16) & 255u)};
-  if (!(d.y >> 24)) return r;
-  r.len = d.y & 0xFFFFu;
-  const uint8_t* a = g + d.x;
-  if (r.len <= (uint32_t)kBuf) {
+  Unit r{fed, u, nullptr, 0, 0, 0, (uint8_t)((dA.y >> 16) & 255u)};
+  if (!(dA.y >> 24)) return r;
+  r.len = dA.y & 0xFFFFu;
+  r.len1 = dB.y & 0xFFFFu;
+  r.off1 = dB.x - dA.x;
+  const uint32_t span = r.off1 + r.len1;
+  const uint8_t* a = g + dA.x;
+  if (span <= (uint32_t)kBuf) {
     if ((((uintptr_t)a) & 7u) == 0) {
-      const uint32_t nv = (r.len + 7u) >> 3;
+      const uint32_t nv = (span + 7u) >> 3;  // whole 8-byte words; padding bytes exist up to the next 8
       for (uint32_t i = lane; i < nv; i += 32)
         *reinterpret_cast<uint2*>(w.fe + 8 * i) = __ldg(reinterpret_cast<const uint2*>(a) + i);
     } else {
-      for (uint32_t i = lane; i < r.len; i += 32) w.fe[i] = __ldg(a + i);
+      for (uint32_t i = lane; i < span; i += 32) w.fe[i] = __ldg(a + i);
     }
     r.src = w.fe;
   } else {

@@ -46,9 +46,9 @@ struct Shape {
 struct Scratch {
   unsigned long long* lb = nullptr;  // look-back states, one per FED (per-event unpack)
   uint64_t* fed_off = nullptr;       // absolute byte offset per (event, FED)
-  uint32_t* fed_cnt = nullptr;       // clusters found per (event, FED, FE unit)
-  uint32_t* fed_start = nullptr;     // staging offset per (event, FED, FE unit), within its event's slice
-  uint32_t* fed_dest = nullptr;      // output offset per (event, FED, FE unit), within its event's slice
+  uint32_t* fed_cnt = nullptr;       // clusters found per work item (event, FED, pair of FE units)
+  uint32_t* fed_start = nullptr;     // staging offset per work item, within its event's slice
+  uint32_t* fed_dest = nullptr;      // output offset per work item, within its event's slice
   uint2* unit_desc = nullptr;        // per (event, FED, FE unit): offset in the FED record, length | status
   size_t items_cap = 0;
   uint32_t* ev_alloc = nullptr;      // staging allocation counter per event
@@ -60,7 +60,7 @@ struct Scratch {
   uint8_t* amp_stage = nullptr;      // staged amplitudes, sliced per event like the output
   size_t amp_stage_cap = 0;
   uint32_t* amp_alloc = nullptr;     // amplitude allocation counter per event
-  uint32_t* seg_amp_cnt = nullptr;   // amplitudes per (event, FED, FE unit); 0 when they did not fit
+  uint32_t* seg_amp_cnt = nullptr;   // amplitudes per work item; 0 when they did not fit
   uint32_t* seg_amp_start = nullptr; // their offset in the event's slice, or kNoAmp
   uint32_t* seg_amp_dest = nullptr;  // their offset in the event's output slice
   size_t amp_items_cap = 0, amp_ev_cap = 0;

@@ -2,16 +2,16 @@
 // three-threshold clustering (arXiv 2101.11489, section 2), per event and batched
 // (section 3).
 //
-// Clustering work unit: one FE unit (12 channels) of one FED of one event, handled
-// by one warp end to end (sst_fe.cuh): the FE unit's channel length chain (the
-// paper's "map of channel locations", here on the device), run validation and
-// counts (one lane per channel), expansion of the runs into an on-chip digi tile
-// sorted by strip (one lane per digi), thresholds (one lane per digi), candidate
-// boundaries, the leftmost seed of each candidate (warp ballots; the paper's array
-// of seed strips), and cluster forming (one lane per kept candidate).  No
-// block-wide barrier: a GB300 SM keeps some thirty independent units in flight.
-// The FED headers are checked once per FED by the prologue kernel (k_fed_scan),
-// which hands every unit its byte range.
+// Clustering work item: two adjacent FE units (24 channels) of one FED of one
+// event, handled by one warp end to end (sst_fe.cuh): the FE units' channel length
+// chains (the paper's "map of channel locations", here on the device), run
+// validation and counts (one lane per channel), expansion of the runs into an
+// on-chip digi tile sorted by strip (one lane per digi), thresholds (one lane per
+// digi), candidate boundaries, the leftmost seed of each candidate (warp ballots;
+// the paper's array of seed strips), and cluster forming (one lane per kept
+// candidate).  No block-wide barrier: a GB300 SM keeps 32 independent items in
+// flight.  The FED headers are checked once per FED by the prologue kernel
+// (k_fed_scan), which hands every FE unit its byte range.
 //
 // Output order without device-side waits: every unit allocates an exact-size
 // staging region with one atomic per event; k_clu_scan prefix-sums the units'
@@ -462,9 +462,9 @@ struct AmpArgs {
   const uint64_t* off = nullptr;  // [n_events + 1] event slices (batch), or null (one event at 0)
   uint64_t cap = 0;               // bytes of staging and of output
   uint32_t* alloc = nullptr;      // allocation counter per event
-  uint32_t* cnt = nullptr;        // per unit: amplitudes stored (0 when they did not fit)
-  uint32_t* start = nullptr;      // per unit: offset in the event's staging slice, or kNoAmp
-  uint32_t* dest = nullptr;       // per unit: offset in the event's output slice
+  uint32_t* cnt = nullptr;        // per work item: amplitudes stored (0 when they did not fit)
+  uint32_t* start = nullptr;      // per work item: offset in the event's staging slice, or kNoAmp
+  uint32_t* dest = nullptr;       // per work item: offset in the event's output slice
   uint8_t* out = nullptr;         // caller's amp
   uint32_t* first = nullptr;      // caller's amp_first
 };
@@ -568,10 +568,10 @@ __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_
   if (threadIdx.x == 0 && ev0 + carry_s != ev1) atomicOr(&status[e].flags, SST_EV_SIZE);
 }
 
-// a6, ordering: per event, the exclusive scan of its FE units' cluster counts
-// gives every unit's position in the event's sorted cluster SoA; the event's total
-// is its cluster count.  One CTA of 1024 threads per event (3,520 units of a full
-// event in four block scans).  With pack_off (events packed back to back),
+// a6, ordering: per event, the exclusive scan of its work items' cluster counts
+// gives every item's position in the event's sorted cluster SoA; the event's
+// total is its cluster count.  One CTA of 1024 threads per event (1,760 items of a
+// full event in two block scans).  With pack_off (events packed back to back),
 // the CTA that finishes last (counted in *done, which the prologue cleared; no
 // CTA waits for another) also scans the events' counts: pack_off[e] = clusters
 // of the events before e, pack_off[n_events] = all clusters.
@@ -634,7 +634,7 @@ __global__ void __launch_bounds__(1024) k_clu_scan(const uint32_t* __restrict__ 
   }
 }
 
-// a6, output: copies every segment's staged clusters (one segment per FE unit)
+// a6, output: copies every segment's staged clusters (one segment per work item)
 // to its place in the event's sorted cluster SoA, one warp per segment (16-byte
 // loads, coalesced stores).  The event's clusters start at clu_off[e] (its slice),
 // or at pack_off[e] when pack_off is given (events packed back to back).  With
@@ -786,8 +786,8 @@ __global__ void __launch_bounds__(256, 4) k_unpack(const uint8_t* __restrict__ r
   }
 }
 
-// a3 - a6 per event: one warp per FE unit over the global digi SoA; clusters
-// staged per unit.
+// a3 - a6 per event: one warp per FE unit over the global digi SoA (a single
+// event has too few pairs of units to fill the GPU); clusters staged per unit.
 template <bool AMP>
 __global__ void __launch_bounds__(256, 4) k_cluster(sst_digis in, uint32_t n_feds, KParams kp, uint4* stage,
                                                     uint64_t cap, uint32_t* ev_alloc, uint32_t* seg_cnt,
@@ -795,11 +795,10 @@ __global__ void __launch_bounds__(256, 4) k_cluster(sst_digis in, uint32_t n_fed
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   fe::Warp& w = reinterpret_cast<fe::Warp*>(smem_raw)[warp];
-  const uint32_t unit = blockIdx.x * nw + warp;
+  const uint32_t unit = blockIdx.x * nw + warp;  // work item: one FE unit (12 channels)
   if (unit >= n_feds * kFe) return;
-  const uint32_t f = unit / kFe, u = unit % kFe;
-  const uint32_t ch0 = f * kCh + u * kChPerFe;
-  fe::load_calib(w, kp, ch0);
+  const uint32_t ch0 = unit * kChPerFe;
+  fe::load_calib<kChPerFe>(w, kp, ch0);
   // channel digi ranges from the CSR row pointers, clamped to the input capacity
   // and to 256 digis per channel, so that malformed input cannot leave the tile
   uint32_t cnt = 0;
@@ -813,7 +812,7 @@ __global__ void __launch_bounds__(256, 4) k_cluster(sst_digis in, uint32_t n_fed
   }
   uint32_t x = cnt;
 #pragma unroll
-  for (int d = 1; d < 16; d <<= 1) {
+  for (int d = 1; d < 32; d <<= 1) {
     const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
     if (lane >= d) x += y;
   }
@@ -844,13 +843,13 @@ __global__ void __launch_bounds__(256, 4) k_cluster(sst_digis in, uint32_t n_fed
     so.seg_amp_cnt = am.cnt + unit;
     so.seg_amp_start = am.start + unit;
   }
-  fe::cluster_unit<AMP>(w, kp, kp.noise + (size_t)g0, ch0, total, fill, so, in.status);
+  fe::cluster_unit<kChPerFe, AMP>(w, kp, kp.noise + (size_t)g0, ch0, total, fill, so, in.status);
 }
 
 // a7: every FE unit of every FED of every event of a batch, unpacked and
-// clustered on chip, one warp per unit.  Persistent warps take tickets
-// FED-major (FED, then event, then FE unit), so that the warps working at any
-// moment share the same FED's calibration in L2.
+// clustered on chip, one warp per pair of FE units.  Persistent warps take
+// tickets FED-major (FED, then event, then pair), so that the warps working at
+// any moment share the same FED's calibration in L2.
 template <bool AMP>
 __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ raw,
                                                   const uint32_t* __restrict__ fed_len,
@@ -863,20 +862,22 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   fe::Warp& w = reinterpret_cast<fe::Warp*>(smem_raw)[warp];
-  const uint32_t per_fed = n_events * kFe;
+  constexpr uint32_t kItems = kFe / fe::kUnits;  // work items (FE-unit pairs) per FED
+  const uint32_t per_fed = n_events * kItems;
   const uint32_t n_units = n_feds * per_fed;
   for (;;) {
     uint32_t t = 0;
     if (lane == 0) t = atomicAdd(ticket, 1u);
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= n_units) break;
-    const uint32_t f = t / per_fed, r = t % per_fed, e = r / kFe, u = r % kFe;
+    const uint32_t f = t / per_fed, r = t % per_fed, e = r / kItems, p = r % kItems, u = p * fe::kUnits;
     const size_t item = (size_t)e * n_feds + f;
     const uint64_t fo = fed_off[item];
     const bool in_range = fo != kBadOff;
     const uint32_t ch0 = f * kCh + u * kChPerFe;
-    fe::load_calib(w, kp, ch0);
-    const fe::Unit un = fe::locate(w, raw + (in_range ? fo : 0), unit_desc[item * kFe + u], f, u);
+    fe::load_calib<fe::kChW>(w, kp, ch0);
+    const fe::Unit un = fe::locate(w, raw + (in_range ? fo : 0), unit_desc[item * kFe + u],
+                                   unit_desc[item * kFe + u + 1], f, u);
     uint32_t flags, nbad;
     const uint32_t total = fe::parse_unit(w, un, &flags, &nbad);
     if (lane == 0) {
@@ -887,19 +888,19 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
     const uint64_t off = clu_off[e];
     const uint64_t end = clu_off[e + 1] < out_cap ? clu_off[e + 1] : out_cap;
     const uint64_t cap = end > off ? end - off : 0;
-    fe::SegOut so{stage + (off < out_cap ? off : 0), cap, ev_alloc + e, seg_cnt + item * kFe + u,
-                  seg_start + item * kFe + u};
+    fe::SegOut so{stage + (off < out_cap ? off : 0), cap, ev_alloc + e, seg_cnt + item * kItems + p,
+                  seg_start + item * kItems + p};
     if (AMP) {
       uint64_t a0, a1;
       amp_slice(am, e, &a0, &a1);
       so.amp = am.stage + a0;
       so.amp_cap = a1 - a0;
       so.amp_alloc = am.alloc + e;
-      so.seg_amp_cnt = am.cnt + item * kFe + u;
-      so.seg_amp_start = am.start + item * kFe + u;
+      so.seg_amp_cnt = am.cnt + item * kItems + p;
+      so.seg_amp_start = am.start + item * kItems + p;
     }
     auto fill = [&](int c0, int c1) { fe::copy_runs(w, un, c0, c1); };
-    fe::cluster_unit<AMP>(w, kp, kp.noise + (size_t)ch0 * kStrips, ch0, total, fill, so, &status[e]);
+    fe::cluster_unit<fe::kChW, AMP>(w, kp, kp.noise + (size_t)ch0 * kStrips, ch0, total, fill, so, &status[e]);
     __syncwarp();
   }
 }
@@ -1013,7 +1014,7 @@ cudaError_t launch_batch_fe(const uint8_t* raw, const uint32_t* fed_len, uint32_
                             cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   const int nw = sh.block / 32;
   const size_t sm = sizeof(fe::Warp) * nw;
-  const size_t units = (size_t)n_events * n_feds * kFe;
+  const size_t units = (size_t)n_events * n_feds * (kFe / fe::kUnits);
   int per_sm = 0;
   const void* fn = am.stage ? (const void*)k_batch<true> : (const void*)k_batch<false>;
   cudaError_t e = prepare(fn, sh.block, sm, &per_sm);
@@ -1111,7 +1112,7 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
   e = launch_batch_fe(raw, fed_len, n_events, n_feds, clu_off, out.capacity, status, kp, s, sh, n_sm, am, st,
                       ev_begin, ev_end);
   if (e) return e;
-  return launch_order(clu_off, n_events, n_feds * kFe, out, status, s, pack_off, am, st);
+  return launch_order(clu_off, n_events, n_feds * (kFe / fe::kUnits), out, status, s, pack_off, am, st);
 }
 
 cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st) {
