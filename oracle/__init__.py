@@ -94,11 +94,12 @@ def _load():
             lib.orc_cluster_event.restype = ctypes.c_int64
             lib.orc_cluster_event.argtypes = [u32p, u8p, u32p, ctypes.c_uint32, f32p, f32p, u8p, _P(_Params),
                                               u32p, u16p, u16p, u32p, f32p, ctypes.c_uint64]
-            lib.orc_is_active.restype = ctypes.c_int
             lib.orc_cluster_amplitudes.argtypes = [u32p, u8p, u32p, f32p, f32p, u8p, _P(_Params), u32p,
-                                                   ctypes.POINTER(ctypes.c_uint16), ctypes.POINTER(ctypes.c_uint16),
-                                                   ctypes.c_uint64, u32p, u8p, ctypes.c_uint64]
+                                                   u16p, u16p, ctypes.c_uint64, u32p, u8p, ctypes.c_uint64]
             lib.orc_cluster_amplitudes.restype = ctypes.c_int64
+            lib.orc_local_x.argtypes = [u32p, f32p, ctypes.c_uint64, f32p, f32p]
+            lib.orc_local_x.restype = None
+            lib.orc_is_active.restype = ctypes.c_int
             lib.orc_is_active.argtypes = [ctypes.c_uint8, ctypes.c_float, ctypes.c_uint8, _P(_Params)]
             lib.orc_is_seed.restype = ctypes.c_int
             lib.orc_is_seed.argtypes = [ctypes.c_uint8, ctypes.c_float, ctypes.c_uint8, _P(_Params)]
@@ -256,6 +257,18 @@ def cluster_amplitudes(digis: dict, clusters: dict, noise, gain, bad, p: Params)
     if k < 0:
         raise RuntimeError("oracle amplitudes failed")
     return amp_first[:n].copy(), amp[:k].copy()
+
+
+def local_x(det: np.ndarray, barycenter: np.ndarray, pitch: np.ndarray) -> np.ndarray:
+    """Local x of clusters: (barycenter - 128) * pitch[det], binary32."""
+    det = np.ascontiguousarray(det, dtype=np.uint32)
+    bary = np.ascontiguousarray(barycenter, dtype=np.float32)
+    pitch = np.ascontiguousarray(pitch, dtype=np.float32)
+    assert det.size == bary.size and (det.size == 0 or int(det.max()) < pitch.size)
+    x = np.zeros(max(det.size, 1), np.float32)
+    _load().orc_local_x(_ptr(det, ctypes.c_uint32), _ptr(bary, ctypes.c_float), det.size,
+                        _ptr(pitch, ctypes.c_float), _ptr(x, ctypes.c_float))
+    return x[:det.size].copy()
 
 
 def process_event(raw, fed_len, n_feds: int, noise, gain, bad, p: Params) -> tuple[dict, dict]:

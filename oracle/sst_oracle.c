@@ -484,3 +484,12 @@ int64_t orc_cluster_amplitudes(const uint32_t* strip, const uint8_t* adc, const 
   }
   return (int64_t)out;
 }
+
+/* ---- local positions ------------------------------------------------------- */
+
+void orc_local_x(const uint32_t* det, const float* barycenter, uint64_t n, const float* pitch, float* x) {
+  for (uint64_t k = 0; k < n; k++) {
+    float from_centre = barycenter[k] - 128.0f;
+    x[k] = from_centre * pitch[det[k]];
+  }
+}

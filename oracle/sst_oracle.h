@@ -100,6 +100,13 @@ int64_t orc_cluster_amplitudes(const uint32_t* strip, const uint8_t* adc, const 
                                const uint16_t* width, uint64_t n_clusters, uint32_t* amp_first,
                                uint8_t* amp, uint64_t cap);
 
+/* Local position of clusters on their module (CMS-style local x, here with a
+ * synthetic per-module strip pitch; arXiv 2101.11489 section 4: the clusters are
+ * turned into hits with positions for tracking).  The origin is the module's
+ * centre, between strips 127 and 128, so x = (barycenter - 128) * pitch[det]:
+ * one binary32 subtraction, then one binary32 multiplication. */
+void orc_local_x(const uint32_t* det, const float* barycenter, uint64_t n, const float* pitch, float* x);
+
 int orc_is_active(uint8_t adc, float noise, uint8_t bad, const orc_params* p);
 int orc_is_seed(uint8_t adc, float noise, uint8_t bad, const orc_params* p);
 int orc_passes_cluster(uint32_t s_raw, float n2, const orc_params* p);
