@@ -401,6 +401,21 @@ def main():
     assert np.array_equal(st_d.cpu().numpy().view(np.uint32).reshape(n_events, 4), st_h), "graph replay differs"
     del graph
 
+    # ---- local positions of the step's clusters (synthetic strip pitch per module)
+    sst.sst_pitch_upload(ctx, np.random.default_rng(11).uniform(0.008, 0.0205, w.n_feds * 96).astype(np.float32))
+    n_pos = int(coff[-1])
+    x_pos = torch.empty(n_pos, dtype=torch.float32, device=dev)
+    sst.sst_local_x(ctx, cb.det, cb.barycenter, n_pos, x_pos)
+    torch.cuda.synchronize()
+    pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pa.record(stream)
+    for _ in range(20):
+        sst.sst_local_x(ctx, cb.det, cb.barycenter, n_clu, x_pos)
+    pb.record(stream)
+    torch.cuda.synchronize()
+    pos_ms = pa.elapsed_time(pb) / 20
+    del x_pos
+
     # ---- per-event launches on the same events (the paper's one-event-at-a-time form)
     pe_raw = [torch.from_numpy(e[0]).to(dev) for e in events]
     pe_fl = [torch.from_numpy(e[1].view(np.int32)).to(dev) for e in events]
@@ -518,6 +533,8 @@ def main():
             "batched_over_per_event": round((total_events / (ms_per_step / 1e3)) / (pe_value * world), 2),
             "graph": {"value": round(total_events / (g_ms / 1e3), 1), "unit": "events/s", "ms_per_step": round(g_ms, 4),
                       "steps": g_steps, "what": "the same step captured once as a CUDA graph and replayed"},
+            "local_x": {"clusters_per_s": round(n_clu / (pos_ms / 1e3), 1), "ms": round(pos_ms, 4),
+                        "what": "local x of the step's clusters from a per-module strip pitch (sst_local_x)"},
             "paper_context": {"cpu": "560 events/s, 28 Broadwell cores (real TTBar PU70 events)",
                               "gpu": "649 events/s, one Tesla P100 (real TTBar PU70 events)",
                               "note": "other hardware and real events; context, not a baseline"},

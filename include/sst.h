@@ -293,6 +293,21 @@ sst_status sst_batch_host(sst_ctx* ctx, const uint8_t* raw, const uint64_t* even
                           uint32_t n_events, uint32_t n_feds, const sst_clusters* out, uint64_t* event_first,
                           sst_event_status* status);
 
+/* ---- local positions (section 4: clusters become hits for tracking) --------------
+ * The detector geometry is not available: the caller gives every module a strip
+ * pitch (a synthetic geometry).  The local x of a cluster is measured from its
+ * module's centre, between strips 127 and 128:
+ *   x = (barycenter - 128) * pitch[det]     (binary32, each operation rounded once)
+ * in the pitch's length unit.
+ * sst_pitch_upload: pitch = host [n_feds * 96] floats, finite and > 0 (copied;
+ *   INVALID_ARG otherwise).
+ * sst_local_x: det, barycenter = device [n] (a cluster SoA), x = device [n] output;
+ *   a det outside the context's modules gives NaN.  STATE before sst_pitch_upload.
+ *   Enqueued on `stream`. */
+sst_status sst_pitch_upload(sst_ctx* ctx, const float* pitch);
+sst_status sst_local_x(sst_ctx* ctx, const uint32_t* det, const float* barycenter, uint64_t n, float* x,
+                       void* stream);
+
 /* Launch-shape knobs of the batched kernel (picked by sst_autotune). */
 typedef struct {
   uint32_t block;       /* threads per CTA: 128 or 256 */

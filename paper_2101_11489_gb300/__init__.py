@@ -116,6 +116,8 @@ def load_library():
         "sst_cluster": ([vp, P(sst_digis), u32, P(sst_clusters), vp], i32),
         "sst_batch": ([vp, vp, vp, vp, u32, u32, vp, P(sst_clusters), vp, vp], i32),
         "sst_batch_host": ([vp, vp, vp, vp, u32, u32, P(sst_clusters), vp, vp], i32),
+        "sst_pitch_upload": ([vp, vp], i32),
+        "sst_local_x": ([vp, vp, vp, u64, vp, vp], i32),
         "sst_set_tune": ([vp, P(sst_tune)], i32),
         "sst_get_tune": ([vp, P(sst_tune)], i32),
         "sst_autotune": ([vp, vp, vp, vp, u32, u32, vp, P(sst_clusters), vp, vp, P(sst_tune), P(ctypes.c_float)], i32),
@@ -137,7 +139,7 @@ def load_library():
 def exported_symbols() -> list[str]:
     return ["sst_create", "sst_destroy", "sst_last_error", "sst_calib_upload", "sst_unpack", "sst_unpack_noalloc",
             "sst_cluster",
-            "sst_batch", "sst_batch_host", "sst_set_tune", "sst_get_tune", "sst_autotune", "sst_profile_enable", "sst_profile_read",
+            "sst_batch", "sst_batch_host", "sst_pitch_upload", "sst_local_x", "sst_set_tune", "sst_get_tune", "sst_autotune", "sst_profile_enable", "sst_profile_read",
             "sst_server_start", "sst_server_stop",
             "sst_submit", "sst_poll"]
 
@@ -238,6 +240,18 @@ def sst_batch_host(ctx: int, raw: np.ndarray, event_off: np.ndarray, fed_len: np
     code = load_library().sst_batch_host(ctx, _hp(raw), _hp(event_off), _hp(fed_len), n_events, n_feds,
                                          ctypes.byref(out.record()), _hp(event_first), _hp(status))
     _check(ctx, code, "sst_batch_host")
+
+
+def sst_pitch_upload(ctx: int, pitch: np.ndarray) -> None:
+    """Strip pitch of every module (n_feds * 96 floats, host)."""
+    pitch = np.ascontiguousarray(pitch, dtype=np.float32)
+    _check(ctx, load_library().sst_pitch_upload(ctx, _hp(pitch)), "sst_pitch_upload")
+
+
+def sst_local_x(ctx: int, det, barycenter, n: int, x, stream=None) -> None:
+    """Local x of n clusters (device tensors det, barycenter -> x)."""
+    _check(ctx, load_library().sst_local_x(ctx, _dp(det), _dp(barycenter), n, _dp(x), _stream(stream)),
+           "sst_local_x")
 
 
 def sst_set_tune(ctx: int, block: int, ctas_per_sm: int, tile_digis: int, lanes_per_channel: int,

@@ -159,6 +159,7 @@ sst_status sst_destroy(sst_ctx* ctx) {
   if (ctx->noise) cudaFree(ctx->noise);
   if (ctx->badmask) cudaFree(ctx->badmask);
   if (ctx->gain) cudaFree(ctx->gain);
+  if (ctx->pitch) cudaFree(ctx->pitch);
   delete ctx;
   return SST_OK;
 }

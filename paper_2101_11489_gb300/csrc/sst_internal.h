@@ -110,6 +110,7 @@ struct sst_ctx {
   std::mutex mu;
   sst_server* server = nullptr;
   sst_host_pipe* pipe = nullptr;  // streams and arenas of sst_batch_host, made on first use
+  float* pitch = nullptr;         // strip pitch per module (sst_pitch_upload), or null
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;  // recorded launches
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_free;    // reusable pairs
