@@ -75,6 +75,66 @@ def _gen_served_event(ev):
     return e.raw, e.fed_len
 
 
+_SWEEP = None  # (inner thread count, thread pool) of a CPU-sweep worker
+
+
+def _sweep_init(wid, inner):
+    global _SWEEP
+    _worker_init(wid)
+    from concurrent.futures import ThreadPoolExecutor
+    _SWEEP = (inner, ThreadPoolExecutor(inner) if inner > 1 else None)
+
+
+def _sweep_event(args):
+    """One event through the oracle, its FEDs split into `inner` ranges of about
+    equal bytes processed by threads (the inner level of the nested CPU scheme;
+    the oracle's C code runs with the GIL released)."""
+    raw, fl = args
+    import oracle as orc
+    w_calib = _W_CALIB
+    inner, tp = _SWEEP
+    nf = fl.size
+    off = np.concatenate([[0], np.cumsum(fl.astype(np.int64))])
+    cuts = sorted(set([0, nf] + [int(np.searchsorted(off, off[-1] * k / inner)) for k in range(1, inner)]))
+
+    def part(k):
+        f0, f1 = cuts[k], cuts[k + 1]
+        return orc.process_feds(raw[off[f0]:off[f1]], fl[f0:f1], f0, f1 - f0, w_calib.noise, w_calib.gain,
+                                w_calib.bad, orc.Params())["det"].size
+
+    if tp is None:
+        return sum(part(k) for k in range(len(cuts) - 1))
+    return sum(tp.map(part, range(len(cuts) - 1)))
+
+
+def cpu_sweep(args, wid, n_events):
+    """Oracle throughput on the host cores for outer (events, processes) x inner
+    (FED ranges of one event, threads) = cores; the nested scheme of the paper's
+    CPU design beside the GPU path."""
+    cores = os.cpu_count() or 1
+    gen_pool = mp.get_context("spawn").Pool(cores, initializer=_worker_init, initargs=(wid,))
+    events = [(r, f) for r, f, _ in gen_pool.map(_gen_event, [(wid, i) for i in range(n_events)], chunksize=1)]
+    gen_pool.terminate()
+    res = []
+    outer = cores
+    while outer >= 1:
+        inner = cores // outer
+        pool = mp.get_context("spawn").Pool(outer, initializer=_sweep_init, initargs=(wid, inner))
+        pool.map(_sweep_event, events[:outer], chunksize=1)  # warm-up
+        t0 = time.perf_counter()
+        for _ in range(2):
+            pool.map(_sweep_event, events, chunksize=1)
+        t = (time.perf_counter() - t0) / 2
+        pool.terminate()
+        res.append({"outer_events": outer, "inner_fed_ranges": inner, "events_per_s": round(len(events) / t, 2),
+                    "ms_per_event_latency": round(1e3 * t * outer / len(events), 2)})
+        outer //= 2
+    w = eg.WORKLOADS[wid]
+    print(json.dumps({"metric": "events/s, CPU oracle, outer events x inner FED ranges", "unit": "events/s",
+                      "cores": cores, "config": {"workload": f"{args.workload}: {w.name}", "events": n_events},
+                      "cpu_sweep": res}), flush=True)
+
+
 def _oracle_event(args):
     raw, fed_len = args
     import oracle as orc
@@ -286,6 +346,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--served-events", type=int, default=10000, help="events per served-stream point (0: skip)")
+    ap.add_argument("--cpu-sweep", action="store_true",
+                    help="only time the CPU oracle over outer events x inner FED ranges on the host cores")
     args = ap.parse_args()
     rank, world, local = dist_env()
     wid, n_events = WORKLOADS[args.workload]
@@ -295,6 +357,8 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, rank, world, wid, n_events)
+    if args.cpu_sweep:
+        return cpu_sweep(args, wid, n_events) if rank == 0 else None
 
     cores = os.cpu_count() or 1
     # the process pool is started (spawn) before the first CUDA call

@@ -94,6 +94,12 @@ def _load():
             lib.orc_cluster_event.restype = ctypes.c_int64
             lib.orc_cluster_event.argtypes = [u32p, u8p, u32p, ctypes.c_uint32, f32p, f32p, u8p, _P(_Params),
                                               u32p, u16p, u16p, u32p, f32p, ctypes.c_uint64]
+            lib.orc_unpack_feds.restype = ctypes.c_int64
+            lib.orc_unpack_feds.argtypes = [u8p, u32p, ctypes.c_uint32, ctypes.c_uint32, u32p, u8p, ctypes.c_uint64,
+                                            u32p, u8p]
+            lib.orc_cluster_feds.restype = ctypes.c_int64
+            lib.orc_cluster_feds.argtypes = [u32p, u8p, u32p, ctypes.c_uint32, ctypes.c_uint32, f32p, f32p, u8p,
+                                             _P(_Params), u32p, u16p, u16p, u32p, f32p, ctypes.c_uint64]
             lib.orc_cluster_amplitudes.argtypes = [u32p, u8p, u32p, f32p, f32p, u8p, _P(_Params), u32p,
                                                    u16p, u16p, ctypes.c_uint64, u32p, u8p, ctypes.c_uint64]
             lib.orc_cluster_amplitudes.restype = ctypes.c_int64
@@ -257,6 +263,44 @@ def cluster_amplitudes(digis: dict, clusters: dict, noise, gain, bad, p: Params)
     if k < 0:
         raise RuntimeError("oracle amplitudes failed")
     return amp_first[:n].copy(), amp[:k].copy()
+
+
+def process_feds(raw, fed_len, fed_base: int, n_feds: int, noise, gain, bad, p: Params) -> dict:
+    """Unpack and cluster FEDs fed_base .. fed_base + n_feds - 1 of an event (their
+    records back to back in raw): the clusters of that FED range, with the
+    event's module ids.  Clusters never cross a FED, so an event's FED ranges can
+    be processed independently (the inner level of the nested CPU scheme)."""
+    raw = np.ascontiguousarray(raw, dtype=np.uint8)
+    fed_len = np.ascontiguousarray(fed_len, dtype=np.uint32)
+    assert fed_len.size == n_feds
+    lib = _load()
+    cap = max(int(raw.size), 1)
+    strip = np.zeros(cap, np.uint32)
+    adc = np.zeros(cap, np.uint8)
+    chan_off = np.zeros(n_feds * CH_PER_FED + 1, np.uint32)
+    chan_status = np.zeros(n_feds * CH_PER_FED, np.uint8)
+    n = lib.orc_unpack_feds(_ptr(raw, ctypes.c_uint8), _ptr(fed_len, ctypes.c_uint32), fed_base, n_feds,
+                            _ptr(strip, ctypes.c_uint32), _ptr(adc, ctypes.c_uint8), cap,
+                            _ptr(chan_off, ctypes.c_uint32), _ptr(chan_status, ctypes.c_uint8))
+    if n < 0:
+        raise RuntimeError("oracle unpacker: capacity too small")
+    noise = np.ascontiguousarray(noise, dtype=np.float32)
+    gain = np.ascontiguousarray(gain, dtype=np.float32)
+    bad = np.ascontiguousarray(bad, dtype=np.uint8)
+    det = np.zeros(cap, np.uint32)
+    first = np.zeros(cap, np.uint16)
+    width = np.zeros(cap, np.uint16)
+    charge = np.zeros(cap, np.uint32)
+    bary = np.zeros(cap, np.float32)
+    k = lib.orc_cluster_feds(_ptr(strip, ctypes.c_uint32), _ptr(adc, ctypes.c_uint8), _ptr(chan_off, ctypes.c_uint32),
+                             fed_base, n_feds, _ptr(noise, ctypes.c_float), _ptr(gain, ctypes.c_float),
+                             _ptr(bad, ctypes.c_uint8), ctypes.byref(p._c()), _ptr(det, ctypes.c_uint32),
+                             _ptr(first, ctypes.c_uint16), _ptr(width, ctypes.c_uint16), _ptr(charge, ctypes.c_uint32),
+                             _ptr(bary, ctypes.c_float), cap)
+    if k < 0:
+        raise RuntimeError("oracle clusterizer: capacity too small")
+    return {"det": det[:k].copy(), "first": first[:k].copy(), "width": width[:k].copy(),
+            "charge": charge[:k].copy(), "barycenter": bary[:k].copy(), "n_digi": int(n)}
 
 
 def local_x(det: np.ndarray, barycenter: np.ndarray, pitch: np.ndarray) -> np.ndarray:

@@ -174,6 +174,12 @@ static uint8_t unpack_channel(const uint8_t* rec, uint32_t len, uint32_t ch_glob
 int64_t orc_unpack_event(const uint8_t* raw, const uint32_t* fed_len, uint32_t n_feds,
                          uint32_t* strip, uint8_t* adc, uint64_t cap, uint32_t* chan_off,
                          uint8_t* chan_status) {
+  return orc_unpack_feds(raw, fed_len, 0, n_feds, strip, adc, cap, chan_off, chan_status);
+}
+
+int64_t orc_unpack_feds(const uint8_t* raw, const uint32_t* fed_len, uint32_t fed_base, uint32_t n_feds,
+                        uint32_t* strip, uint8_t* adc, uint64_t cap, uint32_t* chan_off,
+                        uint8_t* chan_status) {
   uint64_t n = 0;
   uint64_t fed_pos = 0;
   int overflow = 0;
@@ -201,7 +207,7 @@ int64_t orc_unpack_event(const uint8_t* raw, const uint32_t* fed_len, uint32_t n
         fe_len[u] = rd_u16(fed + 16 + 2 * u);
         body += pad_to(fe_len[u], 8);
       }
-      if (rd_u32(fed) != ORC_FED_MAGIC || rd_u16(fed + 4) != f || fed[6] != ORC_CH_PER_FED ||
+      if (rd_u32(fed) != ORC_FED_MAGIC || rd_u16(fed + 4) != fed_base + f || fed[6] != ORC_CH_PER_FED ||
           fed[7] != ORC_FE_PER_FED || rd_u32(fed + 8) != L ||
           pad_to(ORC_FED_HEADER_BYTES + body, 16) != L)
         fed_status = ORC_ST_FED_HDR;
@@ -248,7 +254,8 @@ int64_t orc_unpack_event(const uint8_t* raw, const uint32_t* fed_len, uint32_t n
           continue;
         }
         uint64_t n_before = n;
-        uint8_t st = unpack_channel(fed + rec_pos[k], rec_len[k], c, strip, adc, &n, cap, &overflow);
+        uint8_t st = unpack_channel(fed + rec_pos[k], rec_len[k], fed_base * ORC_CH_PER_FED + c, strip, adc, &n,
+                                    cap, &overflow);
         if (overflow) return -1;
         if (st) n = n_before;
         chan_status[c] = st;
@@ -426,6 +433,14 @@ int64_t orc_cluster_event(const uint32_t* strip, const uint8_t* adc, const uint3
                           const uint8_t* bad, const orc_params* p, uint32_t* det,
                           uint16_t* first, uint16_t* width, uint32_t* charge,
                           float* barycenter, uint64_t cap) {
+  return orc_cluster_feds(strip, adc, chan_off, 0, n_feds, noise, gain, bad, p, det, first, width, charge, barycenter,
+                          cap);
+}
+
+int64_t orc_cluster_feds(const uint32_t* strip, const uint8_t* adc, const uint32_t* chan_off, uint32_t fed_base,
+                         uint32_t n_feds, const float* noise, const float* gain, const uint8_t* bad,
+                         const orc_params* p, uint32_t* det, uint16_t* first, uint16_t* width, uint32_t* charge,
+                         float* barycenter, uint64_t cap) {
   uint64_t out = 0;
   uint32_t n_ch = n_feds * ORC_CH_PER_FED;
   uint8_t row_adc[ORC_STRIPS_PER_CH];
@@ -436,7 +451,7 @@ int64_t orc_cluster_event(const uint32_t* strip, const uint8_t* adc, const uint3
   for (uint32_t c = 0; c < n_ch; c++) {
     uint32_t d0 = chan_off[c], d1 = chan_off[c + 1];
     if (d0 == d1) continue; /* no recorded strip: no active strip, no cluster */
-    uint64_t g0 = (uint64_t)c * ORC_STRIPS_PER_CH;
+    uint64_t g0 = ((uint64_t)fed_base * ORC_CH_PER_FED + c) * ORC_STRIPS_PER_CH;
     memset(row_adc, 0, sizeof row_adc);
     for (uint32_t d = d0; d < d1; d++) row_adc[strip[d] - g0] = adc[d];
     for (int i = 0; i < ORC_STRIPS_PER_CH; i++)
@@ -446,7 +461,7 @@ int64_t orc_cluster_event(const uint32_t* strip, const uint8_t* adc, const uint3
     if (k < 0) return -1;
     if (out + (uint64_t)k > cap) return -1;
     for (int j = 0; j < k; j++) {
-      det[out] = c;
+      det[out] = fed_base * ORC_CH_PER_FED + c;
       first[out] = f_first[j];
       width[out] = f_width[j];
       charge[out] = f_charge[j];

@@ -78,6 +78,18 @@ int orc_cluster_module(const uint8_t* adc, const float* noise, const uint8_t* ba
  * them).  Calibration is indexed by global strip (noise, bad) and by global APV
  * (gain).  det[k] is the global module (channel) id.  Returns the number of
  * clusters, or -1 when `cap` is too small. */
+/* The same for FEDs fed_base .. fed_base + n_feds - 1 of an event only (their
+ * records back to back in `raw`, their lengths in fed_len[0 .. n_feds)): FED ids
+ * in the headers, strip indices, module ids (det) and calibration indices are the
+ * event's, channel arrays (chan_off, chan_status) are the range's.  Clusters
+ * never cross a FED, so an event can be processed as independent FED ranges. */
+int64_t orc_unpack_feds(const uint8_t* raw, const uint32_t* fed_len, uint32_t fed_base, uint32_t n_feds,
+                        uint32_t* strip, uint8_t* adc, uint64_t cap, uint32_t* chan_off, uint8_t* chan_status);
+int64_t orc_cluster_feds(const uint32_t* strip, const uint8_t* adc, const uint32_t* chan_off, uint32_t fed_base,
+                         uint32_t n_feds, const float* noise, const float* gain, const uint8_t* bad,
+                         const orc_params* p, uint32_t* det, uint16_t* first, uint16_t* width, uint32_t* charge,
+                         float* barycenter, uint64_t cap);
+
 int64_t orc_cluster_event(const uint32_t* strip, const uint8_t* adc, const uint32_t* chan_off,
                           uint32_t n_feds, const float* noise, const float* gain,
                           const uint8_t* bad, const orc_params* p, uint32_t* det,

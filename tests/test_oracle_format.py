@@ -262,3 +262,20 @@ def test_absent_fed():
     assert not d1["chan_status"].any()
     assert d1["chan_off"][96] == 0
     assert np.array_equal(d1["strip"], d0["strip"][d0["chan_off"][96]:])
+
+
+def test_fed_ranges_give_the_whole_event():
+    """Processing an event as independent FED ranges (the inner level of the
+    nested CPU scheme) gives exactly the whole event's digis and clusters."""
+    w = eg.WORKLOADS[0]
+    calib = eg.make_calibration(w.n_feds, w.seed, w.p_bad)
+    e = eg.make_event(w, calib, 3)
+    d, c = orc.process_event(e.raw, e.fed_len, w.n_feds, calib.noise, calib.gain, calib.bad, orc.Params())
+    off = np.concatenate([[0], np.cumsum(e.fed_len)]).astype(np.int64)
+    parts = []
+    for f0, f1 in ((0, 7), (7, 8), (8, 31), (31, 50)):
+        parts.append(orc.process_feds(e.raw[off[f0]:off[f1]], e.fed_len[f0:f1], f0, f1 - f0, calib.noise,
+                                      calib.gain, calib.bad, orc.Params()))
+    assert sum(p["n_digi"] for p in parts) == d["strip"].size
+    for k in ("det", "first", "width", "charge", "barycenter"):
+        assert np.array_equal(np.concatenate([p[k] for p in parts]), c[k]), k
