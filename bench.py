@@ -557,8 +557,18 @@ def main():
     achieved = b_alg / (k_ms / 1e3) / 1e9
     tr = kernel_traffic()
     traffic = None
+    issue = None
     if tr is not None and tr.get("workload") == args.workload:
         traffic = tr.get("dram_bytes_per_launch")
+        if tr.get("warp_instructions"):
+            # the kernel is bound by instruction issue, not by HBM: one warp
+            # instruction per scheduler per cycle, 4 schedulers per SM
+            n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+            peak_ips = n_sm * 4 * (clk.get("sm_mhz") or 2070.0) * 1e6
+            ips = tr["warp_instructions"] / (k_ms / 1e3)
+            issue = {"warp_instructions_per_launch": tr["warp_instructions"], "achieved_per_s": round(ips, 1),
+                     "peak_per_s": round(peak_ips, 1), "frac": round(ips / peak_ips, 4),
+                     "source": "instruction count from the committed ncu capture of this kernel"}
 
     # ---- oracle on the host cores (rank 0 at N = 1 only)
     cpu = None
@@ -609,7 +619,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "kernel": "k_batch", "kernels_per_step": 4, "kernel_ms": round(k_ms, 4), "algorithmic_bytes": int(b_alg),
-                         "peak_kind": peak_kind},
+                         "peak_kind": peak_kind, "issue": issue},
             "served": served,
             "cpu_baseline": cpu,
             "clocks": clk,
