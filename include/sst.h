@@ -284,14 +284,31 @@ sst_status sst_batch(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off
  * Pinned host memory (cudaHostAlloc, cudaHostRegister) gives full copy speed;
  * pageable memory works, with copies staged by the CUDA driver.  Device arenas
  * grow on demand (cudaMalloc only when a call needs more than any call before it
- * on the context) and are freed by sst_destroy.  A context runs one
- * sst_batch_host call at a time (calls from several threads are serialised).
+ * on the context) and are freed by sst_destroy.  Calls from several threads are
+ * processed one batch after another, in the order they were made.
  * Errors: INVALID_ARG (null pointer, n_events == 0, n_feds outside 1..context
  * FEDs, decreasing event_off, out->amp set: amplitudes are not produced here),
  * NO_CALIB, CUDA. */
 sst_status sst_batch_host(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len,
                           uint32_t n_events, uint32_t n_feds, const sst_clusters* out, uint64_t* event_first,
                           sst_event_status* status);
+
+/* The same batch, submitted without waiting: the call checks the arguments,
+ * queues the batch on the context's host pipeline and returns a ticket.  Batches
+ * are processed in submission order as one stream of chunks, so the copies and
+ * kernels of a batch overlap the end of the one before it.  Every buffer of the
+ * batch (inputs and outputs) belongs to the library until sst_batch_host_wait
+ * returns for its ticket: do not modify the inputs or read the outputs before.
+ * Do not change the context's tune while batches are pending.  Thread safe with
+ * respect to each other (submit and wait may come from different threads).
+ * sst_batch_host_wait: blocks until the batch's results are in the caller's
+ * arrays and releases the ticket; INVALID_ARG for an unknown ticket, CUDA when the
+ * batch (or one before it) failed. */
+sst_status sst_batch_host_submit(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off,
+                                 const uint32_t* fed_len, uint32_t n_events, uint32_t n_feds,
+                                 const sst_clusters* out, uint64_t* event_first, sst_event_status* status,
+                                 uint64_t* ticket);
+sst_status sst_batch_host_wait(sst_ctx* ctx, uint64_t ticket);
 
 /* ---- local positions (section 4: clusters become hits for tracking) --------------
  * The detector geometry is not available: the caller gives every module a strip

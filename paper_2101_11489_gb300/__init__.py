@@ -116,6 +116,8 @@ def load_library():
         "sst_cluster": ([vp, P(sst_digis), u32, P(sst_clusters), vp], i32),
         "sst_batch": ([vp, vp, vp, vp, u32, u32, vp, P(sst_clusters), vp, vp], i32),
         "sst_batch_host": ([vp, vp, vp, vp, u32, u32, P(sst_clusters), vp, vp], i32),
+        "sst_batch_host_submit": ([vp, vp, vp, vp, u32, u32, P(sst_clusters), vp, vp, P(u64)], i32),
+        "sst_batch_host_wait": ([vp, u64], i32),
         "sst_pitch_upload": ([vp, vp], i32),
         "sst_local_x": ([vp, vp, vp, u64, vp, vp], i32),
         "sst_set_tune": ([vp, P(sst_tune)], i32),
@@ -139,7 +141,7 @@ def load_library():
 def exported_symbols() -> list[str]:
     return ["sst_create", "sst_destroy", "sst_last_error", "sst_calib_upload", "sst_unpack", "sst_unpack_noalloc",
             "sst_cluster",
-            "sst_batch", "sst_batch_host", "sst_pitch_upload", "sst_local_x", "sst_set_tune", "sst_get_tune", "sst_autotune", "sst_profile_enable", "sst_profile_read",
+            "sst_batch", "sst_batch_host", "sst_batch_host_submit", "sst_batch_host_wait", "sst_pitch_upload", "sst_local_x", "sst_set_tune", "sst_get_tune", "sst_autotune", "sst_profile_enable", "sst_profile_read",
             "sst_server_start", "sst_server_stop",
             "sst_submit", "sst_poll"]
 
@@ -240,6 +242,27 @@ def sst_batch_host(ctx: int, raw: np.ndarray, event_off: np.ndarray, fed_len: np
     code = load_library().sst_batch_host(ctx, _hp(raw), _hp(event_off), _hp(fed_len), n_events, n_feds,
                                          ctypes.byref(out.record()), _hp(event_first), _hp(status))
     _check(ctx, code, "sst_batch_host")
+
+
+def sst_batch_host_submit(ctx: int, raw: np.ndarray, event_off: np.ndarray, fed_len: np.ndarray, n_events: int,
+                          n_feds: int, out: "HostClusters", event_first: np.ndarray, status: np.ndarray) -> int:
+    """Queues a host-memory batch; returns its ticket.  The arrays belong to the
+    library until sst_batch_host_wait(ticket) returns."""
+    for a, dt in ((raw, np.uint8), (event_off, np.uint64), (fed_len, np.uint32), (event_first, np.uint64),
+                  (status, np.uint32)):
+        assert a.dtype == dt and a.flags["C_CONTIGUOUS"], "sst_batch_host_submit: wrong dtype or layout"
+    assert event_off.size >= n_events + 1 and event_first.size >= n_events + 1 and status.size >= 4 * n_events
+    assert fed_len.size >= n_events * n_feds and raw.size >= int(event_off[n_events])
+    t = ctypes.c_uint64()
+    code = load_library().sst_batch_host_submit(ctx, _hp(raw), _hp(event_off), _hp(fed_len), n_events, n_feds,
+                                                ctypes.byref(out.record()), _hp(event_first), _hp(status),
+                                                ctypes.byref(t))
+    _check(ctx, code, "sst_batch_host_submit")
+    return t.value
+
+
+def sst_batch_host_wait(ctx: int, ticket: int) -> None:
+    _check(ctx, load_library().sst_batch_host_wait(ctx, ticket), "sst_batch_host_wait")
 
 
 def sst_pitch_upload(ctx: int, pitch: np.ndarray) -> None:

@@ -20,9 +20,21 @@
 // The kernels of the next chunks are already queued, so the GPU does not wait
 // for the host, and a chunk's copies overlap the kernels of the chunks after it.
 //
-// Device arenas grow on demand (a cudaMalloc only when a call needs more than
-// any call before it on this context) and live until sst_destroy.
+// Batches are submitted to a worker thread of the context (sst_batch_host_submit)
+// and processed in submission order as one continuous stream of chunks: the next
+// batch's first chunks are copied in and computed while the previous batch's
+// last chunks are still being copied out, so consecutive batches overlap.
+// sst_batch_host_wait returns when a batch's results are in the caller's arrays;
+// sst_batch_host is submit + wait.
+//
+// Device arenas grow on demand (a cudaMalloc only when a batch needs more than
+// any batch before it on this context; the worker drains the pipeline first) and
+// live until sst_destroy.
+#include <condition_variable>
 #include <cstring>
+#include <deque>
+#include <map>
+#include <thread>
 #include <vector>
 
 #include "sst_internal.h"
@@ -86,8 +98,9 @@ struct PipeSlot {
   size_t h_st_cap = 0;
   uint64_t* h_pack_off = nullptr;
   size_t h_po_cap = 0;
-  // the chunk in flight: events [e0, e1), or e1 == e0 when the slot is idle
-  uint32_t e0 = 0, e1 = 0;
+  // the chunk in flight: chunk `chunk` of `job`, or job == null when the slot is idle
+  struct HostJob* job = nullptr;
+  size_t chunk = 0;
 };
 
 // One chunk's sizes.
@@ -97,6 +110,34 @@ struct Chunk {
   uint64_t bytes;      // raw bytes copied
   uint64_t clu_total;  // staging records (sum over events of bytes / 2 + 1)
 };
+
+// A batch submitted with sst_batch_host_submit: the caller's buffers, its chunks
+// and how far the pipeline has got with it.
+struct HostJob {
+  uint64_t ticket = 0;
+  const uint8_t* raw = nullptr;
+  const uint64_t* event_off = nullptr;
+  const uint32_t* fed_len = nullptr;
+  uint32_t n_events = 0, n_feds = 0;
+  sst_clusters out{};
+  uint64_t* event_first = nullptr;
+  sst_event_status* status = nullptr;
+  std::vector<Chunk> chunks;
+  uint32_t max_e = 0;
+  uint64_t max_bytes = 0, max_clu = 0;
+  size_t next = 0;      // next chunk to issue
+  size_t finished = 0;  // chunks whose clusters are on their way to the caller
+  uint64_t pos = 0;     // clusters stored so far
+  cudaEvent_t done = nullptr;  // recorded after the batch's last copies
+  bool recorded = false;
+  cudaError_t err = cudaSuccess;
+};
+
+bool slot_fits(const PipeSlot& s, uint32_t E, uint32_t nf, uint64_t bytes, uint64_t clu) {
+  return s.raw_cap >= bytes && s.fl_cap >= (size_t)E * nf && s.eo_cap >= E + 1u && s.co_cap >= E + 1u &&
+         s.st_cap >= E && s.po_cap >= E + 1u && s.clu_cap >= clu && s.h_eo_cap >= E + 1u && s.h_co_cap >= E + 1u &&
+         s.h_st_cap >= E && s.h_po_cap >= E + 1u && s.ev_h2d != nullptr;
+}
 
 cudaError_t grow_slot(PipeSlot& s, uint32_t E, uint32_t nf, uint64_t bytes, uint64_t clu) {
   cudaError_t e;
@@ -149,6 +190,17 @@ struct sst_host_pipe {
   cudaStream_t h2d = nullptr, comp = nullptr, stat = nullptr, d2h = nullptr;
   sst::Scratch scratch;  // the kernels' scratch, shared by the slots (one chunk runs at a time)
   PipeSlot slots[kSlots];
+  // worker
+  sst_ctx* ctx = nullptr;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::thread worker;
+  bool stop = false;
+  std::deque<HostJob*> queue;            // batches with chunks still to issue, in order
+  std::map<uint64_t, HostJob*> jobs;     // every batch not yet waited for
+  uint64_t next_ticket = 1;
+  uint64_t issued = 0, retired = 0;      // chunks issued / finished; chunk g uses slot g % kSlots
+  cudaError_t fatal = cudaSuccess;       // a CUDA error ends the pipeline; later calls report it
 };
 
 namespace sst {
@@ -156,6 +208,16 @@ namespace sst {
 void free_host_pipe(sst_ctx* ctx) {
   sst_host_pipe* p = ctx->pipe;
   if (!p) return;
+  {
+    std::lock_guard<std::mutex> lock(p->mu);
+    p->stop = true;
+  }
+  p->cv_work.notify_all();
+  if (p->worker.joinable()) p->worker.join();
+  for (auto& kv : p->jobs) {
+    if (kv.second->done) cudaEventDestroy(kv.second->done);
+    delete kv.second;
+  }
   for (cudaStream_t st : {p->h2d, p->comp, p->stat, p->d2h})
     if (st) cudaStreamSynchronize(st);
   for (PipeSlot& s : p->slots) free_slot(s);
@@ -173,8 +235,12 @@ namespace {
 // Enqueues chunk c on slot s: host staging of the rebased offsets, the H2D
 // copies, the batched kernels in packed mode and the D2H of statuses and
 // pack_off, with the events that order them across the three streams.
-cudaError_t enqueue_chunk(sst_ctx* ctx, sst_host_pipe& p, PipeSlot& s, const Chunk& c, const uint8_t* raw,
-                          const uint64_t* event_off, const uint32_t* fed_len, uint32_t nf) {
+cudaError_t enqueue_chunk(sst_ctx* ctx, sst_host_pipe& p, PipeSlot& s, HostJob* job, size_t ci) {
+  const Chunk& c = job->chunks[ci];
+  const uint8_t* raw = job->raw;
+  const uint64_t* event_off = job->event_off;
+  const uint32_t* fed_len = job->fed_len;
+  const uint32_t nf = job->n_feds;
   const uint32_t E = c.e1 - c.e0;
   uint64_t co = 0;
   for (uint32_t i = 0; i <= E; i++) {
@@ -215,22 +281,25 @@ cudaError_t enqueue_chunk(sst_ctx* ctx, sst_host_pipe& p, PipeSlot& s, const Chu
   if ((e = cudaMemcpyAsync(s.h_pack_off, s.d_pack_off, (E + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, p.stat)))
     return e;
   if ((e = cudaEventRecord(s.ev_status, p.stat))) return e;
-  s.e0 = c.e0;
-  s.e1 = c.e1;
+  s.job = job;
+  s.chunk = ci;
   return cudaSuccess;
 }
 
 // Waits for slot s's statuses, writes them and the event starts, and enqueues
-// the D2H copies of the chunk's clusters at *pos in the caller's arrays
-// (truncated to out->capacity, the cut events flagged).
-cudaError_t finish_chunk(sst_host_pipe& p, PipeSlot& s, const sst_clusters* out, uint64_t* event_first,
-                         sst_event_status* status, uint64_t* pos) {
-  if (s.e1 == s.e0) return cudaSuccess;
+// the D2H copies of the chunk's clusters at the job's next position in the
+// caller's arrays (truncated to out.capacity, the cut events flagged).  After a
+// job's last chunk, writes event_first[n_events] and records the job's event.
+cudaError_t finish_chunk(sst_host_pipe& p, PipeSlot& s) {
+  HostJob* job = s.job;
+  if (!job) return cudaSuccess;
+  const Chunk& c = job->chunks[s.chunk];
   cudaError_t e = cudaEventSynchronize(s.ev_status);
   if (e) return e;
-  const uint32_t E = s.e1 - s.e0;
+  const sst_clusters* out = &job->out;
+  const uint32_t E = c.e1 - c.e0;
   const uint64_t total = s.h_pack_off[E];
-  const uint64_t room = out->capacity > *pos ? out->capacity - *pos : 0;
+  const uint64_t room = out->capacity > job->pos ? out->capacity - job->pos : 0;
   const uint64_t stored = total < room ? total : room;
   for (uint32_t i = 0; i < E; i++) {
     sst_event_status st = s.h_status[i];
@@ -240,11 +309,11 @@ cudaError_t finish_chunk(sst_host_pipe& p, PipeSlot& s, const sst_clusters* out,
       st.n_clusters = (uint32_t)(a < stored ? stored - a : 0);
       st.flags |= SST_EV_CLUSTER_CAPACITY;
     }
-    status[s.e0 + i] = st;
-    event_first[s.e0 + i] = *pos + (a < stored ? a : stored);
+    job->status[c.e0 + i] = st;
+    job->event_first[c.e0 + i] = job->pos + (a < stored ? a : stored);
   }
   if (stored) {
-    const uint64_t q = *pos;
+    const uint64_t q = job->pos;
     if ((e = cudaMemcpyAsync(out->det + q, s.d_det, stored * 4, cudaMemcpyDeviceToHost, p.d2h))) return e;
     if ((e = cudaMemcpyAsync(out->first + q, s.d_first, stored * 2, cudaMemcpyDeviceToHost, p.d2h))) return e;
     if ((e = cudaMemcpyAsync(out->width + q, s.d_width, stored * 2, cudaMemcpyDeviceToHost, p.d2h))) return e;
@@ -252,8 +321,19 @@ cudaError_t finish_chunk(sst_host_pipe& p, PipeSlot& s, const sst_clusters* out,
     if ((e = cudaMemcpyAsync(out->barycenter + q, s.d_bary, stored * 4, cudaMemcpyDeviceToHost, p.d2h))) return e;
   }
   if ((e = cudaEventRecord(s.ev_d2h, p.d2h))) return e;
-  *pos += stored;
-  s.e0 = s.e1 = 0;
+  job->pos += stored;
+  s.job = nullptr;
+  if (++job->finished == job->chunks.size()) {
+    job->event_first[job->n_events] = job->pos;
+    if ((e = cudaEventRecord(job->done, p.d2h))) return e;
+    {
+      std::lock_guard<std::mutex> lock(p.mu);
+      job->recorded = true;
+    }
+    p.cv_done.notify_all();
+  }
+  std::lock_guard<std::mutex> lock(p.mu);
+  p.retired++;
   return cudaSuccess;
 }
 
@@ -284,16 +364,112 @@ std::vector<uint32_t> plan_chunks(uint32_t n_events, int tuned) {
   return cut;
 }
 
+// Finishes every chunk in flight, in order, and waits for all copies.
+cudaError_t drain(sst_host_pipe& p) {
+  cudaError_t e = cudaSuccess;
+  while (!e) {
+    uint64_t r, n;
+    {
+      std::lock_guard<std::mutex> lock(p.mu);
+      r = p.retired;
+      n = p.issued;
+    }
+    if (r == n) break;
+    e = finish_chunk(p, p.slots[r % kSlots]);
+  }
+  for (cudaStream_t st : {p.h2d, p.comp, p.stat, p.d2h})
+    if (!e) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+// Before a job's first chunk: grow the arenas when the job needs more than they
+// hold (after draining the pipeline, so that no chunk in flight uses them).
+cudaError_t prepare_job(sst_host_pipe& p, const HostJob* job) {
+  const uint32_t nf = job->n_feds;
+  bool fits = p.scratch.items_cap >= (size_t)job->max_e * nf * sst::kFe && p.scratch.ev_cap >= job->max_e &&
+              p.scratch.stage_cap >= job->max_clu;
+  for (const PipeSlot& s : p.slots) fits = fits && slot_fits(s, job->max_e, nf, job->max_bytes, job->max_clu);
+  if (fits) return cudaSuccess;
+  cudaError_t e = drain(p);
+  if (!e) e = sst::ensure_scratch(p.scratch, (size_t)job->max_e * nf * sst::kFe, job->max_e, job->max_clu);
+  for (PipeSlot& s : p.slots)
+    if (!e) e = grow_slot(s, job->max_e, nf, job->max_bytes, job->max_clu);
+  return e;
+}
+
+// Marks every job not yet complete as failed with e; the pipeline stays failed.
+void fail_all(sst_host_pipe& p, cudaError_t e) {
+  {
+    std::lock_guard<std::mutex> lock(p.mu);
+    p.fatal = e;
+    for (auto& kv : p.jobs)
+      if (!kv.second->recorded) kv.second->err = e;
+    p.queue.clear();
+    p.issued = p.retired;
+  }
+  for (PipeSlot& s : p.slots) s.job = nullptr;
+  p.cv_done.notify_all();
+}
+
+// The worker: issues the queued jobs' chunks in order, each into the slot whose
+// previous chunk it first finishes; with nothing left to issue, finishes the
+// chunks still in flight.
+void pipe_main(sst_host_pipe* p) {
+  cudaSetDevice(p->ctx->device);
+  for (;;) {
+    HostJob* job = nullptr;
+    bool in_flight;
+    {
+      std::unique_lock<std::mutex> lock(p->mu);
+      p->cv_work.wait(lock, [&] { return p->stop || !p->queue.empty() || p->retired < p->issued; });
+      in_flight = p->retired < p->issued;
+      if (p->queue.empty() && !in_flight) return;  // stop requested, nothing left
+      if (!p->queue.empty()) job = p->queue.front();
+    }
+    cudaError_t e = cudaSuccess;
+    if (job) {
+      if (job->next == 0) e = prepare_job(*p, job);
+      if (!e) {
+        uint64_t g;
+        {
+          std::lock_guard<std::mutex> lock(p->mu);
+          g = p->issued;
+        }
+        PipeSlot& s = p->slots[g % kSlots];
+        if (s.job) e = finish_chunk(*p, s);  // the chunk issued kSlots before
+        if (!e) e = enqueue_chunk(p->ctx, *p, s, job, job->next);
+        if (!e) {
+          std::lock_guard<std::mutex> lock(p->mu);
+          job->next++;
+          p->issued++;
+          if (job->next == job->chunks.size()) p->queue.pop_front();
+        }
+      }
+    } else {
+      uint64_t r;
+      {
+        std::lock_guard<std::mutex> lock(p->mu);
+        r = p->retired;
+      }
+      e = finish_chunk(*p, p->slots[r % kSlots]);
+    }
+    if (e) fail_all(*p, e);
+  }
+}
+
 }  // namespace
 
 using namespace sst;
 
-extern "C" sst_status sst_batch_host(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off,
-                                     const uint32_t* fed_len, uint32_t n_events, uint32_t n_feds,
-                                     const sst_clusters* out, uint64_t* event_first, sst_event_status* status) {
+extern "C" {
+
+sst_status sst_batch_host_submit(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off,
+                                 const uint32_t* fed_len, uint32_t n_events, uint32_t n_feds,
+                                 const sst_clusters* out, uint64_t* event_first, sst_event_status* status,
+                                 uint64_t* ticket) {
   if (!ctx) return SST_ERR_INVALID_ARG;
   if (!ctx->has_calib) return set_err(ctx, SST_ERR_NO_CALIB, "sst_batch_host: no calibration");
-  if (!raw || !event_off || !fed_len || !out || !event_first || !status || !out->det || !out->first ||
+  if (!raw || !event_off || !fed_len || !out || !event_first || !status || !ticket || !out->det || !out->first ||
       !out->width || !out->charge || !out->barycenter)
     return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch_host: null pointer");
   if (n_events == 0 || n_feds == 0 || n_feds > ctx->n_feds)
@@ -303,49 +479,107 @@ extern "C" sst_status sst_batch_host(sst_ctx* ctx, const uint8_t* raw, const uin
   for (uint32_t i = 0; i < n_events; i++)
     if (event_off[i + 1] < event_off[i])
       return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch_host: event_off decreases");
+  auto* job = new HostJob();
+  job->raw = raw;
+  job->event_off = event_off;
+  job->fed_len = fed_len;
+  job->n_events = n_events;
+  job->n_feds = n_feds;
+  job->out = *out;
+  job->event_first = event_first;
+  job->status = status;
   // chunks of consecutive events
   const std::vector<uint32_t> cut = plan_chunks(n_events, ctx->shape.host_chunk);
-  std::vector<Chunk> chunks;
-  uint32_t max_e = 0;
-  uint64_t max_bytes = 0, max_clu = 0;
   for (size_t k = 0; k + 1 < cut.size(); k++) {
     const uint32_t e0 = cut[k], e1 = cut[k + 1];
     Chunk c{e0, e1, event_off[e0] & ~15ull, 0, 0};
     c.bytes = event_off[e1] - c.base;
     for (uint32_t i = e0; i < e1; i++) c.clu_total += (event_off[i + 1] - event_off[i]) / 2 + 1;
-    chunks.push_back(c);
-    if (e1 - e0 > max_e) max_e = e1 - e0;
-    if (c.bytes > max_bytes) max_bytes = c.bytes;
-    if (c.clu_total > max_clu) max_clu = c.clu_total;
+    job->chunks.push_back(c);
+    if (e1 - e0 > job->max_e) job->max_e = e1 - e0;
+    if (c.bytes > job->max_bytes) job->max_bytes = c.bytes;
+    if (c.clu_total > job->max_clu) job->max_clu = c.clu_total;
   }
-  if ((uint64_t)max_e * n_feds >= (1ull << 31))
+  if ((uint64_t)job->max_e * n_feds >= (1ull << 31)) {
+    delete job;
     return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch_host: too many FED records in one chunk");
-  std::lock_guard<std::mutex> lock(ctx->mu);
+  }
   DeviceGuard g(ctx->device);
-  cudaError_t e = cudaSuccess;
-  if (!ctx->pipe) ctx->pipe = new sst_host_pipe();
-  sst_host_pipe& p = *ctx->pipe;
-  for (cudaStream_t* st : {&p.h2d, &p.comp, &p.stat, &p.d2h})
-    if (!e && !*st) e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
-  if (!e) e = ensure_scratch(p.scratch, (size_t)max_e * n_feds * kFe, max_e, max_clu);
-  PipeSlot* slots = p.slots;
-  const int used = chunks.size() < (size_t)kSlots ? (int)chunks.size() : kSlots;
-  for (int k = 0; k < used && !e; k++) e = grow_slot(slots[k], max_e, n_feds, max_bytes, max_clu);
-  uint64_t pos = 0;
-  for (size_t j = 0; j < chunks.size() && !e; j++) {
-    PipeSlot& s = slots[j % kSlots];
-    e = finish_chunk(p, s, out, event_first, status, &pos);
-    if (!e) e = enqueue_chunk(ctx, p, s, chunks[j], raw, event_off, fed_len, n_feds);
+  cudaError_t e = cudaEventCreateWithFlags(&job->done, cudaEventDisableTiming);
+  if (e) {
+    delete job;
+    return cuda_err(ctx, e, "sst_batch_host event");
   }
-  // the remaining chunks, in order, then every copy
-  for (size_t j = chunks.size() > (size_t)kSlots ? chunks.size() - kSlots : 0; j < chunks.size() && !e; j++)
-    e = finish_chunk(p, slots[j % kSlots], out, event_first, status, &pos);
-  for (cudaStream_t st : {p.h2d, p.comp, p.stat, p.d2h}) {
-    const cudaError_t q = st ? cudaStreamSynchronize(st) : cudaSuccess;
-    if (!e) e = q;
+  sst_host_pipe* p;
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);  // creates the pipeline once
+    if (!ctx->pipe) {
+      p = new sst_host_pipe();
+      p->ctx = ctx;
+      for (cudaStream_t* st : {&p->h2d, &p->comp, &p->stat, &p->d2h})
+        if (!e && !*st) e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
+      if (!e) {
+        ctx->pipe = p;
+        p->worker = std::thread(pipe_main, p);
+      } else {
+        for (cudaStream_t st : {p->h2d, p->comp, p->stat, p->d2h})
+          if (st) cudaStreamDestroy(st);
+        delete p;
+      }
+    }
+    p = ctx->pipe;
   }
-  for (int k = 0; k < kSlots; k++) slots[k].e0 = slots[k].e1 = 0;
-  if (e) return cuda_err(ctx, e, "sst_batch_host");
-  event_first[n_events] = pos;
+  if (e) {
+    cudaEventDestroy(job->done);
+    delete job;
+    return cuda_err(ctx, e, "sst_batch_host streams");
+  }
+  {
+    std::lock_guard<std::mutex> lock(p->mu);
+    if (p->fatal) {
+      cudaEventDestroy(job->done);
+      delete job;
+      return cuda_err(ctx, p->fatal, "sst_batch_host (an earlier batch failed)");
+    }
+    job->ticket = p->next_ticket++;
+    *ticket = job->ticket;
+    p->jobs[job->ticket] = job;
+    p->queue.push_back(job);
+  }
+  p->cv_work.notify_all();
   return SST_OK;
 }
+
+sst_status sst_batch_host_wait(sst_ctx* ctx, uint64_t ticket) {
+  if (!ctx) return SST_ERR_INVALID_ARG;
+  sst_host_pipe* p = ctx->pipe;
+  if (!p) return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch_host_wait: unknown ticket");
+  HostJob* job;
+  {
+    std::unique_lock<std::mutex> lock(p->mu);
+    auto it = p->jobs.find(ticket);
+    if (it == p->jobs.end()) return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch_host_wait: unknown ticket");
+    job = it->second;
+    p->cv_done.wait(lock, [&] { return job->recorded || job->err != cudaSuccess; });
+  }
+  cudaError_t e = job->err;
+  if (!e) e = cudaEventSynchronize(job->done);
+  {
+    std::lock_guard<std::mutex> lock(p->mu);
+    p->jobs.erase(ticket);
+  }
+  cudaEventDestroy(job->done);
+  delete job;
+  return cuda_err(ctx, e, "sst_batch_host");
+}
+
+sst_status sst_batch_host(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len,
+                          uint32_t n_events, uint32_t n_feds, const sst_clusters* out, uint64_t* event_first,
+                          sst_event_status* status) {
+  uint64_t t = 0;
+  const sst_status r = sst_batch_host_submit(ctx, raw, event_off, fed_len, n_events, n_feds, out, event_first, status,
+                                             &t);
+  return r == SST_OK ? sst_batch_host_wait(ctx, t) : r;
+}
+
+}  // extern "C"

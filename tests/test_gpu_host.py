@@ -124,3 +124,31 @@ def test_host_batch_rejects_decreasing_offsets(w0):
     with pytest.raises(sst.SstError):
         sst.sst_batch_host(g.ctx, np.concatenate([raw, np.zeros(32, np.uint8)]), eoff, fl, 2, g.n_feds, out,
                            np.zeros(3, np.uint64), np.zeros((2, 4), np.uint32))
+
+
+def test_submitted_batches_overlap_and_each_equals_the_oracle(w0):
+    """Three batches queued back to back (the second larger, so the arenas grow
+    between batches), waited in reverse order; each equals the oracle."""
+    w, calib, g = w0
+    sets = [[eg.make_event(w, calib, 800 + 10 * b + i, occupancy=0.003 + 0.01 * b) for i in range(n)]
+            for b, n in enumerate((5, 9, 3))]
+    pending = []
+    for events in sets:
+        raw, eoff, fl = _arena(events)
+        out = sst.HostClusters.alloc(sum(e.nbytes // 2 + 1 for e in events), pinned=True)
+        first = np.zeros(len(events) + 1, np.uint64)
+        status = np.zeros((len(events), 4), np.uint32)
+        t = sst.sst_batch_host_submit(g.ctx, raw, eoff, fl, len(events), g.n_feds, out, first, status)
+        pending.append((t, events, raw, eoff, fl, out, first, status))
+    for t, events, raw, eoff, fl, out, first, status in reversed(pending):
+        sst.sst_batch_host_wait(g.ctx, t)
+        pos = 0
+        for k, e in enumerate(events):
+            _, oc, ost = g.oracle(e.raw, e.fed_len, w.n_feds)
+            assert _status(status[k]) == ost
+            assert int(first[k]) == pos
+            assert_clusters_equal(out.view(pos, ost["n_clusters"]), oc)
+            pos += ost["n_clusters"]
+        assert int(first[-1]) == pos
+    with pytest.raises(sst.SstError):
+        sst.sst_batch_host_wait(g.ctx, pending[0][0])  # already released
