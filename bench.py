@@ -562,18 +562,24 @@ def main():
     # ---- served stream: continuous batching behind sst_submit / sst_poll
     served = None
     if served_pool:
-        sst.sst_server_start(ctx, 8 << 30, 64, 3, 4096, w.n_feds)
+        # the events live in pinned memory and are lent to the server (zero-copy
+        # submission): the client does no per-event copy
+        pinned = [torch.from_numpy(r).pin_memory() for r, _ in served_pool]
+        lent = [(p.numpy(), f) for p, (_, f) in zip(pinned, served_pool)]
+        sst.sst_server_start(ctx, 8 << 30, 64, 3, 4096, w.n_feds, zero_copy=True)
         try:
-            run_served(sst, ctx, served_pool, w.n_feds, 500, 0.0)  # warm-up
-            cap = run_served(sst, ctx, served_pool, w.n_feds, args.served_events, 0.0)
-            pts = [run_served(sst, ctx, served_pool, w.n_feds, args.served_events, f * cap["throughput"])
+            run_served(sst, ctx, lent, w.n_feds, 500, 0.0)  # warm-up
+            cap = run_served(sst, ctx, lent, w.n_feds, args.served_events, 0.0)
+            pts = [run_served(sst, ctx, lent, w.n_feds, args.served_events, f * cap["throughput"])
                    for f in (0.5, 0.9)]
             served = {"workload": "served-440fed-lognormal: occupancy lognormal median 1.5%, clip [0.5%, 5%], "
-                                  "64 distinct events cycled, Poisson arrivals, 8 Python submitter threads",
+                                  "64 distinct events cycled, Poisson arrivals, 8 Python submitter threads, "
+                                  "zero-copy submission from pinned event buffers",
                       "budget_bytes": 8 << 30, "max_batch_events": 64, "max_inflight": 3,
                       "saturation": cap, "points": pts}
         finally:
             sst.sst_server_stop(ctx)
+        del pinned, lent
 
     # ---- roofline of the dominant kernel (the batched kernel)
     peak, peak_kind = measured_peaks()

@@ -364,6 +364,10 @@ typedef struct {
   uint32_t max_inflight;     /* launches in flight at once (streams) */
   uint32_t max_requests;     /* request slots (admitted + finished-not-polled) */
   uint32_t n_feds;           /* FEDs per event */
+  uint32_t zero_copy;        /* 0: sst_submit copies the event into the server's pinned pool, the
+                                caller may reuse its buffer at once; 1: no copy, the server reads
+                                the caller's buffer (pinned memory gives full copy speed), which
+                                must stay unchanged until sst_poll returns for the ticket */
 } sst_server_opts;
 
 /* Starts the request loop (one host thread, max_inflight streams).  Requires

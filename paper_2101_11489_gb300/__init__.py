@@ -86,7 +86,8 @@ class sst_tune(ctypes.Structure):
 
 class sst_server_opts(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("max_batch_events", ctypes.c_uint32),
-                ("max_inflight", ctypes.c_uint32), ("max_requests", ctypes.c_uint32), ("n_feds", ctypes.c_uint32)]
+                ("max_inflight", ctypes.c_uint32), ("max_requests", ctypes.c_uint32), ("n_feds", ctypes.c_uint32),
+                ("zero_copy", ctypes.c_uint32)]
 
 
 class sst_result_info(ctypes.Structure):
@@ -316,8 +317,10 @@ def sst_profile_read(ctx: int, reset: bool = True) -> tuple[int, float]:
 
 
 def sst_server_start(ctx: int, mem_budget_bytes: int, max_batch_events: int, max_inflight: int, max_requests: int,
-                     n_feds: int) -> None:
-    o = sst_server_opts(mem_budget_bytes, max_batch_events, max_inflight, max_requests, n_feds)
+                     n_feds: int, zero_copy: bool = False) -> None:
+    """zero_copy: sst_submit lends the caller's buffer to the server (no copy); it
+    must stay alive and unchanged until sst_poll returns for the ticket."""
+    o = sst_server_opts(mem_budget_bytes, max_batch_events, max_inflight, max_requests, n_feds, 1 if zero_copy else 0)
     _check(ctx, load_library().sst_server_start(ctx, ctypes.byref(o)), "sst_server_start")
 
 

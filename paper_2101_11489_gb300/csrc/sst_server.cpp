@@ -91,7 +91,8 @@ enum class SlotState { kFree, kRunning, kReading };
 struct Req {
   ReqState state = ReqState::kFree;
   uint64_t ticket = 0;
-  size_t host_off = 0;   // raw bytes in the host pool
+  size_t host_off = 0;   // raw bytes in the host pool (reserved also in zero-copy mode, for admission)
+  const uint8_t* src = nullptr;  // zero-copy mode: the caller's bytes
   uint64_t bytes = 0;
   std::vector<uint32_t> fed_len;
   double t_submit = 0, t_done = 0;
@@ -263,7 +264,8 @@ bool launch_on(sst_server* sv, int si) {
     s.h_event_off[i] = off;
     s.h_clu_off[i] = coff;
     std::memcpy(s.h_fed_len + (size_t)i * nf, r.fed_len.data(), nf * sizeof(uint32_t));
-    if (!e) e = cudaMemcpyAsync(s.d_raw + off, sv->host_pool + r.host_off, r.bytes, cudaMemcpyHostToDevice, s.st);
+    const uint8_t* src = r.src ? r.src : sv->host_pool + r.host_off;
+    if (!e) e = cudaMemcpyAsync(s.d_raw + off, src, r.bytes, cudaMemcpyHostToDevice, s.st);
     off += r.bytes;
     coff += r.bytes / 2 + 1;
     r.state = ReqState::kLaunched;
@@ -385,10 +387,10 @@ sst_status sst_server_start(sst_ctx* ctx, const sst_server_opts* opts) {
   const sst_server_opts& o = *opts;
   if (o.mem_budget_bytes < (64ull << 20) || o.max_batch_events == 0 || o.max_batch_events > 4096 ||
       o.max_inflight == 0 || o.max_inflight > 8 || o.max_requests == 0 || o.max_requests > (1u << 20) ||
-      o.n_feds == 0 || o.n_feds > ctx->n_feds)
+      o.n_feds == 0 || o.n_feds > ctx->n_feds || o.zero_copy > 1)
     return sst::set_err(ctx, SST_ERR_INVALID_ARG,
                         "sst_server_start: need budget >= 64 MiB, 1..4096 events per batch, 1..8 in flight, "
-                        "1..2^20 requests and 1..context FEDs per event");
+                        "1..2^20 requests, 1..context FEDs per event and zero_copy 0 or 1");
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(ctx->device);
@@ -473,12 +475,13 @@ sst_status sst_submit(sst_ctx* ctx, const uint8_t* raw, uint64_t raw_bytes, cons
     r.ticket = sv->next_ticket++;
     *ticket = r.ticket;
   }
-  // copy outside the lock, then queue
-  std::memcpy(sv->host_pool + off, raw, raw_bytes);
+  // copy outside the lock (unless the caller lends its buffer), then queue
+  if (!sv->opts.zero_copy) std::memcpy(sv->host_pool + off, raw, raw_bytes);
   std::vector<uint32_t> fl(fed_len, fed_len + sv->opts.n_feds);
   {
     std::lock_guard<std::mutex> lock(sv->mu);
     Req& r = sv->reqs[ri];
+    r.src = sv->opts.zero_copy ? raw : nullptr;
     r.fed_len.swap(fl);
     r.t_submit = now_us();
     sv->pending.push_back(ri);

@@ -96,3 +96,28 @@ def test_admission_limits(served):
         assert sst.sst_poll(g.ctx, t, -1, 0)[0] == sst.SST_OK
     with pytest.raises(sst.SstError):
         sst.sst_poll(g.ctx, 123456789, 0, 0)
+
+
+def test_zero_copy_submission_equals_the_oracle():
+    """With zero_copy the server reads each event from the caller's (pinned)
+    buffer, which the caller keeps until the event is polled."""
+    w = eg.WORKLOADS[0]
+    calib = eg.make_calibration(w.n_feds, w.seed, w.p_bad)
+    g = Gpu(calib.noise, calib.gain, calib.bad)
+    sst.sst_server_start(g.ctx, 256 << 20, 4, 2, 64, w.n_feds, zero_copy=True)
+    try:
+        events = [eg.make_event(w, calib, 900 + i, occupancy=0.002 + 0.004 * (i % 5)) for i in range(12)]
+        pinned = [torch.from_numpy(e.raw).pin_memory() for e in events]  # lent to the server until polled
+        tickets = []
+        for e, p in zip(events, pinned):
+            code, t = sst.sst_submit(g.ctx, p.numpy(), e.fed_len)
+            assert code == sst.SST_OK
+            tickets.append(t)
+        for e, t in zip(events, tickets):
+            st, cl = _poll(g, t, e.nbytes)
+            _, oc, ost = g.oracle(e.raw, e.fed_len, w.n_feds)
+            assert st == ost
+            assert_clusters_equal(cl, oc)
+    finally:
+        sst.sst_server_stop(g.ctx)
+        g.close()
