@@ -161,9 +161,10 @@ typedef struct {
    * gain-corrected charge when the strip is active, else 0 (a hole, a bad strip
    * inside, a bad strip the cluster was widened over): cluster k's width[k]
    * amplitudes are amp[amp_first[k] ..].  Within an event they follow the
-   * cluster order.  When an FE unit's amplitudes do not fit, none of them is
-   * stored, its clusters get amp_first = 0xFFFFFFFF and the event
-   * SST_EV_AMP_CAPACITY (the clusters themselves are unaffected). */
+   * cluster order.  Amplitudes are allocated per work item (one FE unit per
+   * warp in sst_cluster, two in sst_batch); when an item's amplitudes do not
+   * fit, none of them is stored, its clusters get amp_first = 0xFFFFFFFF and the
+   * event SST_EV_AMP_CAPACITY (the clusters themselves are unaffected). */
   uint8_t* amp;            /* [amp_capacity] */
   uint32_t* amp_first;     /* [capacity], absolute index into amp */
   const uint64_t* amp_off; /* sst_batch: [n_events + 1] device; event e's amplitudes lie in
@@ -216,8 +217,8 @@ sst_status sst_unpack(sst_ctx* ctx, const uint8_t* raw, uint64_t raw_bytes, cons
  * three-threshold algorithm (section 2).  Writes the cluster SoA and sets
  * in->status->n_clusters.  When the event has more clusters than out->capacity,
  * SST_EV_CLUSTER_CAPACITY is ORed into in->status->flags and the arrays hold a
- * sorted subset of the event's clusters (whole FEDs first, in allocation order).
- * NO_CALIB before sst_calib_upload. */
+ * sorted subset of the event's clusters (those of whole FE units, in allocation
+ * order).  NO_CALIB before sst_calib_upload. */
 sst_status sst_cluster(sst_ctx* ctx, const sst_digis* in, uint32_t n_feds, const sst_clusters* out,
                        void* stream);
 
@@ -247,9 +248,11 @@ sst_status sst_unpack_noalloc(const uint8_t* raw, uint64_t raw_bytes, const uint
 /* ---- batched path (section 3: many events concurrently on one GPU) -------------- */
 
 /* Unpacks and clusters n_events events in one persistent launch; digis stay on
- * chip.  Every FED's clusters are staged (context scratch of out->capacity
- * records), then ordered per event by a scan and a copy kernel.  All pointers are
- * device memory:
+ * chip.  Each warp takes two adjacent FE units at a time; their clusters are
+ * staged (context scratch of out->capacity records), then ordered per event by a
+ * scan and a copy kernel.  The launch sequence allocates nothing once the context
+ * has run one batch of this size, so it can be captured in a CUDA graph.  All
+ * pointers are device memory:
  *   raw        events back to back; event e occupies [event_off[e], event_off[e+1]),
  *              every event_off[e] a multiple of 16
  *   event_off  [n_events + 1] uint64
@@ -269,7 +272,10 @@ sst_status sst_batch(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off
  * pointer is host memory and the call is synchronous: it returns when all
  * results are in the caller's arrays.  The batch is cut into chunks of
  * consecutive events; the host->device copy, the kernels and the device->host
- * copy of successive chunks overlap on three streams of the context.
+ * copy of successive chunks overlap on the context's streams (by default 4, 16,
+ * ..., 16, 8, 4 events: short first and last chunks; sst_tune.host_chunk_events
+ * sets equal chunks, best with the batch size when several batches are in
+ * flight through sst_batch_host_submit).
  *   raw, event_off, fed_len  as for sst_batch, in host memory; event_off need
  *              not start at 0 (only [event_off[0], event_off[n_events]) is read)
  *   out        host arrays of out->capacity records; the events' clusters are
