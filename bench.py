@@ -296,6 +296,18 @@ def dist_env():
     return rank, world, local
 
 
+def cpu_model() -> str:
+    """The host CPU as the OS describes it (model name, or the Arm part number)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -606,6 +618,7 @@ def main():
         n_sample = min(len(events), max(cores * 4, 16))
         v, wall, cpu_s = time_oracle(pool, cores, events, n_sample)
         cpu = {"value": round(v, 2), "unit": "events/s", "cores": cores, "kind": "oracle",
+               "per_core": round(v / cores, 2), "cpu_model": cpu_model(),
                "sample": f"{n_sample} of the {n_events} events (unpack + cluster, sequential C, one event per "
                          f"process), {wall:.1f} s wall, {cpu_s:.1f} s CPU"}
     pool.terminate()
@@ -620,6 +633,9 @@ def main():
             "steps": args.steps,
             "warmup": args.warmup,
             "ms_per_step": round(ms_per_step, 4),
+            "step_ms_percentiles": {"p10": round(float(np.percentile(step_ms, 10)), 4),
+                                    "median": round(float(np.median(step_ms)), 4),
+                                    "p90": round(float(np.percentile(step_ms, 90)), 4)},
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
