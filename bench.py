@@ -338,12 +338,13 @@ def kernel_source_sha256():
 
 def algorithmic_bytes(events, n_digi, n_clusters):
     """Bytes the batched kernel must move, per the path's dataflow: FED payload read
-    once, noise (4 B) of every recorded strip, the 256-bit bad-strip mask (32 B) and
-    two APV gains (8 B) of every channel, fed_len / fed_off (12 B) per FED, the
-    cluster SoA (16 B per cluster) and one 16-byte status per event."""
+    once, noise (4 B) and longest linking gap (1 B) of every recorded strip, the
+    256-bit bad-strip mask (32 B) and two APV gains (8 B) of every channel, fed_len /
+    fed_off (12 B) per FED, the cluster SoA (16 B per cluster) and one 16-byte status
+    per event."""
     payload = sum(int(e[0].size) for e in events)
     n_feds = sum(int(e[1].size) for e in events)
-    return payload + 4 * n_digi + n_feds * 96 * (32 + 8) + 12 * n_feds + 16 * n_clusters + 16 * len(events)
+    return payload + 5 * n_digi + n_feds * 96 * (32 + 8) + 12 * n_feds + 16 * n_clusters + 16 * len(events)
 
 
 # ---------------------------------------------------------------- main

@@ -29,6 +29,7 @@ KParams kparams(const sst_ctx* c) {
   k.max_adj = c->params.max_adj_bad;
   k.noise = c->noise;
   k.badmask = c->badmask;
+  k.gapmax = c->gapmax;
   k.gain = c->gain;
   return k;
 }
@@ -158,6 +159,7 @@ sst_status sst_destroy(sst_ctx* ctx) {
   free_scratch(ctx->scratch);
   if (ctx->noise) cudaFree(ctx->noise);
   if (ctx->badmask) cudaFree(ctx->badmask);
+  if (ctx->gapmax) cudaFree(ctx->gapmax);
   if (ctx->gain) cudaFree(ctx->gain);
   if (ctx->pitch) cudaFree(ctx->pitch);
   delete ctx;
@@ -190,6 +192,7 @@ sst_status sst_calib_upload(sst_ctx* ctx, const float* noise, const float* gain,
   if (!ctx->noise) {
     if ((e = cudaMalloc(&ctx->noise, n * sizeof(float)))) return cuda_err(ctx, e, "cudaMalloc noise");
     if ((e = cudaMalloc(&ctx->badmask, n / 8))) return cuda_err(ctx, e, "cudaMalloc badmask");
+    if ((e = cudaMalloc(&ctx->gapmax, n))) return cuda_err(ctx, e, "cudaMalloc gapmax");
     if ((e = cudaMalloc(&ctx->gain, n_apv * sizeof(float)))) return cuda_err(ctx, e, "cudaMalloc gain");
   }
   uint8_t* bad_dev = nullptr;
@@ -200,6 +203,7 @@ sst_status sst_calib_upload(sst_ctx* ctx, const float* noise, const float* gain,
   if (!e) e = cudaMemcpyAsync(ctx->gain, gain, n_apv * sizeof(float), cudaMemcpyHostToDevice, st);
   if (!e) e = cudaMemcpyAsync(bad_dev, bad, n, cudaMemcpyHostToDevice, st);
   if (!e) e = build_badmask(bad_dev, ctx->badmask, n, st);
+  if (!e) e = build_gapmax(ctx->badmask, ctx->gapmax, n, params->max_seq_holes, params->max_seq_bad, st);
   if (!e) e = cudaStreamSynchronize(st);
   cudaFree(bad_dev);
   if (e) return cuda_err(ctx, e, "sst_calib_upload");

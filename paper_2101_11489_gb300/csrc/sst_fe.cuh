@@ -12,8 +12,8 @@
 // chains, run walks) then occupy 24 lanes instead of 12, and the fixed cost of an
 // item is paid once per pair.
 //
-// Included by sst_kernels.cu only, inside its namespace, after the mask and
-// gap helpers it uses (bit, count_range, linked_gap).
+// Included by sst_kernels.cu only, inside its namespace, after the mask helper it
+// uses (bit).
 #pragma once
 
 namespace fe {
@@ -156,7 +156,7 @@ __device__ __forceinline__ int chunk_end(const Warp& w, int c0) {
 // time and finds its run as the last run start at or before it: the highest set
 // bit at or below the lane in the ballot of its 32-digi window, or the last run
 // start of the windows before.  Descriptors and flags live in nsq[] and flag[],
-// which flag_unit overwrites afterwards.
+// which scan_unit overwrites afterwards.
 __device__ void copy_runs(Warp& w, const Unit& un, int c0, int c1) {
   const int lane = threadIdx.x & 31;
   uint32_t* desc = reinterpret_cast<uint32_t*>(w.nsq);
@@ -203,107 +203,87 @@ __device__ void copy_runs(Warp& w, const Unit& un, int c0, int c1) {
   __syncwarp();
 }
 
-// a3 for the n digis of the tile, one lane per digi, two noise loads in flight:
-// the channel and seed thresholds (binary32 product threshold x noise, strict
-// "larger than"), the gain-corrected charge and noise^2 of active digis.
+// a3 + a4 in one pass over the tile, 32 digis at a time in strip order, with the
+// next window's noise gather in flight:
+//  - thresholds (binary32 product threshold x noise, strict "larger than"), the
+//    gain-corrected charge (saturation codes 254/255 kept) and noise^2 of active
+//    digis;
+//  - candidate starts: an active digi whose previous active digi in the tile lies
+//    in another channel (the tile is sorted by channel, then strip) or is not
+//    linked to it by the hole / bad-strip rules, i.e. is more than gapmax[strip]
+//    strips below it (the longest linking gap, built from the bad-strip mask
+//    when the calibration is uploaded);
+//  - owners, the leftmost seed of every candidate: two ballots (seeds, candidate
+//    starts) and a carry across windows decide whether another seed lies between
+//    a seed's candidate start and it.
+// The first digis of owned candidates are compacted in strip order into own[];
+// returns their number.
 template <int NCH>
-__device__ __forceinline__ void flag_one(Warp& w, const KParams& kp, int i, float nz) {
-  const uint32_t key = w.key[i];
-  const uint32_t c = key >> 8, st = key & 255u;
-  if (c >= (uint32_t)NCH) {  // a digi that takes no part in clustering
-    w.flag[i] = 0;
-    w.q[i] = 0;
-    w.nsq[i] = 0.f;
-    return;
-  }
-  const bool isbad = (w.bad[c * kMaskWords + (st >> 5)] >> (st & 31u)) & 1u;
-  const uint32_t adc = w.adc[i];
-  const float a = __uint2float_rn(adc);
-  const bool act = !isbad && a > __fmul_rn(kp.t_channel, nz);
-  const bool sd = !isbad && a > __fmul_rn(kp.t_seed, nz);
-  uint32_t q = 0;
-  float nsq = 0.f;
-  if (act) {
-    if (adc >= 254u) {
-      q = adc;  // saturation codes are kept
-    } else {
-      const float x = __fdiv_rn(a, w.gain[c * 2 + (st >> 7)]);
-      const int ci = __float2int_rz(__fadd_rn(x, 0.5f));
-      q = ci > 253 ? 254u : (uint32_t)ci;
-    }
-    nsq = __fmul_rn(nz, nz);
-  }
-  w.flag[i] = (uint8_t)((act ? 1 : 0) | (sd ? 2 : 0));
-  w.q[i] = (uint8_t)q;
-  w.nsq[i] = nsq;
-}
-
-template <int NCH>
-__device__ void flag_unit(Warp& w, const KParams& kp, const float* noise, int n) {
+__device__ int scan_unit(Warp& w, const KParams& kp, const float* noise, const uint8_t* gapmax, int n) {
   const int lane = threadIdx.x & 31;
-  for (int i0 = lane; i0 < n; i0 += 64) {
-    const int i1 = i0 + 32;
-    const uint32_t k0 = w.key[i0], k1 = i1 < n ? w.key[i1] : k0;
-    const float nz0 = __ldg(noise + (k0 >> 8 < (uint32_t)NCH ? k0 : 0u));
-    const float nz1 = __ldg(noise + (k1 >> 8 < (uint32_t)NCH ? k1 : 0u));
-    flag_one<NCH>(w, kp, i0, nz0);
-    if (i1 < n) flag_one<NCH>(w, kp, i1, nz1);
-  }
-  __syncwarp();
-}
-
-// a4, candidate boundaries: an active digi not linked (hole / bad-strip rules) to
-// the previous active strip of its channel is the first strip of a candidate.
-__device__ void starts_unit(Warp& w, const KParams& kp, int n) {
-  const int lane = threadIdx.x & 31;
-  for (int i = lane; i < n; i += 32) {
-    if (!(w.flag[i] & 1)) continue;
-    const uint32_t key = w.key[i];
-    const uint32_t c = key >> 8;
-    int a = -1;
-    for (int j = i - 1; j >= 0; --j) {
-      const uint32_t kj = w.key[j];
-      if ((kj >> 8) != c) break;
-      if (w.flag[j] & 1) {
-        a = (int)(kj & 255u);
-        break;
-      }
-    }
-    if (a < 0 || !linked_gap(w.bad + c * kMaskWords, a, (int)(key & 255u), kp.max_holes, kp.max_bad))
-      w.flag[i] |= 4;
-  }
-  __syncwarp();
-}
-
-// a4, seed array: the leftmost seed of every candidate owns it.  The digis are
-// scanned 32 at a time in strip order; two ballots (seeds, candidate starts) and
-// a carry across windows decide, for every seed, whether another seed lies
-// between its candidate's first strip and it.  The first digis of owned
-// candidates are compacted in strip order into own[]; returns their number.
-__device__ int owners_unit(Warp& w, int n) {
-  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt(lane);
+  const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+  constexpr uint32_t kNone = 0xffffffffu;  // no digi: its channel is out of range
   int n_own = 0, carry_start = -1;
   bool carry_seen = false;
+  uint32_t carry_key = kNone;  // key of the last active digi of the windows before
+  uint32_t kn = lane < n ? (uint32_t)w.key[lane] : kNone;
+  uint32_t xn = (kn >> 8) < (uint32_t)NCH ? kn : 0u;
+  float zn = __ldg(noise + xn);
+  uint32_t gn = __ldg(gapmax + xn);
   for (int base = 0; base < n; base += 32) {
     const int i = base + lane;
-    const uint8_t f = i < n ? w.flag[i] : 0;
-    const unsigned S = __ballot_sync(0xffffffffu, (f & 2) != 0);
-    const unsigned B = __ballot_sync(0xffffffffu, (f & 4) != 0);
-    const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    const uint32_t key = kn;
+    const float nz = zn;
+    const uint32_t gmax = gn;
+    if (base + 32 < n) {
+      kn = i + 32 < n ? (uint32_t)w.key[i + 32] : kNone;
+      xn = (kn >> 8) < (uint32_t)NCH ? kn : 0u;
+      zn = __ldg(noise + xn);
+      gn = __ldg(gapmax + xn);
+    }
+    const uint32_t c = key >> 8, st = key & 255u;
+    bool act = false, sd = false;
+    uint32_t q = 0;
+    float nsq = 0.f;
+    if (c < (uint32_t)NCH) {
+      const bool isbad = (w.bad[c * kMaskWords + (st >> 5)] >> (st & 31u)) & 1u;
+      const uint32_t adc = w.adc[i];
+      const float a = __uint2float_rn(adc);
+      act = !isbad && a > __fmul_rn(kp.t_channel, nz);
+      sd = !isbad && a > __fmul_rn(kp.t_seed, nz);
+      if (act) {
+        if (adc >= 254u) {
+          q = adc;  // saturation codes are kept
+        } else {
+          const float x = __fdiv_rn(a, w.gain[c * 2 + (st >> 7)]);
+          const int ci = __float2int_rz(__fadd_rn(x, 0.5f));
+          q = ci > 253 ? 254u : (uint32_t)ci;
+        }
+        nsq = __fmul_rn(nz, nz);
+      }
+    }
+    const unsigned A = __ballot_sync(0xffffffffu, act);
+    const unsigned Al = A & lt;
+    const uint32_t pk_l = __shfl_sync(0xffffffffu, key, Al ? 31 - __clz(Al) : lane);
+    const uint32_t pk = Al ? pk_l : carry_key;
+    const bool start = act && ((pk >> 8) != c || st - (pk & 255u) - 1u > gmax);
+    const unsigned S = __ballot_sync(0xffffffffu, sd);
+    const unsigned B = __ballot_sync(0xffffffffu, start);
     const unsigned mb = B & upto;
     bool seen;
-    int start;
+    int cs;
     if (mb) {
       const int ls = 31 - __clz(mb);
-      seen = (S & lanemask_lt(lane) & ~lanemask_lt(ls)) != 0;
-      start = base + ls;
+      seen = (S & lt & ~lanemask_lt(ls)) != 0;
+      cs = base + ls;
     } else {
-      seen = carry_seen || (S & lanemask_lt(lane)) != 0;
-      start = carry_start;
+      seen = carry_seen || (S & lt) != 0;
+      cs = carry_start;
     }
-    const bool owner = (f & 2) && !seen;
+    const bool owner = sd && !seen;
     const unsigned O = __ballot_sync(0xffffffffu, owner);
-    if (owner) w.own[n_own + __popc(O & lanemask_lt(lane))] = (uint16_t)start;
+    if (owner) w.own[n_own + __popc(O & lt)] = (uint16_t)cs;
     n_own += __popc(O);
     if (B) {
       const int lw = 31 - __clz(B);
@@ -311,6 +291,12 @@ __device__ int owners_unit(Warp& w, int n) {
       carry_seen = (S >> lw) != 0;
     } else {
       carry_seen = carry_seen || S != 0;
+    }
+    if (A) carry_key = __shfl_sync(0xffffffffu, key, 31 - __clz(A));
+    if (i < n) {
+      w.flag[i] = (uint8_t)((act ? 1 : 0) | (sd ? 2 : 0) | (start ? 4 : 0));
+      w.q[i] = (uint8_t)q;
+      w.nsq[i] = nsq;
     }
   }
   __syncwarp();
@@ -444,13 +430,16 @@ struct SegOut {
 // counted, then their region is allocated in one piece, then they are written; a
 // unit whose digis exceed the tile goes through its channel chunks twice.  Without
 // amplitudes, the records of the first 32 candidates are kept in registers from
-// the counting pass.  NCH: channels of the work item (12 or 24); AMP: amplitudes
+// the counting pass.  s0: the work item's first strip in the per-strip
+// calibration tables; NCH: channels of the work item (12 or 24); AMP: amplitudes
 // are wanted (so.amp is then non-null).
 template <int NCH, bool AMP, typename Fill>
-__device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uint32_t det0, uint32_t total,
+__device__ void cluster_unit(Warp& w, const KParams& kp, size_t s0, uint32_t det0, uint32_t total,
                              Fill& fill, const SegOut& so, sst_event_status* status) {
   const int lane = threadIdx.x & 31;
   const bool single = total <= (uint32_t)kTile;
+  const float* noise = kp.noise + s0;
+  const uint8_t* gapmax = kp.gapmax + s0;
   constexpr bool amps = AMP;
   uint32_t found = 0, found0 = 0, wsum = 0;
   int n = 0, n_own = 0;
@@ -460,9 +449,7 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uin
     n = (int)total;
     if (n > 0) {
       fill(0, NCH);
-      flag_unit<NCH>(w, kp, noise, n);
-      starts_unit(w, kp, n);
-      n_own = owners_unit(w, n);
+      n_own = scan_unit<NCH>(w, kp, noise, gapmax, n);
       if (n_own > 0) {
         if (amps) {
           found = form_unit<AMP>(w, kp, n, 0, n_own, det0, nullptr, 0, 0, nullptr, nullptr, &wsum);
@@ -479,9 +466,7 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uin
       const int nn = (int)(w.chan_cnt[c1] - w.chan_cnt[c0]);
       if (nn > 0) {
         fill(c0, c1);
-        flag_unit<NCH>(w, kp, noise, nn);
-        starts_unit(w, kp, nn);
-        const int no = owners_unit(w, nn);
+        const int no = scan_unit<NCH>(w, kp, noise, gapmax, nn);
         if (no > 0) found += form_unit<AMP>(w, kp, nn, 0, no, det0, nullptr, 0, 0, nullptr, nullptr, amps ? &wsum : nullptr);
       }
       c0 = c1;
@@ -530,9 +515,7 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, const float* noise, uin
       const int nn = (int)(w.chan_cnt[c1] - w.chan_cnt[c0]);
       if (nn > 0) {
         fill(c0, c1);
-        flag_unit<NCH>(w, kp, noise, nn);
-        starts_unit(w, kp, nn);
-        const int no = owners_unit(w, nn);
+        const int no = scan_unit<NCH>(w, kp, noise, gapmax, nn);
         if (no > 0)
           base += form_unit<AMP>(w, kp, nn, 0, no, det0, so.stage, so.cap, base, nullptr, nullptr, nullptr,
                             amps ? &ap : nullptr);

@@ -28,6 +28,7 @@ struct KParams {
   int max_holes, max_bad, max_adj;
   const float* noise;       // [n_strips]
   const uint32_t* badmask;  // [n_strips / 32], bit (s & 31) of word s / 32
+  const uint8_t* gapmax;    // [n_strips], longest gap below strip s that links (see k_gapmax)
   const float* gain;        // [n_strips / 128]
 };
 
@@ -89,6 +90,8 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
                          const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st,
                          uint64_t* pack_off = nullptr, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st);
+cudaError_t build_gapmax(const uint32_t* mask_dev, uint8_t* gapmax_dev, uint64_t n_strips, int max_holes, int max_bad,
+                         cudaStream_t st);
 
 }  // namespace sst
 
@@ -103,6 +106,7 @@ struct sst_ctx {
   sst_params params{};
   float* noise = nullptr;
   uint32_t* badmask = nullptr;
+  uint8_t* gapmax = nullptr;
   float* gain = nullptr;
   sst::Scratch scratch;
   sst::Shape shape{};

@@ -407,42 +407,6 @@ __device__ void emit_channels(Shm<TILE>& s, const uint8_t* src, int c0, int c1, 
 
 __device__ __forceinline__ bool bit(const uint32_t* m, int t) { return (m[t >> 5] >> (t & 31)) & 1u; }
 
-// Number of set strips in [lo, hi).
-__device__ __forceinline__ int count_range(const uint32_t* m, int lo, int hi) {
-  int n = 0;
-  while (lo < hi) {
-    const int w = lo >> 5, b = lo & 31;
-    const int e = min(hi, (w + 1) << 5);
-    const int len = e - lo;
-    const uint32_t mask = len == 32 ? 0xffffffffu : (((1u << len) - 1u) << b);
-    n += __popc(m[w] & mask);
-    lo = e;
-  }
-  return n;
-}
-
-// Are the successive active strips a < t linked?  Every maximal run of holes
-// (non-bad inactive strips) in (a, t) must be at most max_holes long and every
-// maximal run of bad strips at most max_bad long.
-__device__ bool linked_gap(const uint32_t* B, int a, int t, int max_holes, int max_bad) {
-  const int g = t - a - 1;
-  if (g == 0) return true;
-  if (max_holes == 0 && max_bad == 0) return false;
-  if (max_holes == 0) return g <= max_bad && count_range(B, a + 1, t) == g;  // one run of bad strips
-  if (max_bad == 0) return g <= max_holes && count_range(B, a + 1, t) == 0;  // one run of holes
-  int holes = 0, bads = 0;
-  for (int u = a + 1; u < t; ++u) {
-    if (bit(B, u)) {
-      if (++bads > max_bad) return false;
-      holes = 0;
-    } else {
-      if (++holes > max_holes) return false;
-      bads = 0;
-    }
-  }
-  return true;
-}
-
 #include "sst_fe.cuh"
 
 // Greedy channel-aligned chunk [c0, c1) holding at most TILE digis.
@@ -843,7 +807,7 @@ __global__ void __launch_bounds__(256, 4) k_cluster(sst_digis in, uint32_t n_fed
     so.seg_amp_cnt = am.cnt + unit;
     so.seg_amp_start = am.start + unit;
   }
-  fe::cluster_unit<kChPerFe, AMP>(w, kp, kp.noise + (size_t)g0, ch0, total, fill, so, in.status);
+  fe::cluster_unit<kChPerFe, AMP>(w, kp, (size_t)g0, ch0, total, fill, so, in.status);
 }
 
 // a7: every FE unit of every FED of every event of a batch, unpacked and
@@ -900,7 +864,7 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
       so.seg_amp_start = am.start + item * kItems + p;
     }
     auto fill = [&](int c0, int c1) { fe::copy_runs(w, un, c0, c1); };
-    fe::cluster_unit<fe::kChW, AMP>(w, kp, kp.noise + (size_t)ch0 * kStrips, ch0, total, fill, so, &status[e]);
+    fe::cluster_unit<fe::kChW, AMP>(w, kp, (size_t)ch0 * kStrips, ch0, total, fill, so, &status[e]);
     __syncwarp();
   }
 }
@@ -911,6 +875,33 @@ __global__ void k_badmask(const uint8_t* __restrict__ bad, uint32_t* __restrict_
   uint32_t m = 0;
   for (int b = 0; b < 32; b++) m |= (bad[w * 32 + b] != 0 ? 1u : 0u) << b;
   mask[w] = m;
+}
+
+// Longest gap below every strip that still links two successive active strips of
+// a channel (section 2: a candidate continues over at most max_seq_holes
+// consecutive inactive good strips and at most max_seq_bad consecutive bad
+// strips): G(t) is the largest g such that, among strips t-g .. t-1, every maximal
+// run of bad strips is at most max_bad long and every maximal run of good strips
+// at most max_holes long.  The strips between successive active strips a < t are
+// all inactive, so they are linked exactly when their gap t-a-1 is at most G(t):
+// a gap that is valid stays valid when shortened from below, and one longer than
+// G(t) contains the strip t-G(t)-1 that breaks a limit.  One thread per strip
+// walks down from t-1; G(t) <= t <= 255.
+__global__ void k_gapmax(const uint32_t* __restrict__ mask, uint8_t* __restrict__ gapmax, uint64_t n_strips,
+                         int max_holes, int max_bad) {
+  const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_strips) return;
+  const int t = (int)(s % kStrips);
+  const uint32_t* m = mask + (s - (uint64_t)t) / 32;  // the channel's 8 mask words
+  int g = 0, run = 0, prev = -1;
+  for (int u = t - 1; u >= 0; --u) {
+    const int b = (int)((m[u >> 5] >> (u & 31)) & 1u);
+    run = b == prev ? run + 1 : 1;
+    prev = b;
+    if (run > (b ? max_bad : max_holes)) break;
+    ++g;
+  }
+  gapmax[s] = (uint8_t)g;
 }
 
 // ---------------------------------------------------------------- launch helpers
@@ -1118,6 +1109,12 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
 cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st) {
   const uint64_t words = n_strips / 32;
   k_badmask<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(bad_dev, mask_dev, words);
+  return cudaGetLastError();
+}
+
+cudaError_t build_gapmax(const uint32_t* mask_dev, uint8_t* gapmax_dev, uint64_t n_strips, int max_holes, int max_bad,
+                         cudaStream_t st) {
+  k_gapmax<<<(unsigned)((n_strips + 255) / 256), 256, 0, st>>>(mask_dev, gapmax_dev, n_strips, max_holes, max_bad);
   return cudaGetLastError();
 }
 

@@ -111,19 +111,35 @@ def test_full_detector_event_parity():
         g.close()
 
 
+def check_params(params, p_bad, occupancy):
+    """Per-event and batched paths against the oracle under one parameter set."""
+    w = eg.Workload("variant", 3, 1, ("fixed", occupancy), (1, 12), p_bad, 77, overlap=True, sat_frac=0.05)
+    calib = eg.make_calibration(3, 77, p_bad)
+    g = Gpu(calib.noise, calib.gain, calib.bad, sst.params(**params))
+    try:
+        evs = [eg.make_event(w, calib, ev) for ev in range(3)]
+        for e in evs:
+            check_event(g, e.raw, e.fed_len, 3)
+        for e, (st, cl) in zip(evs, g.batch([(e.raw, e.fed_len) for e in evs])):
+            _, oc, ost = g.oracle(e.raw, e.fed_len, 3)
+            assert st == ost
+            assert_clusters_equal(cl, oc)
+    finally:
+        g.close()
+
+
 @pytest.mark.parametrize("params", [
     dict(), dict(max_seq_bad=0), dict(max_seq_holes=1), dict(max_seq_holes=2, max_seq_bad=2, max_adj_bad=1),
     dict(t_channel=2.5, t_seed=4.0, t_cluster=3.0), dict(t_cluster=0.0)])
 def test_parameter_variants(params):
-    w = eg.Workload("variant", 3, 1, ("fixed", 0.05), (1, 12), 0.03, 77, overlap=True, sat_frac=0.05)
-    calib = eg.make_calibration(3, 77, 0.03)
-    g = Gpu(calib.noise, calib.gain, calib.bad, sst.params(**params))
-    try:
-        for ev in range(3):
-            e = eg.make_event(w, calib, ev)
-            check_event(g, e.raw, e.fed_len, 3)
-    finally:
-        g.close()
+    check_params(params, 0.03, 0.05)
+
+
+@pytest.mark.parametrize("holes,bad", [(0, 0), (0, 3), (3, 0), (1, 1), (2, 3), (5, 4), (255, 255)])
+def test_gap_rules_on_a_dense_bad_strip_map(holes, bad):
+    """Hole / bad-strip linking where a third of the strips are bad, so that gaps
+    alternate between runs of bad strips and holes of every length."""
+    check_params(dict(max_seq_holes=holes, max_seq_bad=bad, max_adj_bad=1), 0.33, 0.08)
 
 
 def test_batch_equals_per_event(w0):
