@@ -664,10 +664,10 @@ def main():
                     "steps": e2e_steps,
                     "api": "sst_batch_host_submit / sst_batch_host_wait, pinned host buffers, up to 3 steps in "
                            "flight, one chunk per step (host_chunk_events = batch)"},
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": 3 * args.steps,
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "kernel": "k_batch", "kernels_per_step": 4, "kernel_ms": round(k_ms, 4), "algorithmic_bytes": int(b_alg),
+                         "kernel": "k_batch", "kernels_per_step": 3, "kernel_ms": round(k_ms, 4), "algorithmic_bytes": int(b_alg),
                          "peak_kind": peak_kind, "issue": issue},
             "served": served,
             "cpu_baseline": cpu,

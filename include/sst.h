@@ -249,8 +249,8 @@ sst_status sst_unpack_noalloc(const uint8_t* raw, uint64_t raw_bytes, const uint
 
 /* Unpacks and clusters n_events events in one persistent launch; digis stay on
  * chip.  Each warp takes two adjacent FE units at a time; their clusters are
- * staged (context scratch of out->capacity records), then ordered per event by a
- * scan and a copy kernel.  The launch sequence allocates nothing once the context
+ * staged (context scratch of out->capacity records), then ordered and copied per
+ * event by one more kernel (two with amplitudes).  The launch sequence allocates nothing once the context
  * has run one batch of this size, so it can be captured in a CUDA graph.  All
  * pointers are device memory:
  *   raw        events back to back; event e occupies [event_off[e], event_off[e+1]),

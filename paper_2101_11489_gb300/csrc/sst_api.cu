@@ -256,8 +256,8 @@ sst_status sst_batch(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off
   if (((uintptr_t)raw & 15u) != 0) return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch: raw not 16-byte aligned");
   if (n_events == 0 || n_feds == 0 || n_feds > ctx->n_feds)
     return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch: bad n_events / n_feds");
-  if ((uint64_t)n_events * n_feds >= (1ull << 31))
-    return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch: too many FED records in one batch");
+  if ((uint64_t)n_events * n_feds * kFe >= (1ull << 31))
+    return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch: too many FE units in one batch (2^31)");
   if (out->amp && (!out->amp_first || !out->amp_off || out->amp_capacity == 0 || out->amp_capacity >= kNoAmp))
     return set_err(ctx, SST_ERR_INVALID_ARG,
                    "sst_batch: amp needs amp_first, amp_off and 1 <= amp_capacity < 2^32 - 1");

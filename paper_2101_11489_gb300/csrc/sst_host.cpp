@@ -500,9 +500,9 @@ sst_status sst_batch_host_submit(sst_ctx* ctx, const uint8_t* raw, const uint64_
     if (c.bytes > job->max_bytes) job->max_bytes = c.bytes;
     if (c.clu_total > job->max_clu) job->max_clu = c.clu_total;
   }
-  if ((uint64_t)job->max_e * n_feds >= (1ull << 31)) {
+  if ((uint64_t)job->max_e * n_feds * sst::kFe >= (1ull << 31)) {
     delete job;
-    return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch_host: too many FED records in one chunk");
+    return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch_host: too many FE units in one chunk (2^31)");
   }
   DeviceGuard g(ctx->device);
   cudaError_t e = cudaEventCreateWithFlags(&job->done, cudaEventDisableTiming);

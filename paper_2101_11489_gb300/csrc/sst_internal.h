@@ -77,9 +77,8 @@ cudaError_t launch_unpack(const uint8_t* raw, uint64_t raw_bytes, const uint32_t
                           const sst_digis& out, const Scratch& s, const Shape& sh, cudaStream_t st);
 cudaError_t launch_cluster(const sst_digis& in, uint32_t n_feds, const sst_clusters& out, const KParams& kp,
                            const Scratch& s, const Shape& sh, cudaStream_t st);
-// Kernels launched per batch step (for launch counting): scan, batch, cluster scan, compaction
-// (one more, the event scan, in packed mode).
-constexpr int kBatchKernels = 4;
+// Kernels launched per batched call: k_fed_scan, k_batch, k_order; one more
+// (k_clu_scan) for packed output or amplitudes (then k_compact instead of k_order).
 // Batched unpack + cluster.  Event e's clusters are staged in, and by default
 // written to, the slice [clu_off[e], clu_off[e+1]) of `out` (bounded by
 // out.capacity).  With pack_off (device, n_events + 1 values) the events' clusters

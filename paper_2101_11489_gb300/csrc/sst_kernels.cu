@@ -14,9 +14,12 @@
 // (k_fed_scan), which hands every FE unit its byte range.
 //
 // Output order without device-side waits: every unit allocates an exact-size
-// staging region with one atomic per event; k_clu_scan prefix-sums the units'
-// counts per event and k_compact copies the staged records into each event's
-// sorted cluster SoA.
+// staging region with one atomic per event; k_order prefix-sums the units' counts
+// per event and copies the staged records into each event's sorted cluster SoA
+// (with amplitudes: k_clu_scan scans, k_compact copies).  Placing each unit's
+// clusters directly with a look-back over the units before it, in the batched
+// kernel, measured slower: the look-back's L2 round trips and the waits for
+// units still being counted cost more than the ordering pass.
 //
 // Per-event unpacking (k_unpack) keeps one CTA per FED and places the FED's digis
 // with a warp-parallel decoupled look-back over the FEDs before it.
@@ -598,14 +601,14 @@ __global__ void __launch_bounds__(1024) k_clu_scan(const uint32_t* __restrict__ 
   }
 }
 
-// a6, output: copies every segment's staged clusters (one segment per work item)
-// to its place in the event's sorted cluster SoA, one warp per segment (16-byte
-// loads, coalesced stores).  The event's clusters start at clu_off[e] (its slice),
-// or at pack_off[e] when pack_off is given (events packed back to back).  With
-// amplitudes, each cluster's amp_first is the segment's output offset plus the
+// a6, output with amplitudes: copies every segment's staged clusters (one segment
+// per work item) to its place in the event's sorted cluster SoA, one warp per
+// segment (16-byte loads, coalesced stores), k_clu_scan having scanned the
+// segments' cluster and amplitude counts.  The event's clusters start at
+// clu_off[e] (its slice), or at pack_off[e] when pack_off is given (events packed
+// back to back).  Each cluster's amp_first is the segment's output offset plus the
 // widths of the segment's clusters before it, and the segment's amplitude bytes
 // are copied after its clusters.
-template <bool AMP>
 __global__ void __launch_bounds__(256) k_compact(const uint4* __restrict__ stage, const uint64_t* __restrict__ clu_off,
                                                  const uint64_t* __restrict__ pack_off,
                                                  const uint32_t* __restrict__ seg_cnt,
@@ -622,25 +625,10 @@ __global__ void __launch_bounds__(256) k_compact(const uint4* __restrict__ stage
   const uint64_t off = clu_off ? clu_off[e] : 0;
   const uint4* src = stage + off + seg_start[it];
   const uint64_t dst = (pack_off ? pack_off[e] : off) + seg_dest[it];
-  if (!AMP) {
-    for (uint32_t k = lane; k < n; k += 32) {
-      const uint4 r = __ldg(src + k);
-      const uint64_t o = dst + k;
-      out.det[o] = r.x;
-      out.first[o] = (uint16_t)(r.y & 0xFFFFu);
-      out.width[o] = (uint16_t)(r.y >> 16);
-      out.charge[o] = r.z;
-      out.barycenter[o] = __uint_as_float(r.w);
-    }
-    return;
-  }
-  uint64_t a0 = 0, a1 = 0, acarry = 0;
-  bool amps = false;
-  {
-    amp_slice(am, e, &a0, &a1);
-    amps = am.start[it] != kNoAmp;
-    acarry = a0 + am.dest[it];
-  }
+  uint64_t a0 = 0, a1 = 0;
+  amp_slice(am, e, &a0, &a1);
+  const bool amps = am.start[it] != kNoAmp;
+  uint64_t acarry = a0 + am.dest[it];
   for (uint32_t k0 = 0; k0 < n; k0 += 32) {
     const uint32_t k = k0 + lane;
     uint4 r = make_uint4(0u, 0u, 0u, 0u);
@@ -671,6 +659,81 @@ __global__ void __launch_bounds__(256) k_compact(const uint4* __restrict__ stage
     uint8_t* ad = am.out + a0 + am.dest[it];
     for (uint32_t i = lane; i < na; i += 32) ad[i] = as[i];
   }
+}
+
+// a6, output without amplitudes: orders and copies the staged clusters in one
+// pass.  CTA c of event e takes the event's segments [c * SEGS, (c + 1) * SEGS):
+// it sums the counts of the event's segments before them (its place in the
+// event), scans its own counts in shared memory, and copies its clusters to one
+// contiguous range of the output, thread t taking output records t, t + 256, ...
+// (four loads in flight per thread) and finding each one's segment by binary
+// search over the scanned counts (coalesced stores; each segment's staged records
+// are contiguous).  The event's
+// clusters start at clu_off[e] (its slice; 0 without clu_off), or at pack_off[e]
+// when pack_off is given (k_clu_scan computed it and the events' counts); the
+// event's last CTA otherwise stores its cluster count.
+template <int SEGS>
+__global__ void __launch_bounds__(256) k_order(const uint4* __restrict__ stage, const uint64_t* __restrict__ clu_off,
+                                               const uint64_t* __restrict__ pack_off,
+                                               const uint32_t* __restrict__ seg_cnt,
+                                               const uint32_t* __restrict__ seg_start, uint32_t n_segs, uint32_t cpe,
+                                               sst_clusters out, sst_event_status* status) {
+  static_assert(SEGS <= 256 && (SEGS & (SEGS - 1)) == 0, "one scan entry per thread, binary search");
+  __shared__ uint32_t s_dest[SEGS + 1], s_start[SEGS];
+  __shared__ uint32_t wsum[32];
+  const uint32_t e = blockIdx.x / cpe, c = blockIdx.x % cpe;
+  const uint32_t seg0 = c * SEGS;
+  const uint32_t nseg = n_segs - seg0 < (uint32_t)SEGS ? n_segs - seg0 : (uint32_t)SEGS;
+  const uint32_t* cnt_e = seg_cnt + (size_t)e * n_segs;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // clusters of the event's segments before this CTA's
+  uint32_t part = 0;
+  for (uint32_t i = tid; i < seg0; i += blockDim.x) part += __ldg(cnt_e + i);
+  part = __reduce_add_sync(0xffffffffu, part);
+  if (lane == 0) wsum[warp] = part;
+  __syncthreads();
+  uint32_t pre = 0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); k++) pre += wsum[k];
+  __syncthreads();
+  // this CTA's segments: exclusive scan of their counts
+  const uint32_t v = tid < (int)nseg ? __ldg(cnt_e + seg0 + tid) : 0u;
+  if (tid < SEGS) s_start[tid] = tid < (int)nseg ? __ldg(seg_start + (size_t)e * n_segs + seg0 + tid) : 0u;
+  uint32_t tot;
+  const uint32_t ex = block_excl_scan(v, wsum, &tot);
+  if (tid < SEGS) s_dest[tid] = ex;
+  if (tid == 0) s_dest[SEGS] = tot;
+  __syncthreads();
+  const uint64_t off = clu_off ? clu_off[e] : 0;
+  const uint4* src = stage + off;
+  const uint64_t dst = (pack_off ? pack_off[e] : off) + pre;
+  constexpr int kU = 4;  // records per thread in flight
+  for (uint32_t d0 = tid; d0 < tot; d0 += kU * blockDim.x) {
+    uint4 r[kU];
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+      const uint32_t d = d0 + u * blockDim.x;
+      if (d < tot) {
+        int lo = 0;  // the last segment starting at or before d: it holds d
+#pragma unroll
+        for (int step = SEGS / 2; step > 0; step >>= 1)
+          if (s_dest[lo + step] <= d) lo += step;
+        r[u] = __ldg(src + s_start[lo] + (d - s_dest[lo]));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+      const uint32_t d = d0 + u * blockDim.x;
+      if (d < tot) {
+        const uint64_t o = dst + d;
+        out.det[o] = r[u].x;
+        out.first[o] = (uint16_t)(r[u].y & 0xFFFFu);
+        out.width[o] = (uint16_t)(r[u].y >> 16);
+        out.charge[o] = r[u].z;
+        out.barycenter[o] = __uint_as_float(r[u].w);
+      }
+    }
+  }
+  if (!pack_off && c == cpe - 1 && tid == 0) status[e].n_clusters = pre + tot;
 }
 
 // a1 + a2 per event: one CTA per FED (ticket order), digis written to the global
@@ -1032,16 +1095,21 @@ cudaError_t launch_batch_fe(const uint8_t* raw, const uint32_t* fed_len, uint32_
 cudaError_t launch_order(const uint64_t* clu_off, uint32_t n_events, uint32_t n_segs, const sst_clusters& out,
                          sst_event_status* status, const Scratch& s, uint64_t* pack_off, const AmpArgs& am,
                          cudaStream_t st) {
-  k_clu_scan<<<n_events, 1024, 0, st>>>(s.fed_cnt, n_segs, s.fed_dest, status, pack_off, s.tickets + 1, am);
-  cudaError_t e = cudaGetLastError();
-  if (e) return e;
-  const uint64_t items = (uint64_t)n_events * n_segs;
-  if (am.stage)
-    k_compact<true><<<(unsigned)((items + 7) / 8), 256, 0, st>>>(s.stage, clu_off, pack_off, s.fed_cnt, s.fed_start,
-                                                                s.fed_dest, n_events, n_segs, out, am);
-  else
-    k_compact<false><<<(unsigned)((items + 7) / 8), 256, 0, st>>>(s.stage, clu_off, pack_off, s.fed_cnt,
-                                                                 s.fed_start, s.fed_dest, n_events, n_segs, out, am);
+  cudaError_t e;
+  if (am.stage || pack_off) {
+    k_clu_scan<<<n_events, 1024, 0, st>>>(s.fed_cnt, n_segs, s.fed_dest, status, pack_off, s.tickets + 1, am);
+    if ((e = cudaGetLastError())) return e;
+  }
+  if (am.stage) {
+    const uint64_t items = (uint64_t)n_events * n_segs;
+    k_compact<<<(unsigned)((items + 7) / 8), 256, 0, st>>>(s.stage, clu_off, pack_off, s.fed_cnt, s.fed_start,
+                                                          s.fed_dest, n_events, n_segs, out, am);
+  } else {
+    constexpr int kSegs = 64;
+    const uint32_t cpe = (n_segs + kSegs - 1) / kSegs;
+    k_order<kSegs><<<(unsigned)((uint64_t)n_events * cpe), 256, 0, st>>>(s.stage, clu_off, pack_off, s.fed_cnt,
+                                                                        s.fed_start, n_segs, cpe, out, status);
+  }
   return cudaGetLastError();
 }
 

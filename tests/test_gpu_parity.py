@@ -181,11 +181,21 @@ def test_cluster_capacity_overflow_is_flagged_and_bounded(w0):
     key = ch["det"].astype(np.int64) * 256 + ch["first"]
     assert np.all(np.diff(key) > 0)  # still sorted
     assert _as_set(ch) <= _as_set(oc)  # a subset of the true clusters
-    # the batched path flags the same event the same way
-    out = g.batch([(e.raw, e.fed_len)], clu_caps=[cap])
-    st, cl = out[0]
+    # the batched path flags the same event the same way (a sorted subset of its
+    # clusters, those of whole work items) and leaves the events around it intact,
+    # one of them with exactly the capacity it needs
+    other = eg.make_event(w, calib, 5)
+    _, oc2, ost2 = g.oracle(other.raw, other.fed_len, w.n_feds)
+    out = g.batch([(other.raw, other.fed_len), (e.raw, e.fed_len), (other.raw, other.fed_len)],
+                  clu_caps=[oc2["det"].size, cap, oc2["det"].size + 5])
+    st, cl = out[1]
     assert st["flags"] & sst.SST_EV_CLUSTER_CAPACITY and st["n_clusters"] <= cap
+    key = cl["det"].astype(np.int64) * 256 + cl["first"]
+    assert np.all(np.diff(key) > 0)
     assert _as_set(cl) <= _as_set(oc)
+    for st2, cl2 in (out[0], out[2]):
+        assert st2 == ost2
+        assert_clusters_equal(cl2, oc2)
 
 
 def test_digi_capacity_overflow_is_flagged_and_bounded(w0):
