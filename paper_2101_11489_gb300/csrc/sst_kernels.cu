@@ -31,6 +31,7 @@
 // Every device wait (the look-back) has an iteration limit; when it runs out the
 // event is flagged SST_EV_TIMEOUT and the CTA carries on without the value.
 #include <cstddef>
+#include <utility>
 
 #include "sst_internal.h"
 
@@ -46,6 +47,7 @@ constexpr unsigned long long kLbMask = 3ull << 62;
 constexpr int kLbSpinLimit = 1 << 20;              // polls before giving up (about a second)
 constexpr uint64_t kBadOff = ~0ull;                // fed_off marker: record outside the event
 constexpr int kFedBufMin = 16384;                  // bytes of FED record staged on chip (at least)
+constexpr int kFedScanThreads = 128;               // FEDs per k_fed_scan CTA
 
 // Shared scalars.
 enum {
@@ -100,6 +102,14 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 __device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start before the kernel ahead of it on the stream has
+// finished; pdl_wait() returns once that kernel has completed and its writes are
+// visible (at once for a kernel launched the ordinary way).  pdl_release() lets
+// the next such kernel be launched before this one ends.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t rd16(const uint8_t* p) { return (uint32_t)p[0] | ((uint32_t)p[1] << 8); }
 __device__ __forceinline__ uint32_t rd32(const uint8_t* p) {
@@ -491,48 +501,56 @@ __device__ void describe_fed(const uint8_t* __restrict__ raw, uint64_t fo, uint3
 
 // a1, outer level: byte offset of every FED record (exclusive scan of fed_len per
 // event, plus the event's start).  A record that would end past its event is
-// marked kBadOff; a size mismatch sets SST_EV_SIZE.  One CTA per event.  With
-// unit_desc (batched path) every FED's header is checked and its FE units
-// described (describe_fed).  It is also the launch sequence's prologue: it clears
-// the event's status and staging counter (ev_alloc, when given), CTA 0 clears the
-// work tickets, and the look-back states lb[0 .. n_lb) are cleared (per-event
-// unpacking, one CTA).
+// marked kBadOff; a size mismatch sets SST_EV_SIZE.  `cpe` CTAs per event, CTA c
+// taking the event's FEDs [c * blockDim.x, (c + 1) * blockDim.x) and summing the
+// lengths of the FEDs before them itself.  With unit_desc (batched path) every
+// FED's header is checked and its FE units described (describe_fed).  It is also
+// the launch sequence's prologue: the event's last CTA writes its status (zero but
+// SST_EV_SIZE), its first clears the staging counters (ev_alloc, amp_alloc, when
+// given), the very first clears the work tickets, and every event's n_lb
+// look-back states (lb[e * n_lb ..]) are cleared.
 __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_bytes,
-                           const uint32_t* __restrict__ fed_len, uint32_t n_feds, uint64_t* __restrict__ fed_off,
-                           sst_event_status* status, uint32_t* ev_alloc, uint32_t* tickets, unsigned long long* lb,
-                           uint32_t n_lb, const uint8_t* __restrict__ raw, uint2* unit_desc, uint32_t* amp_alloc) {
+                           const uint32_t* __restrict__ fed_len, uint32_t n_feds, uint32_t cpe,
+                           uint64_t* __restrict__ fed_off, sst_event_status* status, uint32_t* ev_alloc,
+                           uint32_t* tickets, unsigned long long* lb, uint32_t n_lb, const uint8_t* __restrict__ raw,
+                           uint2* unit_desc, uint32_t* amp_alloc) {
   __shared__ uint32_t wsum[32];
-  __shared__ uint64_t carry_s;
-  const uint32_t e = blockIdx.x;
+  __shared__ unsigned long long psum[32];
+  pdl_release();
+  const uint32_t e = blockIdx.x / cpe, c = blockIdx.x % cpe;
+  const uint32_t f0 = c * blockDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t ev0 = event_off ? event_off[e] : 0;
   const uint64_t ev1 = event_off ? event_off[e + 1] : raw_bytes;
-  if (threadIdx.x == 0) {
-    carry_s = 0;
-    status[e] = sst_event_status{0u, 0u, 0u, 0u};
+  if (c == 0 && threadIdx.x == 0) {
     if (ev_alloc) ev_alloc[e] = 0;
     if (amp_alloc) amp_alloc[e] = 0;
   }
-  if (e == 0 && threadIdx.x < 16) tickets[threadIdx.x] = 0;
+  if (e == 0 && c == 0 && threadIdx.x < 16) tickets[threadIdx.x] = 0;
   if (lb)
-    for (uint32_t i = threadIdx.x; i < n_lb; i += blockDim.x) lb[i] = 0;
+    for (uint32_t i = f0 + threadIdx.x; i < n_lb; i += cpe * blockDim.x) lb[(size_t)e * n_lb + i] = 0;
+  const uint32_t* len_e = fed_len + (size_t)e * n_feds;
+  // bytes of the event's FEDs before this CTA's
+  unsigned long long part = 0;
+  for (uint32_t i = threadIdx.x; i < f0 && i < n_feds; i += blockDim.x) part += len_e[i];
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) part += __shfl_down_sync(0xffffffffu, part, d);
+  if (lane == 0) psum[warp] = part;
   __syncthreads();
-  for (uint32_t b = 0; b < n_feds; b += blockDim.x) {
-    const uint32_t f = b + threadIdx.x;
-    const uint32_t len = f < n_feds ? fed_len[(size_t)e * n_feds + f] : 0u;
-    uint32_t tot;
-    const uint32_t ex = block_excl_scan(len, wsum, &tot);
-    const uint64_t carry = carry_s;
-    if (f < n_feds) {
-      const uint64_t o = ev0 + carry + ex;
-      const uint64_t fo = (ev1 >= ev0 && o + len <= ev1) ? o : kBadOff;
-      fed_off[(size_t)e * n_feds + f] = fo;
-      if (unit_desc) describe_fed(raw, fo, len, f, unit_desc + ((size_t)e * n_feds + f) * kFe);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) carry_s = carry + tot;
-    __syncthreads();
+  uint64_t pre = 0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); k++) pre += psum[k];
+  const uint32_t f = f0 + threadIdx.x;
+  const uint32_t len = f < n_feds ? len_e[f] : 0u;
+  uint32_t tot;
+  const uint32_t ex = block_excl_scan(len, wsum, &tot);
+  if (f < n_feds) {
+    const uint64_t o = ev0 + pre + ex;
+    const uint64_t fo = (ev1 >= ev0 && o + len <= ev1) ? o : kBadOff;
+    fed_off[(size_t)e * n_feds + f] = fo;
+    if (unit_desc) describe_fed(raw, fo, len, f, unit_desc + ((size_t)e * n_feds + f) * kFe);
   }
-  if (threadIdx.x == 0 && ev0 + carry_s != ev1) atomicOr(&status[e].flags, SST_EV_SIZE);
+  if (c == cpe - 1 && threadIdx.x == 0)
+    status[e] = sst_event_status{0u, 0u, ev0 + pre + tot != ev1 ? SST_EV_SIZE : 0u, 0u};
 }
 
 // a6, ordering: per event, the exclusive scan of its work items' cluster counts
@@ -681,6 +699,7 @@ __global__ void __launch_bounds__(256) k_order(const uint4* __restrict__ stage, 
   static_assert(SEGS <= 256 && (SEGS & (SEGS - 1)) == 0, "one scan entry per thread, binary search");
   __shared__ uint32_t s_dest[SEGS + 1], s_start[SEGS];
   __shared__ uint32_t wsum[32];
+  pdl_wait();  // the staged clusters and counts
   const uint32_t e = blockIdx.x / cpe, c = blockIdx.x % cpe;
   const uint32_t seg0 = c * SEGS;
   const uint32_t nseg = n_segs - seg0 < (uint32_t)SEGS ? n_segs - seg0 : (uint32_t)SEGS;
@@ -892,6 +911,7 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
   constexpr uint32_t kItems = kFe / fe::kUnits;  // work items (FE-unit pairs) per FED
   const uint32_t per_fed = n_events * kItems;
   const uint32_t n_units = n_feds * per_fed;
+  pdl_wait();  // the prologue's tickets, offsets and unit descriptors
   for (;;) {
     uint32_t t = 0;
     if (lane == 0) t = atomicAdd(ticket, 1u);
@@ -930,6 +950,7 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
     fe::cluster_unit<fe::kChW, AMP>(w, kp, (size_t)ch0 * kStrips, ch0, total, fill, so, &status[e]);
     __syncwarp();
   }
+  pdl_release();
 }
 
 __global__ void k_badmask(const uint8_t* __restrict__ bad, uint32_t* __restrict__ mask, uint64_t n_words) {
@@ -1044,6 +1065,24 @@ AmpArgs amp_args(const sst_clusters& out, const Scratch& s) {
   return a;
 }
 
+// Launches `k` with programmatic stream serialization: it may start while the
+// kernel before it on the stream drains, and waits for it with pdl_wait().
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
 cudaError_t launch_cluster_fe(const sst_digis& in, uint32_t n_feds, const KParams& kp, const Scratch& s,
                               uint64_t cap, const Shape& sh, const AmpArgs& am, cudaStream_t st) {
   const int nw = sh.block / 32;
@@ -1082,10 +1121,10 @@ cudaError_t launch_batch_fe(const uint8_t* raw, const uint32_t* fed_len, uint32_
     k_batch<true><<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out_cap, status, kp,
                                               s.stage, s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets, s.unit_desc,
                                               am);
-  else
-    k_batch<false><<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out_cap, status,
-                                               kp, s.stage, s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets,
-                                               s.unit_desc, am);
+  else if ((e = launch_pdl(k_batch<false>, (unsigned)grid, (unsigned)sh.block, sm, st, raw, fed_len,
+                           (const uint64_t*)s.fed_off, n_events, n_feds, clu_off, out_cap, status, kp, s.stage,
+                           s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets, (const uint2*)s.unit_desc, am)))
+    return e;
   if ((e = cudaGetLastError())) return e;
   if (ev_end && (e = cudaEventRecord(ev_end, st))) return e;
   return cudaSuccess;
@@ -1105,10 +1144,22 @@ cudaError_t launch_order(const uint64_t* clu_off, uint32_t n_events, uint32_t n_
     k_compact<<<(unsigned)((items + 7) / 8), 256, 0, st>>>(s.stage, clu_off, pack_off, s.fed_cnt, s.fed_start,
                                                           s.fed_dest, n_events, n_segs, out, am);
   } else {
-    constexpr int kSegs = 64;
-    const uint32_t cpe = (n_segs + kSegs - 1) / kSegs;
-    k_order<kSegs><<<(unsigned)((uint64_t)n_events * cpe), 256, 0, st>>>(s.stage, clu_off, pack_off, s.fed_cnt,
-                                                                        s.fed_start, n_segs, cpe, out, status);
+    // 64 segments per CTA for a batch; 16 when that would give a small grid (one
+    // event, a short chunk), so that enough CTAs share the copy
+    const uint32_t cpe64 = (n_segs + 63) / 64;
+    const uint4* stage = s.stage;
+    const uint64_t* pack = pack_off;
+    const uint32_t* cnt = s.fed_cnt;
+    const uint32_t* start = s.fed_start;
+    if ((uint64_t)n_events * cpe64 >= 256) {
+      e = launch_pdl(k_order<64>, (unsigned)((uint64_t)n_events * cpe64), 256u, 0, st, stage, clu_off, pack, cnt, start,
+                     n_segs, cpe64, out, status);
+    } else {
+      const uint32_t cpe16 = (n_segs + 15) / 16;
+      e = launch_pdl(k_order<16>, (unsigned)((uint64_t)n_events * cpe16), 256u, 0, st, stage, clu_off, pack, cnt, start,
+                     n_segs, cpe16, out, status);
+    }
+    if (e) return e;
   }
   return cudaGetLastError();
 }
@@ -1138,8 +1189,9 @@ bool shape_valid(const Shape& s) {
 cudaError_t launch_unpack(const uint8_t* raw, uint64_t raw_bytes, const uint32_t* fed_len, uint32_t n_feds,
                           const sst_digis& out, const Scratch& s, const Shape& sh, cudaStream_t st) {
   cudaError_t e;
-  k_fed_scan<<<1, 256, 0, st>>>(nullptr, raw_bytes, fed_len, n_feds, s.fed_off, out.status, nullptr, s.tickets, s.lb,
-                                n_feds, nullptr, nullptr, nullptr);
+  const uint32_t cpe = (n_feds + kFedScanThreads - 1) / kFedScanThreads;
+  k_fed_scan<<<cpe, kFedScanThreads, 0, st>>>(nullptr, raw_bytes, fed_len, n_feds, cpe, s.fed_off, out.status, nullptr,
+                                              s.tickets, s.lb, n_feds, nullptr, nullptr, nullptr);
   if ((e = cudaGetLastError())) return e;
   switch (sh.tile) {
     case 1024: return launch_unpack_t<1024>(raw, fed_len, n_feds, out, s, sh, st);
@@ -1165,8 +1217,10 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
                          uint64_t* pack_off, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   cudaError_t e;
   const AmpArgs am = amp_args(out, s);
-  k_fed_scan<<<n_events, 256, 0, st>>>(event_off, 0, fed_len, n_feds, s.fed_off, status, s.ev_alloc, s.tickets,
-                                       nullptr, 0, raw, s.unit_desc, am.stage ? s.amp_alloc : nullptr);
+  const uint32_t cpe = (n_feds + kFedScanThreads - 1) / kFedScanThreads;
+  k_fed_scan<<<(unsigned)((uint64_t)n_events * cpe), kFedScanThreads, 0, st>>>(
+      event_off, 0, fed_len, n_feds, cpe, s.fed_off, status, s.ev_alloc, s.tickets, nullptr, 0, raw, s.unit_desc,
+      am.stage ? s.amp_alloc : nullptr);
   if ((e = cudaGetLastError())) return e;
   e = launch_batch_fe(raw, fed_len, n_events, n_feds, clu_off, out.capacity, status, kp, s, sh, n_sm, am, st,
                       ev_begin, ev_end);
