@@ -37,11 +37,10 @@ struct __align__(16) Warp {
   uint32_t chan_cnt[kChW + 1];           // digis per channel, then exclusive prefix
   uint16_t chan_len[kChW];
   uint8_t chan_st[kChW];
-  uint16_t key[kTile];                   // (channel in the work item << 8) | strip, sorted
-  uint16_t own[kTile];                   // first digi of every seeded candidate
+  uint32_t kf[kTile];   // key (channel in the work item << 8 | strip; sorted) | flags << 16 (1 active, 2 seed,
+                        // 4 first strip of a candidate) | gain-corrected charge of active digis << 24
+  uint16_t own[kTile];  // first digi of every seeded candidate; run-start marks (bytes) while the tile fills
   uint8_t adc[kTile];
-  uint8_t flag[kTile];                   // 1 active, 2 seed, 4 first strip of a candidate
-  uint8_t q[kTile];                      // gain-corrected charge of active digis
 };
 
 __device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
@@ -161,8 +160,9 @@ __device__ void copy_runs(Warp& w, const Unit& un, int c0, int c1) {
   const int lane = threadIdx.x & 31;
   uint32_t* desc = reinterpret_cast<uint32_t*>(w.nsq);
   const int n = (int)(w.chan_cnt[c1] - w.chan_cnt[c0]);
-  uint32_t* fl32 = reinterpret_cast<uint32_t*>(w.flag);
-  for (int i = lane; i < (n + 3) / 4; i += 32) fl32[i] = 0;
+  uint8_t* rs = reinterpret_cast<uint8_t*>(w.own);  // run-start marks
+  uint32_t* rs32 = reinterpret_cast<uint32_t*>(w.own);
+  for (int i = lane; i < (n + 3) / 4; i += 32) rs32[i] = 0;
   __syncwarp();
   const int c = c0 + lane;
   if (c < c1) {
@@ -177,7 +177,7 @@ __device__ void copy_runs(Warp& w, const Unit& un, int c0, int c1) {
       const uint32_t wd = wd0 < left ? wd0 : left;
       if (wd > 0) {
         desc[o] = ((pos + p + 2) << 13) | (first << 5) | (uint32_t)c;
-        w.flag[o] = 1;
+        rs[o] = 1;
       }
       o += wd;
       left -= wd;
@@ -188,13 +188,13 @@ __device__ void copy_runs(Warp& w, const Unit& un, int c0, int c1) {
   int carry = 0;
   for (int base = 0; base < n; base += 32) {
     const int i = base + lane;
-    const uint32_t m = __ballot_sync(0xffffffffu, i < n && w.flag[i] != 0);
+    const uint32_t m = __ballot_sync(0xffffffffu, i < n && rs[i] != 0);
     const uint32_t le = m & (lane == 31 ? 0xffffffffu : ((2u << lane) - 1u));
     const int s = le ? base + 31 - __clz(le) : carry;
     if (i < n) {
       const uint32_t d = desc[s];
       const uint32_t k = (uint32_t)(i - s);
-      w.key[i] = (uint16_t)(((d & 31u) << 8) | ((((d >> 5) & 255u) + k) & 255u));
+      w.kf[i] = ((d & 31u) << 8) | ((((d >> 5) & 255u) + k) & 255u);
       const uint32_t b = (d >> 13) + k;
       w.adc[i] = b < un.off1 + un.len1 ? un.src[b] : (uint8_t)0;
     }
@@ -227,7 +227,7 @@ __device__ int scan_unit(Warp& w, const KParams& kp, const float* noise, const u
   int n_own = 0, carry_start = -1;
   bool carry_seen = false;
   uint32_t carry_key = kNone;  // key of the last active digi of the windows before
-  uint32_t kn = lane < n ? (uint32_t)w.key[lane] : kNone;
+  uint32_t kn = lane < n ? (w.kf[lane] & 0xFFFFu) : kNone;
   uint32_t xn = (kn >> 8) < (uint32_t)NCH ? kn : 0u;
   float zn = __ldg(noise + xn);
   uint32_t gn = __ldg(gapmax + xn);
@@ -237,7 +237,7 @@ __device__ int scan_unit(Warp& w, const KParams& kp, const float* noise, const u
     const float nz = zn;
     const uint32_t gmax = gn;
     if (base + 32 < n) {
-      kn = i + 32 < n ? (uint32_t)w.key[i + 32] : kNone;
+      kn = i + 32 < n ? (w.kf[i + 32] & 0xFFFFu) : kNone;
       xn = (kn >> 8) < (uint32_t)NCH ? kn : 0u;
       zn = __ldg(noise + xn);
       gn = __ldg(gapmax + xn);
@@ -294,8 +294,7 @@ __device__ int scan_unit(Warp& w, const KParams& kp, const float* noise, const u
     }
     if (A) carry_key = __shfl_sync(0xffffffffu, key, 31 - __clz(A));
     if (i < n) {
-      w.flag[i] = (uint8_t)((act ? 1 : 0) | (sd ? 2 : 0) | (start ? 4 : 0));
-      w.q[i] = (uint8_t)q;
+      w.kf[i] = key | ((act ? 1u : 0u) << 16) | ((sd ? 2u : 0u) << 16) | ((start ? 4u : 0u) << 16) | (q << 24);
       w.nsq[i] = nsq;
     }
   }
@@ -342,7 +341,7 @@ __device__ uint32_t form_unit(Warp& w, const KParams& kp, int n, int k_begin, in
     float bary = 0.f;
     if (k < n_own) {
       int j = w.own[k];
-      const uint32_t key0 = w.key[j];
+      const uint32_t key0 = w.kf[j] & 0xFFFFu;
       c = key0 >> 8;
       const int l = (int)(key0 & 255u);
       const uint32_t* B = w.bad + c * kMaskWords;
@@ -352,9 +351,9 @@ __device__ uint32_t form_unit(Warp& w, const KParams& kp, int n, int k_begin, in
       float n2 = 0.f;
       int r = l;
       do {
-        const uint32_t kj = w.key[j];
-        if (w.flag[j] & 1) {
-          const uint32_t q = w.q[j];
+        const uint32_t kj = w.kf[j];
+        if (kj & (1u << 16)) {
+          const uint32_t q = kj >> 24;
           const int st = (int)(kj & 255u);
           s_raw += w.adc[j];
           n2 = __fadd_rn(n2, w.nsq[j]);
@@ -363,7 +362,7 @@ __device__ uint32_t form_unit(Warp& w, const KParams& kp, int n, int k_begin, in
           r = st;
         }
         ++j;
-      } while (j < n && (w.key[j] >> 8) == c && !(w.flag[j] & 4));
+      } while (j < n && ((w.kf[j] >> 8) & 255u) == c && !(w.kf[j] & (4u << 16)));
       pass = __uint2float_rn(s_raw) > __fmul_rn(kp.t_cluster, __fsqrt_rn(n2));
       int hi = r;
       for (int m = 0; m < kp.max_adj && hi + 1 < kStrips && bit(B, hi + 1); m++) hi++;
@@ -398,9 +397,10 @@ __device__ uint32_t form_unit(Warp& w, const KParams& kp, int n, int k_begin, in
         for (uint32_t i = 0; i < wd; i++) dst[i] = 0;
         int j = w.own[k];
         do {
-          if (w.flag[j] & 1) dst[(w.key[j] & 255u) - lo] = w.q[j];
+          const uint32_t kj = w.kf[j];
+          if (kj & (1u << 16)) dst[(kj & 255u) - lo] = (uint8_t)(kj >> 24);
           ++j;
-        } while (j < n && (w.key[j] >> 8) == c && !(w.flag[j] & 4));
+        } while (j < n && ((w.kf[j] >> 8) & 255u) == c && !(w.kf[j] & (4u << 16)));
       }
       ap->pos += __shfl_sync(0xffffffffu, incl, 31);
     }
@@ -429,8 +429,9 @@ struct SegOut {
 // channel chunk [c0, c1)) and stages its clusters.  The kept clusters are first
 // counted, then their region is allocated in one piece, then they are written; a
 // unit whose digis exceed the tile goes through its channel chunks twice.  Without
-// amplitudes, the records of the first 32 candidates are kept in registers from
-// the counting pass.  s0: the work item's first strip in the per-strip
+// amplitudes, the records of the first 64 candidates (two per lane) are kept in
+// registers from the counting pass, so that only candidates beyond them are
+// formed twice (a work item of a full event has about 49).  s0: the work item's first strip in the per-strip
 // calibration tables; NCH: channels of the work item (12 or 24); AMP: amplitudes
 // are wanted (so.amp is then non-null).
 template <int NCH, bool AMP, typename Fill>
@@ -441,10 +442,11 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, size_t s0, uint32_t det
   const float* noise = kp.noise + s0;
   const uint8_t* gapmax = kp.gapmax + s0;
   constexpr bool amps = AMP;
-  uint32_t found = 0, found0 = 0, wsum = 0;
+  uint32_t found = 0, found0 = 0, found1 = 0, wsum = 0;
   int n = 0, n_own = 0;
-  uint4 rec0 = make_uint4(0u, 0u, 0u, 0u);  // this lane's record of the first 32 candidates
-  bool pass0 = false;
+  uint4 rec0 = make_uint4(0u, 0u, 0u, 0u);  // this lane's records of the first 64 candidates
+  uint4 rec1 = make_uint4(0u, 0u, 0u, 0u);
+  bool pass0 = false, pass1 = false;
   if (single) {
     n = (int)total;
     if (n > 0) {
@@ -455,8 +457,10 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, size_t s0, uint32_t det
           found = form_unit<AMP>(w, kp, n, 0, n_own, det0, nullptr, 0, 0, nullptr, nullptr, &wsum);
         } else {
           found0 = form_unit<AMP>(w, kp, n, 0, n_own < 32 ? n_own : 32, det0, nullptr, 0, 0, &rec0, &pass0);
-          found = found0;
-          if (n_own > 32) found += form_unit<AMP>(w, kp, n, 32, n_own, det0, nullptr, 0, 0);
+          if (n_own > 32)
+            found1 = form_unit<AMP>(w, kp, n, 32, n_own < 64 ? n_own : 64, det0, nullptr, 0, 0, &rec1, &pass1);
+          found = found0 + found1;
+          if (n_own > 64) found += form_unit<AMP>(w, kp, n, 64, n_own, det0, nullptr, 0, 0);
         }
       }
     }
@@ -500,12 +504,16 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, size_t s0, uint32_t det
   if (found == 0) return;
   AmpPos ap{astart != kNoAmp ? so.amp : nullptr, so.amp_cap, astart != kNoAmp ? (uint64_t)astart : 0u};
   if (single && !amps) {
-    const unsigned b = __ballot_sync(0xffffffffu, pass0);
+    const unsigned b0 = __ballot_sync(0xffffffffu, pass0), b1 = __ballot_sync(0xffffffffu, pass1);
     if (pass0) {
-      const uint64_t pos = (uint64_t)start + __popc(b & lanemask_lt(lane));
+      const uint64_t pos = (uint64_t)start + __popc(b0 & lanemask_lt(lane));
       if (pos < so.cap) so.stage[pos] = rec0;
     }
-    if (n_own > 32) form_unit<AMP>(w, kp, n, 32, n_own, det0, so.stage, so.cap, (uint64_t)start + found0);
+    if (pass1) {
+      const uint64_t pos = (uint64_t)start + found0 + __popc(b1 & lanemask_lt(lane));
+      if (pos < so.cap) so.stage[pos] = rec1;
+    }
+    if (n_own > 64) form_unit<AMP>(w, kp, n, 64, n_own, det0, so.stage, so.cap, (uint64_t)start + found0 + found1);
   } else if (single) {
     form_unit<AMP>(w, kp, n, 0, n_own, det0, so.stage, so.cap, start, nullptr, nullptr, nullptr, &ap);
   } else {
