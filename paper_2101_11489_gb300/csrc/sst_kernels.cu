@@ -875,8 +875,7 @@ __global__ void __launch_bounds__(256, 4) k_cluster(sst_digis in, uint32_t n_fed
       for (uint32_t k = lane; k < n; k += 32) {
         const uint32_t key = in.strip[a + k] - g0;
         // a digi that does not belong to channel c takes no part in clustering
-        w.kf[o + k] = (key >> 8) == (uint32_t)c ? key : 0xFFFFu;
-        w.adc[o + k] = in.adc[a + k];
+        w.kf[o + k] = ((key >> 8) == (uint32_t)c ? key : 0x1FFFu) | ((uint32_t)in.adc[a + k] << 16);
       }
     }
     __syncwarp();
