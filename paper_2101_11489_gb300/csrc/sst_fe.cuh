@@ -156,8 +156,9 @@ __device__ __forceinline__ int chunk_end(const Warp& w, int c0) {
 // first strip, channel) and a run-start flag.  Then every lane takes one digi at a
 // time and finds its run as the last run start at or before it: the highest set
 // bit at or below the lane in the ballot of its 32-digi window, or the last run
-// start of the windows before.  Descriptors and flags live in nsq[] and flag[],
-// which scan_unit overwrites afterwards.
+// start of the windows before, and writes the digi's tile word (key and ADC).
+// Descriptors live in nsq[] and run-start flags in the bytes of own[], which
+// scan_unit overwrites afterwards.
 __device__ void copy_runs(Warp& w, const Unit& un, int c0, int c1) {
   const int lane = threadIdx.x & 31;
   uint32_t* desc = reinterpret_cast<uint32_t*>(w.nsq);
