@@ -158,14 +158,14 @@ def time_oracle(pool, cores, events, n_sample):
 
 # ---------------------------------------------------------------- served stream
 
-def run_served(sst, ctx, events, n_feds, n_requests, rate, submitters=8):
+def run_served(sst, ctx, events, n_feds, n_requests, rate, submitters=8, pollers=2):
     """Submits n_requests events (cycling over `events`) with Poisson arrivals at
     `rate` events/s (0 = as fast as possible) from `submitters` threads (arrival i
-    goes to thread i mod submitters; each sst_submit copies the event into the
-    server's pinned pool with the GIL released) while another thread polls the
-    admitted events in admission order, which frees their space.  Returns
-    throughput and latency percentiles (submit to done, host clock, microseconds).
-    A thread that makes no progress for a minute ends the run with an error."""
+    goes to thread i mod submitters; sst_submit runs with the GIL released) while
+    `pollers` threads take the admitted events from one queue, in admission order,
+    and poll them, which frees their space.  Returns throughput and latency
+    percentiles (submit to done, host clock, microseconds).  A thread that makes no
+    progress for a minute ends the run with an error."""
     import queue
     import sys
     import threading
@@ -204,8 +204,10 @@ def run_served(sst, ctx, events, n_feds, n_requests, rate, submitters=8):
 
     def poller():
         try:
-            for _ in range(n_requests):
+            while True:
                 tk = admitted.get(timeout=limit_s)
+                if tk is None:
+                    return
                 code, info, _ = sst.sst_poll(ctx, tk, -1, 0)
                 if code != sst.SST_OK:
                     raise RuntimeError(f"sst_poll returned {code}")
@@ -215,11 +217,15 @@ def run_served(sst, ctx, events, n_feds, n_requests, rate, submitters=8):
             errors.append(repr(ex))
 
     t0 = time.perf_counter()
-    th = [threading.Thread(target=submitter, args=(k, t0)) for k in range(submitters)]
-    th.append(threading.Thread(target=poller))
-    for x in th:
+    subs = [threading.Thread(target=submitter, args=(k, t0)) for k in range(submitters)]
+    polls = [threading.Thread(target=poller) for _ in range(pollers)]
+    for x in subs + polls:
         x.start()
-    for x in th:
+    for x in subs:
+        x.join()
+    for _ in polls:
+        admitted.put(None)  # after every admitted ticket: the pollers stop once the queue is drained
+    for x in polls:
         x.join()
     sys.setswitchinterval(old_switch)
     if errors or len(lat) != n_requests:
@@ -587,7 +593,8 @@ def main():
             pts = [run_served(sst, ctx, lent, w.n_feds, args.served_events, f * cap["throughput"])
                    for f in (0.5, 0.9)]
             served = {"workload": "served-440fed-lognormal: occupancy lognormal median 1.5%, clip [0.5%, 5%], "
-                                  "64 distinct events cycled, Poisson arrivals, 8 Python submitter threads, "
+                                  "64 distinct events cycled, Poisson arrivals, 8 Python submitter threads and 2 "
+                                  "poller threads, "
                                   "zero-copy submission from pinned event buffers",
                       "budget_bytes": 8 << 30, "max_batch_events": 64, "max_inflight": 3,
                       "saturation": cap, "points": pts}
