@@ -208,9 +208,9 @@ __device__ void copy_runs(Warp& w, const Unit& un, int c0, int c1) {
 
 // a3 + a4 in one pass over the tile, 32 digis at a time in strip order, with the
 // next window's noise gather in flight:
-//  - thresholds (binary32 product threshold x noise, strict "larger than"), the
-//    gain-corrected charge (saturation codes 254/255 kept) and noise^2 of active
-//    digis;
+//  - thresholds (binary32 product threshold x noise, strict "larger than"; a bad
+//    strip, 255 in the linking-gap table, is never active), the gain-corrected
+//    charge (saturation codes 254/255 kept) and noise^2 of active digis;
 //  - candidate starts: an active digi whose previous active digi in the tile lies
 //    in another channel (the tile is sorted by channel, then strip) or is not
 //    linked to it by the hole / bad-strip rules, i.e. is more than gapmax[strip]
@@ -251,7 +251,7 @@ __device__ int scan_unit(Warp& w, const KParams& kp, const float* noise, const u
     uint32_t q = 0;
     float nsq = 0.f;
     if (c < (uint32_t)NCH) {
-      const bool isbad = (w.bad[c * kMaskWords + (st >> 5)] >> (st & 31u)) & 1u;
+      const bool isbad = gmax == kGapBad;
       const uint32_t adc = (word >> 16) & 255u;
       const float a = __uint2float_rn(adc);
       act = !isbad && a > __fmul_rn(kp.t_channel, nz);

@@ -28,7 +28,7 @@ struct KParams {
   int max_holes, max_bad, max_adj;
   const float* noise;       // [n_strips]
   const uint32_t* badmask;  // [n_strips / 32], bit (s & 31) of word s / 32
-  const uint8_t* gapmax;    // [n_strips], longest gap below strip s that links (see k_gapmax)
+  const uint8_t* gapmax;    // [n_strips], longest gap below strip s that links, 255 for a bad strip (k_gapmax)
   const float* gain;        // [n_strips / 128]
 };
 

@@ -48,6 +48,7 @@ constexpr int kLbSpinLimit = 1 << 20;              // polls before giving up (ab
 constexpr uint64_t kBadOff = ~0ull;                // fed_off marker: record outside the event
 constexpr int kFedBufMin = 16384;                  // bytes of FED record staged on chip (at least)
 constexpr int kFedScanThreads = 128;               // FEDs per k_fed_scan CTA
+constexpr uint32_t kGapBad = 255;                  // linking-gap table entry of a bad strip
 
 // Shared scalars.
 enum {
@@ -969,7 +970,9 @@ __global__ void k_badmask(const uint8_t* __restrict__ bad, uint32_t* __restrict_
 // all inactive, so they are linked exactly when their gap t-a-1 is at most G(t):
 // a gap that is valid stays valid when shortened from below, and one longer than
 // G(t) contains the strip t-G(t)-1 that breaks a limit.  One thread per strip
-// walks down from t-1; G(t) <= t <= 255.
+// walks down from t-1.  A gap is at most 254 strips (a >= 0, t <= 255), so G(t) is
+// stored capped at 254 without changing any decision, and the entry of a bad strip
+// (never active) is 255: the clusterizer reads both facts from one byte.
 __global__ void k_gapmax(const uint32_t* __restrict__ mask, uint8_t* __restrict__ gapmax, uint64_t n_strips,
                          int max_holes, int max_bad) {
   const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -984,7 +987,8 @@ __global__ void k_gapmax(const uint32_t* __restrict__ mask, uint8_t* __restrict_
     if (run > (b ? max_bad : max_holes)) break;
     ++g;
   }
-  gapmax[s] = (uint8_t)g;
+  const bool bad = (m[t >> 5] >> (t & 31)) & 1u;
+  gapmax[s] = bad ? (uint8_t)kGapBad : (uint8_t)(g < 254 ? g : 254);
 }
 
 // ---------------------------------------------------------------- launch helpers
