@@ -43,7 +43,8 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     os.makedirs(OUT_DIR, exist_ok=True)
     os.makedirs(BUILD_DIR, exist_ok=True)
     cc = nvcc()
-    common = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"] + ARCH
+    common = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+              "--expt-relaxed-constexpr"] + ARCH
     common += extra or []
     procs, objs = [], []
     for src in SOURCES:

@@ -21,17 +21,53 @@ sst_status cuda_err(sst_ctx* c, cudaError_t e, const char* where) {
 
 KParams kparams(const sst_ctx* c) {
   KParams k;
-  k.t_channel = c->params.t_channel;
-  k.t_seed = c->params.t_seed;
   k.t_cluster = c->params.t_cluster;
   k.max_holes = c->params.max_seq_holes;
   k.max_bad = c->params.max_seq_bad;
   k.max_adj = c->params.max_adj_bad;
-  k.noise = c->noise;
+  k.cal = c->cal;
+  k.nsq = c->nsq;
   k.badmask = c->badmask;
-  k.gapmax = c->gapmax;
-  k.gain = c->gain;
+  k.qmul = c->qmul;
   return k;
+}
+
+// Gain-corrected charge of a non-saturated ADC (section 2: charge corrected by the
+// strip's gain): the ADC divided by the APV gain, rounded half up, capped at 254;
+// each operation one binary32 rounding.  `mul` selects the form the kernels use
+// with a certified multiplier m: the ADC times m instead of divided by the gain.
+static uint32_t charge_of(uint32_t adc, float g, bool mul) {
+  const float a = (float)adc;
+  const float x = mul ? a * g : a / g;
+  const float y = x + 0.5f;
+  return y >= 254.0f ? 254u : (uint32_t)y;  // (uint32_t)y truncates; y >= 0
+}
+
+// A multiplier for one APV: the binary32 reciprocal of the gain, or a neighbour of
+// it within a few units in the last place, that gives exactly the quotient form's
+// charge for every ADC 0..253 (checked here, exhaustively).  When none does, -gain:
+// the kernels then divide.  Needs binary32 arithmetic without contraction (the
+// library's host code is compiled with -ffp-contract=off).
+static float certified_multiplier(float g) {
+  uint32_t want[254];
+  for (uint32_t a = 0; a < 254; a++) want[a] = charge_of(a, g, false);
+  const float r = 1.0f / g;
+  float cand[9];
+  cand[0] = r;
+  float up = r, dn = r;
+  for (int k = 1; k <= 4; k++) {
+    up = std::nextafter(up, INFINITY);
+    dn = std::nextafter(dn, 0.0f);
+    cand[2 * k - 1] = up;
+    cand[2 * k] = dn;
+  }
+  for (float m : cand) {
+    if (!(m > 0.f) || !std::isfinite(m)) continue;
+    bool ok = true;
+    for (uint32_t a = 1; a < 254 && ok; a++) ok = charge_of(a, m, true) == want[a];
+    if (ok) return m;
+  }
+  return -g;
 }
 
 template <typename T>
@@ -59,13 +95,14 @@ cudaError_t ensure_scratch(Scratch& s, size_t items, size_t events, size_t stage
     if ((e = cudaDeviceSynchronize())) return e;
     if (items > s.items_cap) {
       size_t cap = s.items_cap, c2 = s.items_cap, c3 = s.items_cap, c4 = s.items_cap, c5 = s.items_cap;
-      size_t c6 = s.items_cap;
+      size_t c6 = s.items_cap, c7 = s.items_cap * kMapWords;
       if ((e = grow(s.lb, cap, items))) return e;
       if ((e = grow(s.fed_off, c2, items))) return e;
       if ((e = grow(s.fed_cnt, c3, items))) return e;
       if ((e = grow(s.fed_start, c4, items))) return e;
       if ((e = grow(s.fed_dest, c5, items))) return e;
       if ((e = grow(s.unit_desc, c6, items))) return e;
+      if ((e = grow(s.chan_map, c7, items * kMapWords))) return e;
       s.items_cap = items;
     }
     if ((e = grow(s.ev_alloc, s.ev_cap, events))) return e;
@@ -99,6 +136,7 @@ void free_scratch(Scratch& s) {
   if (s.fed_start) cudaFree(s.fed_start);
   if (s.fed_dest) cudaFree(s.fed_dest);
   if (s.unit_desc) cudaFree(s.unit_desc);
+  if (s.chan_map) cudaFree(s.chan_map);
   if (s.ev_alloc) cudaFree(s.ev_alloc);
   if (s.stage) cudaFree(s.stage);
   if (s.tickets) cudaFree(s.tickets);
@@ -157,10 +195,10 @@ sst_status sst_destroy(sst_ctx* ctx) {
     cudaEventDestroy(pr.second);
   }
   free_scratch(ctx->scratch);
-  if (ctx->noise) cudaFree(ctx->noise);
+  if (ctx->cal) cudaFree(ctx->cal);
+  if (ctx->nsq) cudaFree(ctx->nsq);
   if (ctx->badmask) cudaFree(ctx->badmask);
-  if (ctx->gapmax) cudaFree(ctx->gapmax);
-  if (ctx->gain) cudaFree(ctx->gain);
+  if (ctx->qmul) cudaFree(ctx->qmul);
   if (ctx->pitch) cudaFree(ctx->pitch);
   delete ctx;
   return SST_OK;
@@ -186,26 +224,35 @@ sst_status sst_calib_upload(sst_ctx* ctx, const float* noise, const float* gain,
   for (uint64_t i = 0; i < n_apv; i++)
     if (!(gain[i] > 0.f) || !std::isfinite(gain[i]))
       return set_err(ctx, SST_ERR_INVALID_ARG, "sst_calib_upload: gain must be finite and > 0");
+  std::vector<float> qmul(n_apv);
+  for (uint64_t i = 0; i < n_apv; i++) qmul[i] = certified_multiplier(gain[i]);
   DeviceGuard g(ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
-  if (!ctx->noise) {
-    if ((e = cudaMalloc(&ctx->noise, n * sizeof(float)))) return cuda_err(ctx, e, "cudaMalloc noise");
+  if (!ctx->cal) {
+    if ((e = cudaMalloc(&ctx->cal, n * sizeof(uint32_t)))) return cuda_err(ctx, e, "cudaMalloc cal");
+    if ((e = cudaMalloc(&ctx->nsq, n * sizeof(float)))) return cuda_err(ctx, e, "cudaMalloc nsq");
     if ((e = cudaMalloc(&ctx->badmask, n / 8))) return cuda_err(ctx, e, "cudaMalloc badmask");
-    if ((e = cudaMalloc(&ctx->gapmax, n))) return cuda_err(ctx, e, "cudaMalloc gapmax");
-    if ((e = cudaMalloc(&ctx->gain, n_apv * sizeof(float)))) return cuda_err(ctx, e, "cudaMalloc gain");
+    if ((e = cudaMalloc(&ctx->qmul, n_apv * sizeof(float)))) return cuda_err(ctx, e, "cudaMalloc qmul");
   }
+  // staging of the raw tables, freed once the kernels' tables are built
   uint8_t* bad_dev = nullptr;
+  float* noise_dev = nullptr;
   if ((e = cudaMalloc(&bad_dev, n))) return cuda_err(ctx, e, "cudaMalloc bad");
+  if ((e = cudaMalloc(&noise_dev, n * sizeof(float)))) {
+    cudaFree(bad_dev);
+    return cuda_err(ctx, e, "cudaMalloc noise");
+  }
   // Copies are stream-ordered after earlier work on `st`; synchronise before the
-  // pageable host buffers go out of the caller's hands and before freeing bad_dev.
-  if (!e) e = cudaMemcpyAsync(ctx->noise, noise, n * sizeof(float), cudaMemcpyHostToDevice, st);
-  if (!e) e = cudaMemcpyAsync(ctx->gain, gain, n_apv * sizeof(float), cudaMemcpyHostToDevice, st);
+  // host buffers go out of the caller's hands and before freeing the staging.
+  if (!e) e = cudaMemcpyAsync(noise_dev, noise, n * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemcpyAsync(ctx->qmul, qmul.data(), n_apv * sizeof(float), cudaMemcpyHostToDevice, st);
   if (!e) e = cudaMemcpyAsync(bad_dev, bad, n, cudaMemcpyHostToDevice, st);
   if (!e) e = build_badmask(bad_dev, ctx->badmask, n, st);
-  if (!e) e = build_gapmax(ctx->badmask, ctx->gapmax, n, params->max_seq_holes, params->max_seq_bad, st);
+  if (!e) e = build_calib(noise_dev, ctx->badmask, ctx->cal, ctx->nsq, n, *params, st);
   if (!e) e = cudaStreamSynchronize(st);
   cudaFree(bad_dev);
+  cudaFree(noise_dev);
   if (e) return cuda_err(ctx, e, "sst_calib_upload");
   ctx->params = *params;
   ctx->has_calib = true;

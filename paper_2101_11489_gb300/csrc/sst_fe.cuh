@@ -7,10 +7,26 @@
 // 2: channel = module of 256 strips).  One warp handles one work item from the raw
 // bytes to staged clusters with no block-wide barrier, so that a GB300 SM keeps
 // dozens of independent items in flight and hides the latency of each item's
-// serial steps (the FE length chains, the run chains, the L2 gathers of noise).
-// Two FE units per warp rather than one: the serial per-channel steps (length
-// chains, run walks) then occupy 24 lanes instead of 12, and the fixed cost of an
-// item is paid once per pair.
+// serial steps (the run chains, the L2 gathers of calibration).  Two FE units per
+// warp rather than one: the serial per-channel run walks then occupy 24 lanes
+// instead of 12, and the fixed cost of an item is paid once per pair.
+//
+// Phases of an item (batched kernel):
+//   parse_unit  one lane per channel walks the channel's runs once: validates them,
+//               counts digis and, for a staged pair, leaves a descriptor of every
+//               run in a slot indexed by the byte position of its header / 3
+//               (headers are at least 3 bytes apart, so slots never collide and
+//               ascend in (channel, strip) order);
+//   mark_slots  one lane per slot puts each run's descriptor at the tile position
+//               of its first digi (channel base + digis of the channel before the
+//               run) and sets that position's run-start bit;
+//   scan_unit   32 digis at a time: each lane finds its digi's run (the last
+//               run-start bit at or below it), reads its ADC byte, and applies the
+//               thresholds, the gain correction, the candidate rule and the
+//               leftmost-seed rule (warp ballots, carries across windows);
+//   form_unit   one lane per owned candidate: sums, cluster threshold, centroid.
+// Pairs whose digis exceed the tile, or whose bytes exceed the slot area, walk
+// their runs a second time per chunk of channels (mark_walk) instead of using slots.
 //
 // Included by sst_kernels.cu only, inside its namespace, after the mask helper it
 // uses (bit).
@@ -18,39 +34,50 @@
 
 namespace fe {
 
-// Tile and staging sizes share the 56 KB of shared memory that 8 warps of a CTA
-// may use at 4 CTAs per SM: a larger tile sends fewer work items through the
-// chunked (two-pass) path, a larger staging buffer fewer through in-place global
-// reads.  With one 32-bit word per digi (10 bytes of tile per digi in all), 448
-// digis and 1,376 bytes measured fastest on the 64-event batch (448 / 960: +1.1%,
-// 480 / 960: +1.1%).
+// Tile and staging sizes share the shared memory that 8 warps of a CTA may use at
+// 4 CTAs per SM: a larger tile sends fewer work items through the chunked
+// (two-pass) path, a larger staging buffer fewer through in-place global reads.
 constexpr int kTile = 448;    // digis per warp tile (a chunk of whole channels)
 constexpr int kBuf = 1376;    // bytes of the two FE units staged per warp (larger pairs are read in place)
 constexpr int kUnits = 2;     // FE units per work item: two adjacent units of one FED
 constexpr int kChW = kUnits * kChPerFe;  // 24 consecutive channels per work item
+constexpr int kSlots = (kTile * 2 + kChW * kMaskWords * 4) / 4;  // run-header slots (byte position / 3) in own[] + bad[]
+constexpr int kRsWords = kTile / 32;     // run-start bits of the tile
+static_assert(kTile % 32 == 0, "whole windows of 32 digis");
 
 // Per-warp shared memory.
 struct __align__(16) Warp {
   uint8_t fe[kBuf];                      // staged bytes of the two FE units
-  uint32_t bad[kChW * kMaskWords];       // bad-strip masks of the 24 channels
-  float gain[kChW * 2];                  // APV gains of the 24 channels
-  float nsq[kTile];                      // noise^2 of active digis
+  float qmul[kChW * 2];                  // per APV of the 24 channels: certified multiplier, or -gain
+  uint32_t kf[kTile];   // before scan_unit: run descriptors at run starts (ADC byte position << 13 | first
+                        // strip << 5 | channel) or, without run starts, key | ADC << 16 per digi; after: one
+                        // word per digi: key (channel in the work item << 8 | strip, 13 bits; sorted) |
+                        // flags << 13 (1 active, 2 seed, 4 first strip of a candidate) | ADC << 16 |
+                        // gain-corrected charge of active digis << 24
+  float nsq[kTile];     // noise^2 of each digi
+  uint16_t own[kTile];  // first digi of every seeded candidate (run slots, with bad[], until scan_unit)
+  uint32_t bad[kChW * kMaskWords];       // bad-strip masks of the 24 channels (only when max_adj > 0)
   uint32_t chan_pos[kChW];               // channel record offset from the first unit's start
   uint32_t chan_cnt[kChW + 1];           // digis per channel, then exclusive prefix
   uint16_t chan_len[kChW];
   uint8_t chan_st[kChW];
-  uint32_t kf[kTile];   // one word per digi: key (channel in the work item << 8 | strip, 13 bits; sorted) |
-                        // flags << 13 (1 active, 2 seed, 4 first strip of a candidate) | ADC << 16 |
-                        // gain-corrected charge of active digis << 24
-  uint16_t own[kTile];  // first digi of every seeded candidate; run-start marks (bytes) while the tile fills
+  uint32_t rs[kRsWords];                 // run-start bits of the tile
 };
 
 __device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
 
-// Byte b (0..31) of a 32-byte block held one byte per lane.
-__device__ __forceinline__ uint32_t byte_at(uint32_t v, int b) { return __shfl_sync(0xffffffffu, v, b) & 0xFFu; }
-__device__ __forceinline__ uint32_t u16_at(uint32_t v, int b) { return byte_at(v, b) | (byte_at(v, b + 1) << 8); }
-__device__ __forceinline__ uint32_t u32_at(uint32_t v, int b) { return u16_at(v, b) | (u16_at(v, b + 2) << 16); }
+// Exclusive prefix sum of one value per lane; *total (when given) receives the sum.
+__device__ __forceinline__ uint32_t warp_excl_sum(uint32_t v, uint32_t* total) {
+  const int lane = threadIdx.x & 31;
+  uint32_t x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (total) *total = __shfl_sync(0xffffffffu, x, 31);
+  return x - v;
+}
 
 // Where the work item's two FE units are and what the FED header says about them.
 struct Unit {
@@ -60,73 +87,95 @@ struct Unit {
   uint32_t len;            // bytes of the first unit's records
   uint32_t len1;           // bytes of the second unit's records
   uint8_t fed_status;      // SST_CH_FED_HDR when the FED record is corrupt or out of range, else 0
+  bool staged;             // src is the warp's staging buffer
 };
 
-// a1 + a2 for the two FE units: lanes 0 and 16 each walk one unit's 12 channel
-// lengths (the location map); lanes 0..23 then validate their channel's runs and
-// count its digis; the counts are prefix-summed.  A broken length chain
-// invalidates the 12 channels of its unit.  Returns the digi count; *flags /
-// *nbad receive the OR of the channel statuses and the number of bad channels.
-__device__ uint32_t parse_unit(Warp& w, const Unit& un, uint32_t* flags, uint32_t* nbad) {
-  const int lane = threadIdx.x & 31;
-  if ((lane & 15) == 0) {
-    const int h = lane >> 4;
-    const uint32_t base = h ? un.off1 : 0u;
-    const uint32_t end = h ? un.len1 : un.len;
-    bool good = un.src != nullptr;
-    uint32_t p = 0;
-    for (int k = 0; k < kChPerFe; k++) {
-      uint32_t l = 0;
-      if (good) {
-        if (p + 2 > end) {
-          good = false;
-        } else {
-          l = (uint32_t)un.src[base + p] | ((uint32_t)un.src[base + p + 1] << 8);
-          if (l < 3 || p + l > end) good = false;
-        }
-      }
-      w.chan_pos[h * kChPerFe + k] = good ? base + p : 0u;
-      w.chan_len[h * kChPerFe + k] = good ? (uint16_t)l : (uint16_t)0;
-      if (good) p += l;
+// Slots of a staged pair (one per 3 bytes), and whether they fit the slot area.
+__device__ __forceinline__ uint32_t n_slots(const Unit& un) { return (un.off1 + un.len1 + 2u) / 3u; }
+__device__ __forceinline__ bool use_slots(const Unit& un) { return un.staged && n_slots(un) <= (uint32_t)kSlots; }
+__device__ __forceinline__ uint32_t* slot_area(Warp& w) { return reinterpret_cast<uint32_t*>(w.own); }
+
+// Run descriptor in a slot: ADC byte position (11 bits) << 21 | first strip << 13 |
+// channel << 8 | digis of the channel before the run.  Never 0: the ADC bytes of a
+// run start at least 5 bytes into the pair.  An empty slot is 0.
+__device__ __forceinline__ uint32_t slot_desc(uint32_t adc_pos, uint32_t first, uint32_t c, uint32_t toff) {
+  return (adc_pos << 21) | (first << 13) | (c << 8) | toff;
+}
+
+// One lane's walk over its channel's runs (record r, len bytes, the record at
+// byte `pos` of the pair): validates every run in order and counts the digis; with
+// SLOTS, writes each valid run's descriptor to slots[(pos + header) / 3].  The
+// first error found decides the status (SST_CH_RUN_RANGE: width 0 or past strip
+// 256; SST_CH_RUN_ORDER: starts before the previous run's end; SST_CH_TRUNC: a
+// header or ADC bytes past the record end); the channel then has no digis and
+// its slots written so far are cleared again.
+template <bool SLOTS>
+__device__ __forceinline__ uint32_t walk_runs(const uint8_t* r, uint32_t len, uint32_t pos, uint32_t c,
+                                              uint32_t* slots, uint8_t* st) {
+  uint32_t p = 3, prev_end = 0, cnt = 0;
+  uint8_t err = 0;
+  while (p + 2 <= len) {
+    const uint32_t first = r[p], wd = r[p + 1];
+    const uint32_t end = first + wd, np = p + 2 + wd;
+    if (wd == 0 || end > (uint32_t)kStrips || first < prev_end || np > len) {
+      err = (wd == 0 || end > (uint32_t)kStrips) ? SST_CH_RUN_RANGE : first < prev_end ? SST_CH_RUN_ORDER
+                                                                                        : SST_CH_TRUNC;
+      break;
     }
-    if (good && p != end) good = false;
-    uint8_t st = 0;
-    if (un.src == nullptr)
-      st = un.fed_status;
-    else if (!good)
-      st = SST_CH_FRAMING;
-    for (int k = 0; k < kChPerFe; k++) {
-      w.chan_st[h * kChPerFe + k] = st;
-      if (st) w.chan_len[h * kChPerFe + k] = 0;
-    }
+    if (SLOTS) slots[(pos + p) / 3u] = slot_desc(pos + p + 2, first, c, cnt);
+    prev_end = end;
+    cnt += wd;
+    p = np;
   }
-  __syncwarp();
-  uint32_t cnt = 0;
+  if (!err && p != len) err = SST_CH_TRUNC;  // a header cut by the record end
+  if (err) {
+    if (SLOTS)  // the runs before p were valid: walk them again to clear their slots
+      for (uint32_t q = 3; q < p; q += 2 + r[q + 1]) slots[(pos + q) / 3u] = 0u;
+    *st = err;
+    return 0;
+  }
+  return cnt;
+}
+
+// a1 + a2 for the two FE units.  The channel map (k_chan_map: each channel
+// record's offset and length from the FE unit's length chain, and the unit's
+// status; loaded by the caller as mw / mst, see map_words) gives every lane 0..23
+// its channel; the lane validates the channel's
+// runs and counts its digis in one walk and, when the pair is staged and its slots
+// fit, writes a slot descriptor for every valid run.  The counts are prefix-summed into
+// chan_cnt.  Returns the digi count; *flags / *nbad receive the OR of the channel
+// statuses and the number of bad channels.
+__device__ uint32_t parse_unit(Warp& w, const Unit& un, uint32_t mw, uint32_t mst, uint32_t* flags,
+                               uint32_t* nbad) {
+  const int lane = threadIdx.x & 31;
+  uint32_t* slots = slot_area(w);
+  const bool sl = use_slots(un);
+  if (sl) {
+    const uint32_t ns = n_slots(un);
+    for (uint32_t i = lane; i < ns; i += 32) slots[i] = 0u;
+  }
+  uint32_t cnt = 0, pos = 0, len = 0;
   uint8_t st = 0;
   if (lane < kChW) {
-    st = w.chan_st[lane];
-    const uint32_t len_c = w.chan_len[lane];
-    if (st == 0 && len_c >= 3) {
-      const uint8_t* r = un.src + w.chan_pos[lane];
-      if (r[2] != SST_ZS_CODE) {
-        st = SST_CH_BAD_CODE;
-      } else {
-        uint32_t p = 3, prev_end = 0;
-        while (p < len_c) {
-          if (p + 2 > len_c) { st = SST_CH_TRUNC; break; }
-          const uint32_t first = r[p], wd = r[p + 1];
-          if (wd == 0 || first + wd > (uint32_t)kStrips) { st = SST_CH_RUN_RANGE; break; }
-          if (first < prev_end) { st = SST_CH_RUN_ORDER; break; }
-          if (p + 2 + wd > len_c) { st = SST_CH_TRUNC; break; }
-          prev_end = first + wd;
-          cnt += wd;
-          p += 2 + wd;
-        }
-      }
-      if (st) cnt = 0;
-      w.chan_st[lane] = st;
-    }
+    const int h = lane >= kChPerFe ? 1 : 0;
+    st = (uint8_t)mst;
+    pos = (h ? un.off1 : 0u) + (mw & 0xFFFFu);
+    len = un.src ? (mw >> 16) : 0u;
+    w.chan_pos[lane] = pos;
+    w.chan_len[lane] = (uint16_t)len;
   }
+  __syncwarp();
+  if (lane < kChW && st == 0 && len >= 3) {
+    const uint8_t* r = un.src + pos;
+    if (r[2] != SST_ZS_CODE)
+      st = SST_CH_BAD_CODE;
+    else if (sl)
+      cnt = walk_runs<true>(r, len, pos, (uint32_t)lane, slots, &st);
+    else
+      cnt = walk_runs<false>(r, len, pos, (uint32_t)lane, slots, &st);
+  }
+  if (lane < kChW) w.chan_st[lane] = st;
+  if (lane < kRsWords) w.rs[lane] = 0u;
   uint32_t x = cnt;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -142,6 +191,20 @@ __device__ uint32_t parse_unit(Warp& w, const Unit& un, uint32_t* flags, uint32_
   return total;
 }
 
+// Lane l < 24's channel-map words of the pair whose first unit's map is cmap: the
+// channel word (record offset in its FE unit | length << 16) and the unit status.
+__device__ __forceinline__ void map_words(const uint32_t* __restrict__ cmap, uint32_t* mw, uint32_t* mst) {
+  const int lane = threadIdx.x & 31;
+  *mw = 0;
+  *mst = 0;
+  if (lane < kChW) {
+    const int h = lane >= kChPerFe ? 1 : 0;
+    const uint32_t* m = cmap + h * kMapWords;
+    *mw = __ldg(m + (lane - h * kChPerFe));
+    *mst = __ldg(m + kChPerFe);
+  }
+}
+
 // Greedy chunk of whole channels [c0, c1) with at most kTile digis.
 template <int NCH>
 __device__ __forceinline__ int chunk_end(const Warp& w, int c0) {
@@ -150,22 +213,42 @@ __device__ __forceinline__ int chunk_end(const Warp& w, int c0) {
   return c1;
 }
 
-// a2: the digis of channels [c0, c1) into the tile, all lanes at once.  Lanes
-// c0 .. c1-1 walk their channel's runs (validated by parse_unit) and leave, at the
-// tile position of each run's first digi, a descriptor (byte position of its ADCs,
-// first strip, channel) and a run-start flag.  Then every lane takes one digi at a
-// time and finds its run as the last run start at or before it: the highest set
-// bit at or below the lane in the ballot of its 32-digi window, or the last run
-// start of the windows before, and writes the digi's tile word (key and ADC).
-// Descriptors live in nsq[] and run-start flags in the bytes of own[], which
-// scan_unit overwrites afterwards.
-__device__ void copy_runs(Warp& w, const Unit& un, int c0, int c1) {
+// Tile word of digi k of a run: key (channel << 8 | strip) | ADC << 16.
+__device__ __forceinline__ uint32_t tile_word(uint32_t c, uint32_t strip, uint32_t adc) {
+  return (c << 8) | strip | (adc << 16);
+}
+
+// Tile descriptor of a run: ADC byte position << 13 | first strip << 5 | channel.
+__device__ __forceinline__ uint32_t tile_desc(uint32_t adc_pos, uint32_t first, uint32_t c) {
+  return (adc_pos << 13) | (first << 5) | c;
+}
+
+// Single-chunk pair with slots (a2): every valid run's slot descriptor goes to the
+// tile position of its first digi (channel base + digis of the channel before it),
+// with its run-start bit.  A run of a channel found invalid was cleared.
+__device__ void mark_slots(Warp& w, const Unit& un) {
   const int lane = threadIdx.x & 31;
-  uint32_t* desc = reinterpret_cast<uint32_t*>(w.nsq);
-  const int n = (int)(w.chan_cnt[c1] - w.chan_cnt[c0]);
-  uint8_t* rs = reinterpret_cast<uint8_t*>(w.own);  // run-start marks
-  uint32_t* rs32 = reinterpret_cast<uint32_t*>(w.own);
-  for (int i = lane; i < (n + 3) / 4; i += 32) rs32[i] = 0;
+  const uint32_t* slots = slot_area(w);
+  const int ns = (int)n_slots(un);
+  for (int k = lane; k < ns; k += 32) {
+    const uint32_t d = slots[k];
+    if (d) {
+      const uint32_t c = (d >> 8) & 31u;
+      const uint32_t t = w.chan_cnt[c] + (d & 255u);
+      w.kf[t] = tile_desc(d >> 21, (d >> 13) & 255u, c);
+      atomicOr(&w.rs[t >> 5], 1u << (t & 31u));
+    }
+  }
+  __syncwarp();
+}
+
+// Chunk [c0, c1) (or a pair whose slots do not fit): lanes c0 .. c1-1 walk their
+// channel's runs again (validated by parse_unit) and write each run's tile
+// descriptor and run-start bit; the walk is bounded by the counted digis, so that
+// it cannot leave the tile.
+__device__ void mark_walk(Warp& w, const Unit& un, int c0, int c1) {
+  const int lane = threadIdx.x & 31;
+  if (lane < kRsWords) w.rs[lane] = 0u;
   __syncwarp();
   const int c = c0 + lane;
   if (c < c1) {
@@ -179,8 +262,8 @@ __device__ void copy_runs(Warp& w, const Unit& un, int c0, int c1) {
       const uint32_t first = r[p], wd0 = r[p + 1];
       const uint32_t wd = wd0 < left ? wd0 : left;
       if (wd > 0) {
-        desc[o] = ((pos + p + 2) << 13) | (first << 5) | (uint32_t)c;
-        rs[o] = 1;
+        w.kf[o] = tile_desc(pos + p + 2, first, (uint32_t)c);
+        atomicOr(&w.rs[o >> 5], 1u << (o & 31u));
       }
       o += wd;
       left -= wd;
@@ -188,41 +271,34 @@ __device__ void copy_runs(Warp& w, const Unit& un, int c0, int c1) {
     }
   }
   __syncwarp();
-  int carry = 0;
-  for (int base = 0; base < n; base += 32) {
-    const int i = base + lane;
-    const uint32_t m = __ballot_sync(0xffffffffu, i < n && rs[i] != 0);
-    const uint32_t le = m & (lane == 31 ? 0xffffffffu : ((2u << lane) - 1u));
-    const int s = le ? base + 31 - __clz(le) : carry;
-    if (i < n) {
-      const uint32_t d = desc[s];
-      const uint32_t k = (uint32_t)(i - s);
-      const uint32_t b = (d >> 13) + k;
-      const uint32_t adc = b < un.off1 + un.len1 ? un.src[b] : 0u;
-      w.kf[i] = ((d & 31u) << 8) | ((((d >> 5) & 255u) + k) & 255u) | (adc << 16);
-    }
-    if (m) carry = base + 31 - __clz(m);
-  }
-  __syncwarp();
 }
 
-// a3 + a4 in one pass over the tile, 32 digis at a time in strip order, with the
-// next window's noise gather in flight:
-//  - thresholds (binary32 product threshold x noise, strict "larger than"; a bad
-//    strip, 255 in the linking-gap table, is never active), the gain-corrected
-//    charge (saturation codes 254/255 kept) and noise^2 of active digis;
+// a2 + a3 + a4 in one pass over the tile, 32 digis at a time in strip order; the
+// next window's digis are expanded and their calibration gathered while the
+// current window is processed.
+//  - expansion (EXP): the digi's run is the last run start at or below it (the
+//    highest set run-start bit up to the lane, or the last run start of the
+//    windows before, carried with its descriptor); its ADC byte is read from the
+//    pair's bytes.  Without EXP the tile already holds key | ADC << 16 per digi.
+//  - thresholds: the per-strip table holds the channel and seed limits as the
+//    largest failing ADC (for an integer ADC, (float)adc > T x noise exactly when
+//    adc > floor(T x noise); a bad strip has 255, so it is never active or a
+//    seed), and the linking gap; the gain-corrected charge of active digis
+//    (saturation codes 254/255 kept) uses the APV's certified multiplier (a
+//    division, in a warp-uniform branch, for an APV without one); noise^2 comes
+//    from the per-strip table;
 //  - candidate starts: an active digi whose previous active digi in the tile lies
 //    in another channel (the tile is sorted by channel, then strip) or is not
-//    linked to it by the hole / bad-strip rules, i.e. is more than gapmax[strip]
-//    strips below it (the longest linking gap, built from the bad-strip mask
-//    when the calibration is uploaded);
+//    linked to it by the hole / bad-strip rules, i.e. is more than gap[strip]
+//    strips below it (the longest linking gap);
 //  - owners, the leftmost seed of every candidate: two ballots (seeds, candidate
 //    starts) and a carry across windows decide whether another seed lies between
 //    a seed's candidate start and it.
 // The first digis of owned candidates are compacted in strip order into own[];
-// returns their number.
-template <int NCH>
-__device__ int scan_unit(Warp& w, const KParams& kp, const float* noise, const uint8_t* gapmax, int n) {
+// returns their number.  src / src_end: the pair's bytes (EXP).
+template <int NCH, bool EXP>
+__device__ int scan_unit(Warp& w, const KParams& kp, const uint32_t* __restrict__ cal,
+                         const float* __restrict__ nsqt, const uint8_t* src, uint32_t src_end, int n) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt(lane);
   const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
@@ -230,43 +306,62 @@ __device__ int scan_unit(Warp& w, const KParams& kp, const float* noise, const u
   int n_own = 0, carry_start = -1;
   bool carry_seen = false;
   uint32_t carry_key = kNone;  // key of the last active digi of the windows before
-  uint32_t wn = lane < n ? w.kf[lane] : kNone;  // key | ADC << 16
+  int run_s = 0;               // expansion: last run start of the windows before, and its descriptor
+  uint32_t run_d = 0;
+  // key | ADC << 16 of digi base + lane (kNone beyond n)
+  auto word_at = [&](int base) -> uint32_t {
+    const int i = base + lane;
+    if (!EXP) return i < n ? w.kf[i] : kNone;
+    const uint32_t m = w.rs[base >> 5];
+    const uint32_t le = m & upto;
+    int s = run_s;
+    uint32_t d = run_d;
+    if (le) {
+      s = base + 31 - __clz(le);
+      d = w.kf[s];
+    }
+    if (m) {
+      const int l = 31 - __clz(m);
+      run_s = base + l;
+      run_d = __shfl_sync(0xffffffffu, d, l);
+    }
+    if (i >= n) return kNone;
+    const uint32_t k = (uint32_t)(i - s);
+    const uint32_t b = (d >> 13) + k;
+    const uint32_t adc = b < src_end ? (uint32_t)src[b] : 0u;
+    return ((d & 31u) << 8) | ((((d >> 5) & 255u) + k) & 255u) | (adc << 16);
+  };
+  uint32_t wn = word_at(0);
   uint32_t xn = ((wn >> 8) & 31u) < (uint32_t)NCH ? (wn & 0x1FFFu) : 0u;
-  float zn = __ldg(noise + xn);
-  uint32_t gn = __ldg(gapmax + xn);
+  uint32_t cn = __ldg(cal + xn);
+  float zn = __ldg(nsqt + xn);
   for (int base = 0; base < n; base += 32) {
     const int i = base + lane;
     const uint32_t word = wn;
-    const float nz = zn;
-    const uint32_t gmax = gn;
+    const uint32_t cv = cn;
+    const float nq = zn;
     if (base + 32 < n) {
-      wn = i + 32 < n ? w.kf[i + 32] : kNone;
+      wn = word_at(base + 32);
       xn = ((wn >> 8) & 31u) < (uint32_t)NCH ? (wn & 0x1FFFu) : 0u;
-      zn = __ldg(noise + xn);
-      gn = __ldg(gapmax + xn);
+      cn = __ldg(cal + xn);
+      zn = __ldg(nsqt + xn);
     }
     const uint32_t key = word & 0x1FFFu;
     const uint32_t c = key >> 8, st = key & 255u;
-    bool act = false, sd = false;
-    uint32_t q = 0;
-    float nsq = 0.f;
-    if (c < (uint32_t)NCH) {
-      const bool isbad = gmax == kGapBad;
-      const uint32_t adc = (word >> 16) & 255u;
-      const float a = __uint2float_rn(adc);
-      act = !isbad && a > __fmul_rn(kp.t_channel, nz);
-      sd = !isbad && a > __fmul_rn(kp.t_seed, nz);
-      if (act) {
-        if (adc >= 254u) {
-          q = adc;  // saturation codes are kept
-        } else {
-          const float x = __fdiv_rn(a, w.gain[c * 2 + (st >> 7)]);
-          const int ci = __float2int_rz(__fadd_rn(x, 0.5f));
-          q = ci > 253 ? 254u : (uint32_t)ci;
-        }
-        nsq = __fmul_rn(nz, nz);
-      }
-    }
+    const uint32_t adc = (word >> 16) & 255u;
+    const bool inr = c < (uint32_t)NCH;
+    const bool act = inr && adc > (cv & 255u);
+    const bool sd = inr && adc > ((cv >> 8) & 255u);
+    const uint32_t gmax = (cv >> 16) & 255u;
+    // gain-corrected charge with the APV's multiplier; an APV without a certified
+    // multiplier (rq < 0) divides, in a branch the whole warp takes together
+    const float a = __uint2float_rn(adc);
+    const float rq = w.qmul[(inr ? c : 0u) * 2 + (st >> 7)];
+    float xq = __fmul_rn(a, rq);
+    if (__any_sync(0xffffffffu, rq < 0.f))
+      if (rq < 0.f) xq = __fdiv_rn(a, -rq);
+    const int ci = __float2int_rz(__fadd_rn(xq, 0.5f));
+    const uint32_t q = !act ? 0u : (adc >= 254u ? adc : (ci > 253 ? 254u : (uint32_t)ci));
     const unsigned A = __ballot_sync(0xffffffffu, act);
     const unsigned Al = A & lt;
     const uint32_t pk_l = __shfl_sync(0xffffffffu, key, Al ? 31 - __clz(Al) : lane);
@@ -300,7 +395,7 @@ __device__ int scan_unit(Warp& w, const KParams& kp, const float* noise, const u
     if (i < n) {
       w.kf[i] = (word & 0x00FF1FFFu) | ((act ? 1u : 0u) << 13) | ((sd ? 2u : 0u) << 13) | ((start ? 4u : 0u) << 13) |
                 (q << 24);
-      w.nsq[i] = nsq;
+      w.nsq[i] = nq;
     }
   }
   __syncwarp();
@@ -346,17 +441,16 @@ __device__ uint32_t form_unit(Warp& w, const KParams& kp, int n, int k_begin, in
     float bary = 0.f;
     if (k < n_own) {
       int j = w.own[k];
-      const uint32_t key0 = w.kf[j] & 0x1FFFu;
-      c = key0 >> 8;
-      const int l = (int)(key0 & 255u);
+      uint32_t kj = w.kf[j];
+      c = (kj >> 8) & 31u;
+      const int l = (int)(kj & 255u);
       const uint32_t* B = w.bad + c * kMaskWords;
       int lo_i = l;
       for (int m = 0; m < kp.max_adj && lo_i - 1 >= 0 && bit(B, lo_i - 1); m++) lo_i--;
       uint32_t s_raw = 0, moment = 0;
       float n2 = 0.f;
       int r = l;
-      do {
-        const uint32_t kj = w.kf[j];
+      for (;;) {
         if (kj & (1u << 13)) {
           const uint32_t q = kj >> 24;
           const int st = (int)(kj & 255u);
@@ -366,8 +460,10 @@ __device__ uint32_t form_unit(Warp& w, const KParams& kp, int n, int k_begin, in
           moment += (uint32_t)(st - lo_i) * q;
           r = st;
         }
-        ++j;
-      } while (j < n && ((w.kf[j] >> 8) & 31u) == c && !(w.kf[j] & (4u << 13)));
+        if (++j >= n) break;
+        kj = w.kf[j];
+        if (((kj >> 8) & 31u) != c || (kj & (4u << 13))) break;
+      }
       pass = __uint2float_rn(s_raw) > __fmul_rn(kp.t_cluster, __fsqrt_rn(n2));
       int hi = r;
       for (int m = 0; m < kp.max_adj && hi + 1 < kStrips && bit(B, hi + 1); m++) hi++;
@@ -414,6 +510,32 @@ __device__ uint32_t form_unit(Warp& w, const KParams& kp, int n, int k_begin, in
   return kept;
 }
 
+// Loads the APV multipliers (2 per channel) of channels ch0 .. ch0 + NCH - 1 with
+// 16-byte loads (the table starts on a 16-byte boundary: ch0 is a multiple of 12).
+template <int NCH>
+__device__ __forceinline__ void load_calib(Warp& w, const KParams& kp, uint32_t ch0) {
+  const int lane = threadIdx.x & 31;
+  constexpr int kG = NCH * 2 / 4;  // vectors of multipliers
+  static_assert(kG <= 32, "one multiplier vector per lane");
+  if (lane < kG)
+    reinterpret_cast<uint4*>(w.qmul)[lane] = __ldg(reinterpret_cast<const uint4*>(kp.qmul + (size_t)ch0 * 2) + lane);
+}
+
+// Loads the bad-strip masks (8 words per channel) of the same channels when
+// widening over bad strips is enabled (max_adj > 0); otherwise no cluster is
+// widened and the masks are never read.  Called once the run slots, which share
+// their space, are no longer needed.
+template <int NCH>
+__device__ __forceinline__ void load_masks(Warp& w, const KParams& kp, uint32_t ch0) {
+  const int lane = threadIdx.x & 31;
+  constexpr int kB = NCH * kMaskWords / 4;  // vectors of masks
+  if (kp.max_adj > 0) {
+    for (int i = lane; i < kB; i += 32)
+      reinterpret_cast<uint4*>(w.bad)[i] = __ldg(reinterpret_cast<const uint4*>(kp.badmask + (size_t)ch0 * kMaskWords) + i);
+    __syncwarp();
+  }
+}
+
 // Where one unit's clusters go: its event's staging slice (records allocated unit
 // by unit with one atomic each) and the unit's segment bookkeeping; the same for
 // its amplitudes when they are wanted (amp non-null).
@@ -430,22 +552,24 @@ struct SegOut {
   uint32_t* seg_amp_start = nullptr;  // their offset in the slice, or kNoAmp
 };
 
-// Clusters the `total` digis of one unit (placed in the tile by `fill(c0, c1)`,
-// channel chunk [c0, c1)) and stages its clusters.  The kept clusters are first
-// counted, then their region is allocated in one piece, then they are written; a
-// unit whose digis exceed the tile goes through its channel chunks twice.  Without
-// amplitudes, the records of the first 64 candidates (two per lane) are kept in
-// registers from the counting pass, so that only candidates beyond them are
-// formed twice (a work item of a full event has about 49).  s0: the work item's first strip in the per-strip
-// calibration tables; NCH: channels of the work item (12 or 24); AMP: amplitudes
-// are wanted (so.amp is then non-null).
-template <int NCH, bool AMP, typename Fill>
-__device__ void cluster_unit(Warp& w, const KParams& kp, size_t s0, uint32_t det0, uint32_t total,
-                             Fill& fill, const SegOut& so, sst_event_status* status) {
+// Clusters the `total` digis of one unit and stages its clusters.  `fill(c0, c1,
+// single)` prepares the tile for channel chunk [c0, c1) (single: the whole unit
+// fits one chunk) and `scan(nn, single)` runs scan_unit over its nn digis.  det0 is
+// the module id of the unit's first channel (its first channel in the calibration
+// tables).  The kept
+// clusters are first counted, then their region is allocated in one piece, then
+// they are written; a unit whose digis exceed the tile goes through its channel
+// chunks twice.  Without amplitudes, the records of the first 64 candidates (two
+// per lane) are kept in registers from the counting pass, so that only candidates
+// beyond them are formed twice (a work item of a full event has about 49).
+// NCH: channels of the work item (12 or 24); AMP: amplitudes are wanted (so.amp
+// is then non-null).
+template <int NCH, bool AMP, typename Fill, typename Scan>
+__device__ void cluster_unit(Warp& w, const KParams& kp, uint32_t det0, uint32_t total, Fill& fill, Scan& scan,
+                             const SegOut& so, sst_event_status* status) {
+  const uint32_t ch0 = det0;
   const int lane = threadIdx.x & 31;
   const bool single = total <= (uint32_t)kTile;
-  const float* noise = kp.noise + s0;
-  const uint8_t* gapmax = kp.gapmax + s0;
   constexpr bool amps = AMP;
   uint32_t found = 0, found0 = 0, found1 = 0, wsum = 0;
   int n = 0, n_own = 0;
@@ -455,8 +579,9 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, size_t s0, uint32_t det
   if (single) {
     n = (int)total;
     if (n > 0) {
-      fill(0, NCH);
-      n_own = scan_unit<NCH>(w, kp, noise, gapmax, n);
+      fill(0, NCH, true);
+      n_own = scan(n, true);
+      load_masks<NCH>(w, kp, ch0);
       if (n_own > 0) {
         if (amps) {
           found = form_unit<AMP>(w, kp, n, 0, n_own, det0, nullptr, 0, 0, nullptr, nullptr, &wsum);
@@ -470,12 +595,13 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, size_t s0, uint32_t det
       }
     }
   } else {
+    load_masks<NCH>(w, kp, ch0);
     for (int c0 = 0; c0 < NCH;) {
       const int c1 = chunk_end<NCH>(w, c0);
       const int nn = (int)(w.chan_cnt[c1] - w.chan_cnt[c0]);
       if (nn > 0) {
-        fill(c0, c1);
-        const int no = scan_unit<NCH>(w, kp, noise, gapmax, nn);
+        fill(c0, c1, false);
+        const int no = scan(nn, false);
         if (no > 0) found += form_unit<AMP>(w, kp, nn, 0, no, det0, nullptr, 0, 0, nullptr, nullptr, amps ? &wsum : nullptr);
       }
       c0 = c1;
@@ -527,29 +653,14 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, size_t s0, uint32_t det
       const int c1 = chunk_end<NCH>(w, c0);
       const int nn = (int)(w.chan_cnt[c1] - w.chan_cnt[c0]);
       if (nn > 0) {
-        fill(c0, c1);
-        const int no = scan_unit<NCH>(w, kp, noise, gapmax, nn);
+        fill(c0, c1, false);
+        const int no = scan(nn, false);
         if (no > 0)
           base += form_unit<AMP>(w, kp, nn, 0, no, det0, so.stage, so.cap, base, nullptr, nullptr, nullptr,
-                            amps ? &ap : nullptr);
+                                 amps ? &ap : nullptr);
       }
       c0 = c1;
     }
-  }
-}
-
-// Loads the bad-strip masks (8 words per channel) and APV gains (2 per channel)
-// of channels ch0 .. ch0 + NCH - 1 with 16-byte loads (both tables start on a
-// 16-byte boundary: ch0 is a multiple of 12).
-template <int NCH>
-__device__ __forceinline__ void load_calib(Warp& w, const KParams& kp, uint32_t ch0) {
-  const int lane = threadIdx.x & 31;
-  constexpr int kB = NCH * kMaskWords / 4, kG = NCH * 2 / 4;  // vectors of masks, of gains
-  for (int i = lane; i < kB + kG; i += 32) {
-    if (i < kB)
-      reinterpret_cast<uint4*>(w.bad)[i] = __ldg(reinterpret_cast<const uint4*>(kp.badmask + (size_t)ch0 * kMaskWords) + i);
-    else
-      reinterpret_cast<uint4*>(w.gain)[i - kB] = __ldg(reinterpret_cast<const uint4*>(kp.gain + (size_t)ch0 * 2) + (i - kB));
   }
 }
 
@@ -560,7 +671,7 @@ __device__ __forceinline__ void load_calib(Warp& w, const KParams& kp, uint32_t 
 // when they fit, else read in place.  g is the FED record.
 __device__ Unit locate(Warp& w, const uint8_t* g, uint2 dA, uint2 dB, uint32_t fed, uint32_t u) {
   const int lane = threadIdx.x & 31;
-  Unit r{fed, u, nullptr, 0, 0, 0, (uint8_t)((dA.y >> 16) & 255u)};
+  Unit r{fed, u, nullptr, 0, 0, 0, (uint8_t)((dA.y >> 16) & 255u), false};
   if (!(dA.y >> 24)) return r;
   r.len = dA.y & 0xFFFFu;
   r.len1 = dB.y & 0xFFFFu;
@@ -576,6 +687,7 @@ __device__ Unit locate(Warp& w, const uint8_t* g, uint2 dA, uint2 dB, uint32_t f
       for (uint32_t i = lane; i < span; i += 32) w.fe[i] = __ldg(a + i);
     }
     r.src = w.fe;
+    r.staged = true;
   } else {
     r.src = a;
   }
@@ -584,7 +696,12 @@ __device__ Unit locate(Warp& w, const uint8_t* g, uint2 dA, uint2 dB, uint32_t f
 }
 
 static_assert(8 * sizeof(Warp) + 1024 <= 233472 / 4, "8 warps per CTA must fit 4 CTAs per SM");
-static_assert(offsetof(Warp, bad) % 16 == 0 && offsetof(Warp, gain) % 16 == 0 && sizeof(Warp) % 16 == 0,
+static_assert(offsetof(Warp, bad) % 16 == 0 && offsetof(Warp, qmul) % 16 == 0 && sizeof(Warp) % 16 == 0,
               "vector calibration loads need 16-byte aligned tables");
+static_assert(offsetof(Warp, bad) == offsetof(Warp, own) + sizeof(uint16_t) * kTile && offsetof(Warp, own) % 4 == 0 &&
+                  kSlots * 4 <= sizeof(uint16_t) * kTile + sizeof(uint32_t) * kChW * kMaskWords,
+              "run slots live in own[] and bad[]");
+static_assert(kBuf % 8 == 0, "staging in 8-byte words");
+static_assert(kBuf < 2048, "ADC byte positions of a staged pair take 11 bits of a slot");
 
 }  // namespace fe

@@ -22,15 +22,22 @@ constexpr int kHdr = SST_FED_HEADER_BYTES;   // FED header bytes
 constexpr int kFedStrips = kCh * kStrips;    // 24,576 strips per FED
 constexpr int kMaskWords = kStrips / 32;     // 8 words of 32 strips per channel
 
-// Calibration and thresholds as the kernels see them.
+// Calibration and thresholds as the kernels see them.  The per-strip tables are
+// built on the device at calibration upload (k_calib_pack) from the noise, the
+// bad-strip flags and the parameters; the per-APV multipliers on the host.
 struct KParams {
-  float t_channel, t_seed, t_cluster;
+  float t_cluster;
   int max_holes, max_bad, max_adj;
-  const float* noise;       // [n_strips]
+  const uint32_t* cal;      // [n_strips]: thr_ch | thr_seed << 8 | gap << 16 (see k_calib_pack)
+  const float* nsq;         // [n_strips]: noise^2, binary32
   const uint32_t* badmask;  // [n_strips / 32], bit (s & 31) of word s / 32
-  const uint8_t* gapmax;    // [n_strips], longest gap below strip s that links, 255 for a bad strip (k_gapmax)
-  const float* gain;        // [n_strips / 128]
+  const float* qmul;        // [n_strips / 128]: per APV, a multiplier certified to give the
+                            // gain-corrected charge of every ADC 0..253, or -gain (divide)
 };
+
+// Words per FE unit in the channel map (k_chan_map): 12 channel words
+// (record offset in the FE unit | length << 16), the unit's status, padding.
+constexpr int kMapWords = 16;
 
 // Launch shape of the tile kernels.
 struct Shape {
@@ -51,6 +58,7 @@ struct Scratch {
   uint32_t* fed_start = nullptr;     // staging offset per work item, within its event's slice
   uint32_t* fed_dest = nullptr;      // output offset per work item, within its event's slice
   uint2* unit_desc = nullptr;        // per (event, FED, FE unit): offset in the FED record, length | status
+  uint32_t* chan_map = nullptr;      // per (event, FED, FE unit): kMapWords words (k_chan_map)
   size_t items_cap = 0;
   uint32_t* ev_alloc = nullptr;      // staging allocation counter per event
   size_t ev_cap = 0;
@@ -89,8 +97,8 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
                          const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st,
                          uint64_t* pack_off = nullptr, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st);
-cudaError_t build_gapmax(const uint32_t* mask_dev, uint8_t* gapmax_dev, uint64_t n_strips, int max_holes, int max_bad,
-                         cudaStream_t st);
+cudaError_t build_calib(const float* noise_dev, const uint32_t* mask_dev, uint32_t* cal_dev, float* nsq_dev,
+                        uint64_t n_strips, const sst_params& p, cudaStream_t st);
 
 }  // namespace sst
 
@@ -103,10 +111,10 @@ struct sst_ctx {
   int n_sm = 0;
   bool has_calib = false;
   sst_params params{};
-  float* noise = nullptr;
+  uint32_t* cal = nullptr;     // per strip: channel and seed thresholds as ADC limits, linking gap
+  float* nsq = nullptr;        // per strip: noise^2
   uint32_t* badmask = nullptr;
-  uint8_t* gapmax = nullptr;
-  float* gain = nullptr;
+  float* qmul = nullptr;       // per APV: certified multiplier or -gain
   sst::Scratch scratch;
   sst::Shape shape{};
   std::string err;

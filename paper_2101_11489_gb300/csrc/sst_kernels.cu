@@ -3,15 +3,16 @@
 // (section 3).
 //
 // Clustering work item: two adjacent FE units (24 channels) of one FED of one
-// event, handled by one warp end to end (sst_fe.cuh): the FE units' channel length
-// chains (the paper's "map of channel locations", here on the device), run
-// validation and counts (one lane per channel), expansion of the runs into an
-// on-chip digi tile sorted by strip (one lane per digi), thresholds (one lane per
-// digi), candidate boundaries, the leftmost seed of each candidate (warp ballots;
-// the paper's array of seed strips), and cluster forming (one lane per kept
-// candidate).  No block-wide barrier: a GB300 SM keeps 32 independent items in
-// flight.  The FED headers are checked once per FED by the prologue kernel
-// (k_fed_scan), which hands every FE unit its byte range.
+// event, handled by one warp end to end (sst_fe.cuh): run validation and counts
+// (one lane per channel, one walk), expansion of the runs into an on-chip digi
+// tile sorted by strip fused with thresholds, candidate boundaries and the
+// leftmost seed of each candidate (one lane per digi, warp ballots; the paper's
+// array of seed strips), and cluster forming (one lane per kept candidate).  No
+// block-wide barrier: a GB300 SM keeps 32 independent items in flight.  The FED
+// headers are checked once per FED by the prologue kernel (k_fed_scan), which
+// hands every FE unit its byte range; the FE units' channel length chains (the
+// paper's "map of channel locations", here on the device) are walked once per FE
+// unit by a second prologue kernel (k_chan_map), one thread per unit.
 //
 // Output order without device-side waits: every unit allocates an exact-size
 // staging region with one atomic per event; k_order prefix-sums the units' counts
@@ -48,7 +49,7 @@ constexpr int kLbSpinLimit = 1 << 20;              // polls before giving up (ab
 constexpr uint64_t kBadOff = ~0ull;                // fed_off marker: record outside the event
 constexpr int kFedBufMin = 16384;                  // bytes of FED record staged on chip (at least)
 constexpr int kFedScanThreads = 128;               // FEDs per k_fed_scan CTA
-constexpr uint32_t kGapBad = 255;                  // linking-gap table entry of a bad strip
+constexpr int kChanMapThreads = 256;               // FE units per k_chan_map CTA
 
 // Shared scalars.
 enum {
@@ -554,6 +555,62 @@ __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_
     status[e] = sst_event_status{0u, 0u, ev0 + pre + tot != ev1 ? SST_EV_SIZE : 0u, 0u};
 }
 
+// a1, FE-unit level: the map of channel locations.  One thread per FE unit (of
+// every FED of every event, unit x of FED record item = x / 8) walks the unit's
+// chain of 12 channel lengths from the unit descriptor k_fed_scan wrote and stores
+// kMapWords words: for channel k < 12, its record's offset in the FE unit | its
+// length << 16; word 12 the status of all 12 channels (the FED's status when the
+// FED holds no data, SST_CH_FRAMING when a length is below 3, runs past the unit
+// or the lengths do not add up to the unit's length, else 0).  A channel of a
+// unit with a nonzero status has length 0.
+__global__ void __launch_bounds__(kChanMapThreads) k_chan_map(const uint8_t* __restrict__ raw,
+                                                              const uint64_t* __restrict__ fed_off,
+                                                              const uint2* __restrict__ unit_desc, uint64_t n_units,
+                                                              uint32_t* __restrict__ cmap) {
+  pdl_release();
+  pdl_wait();  // the prologue's FED offsets and unit descriptors
+  const uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n_units) return;
+  const uint2 d = unit_desc[x];
+  const uint32_t end = d.y & 0xFFFFu;
+  uint32_t st = (d.y >> 16) & 255u;
+  uint32_t cw[kChPerFe];
+#pragma unroll
+  for (int k = 0; k < kChPerFe; k++) cw[k] = 0;
+  if (d.y >> 24) {  // the FED record holds data (st is 0 then)
+    const uint8_t* g = raw + fed_off[x / kFe] + d.x;
+    bool good = true;
+    uint32_t p = 0;
+#pragma unroll
+    for (int k = 0; k < kChPerFe; k++) {
+      if (good) {
+        if (p + 2 > end) {
+          good = false;
+        } else {
+          const uint32_t l = (uint32_t)__ldg(g + p) | ((uint32_t)__ldg(g + p + 1) << 8);
+          if (l < 3 || p + l > end) {
+            good = false;
+          } else {
+            cw[k] = p | (l << 16);
+            p += l;
+          }
+        }
+      }
+    }
+    if (good && p != end) good = false;
+    if (!good) {
+      st = SST_CH_FRAMING;
+#pragma unroll
+      for (int k = 0; k < kChPerFe; k++) cw[k] = 0;
+    }
+  }
+  uint4* o = reinterpret_cast<uint4*>(cmap + x * kMapWords);
+  o[0] = make_uint4(cw[0], cw[1], cw[2], cw[3]);
+  o[1] = make_uint4(cw[4], cw[5], cw[6], cw[7]);
+  o[2] = make_uint4(cw[8], cw[9], cw[10], cw[11]);
+  o[3] = make_uint4(st, 0u, 0u, 0u);
+}
+
 // a6, ordering: per event, the exclusive scan of its work items' cluster counts
 // gives every item's position in the event's sorted cluster SoA; the event's
 // total is its cluster count.  One CTA of 1024 threads per event (1,760 items of a
@@ -868,7 +925,7 @@ __global__ void __launch_bounds__(256, 4) k_cluster(sst_digis in, uint32_t n_fed
   if (lane == 0) w.chan_cnt[kChPerFe] = total;
   __syncwarp();
   const uint32_t g0 = ch0 * (uint32_t)kStrips;
-  auto fill = [&](int c0, int c1) {
+  auto fill = [&](int c0, int c1, bool) {
     for (int c = c0; c < c1; c++) {
       const uint32_t o = w.chan_cnt[c] - w.chan_cnt[c0];
       const uint32_t n = w.chan_cnt[c + 1] - w.chan_cnt[c];
@@ -889,7 +946,10 @@ __global__ void __launch_bounds__(256, 4) k_cluster(sst_digis in, uint32_t n_fed
     so.seg_amp_cnt = am.cnt + unit;
     so.seg_amp_start = am.start + unit;
   }
-  fe::cluster_unit<kChPerFe, AMP>(w, kp, (size_t)g0, ch0, total, fill, so, in.status);
+  const uint32_t* cal = kp.cal + g0;
+  const float* nsqt = kp.nsq + g0;
+  auto scan = [&](int nn, bool) { return fe::scan_unit<kChPerFe, false>(w, kp, cal, nsqt, nullptr, 0u, nn); };
+  fe::cluster_unit<kChPerFe, AMP>(w, kp, ch0, total, fill, scan, so, in.status);
 }
 
 // a7: every FE unit of every FED of every event of a batch, unpacked and
@@ -904,14 +964,15 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
                                                   uint64_t out_cap, sst_event_status* status, KParams kp,
                                                   uint4* stage, uint32_t* ev_alloc, uint32_t* seg_cnt,
                                                   uint32_t* seg_start, uint32_t* ticket,
-                                                  const uint2* __restrict__ unit_desc, AmpArgs am) {
+                                                  const uint2* __restrict__ unit_desc,
+                                                  const uint32_t* __restrict__ cmap, AmpArgs am) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   fe::Warp& w = reinterpret_cast<fe::Warp*>(smem_raw)[warp];
   constexpr uint32_t kItems = kFe / fe::kUnits;  // work items (FE-unit pairs) per FED
   const uint32_t per_fed = n_events * kItems;
   const uint32_t n_units = n_feds * per_fed;
-  pdl_wait();  // the prologue's tickets, offsets and unit descriptors
+  pdl_wait();  // the prologue's tickets, offsets, unit descriptors and channel map
   for (;;) {
     uint32_t t = 0;
     if (lane == 0) t = atomicAdd(ticket, 1u);
@@ -919,6 +980,8 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
     if (t >= n_units) break;
     const uint32_t f = t / per_fed, r = t % per_fed, e = r / kItems, p = r % kItems, u = p * fe::kUnits;
     const size_t item = (size_t)e * n_feds + f;
+    uint32_t mw, mst;
+    fe::map_words(cmap + (item * kFe + u) * kMapWords, &mw, &mst);
     const uint64_t fo = fed_off[item];
     const bool in_range = fo != kBadOff;
     const uint32_t ch0 = f * kCh + u * kChPerFe;
@@ -926,7 +989,7 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
     const fe::Unit un = fe::locate(w, raw + (in_range ? fo : 0), unit_desc[item * kFe + u],
                                    unit_desc[item * kFe + u + 1], f, u);
     uint32_t flags, nbad;
-    const uint32_t total = fe::parse_unit(w, un, &flags, &nbad);
+    const uint32_t total = fe::parse_unit(w, un, mw, mst, &flags, &nbad);
     if (lane == 0) {
       if (flags) atomicOr(&status[e].flags, flags);
       if (nbad) atomicAdd(&status[e].n_bad_channels, nbad);
@@ -946,8 +1009,16 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
       so.seg_amp_cnt = am.cnt + item * kItems + p;
       so.seg_amp_start = am.start + item * kItems + p;
     }
-    auto fill = [&](int c0, int c1) { fe::copy_runs(w, un, c0, c1); };
-    fe::cluster_unit<fe::kChW, AMP>(w, kp, (size_t)ch0 * kStrips, ch0, total, fill, so, &status[e]);
+    const bool slots = fe::use_slots(un);
+    auto fill = [&](int c0, int c1, bool single) {
+      if (single && slots) fe::mark_slots(w, un);
+      else fe::mark_walk(w, un, c0, c1);
+    };
+    const uint32_t* cal = kp.cal + (size_t)ch0 * kStrips;
+    const float* nsqt = kp.nsq + (size_t)ch0 * kStrips;
+    const uint32_t src_end = un.off1 + un.len1;
+    auto scan = [&](int nn, bool) { return fe::scan_unit<fe::kChW, true>(w, kp, cal, nsqt, un.src, src_end, nn); };
+    fe::cluster_unit<fe::kChW, AMP>(w, kp, ch0, total, fill, scan, so, &status[e]);
     __syncwarp();
   }
   pdl_release();
@@ -961,20 +1032,32 @@ __global__ void k_badmask(const uint8_t* __restrict__ bad, uint32_t* __restrict_
   mask[w] = m;
 }
 
-// Longest gap below every strip that still links two successive active strips of
-// a channel (section 2: a candidate continues over at most max_seq_holes
-// consecutive inactive good strips and at most max_seq_bad consecutive bad
-// strips): G(t) is the largest g such that, among strips t-g .. t-1, every maximal
+// The per-strip calibration word the clusterizers read, built once per upload:
+//   bits 0-7   thr_ch:   channel limit, the largest ADC that is NOT active;
+//   bits 8-15  thr_seed: seed limit, the largest ADC that is NOT a seed;
+//   bits 16-23 gap:      the longest linking gap below the strip;
+// and noise^2 per strip (binary32, rounded once), summed by the cluster threshold.
+//
+// Limits (section 2: a strip is active / a seed when its ADC is larger than the
+// channel / seed threshold times its noise): with P = T x noise rounded once in
+// binary32 (P >= 0), an integer ADC satisfies (float)adc > P exactly when adc >
+// floor(P), since every ADC is exactly representable; so the limit is floor(P),
+// capped at 255 (no 8-bit ADC exceeds it).  A bad strip is never active nor a
+// seed: both limits are 255.
+//
+// Linking gap (a candidate continues over at most max_seq_holes consecutive
+// inactive good strips and at most max_seq_bad consecutive bad strips): G(t) is
+// the largest g such that, among strips t-g .. t-1 of the channel, every maximal
 // run of bad strips is at most max_bad long and every maximal run of good strips
 // at most max_holes long.  The strips between successive active strips a < t are
-// all inactive, so they are linked exactly when their gap t-a-1 is at most G(t):
-// a gap that is valid stays valid when shortened from below, and one longer than
-// G(t) contains the strip t-G(t)-1 that breaks a limit.  One thread per strip
-// walks down from t-1.  A gap is at most 254 strips (a >= 0, t <= 255), so G(t) is
-// stored capped at 254 without changing any decision, and the entry of a bad strip
-// (never active) is 255: the clusterizer reads both facts from one byte.
-__global__ void k_gapmax(const uint32_t* __restrict__ mask, uint8_t* __restrict__ gapmax, uint64_t n_strips,
-                         int max_holes, int max_bad) {
+// all inactive, so they are linked exactly when their gap t-a-1 is at most G(t): a
+// gap that is valid stays valid when shortened from below, and one longer than
+// G(t) contains the strip t-G(t)-1 that breaks a limit.  One thread per strip walks
+// down from t-1.  A gap is at most 254 strips (a >= 0, t <= 255), so G(t) is
+// stored capped at 254 without changing any decision.
+__global__ void k_calib_pack(const float* __restrict__ noise, const uint32_t* __restrict__ mask,
+                             uint32_t* __restrict__ cal, float* __restrict__ nsq, uint64_t n_strips, float t_ch,
+                             float t_seed, int max_holes, int max_bad) {
   const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_strips) return;
   const int t = (int)(s % kStrips);
@@ -988,7 +1071,14 @@ __global__ void k_gapmax(const uint32_t* __restrict__ mask, uint8_t* __restrict_
     ++g;
   }
   const bool bad = (m[t >> 5] >> (t & 31)) & 1u;
-  gapmax[s] = bad ? (uint8_t)kGapBad : (uint8_t)(g < 254 ? g : 254);
+  const float nz = noise[s];
+  auto limit = [&](float thr) -> uint32_t {
+    const float p = __fmul_rn(thr, nz);
+    return p >= 255.f ? 255u : (uint32_t)p;  // truncation = floor for p >= 0
+  };
+  const uint32_t gap = (uint32_t)(g < 254 ? g : 254);
+  cal[s] = bad ? (255u | (255u << 8) | (gap << 16)) : (limit(t_ch) | (limit(t_seed) << 8) | (gap << 16));
+  nsq[s] = __fmul_rn(nz, nz);
 }
 
 // ---------------------------------------------------------------- launch helpers
@@ -1123,10 +1213,11 @@ cudaError_t launch_batch_fe(const uint8_t* raw, const uint32_t* fed_len, uint32_
   if (am.stage)
     k_batch<true><<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out_cap, status, kp,
                                               s.stage, s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets, s.unit_desc,
-                                              am);
+                                              s.chan_map, am);
   else if ((e = launch_pdl(k_batch<false>, (unsigned)grid, (unsigned)sh.block, sm, st, raw, fed_len,
                            (const uint64_t*)s.fed_off, n_events, n_feds, clu_off, out_cap, status, kp, s.stage,
-                           s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets, (const uint2*)s.unit_desc, am)))
+                           s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets, (const uint2*)s.unit_desc,
+                           (const uint32_t*)s.chan_map, am)))
     return e;
   if ((e = cudaGetLastError())) return e;
   if (ev_end && (e = cudaEventRecord(ev_end, st))) return e;
@@ -1225,6 +1316,11 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
       event_off, 0, fed_len, n_feds, cpe, s.fed_off, status, s.ev_alloc, s.tickets, nullptr, 0, raw, s.unit_desc,
       am.stage ? s.amp_alloc : nullptr);
   if ((e = cudaGetLastError())) return e;
+  const uint64_t n_units = (uint64_t)n_events * n_feds * kFe;
+  if ((e = launch_pdl(k_chan_map, (unsigned)((n_units + kChanMapThreads - 1) / kChanMapThreads),
+                      (unsigned)kChanMapThreads, 0, st, raw, (const uint64_t*)s.fed_off, (const uint2*)s.unit_desc,
+                      n_units, s.chan_map)))
+    return e;
   e = launch_batch_fe(raw, fed_len, n_events, n_feds, clu_off, out.capacity, status, kp, s, sh, n_sm, am, st,
                       ev_begin, ev_end);
   if (e) return e;
@@ -1237,9 +1333,11 @@ cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n
   return cudaGetLastError();
 }
 
-cudaError_t build_gapmax(const uint32_t* mask_dev, uint8_t* gapmax_dev, uint64_t n_strips, int max_holes, int max_bad,
-                         cudaStream_t st) {
-  k_gapmax<<<(unsigned)((n_strips + 255) / 256), 256, 0, st>>>(mask_dev, gapmax_dev, n_strips, max_holes, max_bad);
+cudaError_t build_calib(const float* noise_dev, const uint32_t* mask_dev, uint32_t* cal_dev, float* nsq_dev,
+                        uint64_t n_strips, const sst_params& p, cudaStream_t st) {
+  k_calib_pack<<<(unsigned)((n_strips + 255) / 256), 256, 0, st>>>(noise_dev, mask_dev, cal_dev, nsq_dev, n_strips,
+                                                                   p.t_channel, p.t_seed, p.max_seq_holes,
+                                                                   p.max_seq_bad);
   return cudaGetLastError();
 }
 
