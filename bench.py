@@ -343,14 +343,29 @@ def kernel_source_sha256():
 
 
 def algorithmic_bytes(events, n_digi, n_clusters):
-    """Bytes the batched kernel must move, per the path's dataflow: FED payload read
-    once, noise (4 B) and longest linking gap (1 B) of every recorded strip, the
-    256-bit bad-strip mask (32 B) and two APV gains (8 B) of every channel, fed_len /
-    fed_off (12 B) per FED, the cluster SoA (16 B per cluster) and one 16-byte status
-    per event."""
+    """Bytes the path must move per launch, counted as the fused form of the method
+    needs them (payload + the calibration of the recorded strips + the clusters):
+    every FED payload byte read once; for every recorded strip (digi) its noise
+    (4 B) and its bad-strip bit; the gains of every APV (4 B, two APVs per
+    channel); fed_len and fed_off (4 + 8 B) per FED; one 16-byte cluster record
+    per cluster; a 16-byte status per event."""
     payload = sum(int(e[0].size) for e in events)
     n_feds = sum(int(e[1].size) for e in events)
-    return payload + 5 * n_digi + n_feds * 96 * (32 + 8) + 12 * n_feds + 16 * n_clusters + 16 * len(events)
+    return payload + 4 * n_digi + n_digi / 8 + n_feds * 96 * 2 * 4 + 12 * n_feds + 16 * n_clusters + 16 * len(events)
+
+
+def kernel_bytes(events, n_digi, n_clusters):
+    """Bytes the batched kernel's own dataflow touches per launch (a finer model
+    than algorithmic_bytes, for comparison with the measured DRAM traffic): the
+    payload, the per-strip calibration word and noise^2 of every recorded strip (4
+    + 4 B), the APV multipliers (8 B per channel), the channel map (64 B per FE
+    unit, written by the prologue and read), the unit descriptors and FED offsets
+    (8 B per FE unit, 8 B per FED), the staged cluster records (16 B per cluster)
+    and the event status."""
+    payload = sum(int(e[0].size) for e in events)
+    n_feds = sum(int(e[1].size) for e in events)
+    return (payload + 8 * n_digi + n_feds * 96 * 8 + n_feds * 8 * (2 * 64 + 8) + 12 * n_feds + 16 * n_clusters
+            + 16 * len(events))
 
 
 # ---------------------------------------------------------------- main
@@ -362,7 +377,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sst", choices=["sst", "reference"])
     ap.add_argument("--workload", default="batch64", choices=sorted(WORKLOADS))
-    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch knobs: no stored tune, no sweep")
+    ap.add_argument("--retune", action="store_true", help="run the autotuner even when a stored tune exists")
+    ap.add_argument("--tune-file", default=None,
+                    help="JSON file of the workload's tune (default: paper_2101_11489_gb300/tune/<workload>.json)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--served-events", type=int, default=10000, help="events per served-stream point (0: skip)")
     ap.add_argument("--cpu-sweep", action="store_true",
@@ -418,9 +436,26 @@ def main():
     st_d = torch.zeros(n_events * 4, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
+    # launch knobs of the batched kernel: the stored tune of this workload, else the
+    # autotuner's pick (then stored)
     tune = sst.sst_get_tune(ctx)
-    if not args.no_autotune:
-        tune, _ = sst.sst_autotune(ctx, raw, eoff_d, fl_d, n_events, w.n_feds, coff_d, crec, st_d)
+    tune_src = "default"
+    tune_file = args.tune_file or os.path.join(ROOT, "paper_2101_11489_gb300", "tune", f"{args.workload}.json")
+    stored = None if args.retune else sst.load_tune(tune_file, args.workload)
+    if stored is not None and not args.no_autotune:
+        sst.sst_set_tune(ctx, **stored)
+        tune, tune_src = stored, f"stored ({os.path.relpath(tune_file, ROOT)})"
+    elif not args.no_autotune:
+        tune, tune_us = sst.sst_autotune(ctx, raw, eoff_d, fl_d, n_events, w.n_feds, coff_d, crec, st_d)
+        tune_src = "autotuned in this run"
+        try:
+            os.makedirs(os.path.dirname(tune_file), exist_ok=True)
+            sst.save_tune(tune, tune_file, args.workload,
+                          {"us_per_launch_sequence": round(tune_us, 1),
+                           "gpu": torch.cuda.get_device_name(dev)})
+        except OSError:
+            pass
+    launch = sst.sst_get_launch_info(ctx, n_events, w.n_feds)
 
     def step():
         sst.sst_batch(ctx, raw, eoff_d, fl_d, n_events, w.n_feds, coff_d, crec, st_d)
@@ -605,6 +640,7 @@ def main():
     # ---- roofline of the dominant kernel (the batched kernel)
     peak, peak_kind = measured_peaks()
     b_alg = algorithmic_bytes(events, n_digi, n_clu)
+    b_kern = kernel_bytes(events, n_digi, n_clu)
     achieved = b_alg / (k_ms / 1e3) / 1e9
     tr = kernel_traffic()
     traffic = None
@@ -652,7 +688,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {w.name}", "events_per_step": n_events, "n_feds": w.n_feds,
                        "strips_per_event": w.n_feds * 96 * 256, "l2": "flushed: 512 MiB write before every step",
-                       "tune": tune, "digis_per_step": n_digi, "clusters_per_step": n_clu,
+                       "tune": tune, "tune_source": tune_src, "launch": launch, "digis_per_step": n_digi, "clusters_per_step": n_clu,
                        "payload_bytes_per_step": int(sizes.sum()), "status_flags": flags,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "strips_per_s": round(total_events * w.n_feds * 96 * 256 / (ms_per_step / 1e3), 1),
@@ -676,6 +712,13 @@ def main():
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "kernel": "k_batch", "kernels_per_step": 3, "kernel_ms": round(k_ms, 4), "algorithmic_bytes": int(b_alg),
+                         "bytes_definition": "payload + 4 B noise and a bad-strip bit per recorded strip + APV "
+                                             "gains + fed_len/fed_off + 16 B per cluster + 16 B status per event",
+                         "traffic_model": {"bytes": int(b_kern), "achieved": round(b_kern / (k_ms / 1e3) / 1e9, 1),
+                                           "frac": round(b_kern / (k_ms / 1e3) / 1e9 / peak, 4),
+                                           "what": "the kernel's own dataflow: calibration word and noise^2 per "
+                                                   "recorded strip, APV multipliers, channel map, unit "
+                                                   "descriptors, staged cluster records"},
                          "peak_kind": peak_kind, "issue": issue},
             "served": served,
             "cpu_baseline": cpu,

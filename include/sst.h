@@ -335,26 +335,56 @@ sst_status sst_pitch_upload(sst_ctx* ctx, const float* pitch);
 sst_status sst_local_x(sst_ctx* ctx, const uint32_t* det, const float* barycenter, uint64_t n, float* x,
                        void* stream);
 
-/* Launch-shape knobs of the batched kernel (picked by sst_autotune). */
+/* Launch knobs (section 3: the paper tunes the number of events processed
+ * concurrently; here the batched kernel's launch shape and work-item width and
+ * the host path's batch depth are picked by measurement, sst_autotune and
+ * sst_autotune_host). */
 typedef struct {
-  uint32_t block;       /* threads per CTA: 128 or 256 */
-  uint32_t ctas_per_sm; /* persistent CTAs per SM: 1..8 (clamped to what fits) */
-  uint32_t tile_digis;  /* digis per on-chip tile: 1024, 2048 or 4096 */
-  uint32_t lanes_per_channel; /* lanes that copy one channel's runs: 1, 2, 4, 8, 16 or 32 */
-  uint32_t host_chunk_events; /* events per pipeline chunk of sst_batch_host, 0..4096;
-                                 0 = automatic (a quarter of the batch, at most 32) */
+  uint32_t block;             /* batched kernel: threads per CTA, 128 or 256 */
+  uint32_t ctas_per_sm;       /* batched kernel: persistent CTAs per SM, 1..8 (clamped to what fits) */
+  uint32_t units_per_warp;    /* batched kernel: FE units per warp work item, 1 or 2 (12 or 24 channels) */
+  uint32_t host_chunk_events; /* sst_batch_host: events per pipeline chunk (the batch depth of each
+                                 launch), 0..4096; 0 = automatic (a quarter of the batch, at most 32) */
+  uint32_t tile_digis;        /* per-event unpack (sst_unpack): digis per on-chip tile, 1024, 2048 or 4096 */
+  uint32_t lanes_per_channel; /* per-event unpack: lanes that copy one channel's runs: 1, 2, 4, 8, 16 or 32 */
 } sst_tune;
 
+/* Sets / reads the context's knobs.  INVALID_ARG for a value outside its range. */
 sst_status sst_set_tune(sst_ctx* ctx, const sst_tune* t);
 sst_status sst_get_tune(const sst_ctx* ctx, sst_tune* t);
 
-/* Times every candidate launch shape of sst_batch on the given batch (same
- * arguments as sst_batch; the outputs are overwritten), keeps the fastest in the
- * context and returns it in *best with its time per launch in *best_us.
+/* Times every candidate shape of the batched kernel on the given batch (same
+ * arguments as sst_batch; the outputs are overwritten): block 128 / 256 x work
+ * items of 1 / 2 FE units x 2..8 CTAs per SM (shapes that cannot be resident, or
+ * that the occupancy clamps to a shape already timed, are skipped).  Each shape
+ * runs one untimed and two timed launch sequences.  Keeps the fastest in the
+ * context and returns it in *best with its time per launch sequence in *best_us.
  * Synchronises the stream. */
 sst_status sst_autotune(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len,
                         uint32_t n_events, uint32_t n_feds, const uint64_t* clu_off, const sst_clusters* out,
                         sst_event_status* status, void* stream, sst_tune* best, float* best_us);
+
+/* Times sst_batch_host on the given HOST batch (same arguments; outputs are
+ * overwritten) for events per chunk of 0 (automatic), 4, 8, 16, 32, 64 and 128
+ * (those not above n_events), two calls each after one untimed call, keeps the
+ * fastest in the context's host_chunk_events and returns it with its wall time
+ * per call in microseconds.  Synchronous. */
+sst_status sst_autotune_host(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len,
+                             uint32_t n_events, uint32_t n_feds, const sst_clusters* out, uint64_t* event_first,
+                             sst_event_status* status, uint32_t* best_chunk, float* best_us);
+
+/* What the context's knobs make of a batch of n_events x n_feds: the batched
+ * kernel's grid (CTAs), threads per CTA, dynamic shared memory per CTA and work
+ * items per FED, and the number of chunks sst_batch_host cuts the batch into.
+ * Any output pointer may be NULL.  CUDA if the occupancy look-up fails. */
+typedef struct {
+  uint32_t grid;
+  uint32_t block;
+  uint32_t smem_bytes;
+  uint32_t items_per_fed;
+  uint32_t host_chunks;
+} sst_launch_info;
+sst_status sst_get_launch_info(sst_ctx* ctx, uint32_t n_events, uint32_t n_feds, sst_launch_info* info);
 
 /* ---- kernel timing ------------------------------------------------------------
  * When enabled, the context brackets every launch of its batched kernel (the one
@@ -365,6 +395,19 @@ sst_status sst_profile_enable(sst_ctx* ctx, int enable);
 /* Waits for the recorded launches, returns their number and summed device time
  * in milliseconds, and (reset != 0) forgets them. */
 sst_status sst_profile_read(sst_ctx* ctx, uint64_t* launches, double* total_ms, int reset);
+
+/* ---- failure detection ----------------------------------------------------------
+ * The per-event unpacker places each FED's digis after a device-side look-back over
+ * the FEDs before it (section 2: the channel map, here built on the device).  Every
+ * such wait gives up after a bounded number of polls (about a second by default),
+ * flags the event SST_EV_TIMEOUT and lets the kernel finish; the event's output is
+ * then invalid, but no access leaves its buffers.  For tests of that path:
+ * spin_limit sets the polls (1 .. 2^20; 0 = the default) and withhold_fed >= 0
+ * makes the FED of that index never publish its digi count, so that the FEDs after
+ * it run out of polls; withhold_fed = -1 restores normal operation.  Nothing faults,
+ * traps or waits without end.  INVALID_ARG for spin_limit above 2^20 or
+ * withhold_fed below -1. */
+sst_status sst_testing_set_wait(sst_ctx* ctx, uint32_t spin_limit, int32_t withhold_fed);
 
 /* ---- served path: continuous batching ------------------------------------------ */
 

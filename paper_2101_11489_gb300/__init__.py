@@ -80,8 +80,14 @@ class sst_clusters(ctypes.Structure):
 
 
 class sst_tune(ctypes.Structure):
-    _fields_ = [("block", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("tile_digis", ctypes.c_uint32),
-                ("lanes_per_channel", ctypes.c_uint32), ("host_chunk_events", ctypes.c_uint32)]
+    _fields_ = [("block", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("units_per_warp", ctypes.c_uint32),
+                ("host_chunk_events", ctypes.c_uint32), ("tile_digis", ctypes.c_uint32),
+                ("lanes_per_channel", ctypes.c_uint32)]
+
+
+class sst_launch_info(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_uint32), ("block", ctypes.c_uint32), ("smem_bytes", ctypes.c_uint32),
+                ("items_per_fed", ctypes.c_uint32), ("host_chunks", ctypes.c_uint32)]
 
 
 class sst_server_opts(ctypes.Structure):
@@ -124,7 +130,10 @@ def load_library():
         "sst_set_tune": ([vp, P(sst_tune)], i32),
         "sst_get_tune": ([vp, P(sst_tune)], i32),
         "sst_autotune": ([vp, vp, vp, vp, u32, u32, vp, P(sst_clusters), vp, vp, P(sst_tune), P(ctypes.c_float)], i32),
+        "sst_autotune_host": ([vp, vp, vp, vp, u32, u32, P(sst_clusters), vp, vp, P(u32), P(ctypes.c_float)], i32),
+        "sst_get_launch_info": ([vp, u32, u32, P(sst_launch_info)], i32),
         "sst_profile_enable": ([vp, ctypes.c_int], i32),
+        "sst_testing_set_wait": ([vp, u32, ctypes.c_int32], i32),
         "sst_profile_read": ([vp, P(u64), P(ctypes.c_double), ctypes.c_int], i32),
         "sst_server_start": ([vp, P(sst_server_opts)], i32),
         "sst_server_stop": ([vp], i32),
@@ -142,7 +151,7 @@ def load_library():
 def exported_symbols() -> list[str]:
     return ["sst_create", "sst_destroy", "sst_last_error", "sst_calib_upload", "sst_unpack", "sst_unpack_noalloc",
             "sst_cluster",
-            "sst_batch", "sst_batch_host", "sst_batch_host_submit", "sst_batch_host_wait", "sst_pitch_upload", "sst_local_x", "sst_set_tune", "sst_get_tune", "sst_autotune", "sst_profile_enable", "sst_profile_read",
+            "sst_batch", "sst_batch_host", "sst_batch_host_submit", "sst_batch_host_wait", "sst_pitch_upload", "sst_local_x", "sst_set_tune", "sst_get_tune", "sst_autotune", "sst_autotune_host", "sst_get_launch_info", "sst_profile_enable", "sst_profile_read", "sst_testing_set_wait",
             "sst_server_start", "sst_server_stop",
             "sst_submit", "sst_poll"]
 
@@ -278,29 +287,90 @@ def sst_local_x(ctx: int, det, barycenter, n: int, x, stream=None) -> None:
            "sst_local_x")
 
 
-def sst_set_tune(ctx: int, block: int, ctas_per_sm: int, tile_digis: int, lanes_per_channel: int,
-                 host_chunk_events: int = 0) -> None:
-    t = sst_tune(block, ctas_per_sm, tile_digis, lanes_per_channel, host_chunk_events)
+TUNE_KEYS = ("block", "ctas_per_sm", "units_per_warp", "host_chunk_events", "tile_digis", "lanes_per_channel")
+
+
+def _tune_dict(t: sst_tune) -> dict:
+    return {k: int(getattr(t, k)) for k in TUNE_KEYS}
+
+
+def sst_set_tune(ctx: int, **knobs) -> None:
+    """Sets the given knobs (names as in sst_tune); the others keep their values."""
+    cur = sst_get_tune(ctx)
+    unknown = set(knobs) - set(TUNE_KEYS)
+    if unknown:
+        raise TypeError(f"unknown tune knobs {sorted(unknown)}")
+    cur.update(knobs)
+    t = sst_tune(*[cur[k] for k in TUNE_KEYS])
     _check(ctx, load_library().sst_set_tune(ctx, ctypes.byref(t)), "sst_set_tune")
 
 
 def sst_get_tune(ctx: int) -> dict:
     t = sst_tune()
     _check(ctx, load_library().sst_get_tune(ctx, ctypes.byref(t)), "sst_get_tune")
-    return {"block": t.block, "ctas_per_sm": t.ctas_per_sm, "tile_digis": t.tile_digis,
-            "lanes_per_channel": t.lanes_per_channel, "host_chunk_events": t.host_chunk_events}
+    return _tune_dict(t)
 
 
 def sst_autotune(ctx: int, raw, event_off, fed_len, n_events: int, n_feds: int, clu_off, clusters: sst_clusters,
                  status, stream=None) -> tuple[dict, float]:
+    """Times the batched kernel's launch shapes on this batch; keeps and returns the fastest and its time (us)."""
     t = sst_tune()
     us = ctypes.c_float()
     code = load_library().sst_autotune(ctx, _dp(raw), _dp(event_off), _dp(fed_len), n_events, n_feds,
                                        _dp(clu_off), ctypes.byref(clusters), _dp(status), _stream(stream),
                                        ctypes.byref(t), ctypes.byref(us))
     _check(ctx, code, "sst_autotune")
-    return {"block": t.block, "ctas_per_sm": t.ctas_per_sm, "tile_digis": t.tile_digis,
-            "lanes_per_channel": t.lanes_per_channel, "host_chunk_events": t.host_chunk_events}, us.value
+    return _tune_dict(t), us.value
+
+
+def sst_autotune_host(ctx: int, raw: np.ndarray, event_off: np.ndarray, fed_len: np.ndarray, n_events: int,
+                      n_feds: int, clusters: "HostClusters", event_first: np.ndarray, status: np.ndarray
+                      ) -> tuple[int, float]:
+    """Times sst_batch_host over events per chunk on this host batch; keeps and returns the fastest chunk
+    size and its wall time per call (us)."""
+    best = ctypes.c_uint32()
+    us = ctypes.c_float()
+    code = load_library().sst_autotune_host(ctx, _hp(raw), _hp(event_off), _hp(fed_len), n_events, n_feds,
+                                            ctypes.byref(clusters.record()), _hp(event_first), _hp(status),
+                                            ctypes.byref(best), ctypes.byref(us))
+    _check(ctx, code, "sst_autotune_host")
+    return best.value, us.value
+
+
+def sst_get_launch_info(ctx: int, n_events: int, n_feds: int) -> dict:
+    """The batched kernel's grid, block, shared memory per CTA, work items per FED, and the host path's chunk
+    count for a batch of this size under the context's knobs."""
+    info = sst_launch_info()
+    _check(ctx, load_library().sst_get_launch_info(ctx, n_events, n_feds, ctypes.byref(info)), "sst_get_launch_info")
+    return {k: int(getattr(info, k)) for k, _ in sst_launch_info._fields_}
+
+
+def save_tune(tune: dict, path: str, workload: str, extra: dict | None = None) -> None:
+    """Writes a tune (as sst_get_tune returns it) for a workload to a JSON file."""
+    import json
+    rec = {"workload": workload, "tune": {k: int(tune[k]) for k in TUNE_KEYS}}
+    if extra:
+        rec.update(extra)
+    with open(path, "w") as f:
+        json.dump(rec, f, indent=1)
+
+
+def load_tune(path: str, workload: str) -> dict | None:
+    """The tune stored for `workload` in a JSON file written by save_tune, or None."""
+    import json
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if rec.get("workload") != workload or set(rec.get("tune", {})) != set(TUNE_KEYS):
+        return None
+    return {k: int(rec["tune"][k]) for k in TUNE_KEYS}
+
+
+def sst_testing_set_wait(ctx: int, spin_limit: int = 0, withhold_fed: int = -1) -> None:
+    """Failure tests: polls before a look-back wait gives up (0: default) and a FED
+    that never publishes its count (-1: none)."""
+    _check(ctx, load_library().sst_testing_set_wait(ctx, spin_limit, withhold_fed), "sst_testing_set_wait")
 
 
 def sst_profile_enable(ctx: int, enable: bool = True) -> None:

@@ -1,6 +1,7 @@
 // sst_api.cu -- host side of the C ABI declared in include/sst.h: contexts,
 // calibration upload (arXiv 2101.11489 section 2: noise and gain per strip, here
 // plus the bad-strip list), argument checks and kernel launches.
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -95,14 +96,13 @@ cudaError_t ensure_scratch(Scratch& s, size_t items, size_t events, size_t stage
     if ((e = cudaDeviceSynchronize())) return e;
     if (items > s.items_cap) {
       size_t cap = s.items_cap, c2 = s.items_cap, c3 = s.items_cap, c4 = s.items_cap, c5 = s.items_cap;
-      size_t c6 = s.items_cap, c7 = s.items_cap * kMapWords;
+      size_t c6 = s.items_cap;
       if ((e = grow(s.lb, cap, items))) return e;
       if ((e = grow(s.fed_off, c2, items))) return e;
       if ((e = grow(s.fed_cnt, c3, items))) return e;
       if ((e = grow(s.fed_start, c4, items))) return e;
       if ((e = grow(s.fed_dest, c5, items))) return e;
       if ((e = grow(s.unit_desc, c6, items))) return e;
-      if ((e = grow(s.chan_map, c7, items * kMapWords))) return e;
       s.items_cap = items;
     }
     if ((e = grow(s.ev_alloc, s.ev_cap, events))) return e;
@@ -136,7 +136,6 @@ void free_scratch(Scratch& s) {
   if (s.fed_start) cudaFree(s.fed_start);
   if (s.fed_dest) cudaFree(s.fed_dest);
   if (s.unit_desc) cudaFree(s.unit_desc);
-  if (s.chan_map) cudaFree(s.chan_map);
   if (s.ev_alloc) cudaFree(s.ev_alloc);
   if (s.stage) cudaFree(s.stage);
   if (s.tickets) cudaFree(s.tickets);
@@ -338,6 +337,15 @@ sst_status sst_batch(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off
   return cuda_err(ctx, e, "sst_batch");
 }
 
+sst_status sst_testing_set_wait(sst_ctx* ctx, uint32_t spin_limit, int32_t withhold_fed) {
+  if (!ctx) return SST_ERR_INVALID_ARG;
+  if (spin_limit > (1u << 20) || withhold_fed < -1)
+    return set_err(ctx, SST_ERR_INVALID_ARG, "sst_testing_set_wait: spin_limit above 2^20 or withhold_fed below -1");
+  ctx->scratch.lb_spin_limit = spin_limit;
+  ctx->scratch.lb_withhold = withhold_fed;
+  return SST_OK;
+}
+
 sst_status sst_profile_enable(sst_ctx* ctx, int enable) {
   if (!ctx) return SST_ERR_INVALID_ARG;
   ctx->profiling = enable != 0;
@@ -368,7 +376,7 @@ sst_status sst_set_tune(sst_ctx* ctx, const sst_tune* t) {
   if (!ctx || !t) return SST_ERR_INVALID_ARG;
   if (t->host_chunk_events > 4096u) return set_err(ctx, SST_ERR_INVALID_ARG, "sst_set_tune: host_chunk_events > 4096");
   Shape s{(int)t->block, (int)t->tile_digis, (int)t->lanes_per_channel, (int)t->ctas_per_sm,
-          (int)t->host_chunk_events};
+          (int)t->host_chunk_events, (int)t->units_per_warp};
   if (!shape_valid(s)) return set_err(ctx, SST_ERR_INVALID_ARG, "sst_set_tune: unsupported launch shape");
   ctx->shape = s;
   return SST_OK;
@@ -377,10 +385,26 @@ sst_status sst_set_tune(sst_ctx* ctx, const sst_tune* t) {
 sst_status sst_get_tune(const sst_ctx* ctx, sst_tune* t) {
   if (!ctx || !t) return SST_ERR_INVALID_ARG;
   t->block = (uint32_t)ctx->shape.block;
+  t->ctas_per_sm = (uint32_t)ctx->shape.ctas_per_sm;
+  t->units_per_warp = (uint32_t)ctx->shape.units;
+  t->host_chunk_events = (uint32_t)ctx->shape.host_chunk;
   t->tile_digis = (uint32_t)ctx->shape.tile;
   t->lanes_per_channel = (uint32_t)ctx->shape.lanes;
-  t->ctas_per_sm = (uint32_t)ctx->shape.ctas_per_sm;
-  t->host_chunk_events = (uint32_t)ctx->shape.host_chunk;
+  return SST_OK;
+}
+
+sst_status sst_get_launch_info(sst_ctx* ctx, uint32_t n_events, uint32_t n_feds, sst_launch_info* info) {
+  if (!ctx || !info || n_events == 0 || n_feds == 0) return SST_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  int grid = 0, ipf = 0;
+  size_t smem = 0;
+  const cudaError_t e = batch_launch_info(ctx->shape, n_events, n_feds, ctx->n_sm, &grid, &smem, &ipf);
+  if (e) return cuda_err(ctx, e, "sst_get_launch_info");
+  info->grid = (uint32_t)grid;
+  info->block = (uint32_t)ctx->shape.block;
+  info->smem_bytes = (uint32_t)smem;
+  info->items_per_fed = (uint32_t)ipf;
+  info->host_chunks = host_chunks(n_events, ctx->shape.host_chunk);
   return SST_OK;
 }
 
@@ -401,37 +425,46 @@ sst_status sst_autotune(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_
     return cuda_err(ctx, cudaGetLastError(), "autotune event");
   }
   const int blocks[] = {128, 256};
-  const int tiles[] = {1024, 2048, 4096};
-  const int lanes[] = {1, 2, 4, 8};
+  const int widths[] = {1, 2};
   const int per_sm[] = {2, 3, 4, 6, 8};
   float best_t = 1e30f;
   Shape best_s = keep;
+  std::vector<std::pair<int, Shape>> timed;  // (effective grid, shape) already measured
   cudaError_t ce = cudaSuccess;
   for (int b : blocks)
-    for (int t : tiles)
-      for (int l : lanes)
-        for (int p : per_sm) {
-          Shape s{b, t, l, p, ctx->shape.host_chunk};
-          if (!shape_valid(s) || smem_bytes(t) * (size_t)p > 227u * 1024u) continue;
-          ctx->shape = s;
-          float ms_total = 0.f;
-          for (int rep = 0; rep < 3 && ce == cudaSuccess; rep++) {
-            ce = cudaEventRecord(e0, st);
-            if (!ce) ce = launch_batch(raw, event_off, fed_len, n_events, n_feds, clu_off, *out, status,
-                                       kparams(ctx), ctx->scratch, s, ctx->n_sm, st);
-            if (!ce) ce = cudaEventRecord(e1, st);
-            if (!ce) ce = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (!ce) ce = cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) ms_total += ms;  // first launch is a warm-up
-          }
-          if (ce != cudaSuccess) break;
-          const float us = ms_total * 1000.f / 2.f;
-          if (us < best_t) {
-            best_t = us;
-            best_s = s;
-          }
+    for (int u : widths)
+      for (int p : per_sm) {
+        Shape s = keep;
+        s.block = b;
+        s.units = u;
+        s.ctas_per_sm = p;
+        if (!shape_valid(s) || batch_smem(u, b) * (size_t)p > 227u * 1024u) continue;
+        int grid = 0, ipf = 0;
+        size_t smem = 0;
+        if ((ce = batch_launch_info(s, n_events, n_feds, ctx->n_sm, &grid, &smem, &ipf))) break;
+        bool dup = false;  // the occupancy clamps p: the same launch was timed already
+        for (auto& pr : timed)
+          if (pr.first == grid && pr.second.block == b && pr.second.units == u) dup = true;
+        if (dup) continue;
+        timed.emplace_back(grid, s);
+        float ms_total = 0.f;
+        for (int rep = 0; rep < 3 && ce == cudaSuccess; rep++) {
+          ce = cudaEventRecord(e0, st);
+          if (!ce) ce = launch_batch(raw, event_off, fed_len, n_events, n_feds, clu_off, *out, status, kparams(ctx),
+                                     ctx->scratch, s, ctx->n_sm, st);
+          if (!ce) ce = cudaEventRecord(e1, st);
+          if (!ce) ce = cudaEventSynchronize(e1);
+          float ms = 0.f;
+          if (!ce) ce = cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0) ms_total += ms;  // the first launch is a warm-up
         }
+        if (ce != cudaSuccess) break;
+        const float us = ms_total * 1000.f / 2.f;
+        if (us < best_t) {
+          best_t = us;
+          best_s = s;
+        }
+      }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (ce != cudaSuccess) {
@@ -441,6 +474,41 @@ sst_status sst_autotune(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_
   ctx->shape = best_s;
   if (best) sst_get_tune(ctx, best);
   if (best_us) *best_us = best_t;
+  return SST_OK;
+}
+
+sst_status sst_autotune_host(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len,
+                             uint32_t n_events, uint32_t n_feds, const sst_clusters* out, uint64_t* event_first,
+                             sst_event_status* status, uint32_t* best_chunk, float* best_us) {
+  if (!ctx) return SST_ERR_INVALID_ARG;
+  const int keep = ctx->shape.host_chunk;
+  sst_status r = sst_batch_host(ctx, raw, event_off, fed_len, n_events, n_feds, out, event_first, status);
+  if (r != SST_OK) return r;
+  const int chunks[] = {0, 4, 8, 16, 32, 64, 128};
+  double best_t = 1e30;
+  int best_c = keep;
+  for (int c : chunks) {
+    if ((uint32_t)c > n_events) continue;
+    ctx->shape.host_chunk = c;
+    r = sst_batch_host(ctx, raw, event_off, fed_len, n_events, n_feds, out, event_first, status);  // untimed
+    double total = 0;
+    for (int rep = 0; rep < 2 && r == SST_OK; rep++) {
+      const auto t0 = std::chrono::steady_clock::now();
+      r = sst_batch_host(ctx, raw, event_off, fed_len, n_events, n_feds, out, event_first, status);
+      total += std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (r != SST_OK) {
+      ctx->shape.host_chunk = keep;
+      return r;
+    }
+    if (total / 2 < best_t) {
+      best_t = total / 2;
+      best_c = c;
+    }
+  }
+  ctx->shape.host_chunk = best_c;
+  if (best_chunk) *best_chunk = (uint32_t)best_c;
+  if (best_us) *best_us = (float)best_t;
   return SST_OK;
 }
 

@@ -12,7 +12,8 @@
 // instead of 12, and the fixed cost of an item is paid once per pair.
 //
 // Phases of an item (batched kernel):
-//   parse_unit  one lane per channel walks the channel's runs once: validates them,
+//   parse_unit  one lane per FE unit walks the unit's 12 channel lengths; then one
+//               lane per channel walks the channel's runs once: validates them,
 //               counts digis and, for a staged pair, leaves a descriptor of every
 //               run in a slot indexed by the byte position of its header / 3
 //               (headers are at least 3 bytes apart, so slots never collide and
@@ -34,21 +35,21 @@
 
 namespace fe {
 
-// Tile and staging sizes share the shared memory that 8 warps of a CTA may use at
-// 4 CTAs per SM: a larger tile sends fewer work items through the chunked
-// (two-pass) path, a larger staging buffer fewer through in-place global reads.
-constexpr int kTile = 448;    // digis per warp tile (a chunk of whole channels)
-constexpr int kBuf = 1376;    // bytes of the two FE units staged per warp (larger pairs are read in place)
-constexpr int kUnits = 2;     // FE units per work item: two adjacent units of one FED
-constexpr int kChW = kUnits * kChPerFe;  // 24 consecutive channels per work item
-constexpr int kSlots = (kTile * 2 + kChW * kMaskWords * 4) / 4;  // run-header slots (byte position / 3) in own[] + bad[]
-constexpr int kRsWords = kTile / 32;     // run-start bits of the tile
-static_assert(kTile % 32 == 0, "whole windows of 32 digis");
-
-// Per-warp shared memory.
-struct __align__(16) Warp {
-  uint8_t fe[kBuf];                      // staged bytes of the two FE units
-  float qmul[kChW * 2];                  // per APV of the 24 channels: certified multiplier, or -gain
+// Per-warp shared memory of a work item of U adjacent FE units (U = 1 or 2; the
+// work-item width is a launch knob of the batched kernel).  Tile and staging sizes
+// share the shared memory that 8 warps of a CTA may use at 4 CTAs per SM: a larger
+// tile sends fewer work items through the chunked (two-pass) path, a larger
+// staging buffer fewer through in-place global reads.
+template <int U>
+struct __align__(16) WarpT {
+  static constexpr int kUnits = U;                  // FE units per work item
+  static constexpr int kChW = U * kChPerFe;         // consecutive channels per work item
+  static constexpr int kTile = U == 2 ? 448 : 256;  // digis per warp tile (a chunk of whole channels)
+  static constexpr int kBuf = U == 2 ? 1376 : 704;  // bytes of the units staged per warp (larger ones are read in place)
+  static constexpr int kRsWords = kTile / 32;       // run-start bits of the tile
+  static constexpr int kSlots = (kTile * 2 + kChW * kMaskWords * 4) / 4;  // run-header slots in own[] + bad[]
+  uint8_t fe[kBuf];                      // staged bytes of the FE units
+  float qmul[kChW * 2];                  // per APV of the channels: certified multiplier, or -gain
   uint32_t kf[kTile];   // before scan_unit: run descriptors at run starts (ADC byte position << 13 | first
                         // strip << 5 | channel) or, without run starts, key | ADC << 16 per digi; after: one
                         // word per digi: key (channel in the work item << 8 | strip, 13 bits; sorted) |
@@ -56,13 +57,15 @@ struct __align__(16) Warp {
                         // gain-corrected charge of active digis << 24
   float nsq[kTile];     // noise^2 of each digi
   uint16_t own[kTile];  // first digi of every seeded candidate (run slots, with bad[], until scan_unit)
-  uint32_t bad[kChW * kMaskWords];       // bad-strip masks of the 24 channels (only when max_adj > 0)
+  uint32_t bad[kChW * kMaskWords];       // bad-strip masks of the channels (only when max_adj > 0)
   uint32_t chan_pos[kChW];               // channel record offset from the first unit's start
   uint32_t chan_cnt[kChW + 1];           // digis per channel, then exclusive prefix
   uint16_t chan_len[kChW];
   uint8_t chan_st[kChW];
   uint32_t rs[kRsWords];                 // run-start bits of the tile
+  static_assert(kTile % 32 == 0, "whole windows of 32 digis");
 };
+using Warp = WarpT<2>;  // the per-event cluster kernel's warp (it uses 12 of the 24 channels)
 
 __device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
 
@@ -92,8 +95,10 @@ struct Unit {
 
 // Slots of a staged pair (one per 3 bytes), and whether they fit the slot area.
 __device__ __forceinline__ uint32_t n_slots(const Unit& un) { return (un.off1 + un.len1 + 2u) / 3u; }
-__device__ __forceinline__ bool use_slots(const Unit& un) { return un.staged && n_slots(un) <= (uint32_t)kSlots; }
-__device__ __forceinline__ uint32_t* slot_area(Warp& w) { return reinterpret_cast<uint32_t*>(w.own); }
+template <class W>
+__device__ __forceinline__ bool use_slots(const Unit& un) { return un.staged && n_slots(un) <= (uint32_t)W::kSlots; }
+template <class W>
+__device__ __forceinline__ uint32_t* slot_area(W& w) { return reinterpret_cast<uint32_t*>(w.own); }
 
 // Run descriptor in a slot: ADC byte position (11 bits) << 21 | first strip << 13 |
 // channel << 8 | digis of the channel before the run.  Never 0: the ADC bytes of a
@@ -137,79 +142,82 @@ __device__ __forceinline__ uint32_t walk_runs(const uint8_t* r, uint32_t len, ui
   return cnt;
 }
 
-// a1 + a2 for the two FE units.  The channel map (k_chan_map: each channel
-// record's offset and length from the FE unit's length chain, and the unit's
-// status; loaded by the caller as mw / mst, see map_words) gives every lane 0..23
-// its channel; the lane validates the channel's
-// runs and counts its digis in one walk and, when the pair is staged and its slots
-// fit, writes a slot descriptor for every valid run.  The counts are prefix-summed into
-// chan_cnt.  Returns the digi count; *flags / *nbad receive the OR of the channel
-// statuses and the number of bad channels.
-__device__ uint32_t parse_unit(Warp& w, const Unit& un, uint32_t mw, uint32_t mst, uint32_t* flags,
-                               uint32_t* nbad) {
+// a1 + a2 for the work item's FE units.  Lane 16 h (h < U) walks unit h's chain of
+// 12 channel lengths (the paper's map of channel locations): each length at
+// least 3, within the unit, and all of them adding up to the unit's length;
+// otherwise all 12 channels get SST_CH_FRAMING.  Then lane c < 12 U validates
+// channel c's runs and counts its digis in one walk and, when the units are
+// staged and their slots fit, writes a slot descriptor for every valid run.  The
+// counts are prefix-summed into chan_cnt.  Returns the digi count; *flags / *nbad
+// receive the OR of the channel statuses and the number of bad channels.
+template <class W>
+__device__ uint32_t parse_unit(W& w, const Unit& un, uint32_t* flags, uint32_t* nbad) {
   const int lane = threadIdx.x & 31;
   uint32_t* slots = slot_area(w);
-  const bool sl = use_slots(un);
+  const bool sl = use_slots<W>(un);
   if (sl) {
     const uint32_t ns = n_slots(un);
     for (uint32_t i = lane; i < ns; i += 32) slots[i] = 0u;
   }
-  uint32_t cnt = 0, pos = 0, len = 0;
-  uint8_t st = 0;
-  if (lane < kChW) {
-    const int h = lane >= kChPerFe ? 1 : 0;
-    st = (uint8_t)mst;
-    pos = (h ? un.off1 : 0u) + (mw & 0xFFFFu);
-    len = un.src ? (mw >> 16) : 0u;
-    w.chan_pos[lane] = pos;
-    w.chan_len[lane] = (uint16_t)len;
+  if ((lane & 15) == 0 && (lane >> 4) < W::kUnits) {
+    const int h = lane >> 4;
+    const uint32_t base = h ? un.off1 : 0u;
+    const uint32_t end = h ? un.len1 : un.len;
+    bool good = un.src != nullptr;
+    uint32_t p = 0;
+    for (int k = 0; k < kChPerFe; k++) {
+      uint32_t l = 0;
+      if (good) {
+        if (p + 2 > end) {
+          good = false;
+        } else {
+          l = (uint32_t)un.src[base + p] | ((uint32_t)un.src[base + p + 1] << 8);
+          if (l < 3 || p + l > end) good = false;
+        }
+      }
+      w.chan_pos[h * kChPerFe + k] = good ? base + p : 0u;
+      w.chan_len[h * kChPerFe + k] = good ? (uint16_t)l : (uint16_t)0;
+      if (good) p += l;
+    }
+    if (good && p != end) good = false;
+    const uint8_t st = un.src == nullptr ? un.fed_status : (good ? (uint8_t)0 : (uint8_t)SST_CH_FRAMING);
+    for (int k = 0; k < kChPerFe; k++) w.chan_st[h * kChPerFe + k] = st;
   }
   __syncwarp();
-  if (lane < kChW && st == 0 && len >= 3) {
-    const uint8_t* r = un.src + pos;
-    if (r[2] != SST_ZS_CODE)
-      st = SST_CH_BAD_CODE;
-    else if (sl)
-      cnt = walk_runs<true>(r, len, pos, (uint32_t)lane, slots, &st);
-    else
-      cnt = walk_runs<false>(r, len, pos, (uint32_t)lane, slots, &st);
+  uint32_t cnt = 0;
+  uint8_t st = 0;
+  if (lane < W::kChW) {
+    st = w.chan_st[lane];
+    const uint32_t len = st ? 0u : w.chan_len[lane];
+    if (st == 0 && len >= 3) {
+      const uint32_t pos = w.chan_pos[lane];
+      const uint8_t* r = un.src + pos;
+      if (r[2] != SST_ZS_CODE)
+        st = SST_CH_BAD_CODE;
+      else if (sl)
+        cnt = walk_runs<true>(r, len, pos, (uint32_t)lane, slots, &st);
+      else
+        cnt = walk_runs<false>(r, len, pos, (uint32_t)lane, slots, &st);
+    }
+    w.chan_st[lane] = st;
+    if (st) w.chan_len[lane] = 0;
   }
-  if (lane < kChW) w.chan_st[lane] = st;
-  if (lane < kRsWords) w.rs[lane] = 0u;
-  uint32_t x = cnt;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-    if (lane >= d) x += y;
-  }
-  if (lane < kChW) w.chan_cnt[lane] = x - cnt;
-  const uint32_t total = __shfl_sync(0xffffffffu, x, kChW - 1);
-  if (lane == 0) w.chan_cnt[kChW] = total;
-  *flags = __reduce_or_sync(0xffffffffu, lane < kChW ? (uint32_t)st : 0u);
-  *nbad = __popc(__ballot_sync(0xffffffffu, lane < kChW && st != 0));
+  if (lane < W::kRsWords) w.rs[lane] = 0u;
+  uint32_t total = 0;
+  const uint32_t x = warp_excl_sum(cnt, &total);
+  if (lane < W::kChW) w.chan_cnt[lane] = x;
+  if (lane == 0) w.chan_cnt[W::kChW] = total;
+  *flags = __reduce_or_sync(0xffffffffu, lane < W::kChW ? (uint32_t)st : 0u);
+  *nbad = __popc(__ballot_sync(0xffffffffu, lane < W::kChW && st != 0));
   __syncwarp();
   return total;
 }
 
-// Lane l < 24's channel-map words of the pair whose first unit's map is cmap: the
-// channel word (record offset in its FE unit | length << 16) and the unit status.
-__device__ __forceinline__ void map_words(const uint32_t* __restrict__ cmap, uint32_t* mw, uint32_t* mst) {
-  const int lane = threadIdx.x & 31;
-  *mw = 0;
-  *mst = 0;
-  if (lane < kChW) {
-    const int h = lane >= kChPerFe ? 1 : 0;
-    const uint32_t* m = cmap + h * kMapWords;
-    *mw = __ldg(m + (lane - h * kChPerFe));
-    *mst = __ldg(m + kChPerFe);
-  }
-}
-
-// Greedy chunk of whole channels [c0, c1) with at most kTile digis.
-template <int NCH>
-__device__ __forceinline__ int chunk_end(const Warp& w, int c0) {
+// Greedy chunk of whole channels [c0, c1) with at most W::kTile digis.
+template <int NCH, class W>
+__device__ __forceinline__ int chunk_end(const W& w, int c0) {
   int c1 = c0 + 1;
-  while (c1 < NCH && w.chan_cnt[c1 + 1] - w.chan_cnt[c0] <= (uint32_t)kTile) ++c1;
+  while (c1 < NCH && w.chan_cnt[c1 + 1] - w.chan_cnt[c0] <= (uint32_t)W::kTile) ++c1;
   return c1;
 }
 
@@ -226,7 +234,8 @@ __device__ __forceinline__ uint32_t tile_desc(uint32_t adc_pos, uint32_t first, 
 // Single-chunk pair with slots (a2): every valid run's slot descriptor goes to the
 // tile position of its first digi (channel base + digis of the channel before it),
 // with its run-start bit.  A run of a channel found invalid was cleared.
-__device__ void mark_slots(Warp& w, const Unit& un) {
+template <class W>
+__device__ void mark_slots(W& w, const Unit& un) {
   const int lane = threadIdx.x & 31;
   const uint32_t* slots = slot_area(w);
   const int ns = (int)n_slots(un);
@@ -246,9 +255,10 @@ __device__ void mark_slots(Warp& w, const Unit& un) {
 // channel's runs again (validated by parse_unit) and write each run's tile
 // descriptor and run-start bit; the walk is bounded by the counted digis, so that
 // it cannot leave the tile.
-__device__ void mark_walk(Warp& w, const Unit& un, int c0, int c1) {
+template <class W>
+__device__ void mark_walk(W& w, const Unit& un, int c0, int c1) {
   const int lane = threadIdx.x & 31;
-  if (lane < kRsWords) w.rs[lane] = 0u;
+  if (lane < W::kRsWords) w.rs[lane] = 0u;
   __syncwarp();
   const int c = c0 + lane;
   if (c < c1) {
@@ -296,8 +306,8 @@ __device__ void mark_walk(Warp& w, const Unit& un, int c0, int c1) {
 //    a seed's candidate start and it.
 // The first digis of owned candidates are compacted in strip order into own[];
 // returns their number.  src / src_end: the pair's bytes (EXP).
-template <int NCH, bool EXP>
-__device__ int scan_unit(Warp& w, const KParams& kp, const uint32_t* __restrict__ cal,
+template <int NCH, bool EXP, class W>
+__device__ int scan_unit(W& w, const KParams& kp, const uint32_t* __restrict__ cal,
                          const float* __restrict__ nsqt, const uint8_t* src, uint32_t src_end, int n) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt(lane);
@@ -428,8 +438,8 @@ struct AmpPos {
 // `wsum`, the kept clusters' widths are added to it; with `ap` (write pass), the
 // kept clusters' amplitudes are written at ap->pos onwards: 0 for every strip of
 // the cluster, then the gain-corrected charge of its active strips.
-template <bool AMP>
-__device__ uint32_t form_unit(Warp& w, const KParams& kp, int n, int k_begin, int n_own, uint32_t det0, uint4* stage,
+template <bool AMP, class W>
+__device__ uint32_t form_unit(W& w, const KParams& kp, int n, int k_begin, int n_own, uint32_t det0, uint4* stage,
                               uint64_t cap, uint64_t base, uint4* keep = nullptr, bool* keep_pass = nullptr,
                               uint32_t* wsum = nullptr, AmpPos* ap = nullptr) {
   const int lane = threadIdx.x & 31;
@@ -512,8 +522,8 @@ __device__ uint32_t form_unit(Warp& w, const KParams& kp, int n, int k_begin, in
 
 // Loads the APV multipliers (2 per channel) of channels ch0 .. ch0 + NCH - 1 with
 // 16-byte loads (the table starts on a 16-byte boundary: ch0 is a multiple of 12).
-template <int NCH>
-__device__ __forceinline__ void load_calib(Warp& w, const KParams& kp, uint32_t ch0) {
+template <int NCH, class W>
+__device__ __forceinline__ void load_calib(W& w, const KParams& kp, uint32_t ch0) {
   const int lane = threadIdx.x & 31;
   constexpr int kG = NCH * 2 / 4;  // vectors of multipliers
   static_assert(kG <= 32, "one multiplier vector per lane");
@@ -525,8 +535,8 @@ __device__ __forceinline__ void load_calib(Warp& w, const KParams& kp, uint32_t 
 // widening over bad strips is enabled (max_adj > 0); otherwise no cluster is
 // widened and the masks are never read.  Called once the run slots, which share
 // their space, are no longer needed.
-template <int NCH>
-__device__ __forceinline__ void load_masks(Warp& w, const KParams& kp, uint32_t ch0) {
+template <int NCH, class W>
+__device__ __forceinline__ void load_masks(W& w, const KParams& kp, uint32_t ch0) {
   const int lane = threadIdx.x & 31;
   constexpr int kB = NCH * kMaskWords / 4;  // vectors of masks
   if (kp.max_adj > 0) {
@@ -564,12 +574,12 @@ struct SegOut {
 // beyond them are formed twice (a work item of a full event has about 49).
 // NCH: channels of the work item (12 or 24); AMP: amplitudes are wanted (so.amp
 // is then non-null).
-template <int NCH, bool AMP, typename Fill, typename Scan>
-__device__ void cluster_unit(Warp& w, const KParams& kp, uint32_t det0, uint32_t total, Fill& fill, Scan& scan,
+template <int NCH, bool AMP, class W, typename Fill, typename Scan>
+__device__ void cluster_unit(W& w, const KParams& kp, uint32_t det0, uint32_t total, Fill& fill, Scan& scan,
                              const SegOut& so, sst_event_status* status) {
   const uint32_t ch0 = det0;
   const int lane = threadIdx.x & 31;
-  const bool single = total <= (uint32_t)kTile;
+  const bool single = total <= (uint32_t)W::kTile;
   constexpr bool amps = AMP;
   uint32_t found = 0, found0 = 0, found1 = 0, wsum = 0;
   int n = 0, n_own = 0;
@@ -664,21 +674,28 @@ __device__ void cluster_unit(Warp& w, const KParams& kp, uint32_t det0, uint32_t
   }
 }
 
-// FE units u and u + 1 of FED `fed` as described by dA and dB (k_fed_scan checked
+// FE units u and u + 1 (only u when the work item has one unit; dB is then unused)
+// of FED `fed` as described by dA and dB (k_fed_scan checked
 // the FED header and wrote, per FE unit, its byte offset in the FED record, its
 // length, the FED's status and whether the record holds data).  The units' bytes
 // (the first unit, its padding, the second unit) are staged in the warp's buffer
 // when they fit, else read in place.  g is the FED record.
-__device__ Unit locate(Warp& w, const uint8_t* g, uint2 dA, uint2 dB, uint32_t fed, uint32_t u) {
+template <class W>
+__device__ Unit locate(W& w, const uint8_t* g, uint2 dA, uint2 dB, uint32_t fed, uint32_t u) {
   const int lane = threadIdx.x & 31;
   Unit r{fed, u, nullptr, 0, 0, 0, (uint8_t)((dA.y >> 16) & 255u), false};
   if (!(dA.y >> 24)) return r;
   r.len = dA.y & 0xFFFFu;
-  r.len1 = dB.y & 0xFFFFu;
-  r.off1 = dB.x - dA.x;
+  if (W::kUnits == 2) {
+    r.len1 = dB.y & 0xFFFFu;
+    r.off1 = dB.x - dA.x;
+  } else {  // one unit: no second unit, span = its length
+    r.len1 = 0;
+    r.off1 = r.len;
+  }
   const uint32_t span = r.off1 + r.len1;
   const uint8_t* a = g + dA.x;
-  if (span <= (uint32_t)kBuf) {
+  if (span <= (uint32_t)W::kBuf) {
     if ((((uintptr_t)a) & 7u) == 0) {
       const uint32_t nv = (span + 7u) >> 3;  // whole 8-byte words; padding bytes exist up to the next 8
       for (uint32_t i = lane; i < nv; i += 32)
@@ -695,13 +712,14 @@ __device__ Unit locate(Warp& w, const uint8_t* g, uint2 dA, uint2 dB, uint32_t f
   return r;
 }
 
-static_assert(8 * sizeof(Warp) + 1024 <= 233472 / 4, "8 warps per CTA must fit 4 CTAs per SM");
-static_assert(offsetof(Warp, bad) % 16 == 0 && offsetof(Warp, qmul) % 16 == 0 && sizeof(Warp) % 16 == 0,
-              "vector calibration loads need 16-byte aligned tables");
-static_assert(offsetof(Warp, bad) == offsetof(Warp, own) + sizeof(uint16_t) * kTile && offsetof(Warp, own) % 4 == 0 &&
-                  kSlots * 4 <= sizeof(uint16_t) * kTile + sizeof(uint32_t) * kChW * kMaskWords,
-              "run slots live in own[] and bad[]");
-static_assert(kBuf % 8 == 0, "staging in 8-byte words");
-static_assert(kBuf < 2048, "ADC byte positions of a staged pair take 11 bits of a slot");
+template <class W>
+constexpr bool layout_ok() {
+  return 8 * sizeof(W) + 1024 <= 233472 / 4 &&  // 8 warps per CTA fit 4 CTAs per SM
+         offsetof(W, bad) % 16 == 0 && offsetof(W, qmul) % 16 == 0 && sizeof(W) % 16 == 0 &&  // vector loads
+         offsetof(W, bad) == offsetof(W, own) + sizeof(uint16_t) * W::kTile && offsetof(W, own) % 4 == 0 &&
+         W::kSlots * 4 <= sizeof(uint16_t) * W::kTile + sizeof(uint32_t) * W::kChW * kMaskWords &&  // slots
+         W::kBuf % 8 == 0 && W::kBuf < 2048;  // staging in 8-byte words; ADC positions take 11 bits of a slot
+}
+static_assert(layout_ok<WarpT<1>>() && layout_ok<WarpT<2>>(), "per-warp shared memory layout");
 
 }  // namespace fe

@@ -459,6 +459,10 @@ void pipe_main(sst_host_pipe* p) {
 
 }  // namespace
 
+namespace sst {
+uint32_t host_chunks(uint32_t n_events, int tuned) { return (uint32_t)plan_chunks(n_events, tuned).size() - 1; }
+}  // namespace sst
+
 using namespace sst;
 
 extern "C" {

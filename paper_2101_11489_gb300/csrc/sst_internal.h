@@ -35,17 +35,15 @@ struct KParams {
                             // gain-corrected charge of every ADC 0..253, or -gain (divide)
 };
 
-// Words per FE unit in the channel map (k_chan_map): 12 channel words
-// (record offset in the FE unit | length << 16), the unit's status, padding.
-constexpr int kMapWords = 16;
 
-// Launch shape of the tile kernels.
+// Launch shape of the kernels.
 struct Shape {
-  int block;        // threads per CTA
-  int tile;         // digis per on-chip tile
-  int lanes;        // lanes per channel when copying runs
-  int ctas_per_sm;  // persistent CTAs per SM (batched kernel)
+  int block;        // batched kernel: threads per CTA
+  int tile;         // per-event unpack kernel: digis per on-chip tile
+  int lanes;        // per-event unpack kernel: lanes per channel when copying runs
+  int ctas_per_sm;  // batched kernel: persistent CTAs per SM
   int host_chunk = 0;  // events per chunk of sst_batch_host (0: automatic)
+  int units = 2;       // batched kernel: FE units per warp work item (1 or 2)
 };
 
 // Device scratch for one stream of work, owned by a context (or by one server
@@ -58,13 +56,14 @@ struct Scratch {
   uint32_t* fed_start = nullptr;     // staging offset per work item, within its event's slice
   uint32_t* fed_dest = nullptr;      // output offset per work item, within its event's slice
   uint2* unit_desc = nullptr;        // per (event, FED, FE unit): offset in the FED record, length | status
-  uint32_t* chan_map = nullptr;      // per (event, FED, FE unit): kMapWords words (k_chan_map)
   size_t items_cap = 0;
   uint32_t* ev_alloc = nullptr;      // staging allocation counter per event
   size_t ev_cap = 0;
   uint4* stage = nullptr;            // staged cluster records (16 bytes each)
   size_t stage_cap = 0;
   uint32_t* tickets = nullptr;       // [16] work counters
+  uint32_t lb_spin_limit = 0;        // polls before a look-back wait gives up (0: the default, about a second)
+  int32_t lb_withhold = -1;          // failure tests: the FED that never publishes its count (-1: none)
   // optional cluster amplitudes
   uint8_t* amp_stage = nullptr;      // staged amplitudes, sliced per event like the output
   size_t amp_stage_cap = 0;
@@ -77,6 +76,13 @@ struct Scratch {
 constexpr uint32_t kNoAmp = 0xFFFFFFFFu;
 
 size_t smem_bytes(int tile);
+size_t batch_smem(int units, int block);  // shared memory per CTA of the batched kernel
+// Grid, shared memory per CTA and work items per FED of the batched kernel's
+// launch for a shape and batch (the occupancy look-up may call the driver once).
+cudaError_t batch_launch_info(const Shape& sh, uint32_t n_events, uint32_t n_feds, int n_sm, int* grid, size_t* smem,
+                              int* items_per_fed);
+// Chunks sst_batch_host cuts a batch of n_events into (tuned: events per chunk, 0 = automatic).
+uint32_t host_chunks(uint32_t n_events, int tuned);
 Shape default_shape();
 bool shape_valid(const Shape& s);
 

@@ -2,17 +2,17 @@
 // three-threshold clustering (arXiv 2101.11489, section 2), per event and batched
 // (section 3).
 //
-// Clustering work item: two adjacent FE units (24 channels) of one FED of one
-// event, handled by one warp end to end (sst_fe.cuh): run validation and counts
-// (one lane per channel, one walk), expansion of the runs into an on-chip digi
+// Clustering work item: two adjacent FE units (24 channels; one unit as a launch
+// option) of one FED of one event, handled by one warp end to end (sst_fe.cuh):
+// run validation and counts (one lane per channel, one walk), expansion of the runs into an on-chip digi
 // tile sorted by strip fused with thresholds, candidate boundaries and the
 // leftmost seed of each candidate (one lane per digi, warp ballots; the paper's
 // array of seed strips), and cluster forming (one lane per kept candidate).  No
 // block-wide barrier: a GB300 SM keeps 32 independent items in flight.  The FED
 // headers are checked once per FED by the prologue kernel (k_fed_scan), which
 // hands every FE unit its byte range; the FE units' channel length chains (the
-// paper's "map of channel locations", here on the device) are walked once per FE
-// unit by a second prologue kernel (k_chan_map), one thread per unit.
+// paper's "map of channel locations", here on the device) are walked from the
+// staged bytes by the warp that owns the units.
 //
 // Output order without device-side waits: every unit allocates an exact-size
 // staging region with one atomic per event; k_order prefix-sums the units' counts
@@ -45,11 +45,10 @@ namespace {
 constexpr unsigned long long kLbAgg = 1ull << 62;  // state carries this FED's own count
 constexpr unsigned long long kLbPre = 2ull << 62;  // state carries the inclusive prefix
 constexpr unsigned long long kLbMask = 3ull << 62;
-constexpr int kLbSpinLimit = 1 << 20;              // polls before giving up (about a second)
+constexpr uint32_t kLbSpinLimit = 1u << 20;         // polls before giving up (about a second)
 constexpr uint64_t kBadOff = ~0ull;                // fed_off marker: record outside the event
 constexpr int kFedBufMin = 16384;                  // bytes of FED record staged on chip (at least)
 constexpr int kFedScanThreads = 128;               // FEDs per k_fed_scan CTA
-constexpr int kChanMapThreads = 256;               // FE units per k_chan_map CTA
 
 // Shared scalars.
 enum {
@@ -168,11 +167,14 @@ __device__ __forceinline__ uint32_t warp_scan96(uint32_t* a, int lane) {
 // Decoupled look-back over items lo .. idx-1 of one event, by one warp: each
 // round reads 32 predecessors at once and sums back to the nearest inclusive
 // prefix.  Returns the sum of the counts of all earlier items (on every lane).
-__device__ uint32_t lookback_warp(unsigned long long* lb, long long idx, long long lo, bool* timed_out) {
+// After spin_limit polls without progress it gives up: *timed_out is set and the
+// partial sum is returned.
+__device__ uint32_t lookback_warp(unsigned long long* lb, long long idx, long long lo, uint32_t spin_limit,
+                              bool* timed_out) {
   const int lane = threadIdx.x & 31;
   uint32_t excl = 0;
   long long j = idx - 1;
-  int spins = 0;
+  uint32_t spins = 0;
   unsigned ns = 32;
   while (j >= lo) {
     const long long jj = j - lane;
@@ -182,7 +184,7 @@ __device__ uint32_t lookback_warp(unsigned long long* lb, long long idx, long lo
     const int stop = pre ? __ffs(pre) - 1 : 31;
     const unsigned need = stop == 31 ? 0xffffffffu : ((2u << stop) - 1u);
     if ((rdy & need) != need) {
-      if (++spins > kLbSpinLimit) {
+      if (++spins > spin_limit) {
         *timed_out = true;
         return excl;
       }
@@ -555,62 +557,6 @@ __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_
     status[e] = sst_event_status{0u, 0u, ev0 + pre + tot != ev1 ? SST_EV_SIZE : 0u, 0u};
 }
 
-// a1, FE-unit level: the map of channel locations.  One thread per FE unit (of
-// every FED of every event, unit x of FED record item = x / 8) walks the unit's
-// chain of 12 channel lengths from the unit descriptor k_fed_scan wrote and stores
-// kMapWords words: for channel k < 12, its record's offset in the FE unit | its
-// length << 16; word 12 the status of all 12 channels (the FED's status when the
-// FED holds no data, SST_CH_FRAMING when a length is below 3, runs past the unit
-// or the lengths do not add up to the unit's length, else 0).  A channel of a
-// unit with a nonzero status has length 0.
-__global__ void __launch_bounds__(kChanMapThreads) k_chan_map(const uint8_t* __restrict__ raw,
-                                                              const uint64_t* __restrict__ fed_off,
-                                                              const uint2* __restrict__ unit_desc, uint64_t n_units,
-                                                              uint32_t* __restrict__ cmap) {
-  pdl_release();
-  pdl_wait();  // the prologue's FED offsets and unit descriptors
-  const uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= n_units) return;
-  const uint2 d = unit_desc[x];
-  const uint32_t end = d.y & 0xFFFFu;
-  uint32_t st = (d.y >> 16) & 255u;
-  uint32_t cw[kChPerFe];
-#pragma unroll
-  for (int k = 0; k < kChPerFe; k++) cw[k] = 0;
-  if (d.y >> 24) {  // the FED record holds data (st is 0 then)
-    const uint8_t* g = raw + fed_off[x / kFe] + d.x;
-    bool good = true;
-    uint32_t p = 0;
-#pragma unroll
-    for (int k = 0; k < kChPerFe; k++) {
-      if (good) {
-        if (p + 2 > end) {
-          good = false;
-        } else {
-          const uint32_t l = (uint32_t)__ldg(g + p) | ((uint32_t)__ldg(g + p + 1) << 8);
-          if (l < 3 || p + l > end) {
-            good = false;
-          } else {
-            cw[k] = p | (l << 16);
-            p += l;
-          }
-        }
-      }
-    }
-    if (good && p != end) good = false;
-    if (!good) {
-      st = SST_CH_FRAMING;
-#pragma unroll
-      for (int k = 0; k < kChPerFe; k++) cw[k] = 0;
-    }
-  }
-  uint4* o = reinterpret_cast<uint4*>(cmap + x * kMapWords);
-  o[0] = make_uint4(cw[0], cw[1], cw[2], cw[3]);
-  o[1] = make_uint4(cw[4], cw[5], cw[6], cw[7]);
-  o[2] = make_uint4(cw[8], cw[9], cw[10], cw[11]);
-  o[3] = make_uint4(st, 0u, 0u, 0u);
-}
-
 // a6, ordering: per event, the exclusive scan of its work items' cluster counts
 // gives every item's position in the event's sorted cluster SoA; the event's
 // total is its cluster count.  One CTA of 1024 threads per event (1,760 items of a
@@ -819,7 +765,8 @@ template <int TILE>
 __global__ void __launch_bounds__(256, 4) k_unpack(const uint8_t* __restrict__ raw,
                                                 const uint32_t* __restrict__ fed_len,
                                                 const uint64_t* __restrict__ fed_off, uint32_t n_feds,
-                                                sst_digis out, unsigned long long* lb, uint32_t* ticket, int lanes) {
+                                                sst_digis out, unsigned long long* lb, uint32_t* ticket, int lanes,
+                                                uint32_t spin_limit, int32_t withhold) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Shm<TILE>& s = *reinterpret_cast<Shm<TILE>*>(smem_raw);
   const int tid = threadIdx.x;
@@ -836,12 +783,13 @@ __global__ void __launch_bounds__(256, 4) k_unpack(const uint8_t* __restrict__ r
   if (tid < 32) {
     bool to = false;
     uint32_t excl = 0;
+    const bool publish = (int64_t)f != (int64_t)withhold;  // a FED withheld by the failure tests never publishes
     if (f > 0) {
-      if (tid == 0) st_release(lb + f, kLbAgg | total);
-      excl = lookback_warp(lb, f, 0, &to);
+      if (tid == 0 && publish) st_release(lb + f, kLbAgg | total);
+      excl = lookback_warp(lb, f, 0, spin_limit, &to);
     }
     if (tid == 0) {
-      st_release(lb + f, kLbPre | (excl + total));
+      if (publish) st_release(lb + f, kLbPre | (excl + total));
       s.scal[S_BASE] = excl;
       uint32_t fl = s.scal[S_FLAGS];
       if (to) fl |= SST_EV_TIMEOUT;
@@ -953,10 +901,10 @@ __global__ void __launch_bounds__(256, 4) k_cluster(sst_digis in, uint32_t n_fed
 }
 
 // a7: every FE unit of every FED of every event of a batch, unpacked and
-// clustered on chip, one warp per pair of FE units.  Persistent warps take
-// tickets FED-major (FED, then event, then pair), so that the warps working at
-// any moment share the same FED's calibration in L2.
-template <bool AMP>
+// clustered on chip, one warp per work item of U adjacent FE units (U = 1 or 2).
+// Persistent warps take tickets FED-major (FED, then event, then item), so that
+// the warps working at any moment share the same FED's calibration in L2.
+template <bool AMP, int U>
 __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ raw,
                                                   const uint32_t* __restrict__ fed_len,
                                                   const uint64_t* __restrict__ fed_off, uint32_t n_events,
@@ -964,32 +912,30 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
                                                   uint64_t out_cap, sst_event_status* status, KParams kp,
                                                   uint4* stage, uint32_t* ev_alloc, uint32_t* seg_cnt,
                                                   uint32_t* seg_start, uint32_t* ticket,
-                                                  const uint2* __restrict__ unit_desc,
-                                                  const uint32_t* __restrict__ cmap, AmpArgs am) {
+                                                  const uint2* __restrict__ unit_desc, AmpArgs am) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  fe::Warp& w = reinterpret_cast<fe::Warp*>(smem_raw)[warp];
-  constexpr uint32_t kItems = kFe / fe::kUnits;  // work items (FE-unit pairs) per FED
+  using W = fe::WarpT<U>;
+  W& w = reinterpret_cast<W*>(smem_raw)[warp];
+  constexpr uint32_t kItems = kFe / U;  // work items per FED
   const uint32_t per_fed = n_events * kItems;
   const uint32_t n_units = n_feds * per_fed;
-  pdl_wait();  // the prologue's tickets, offsets, unit descriptors and channel map
+  pdl_wait();  // the prologue's tickets, offsets and unit descriptors
   for (;;) {
     uint32_t t = 0;
     if (lane == 0) t = atomicAdd(ticket, 1u);
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= n_units) break;
-    const uint32_t f = t / per_fed, r = t % per_fed, e = r / kItems, p = r % kItems, u = p * fe::kUnits;
+    const uint32_t f = t / per_fed, r = t % per_fed, e = r / kItems, p = r % kItems, u = p * U;
     const size_t item = (size_t)e * n_feds + f;
-    uint32_t mw, mst;
-    fe::map_words(cmap + (item * kFe + u) * kMapWords, &mw, &mst);
     const uint64_t fo = fed_off[item];
     const bool in_range = fo != kBadOff;
     const uint32_t ch0 = f * kCh + u * kChPerFe;
-    fe::load_calib<fe::kChW>(w, kp, ch0);
+    fe::load_calib<W::kChW>(w, kp, ch0);
     const fe::Unit un = fe::locate(w, raw + (in_range ? fo : 0), unit_desc[item * kFe + u],
-                                   unit_desc[item * kFe + u + 1], f, u);
+                                   unit_desc[item * kFe + u + (U - 1)], f, u);
     uint32_t flags, nbad;
-    const uint32_t total = fe::parse_unit(w, un, mw, mst, &flags, &nbad);
+    const uint32_t total = fe::parse_unit(w, un, &flags, &nbad);
     if (lane == 0) {
       if (flags) atomicOr(&status[e].flags, flags);
       if (nbad) atomicAdd(&status[e].n_bad_channels, nbad);
@@ -1009,7 +955,7 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
       so.seg_amp_cnt = am.cnt + item * kItems + p;
       so.seg_amp_start = am.start + item * kItems + p;
     }
-    const bool slots = fe::use_slots(un);
+    const bool slots = fe::use_slots<W>(un);
     auto fill = [&](int c0, int c1, bool single) {
       if (single && slots) fe::mark_slots(w, un);
       else fe::mark_walk(w, un, c0, c1);
@@ -1017,8 +963,8 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
     const uint32_t* cal = kp.cal + (size_t)ch0 * kStrips;
     const float* nsqt = kp.nsq + (size_t)ch0 * kStrips;
     const uint32_t src_end = un.off1 + un.len1;
-    auto scan = [&](int nn, bool) { return fe::scan_unit<fe::kChW, true>(w, kp, cal, nsqt, un.src, src_end, nn); };
-    fe::cluster_unit<fe::kChW, AMP>(w, kp, ch0, total, fill, scan, so, &status[e]);
+    auto scan = [&](int nn, bool) { return fe::scan_unit<W::kChW, true>(w, kp, cal, nsqt, un.src, src_end, nn); };
+    fe::cluster_unit<W::kChW, AMP>(w, kp, ch0, total, fill, scan, so, &status[e]);
     __syncwarp();
   }
   pdl_release();
@@ -1138,7 +1084,8 @@ cudaError_t launch_unpack_t(const uint8_t* raw, const uint32_t* fed_len, uint32_
   int per_sm = 0;
   cudaError_t e = prepare((const void*)k_unpack<TILE>, sh.block, sm, &per_sm);
   if (e) return e;
-  k_unpack<TILE><<<n_feds, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_feds, out, s.lb, s.tickets, sh.lanes);
+  k_unpack<TILE><<<n_feds, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_feds, out, s.lb, s.tickets, sh.lanes,
+                                                s.lb_spin_limit ? s.lb_spin_limit : kLbSpinLimit, s.lb_withhold);
   return cudaGetLastError();
 }
 
@@ -1194,32 +1141,45 @@ cudaError_t launch_cluster_fe(const sst_digis& in, uint32_t n_feds, const KParam
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_fe(const uint8_t* raw, const uint32_t* fed_len, uint32_t n_events, uint32_t n_feds,
-                            const uint64_t* clu_off, uint64_t out_cap, sst_event_status* status, const KParams& kp,
-                            const Scratch& s, const Shape& sh, int n_sm, const AmpArgs& am, cudaStream_t st,
-                            cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+template <bool AMP, int U>
+cudaError_t launch_batch_t(const uint8_t* raw, const uint32_t* fed_len, uint32_t n_events, uint32_t n_feds,
+                           const uint64_t* clu_off, uint64_t out_cap, sst_event_status* status, const KParams& kp,
+                           const Scratch& s, const Shape& sh, int n_sm, const AmpArgs& am, cudaStream_t st) {
   const int nw = sh.block / 32;
-  const size_t sm = sizeof(fe::Warp) * nw;
-  const size_t units = (size_t)n_events * n_feds * (kFe / fe::kUnits);
+  const size_t sm = batch_smem(U, sh.block);
+  const size_t units = (size_t)n_events * n_feds * (kFe / U);
   int per_sm = 0;
-  const void* fn = am.stage ? (const void*)k_batch<true> : (const void*)k_batch<false>;
-  cudaError_t e = prepare(fn, sh.block, sm, &per_sm);
+  cudaError_t e = prepare((const void*)k_batch<AMP, U>, sh.block, sm, &per_sm);
   if (e) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const size_t ctas = (size_t)n_sm * (sh.ctas_per_sm < per_sm ? sh.ctas_per_sm : per_sm);
   const size_t need = (units + nw - 1) / nw;
   const int grid = (int)(ctas < need ? ctas : need);
-  if (ev_begin && (e = cudaEventRecord(ev_begin, st))) return e;
-  if (am.stage)
-    k_batch<true><<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out_cap, status, kp,
-                                              s.stage, s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets, s.unit_desc,
-                                              s.chan_map, am);
-  else if ((e = launch_pdl(k_batch<false>, (unsigned)grid, (unsigned)sh.block, sm, st, raw, fed_len,
-                           (const uint64_t*)s.fed_off, n_events, n_feds, clu_off, out_cap, status, kp, s.stage,
-                           s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets, (const uint2*)s.unit_desc,
-                           (const uint32_t*)s.chan_map, am)))
+  if (AMP) {
+    k_batch<AMP, U><<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out_cap, status, kp,
+                                                s.stage, s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets, s.unit_desc,
+                                                am);
+  } else if ((e = launch_pdl(k_batch<AMP, U>, (unsigned)grid, (unsigned)sh.block, sm, st, raw, fed_len,
+                             (const uint64_t*)s.fed_off, n_events, n_feds, clu_off, out_cap, status, kp, s.stage,
+                             s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets, (const uint2*)s.unit_desc, am))) {
     return e;
-  if ((e = cudaGetLastError())) return e;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_fe(const uint8_t* raw, const uint32_t* fed_len, uint32_t n_events, uint32_t n_feds,
+                            const uint64_t* clu_off, uint64_t out_cap, sst_event_status* status, const KParams& kp,
+                            const Scratch& s, const Shape& sh, int n_sm, const AmpArgs& am, cudaStream_t st,
+                            cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+  cudaError_t e;
+  if (ev_begin && (e = cudaEventRecord(ev_begin, st))) return e;
+  if (sh.units == 1)
+    e = am.stage ? launch_batch_t<true, 1>(raw, fed_len, n_events, n_feds, clu_off, out_cap, status, kp, s, sh, n_sm, am, st)
+                 : launch_batch_t<false, 1>(raw, fed_len, n_events, n_feds, clu_off, out_cap, status, kp, s, sh, n_sm, am, st);
+  else
+    e = am.stage ? launch_batch_t<true, 2>(raw, fed_len, n_events, n_feds, clu_off, out_cap, status, kp, s, sh, n_sm, am, st)
+                 : launch_batch_t<false, 2>(raw, fed_len, n_events, n_feds, clu_off, out_cap, status, kp, s, sh, n_sm, am, st);
+  if (e) return e;
   if (ev_end && (e = cudaEventRecord(ev_end, st))) return e;
   return cudaSuccess;
 }
@@ -1271,13 +1231,36 @@ size_t smem_bytes(int tile) {
   }
 }
 
-Shape default_shape() { return Shape{256, 2048, 2, 4}; }
+// Shared memory per CTA of the batched kernel for a work-item width and block size.
+size_t batch_smem(int units, int block) {
+  return (units == 1 ? sizeof(fe::WarpT<1>) : sizeof(fe::WarpT<2>)) * (size_t)(block / 32);
+}
+
+Shape default_shape() { return Shape{256, 2048, 2, 4, 0, 2}; }
 
 bool shape_valid(const Shape& s) {
   const bool blk = s.block == 128 || s.block == 256;
   const bool til = s.tile == 1024 || s.tile == 2048 || s.tile == 4096;
   const bool ln = s.lanes == 1 || s.lanes == 2 || s.lanes == 4 || s.lanes == 8 || s.lanes == 16 || s.lanes == 32;
-  return blk && til && ln && s.ctas_per_sm >= 1 && s.ctas_per_sm <= 8 && s.host_chunk >= 0 && s.host_chunk <= 4096;
+  return blk && til && ln && s.ctas_per_sm >= 1 && s.ctas_per_sm <= 8 && s.host_chunk >= 0 && s.host_chunk <= 4096 &&
+         (s.units == 1 || s.units == 2);
+}
+
+cudaError_t batch_launch_info(const Shape& sh, uint32_t n_events, uint32_t n_feds, int n_sm, int* grid, size_t* smem,
+                              int* items_per_fed) {
+  const size_t sm = batch_smem(sh.units, sh.block);
+  const void* fn = sh.units == 1 ? (const void*)k_batch<false, 1> : (const void*)k_batch<false, 2>;
+  int per_sm = 0;
+  cudaError_t e = prepare(fn, sh.block, sm, &per_sm);
+  if (e) return e;
+  const int nw = sh.block / 32;
+  const size_t units = (size_t)n_events * n_feds * (kFe / sh.units);
+  const size_t ctas = (size_t)n_sm * (sh.ctas_per_sm < per_sm ? sh.ctas_per_sm : per_sm);
+  const size_t need = (units + nw - 1) / nw;
+  *grid = (int)(ctas < need ? ctas : need);
+  *smem = sm;
+  *items_per_fed = kFe / sh.units;
+  return cudaSuccess;
 }
 
 cudaError_t launch_unpack(const uint8_t* raw, uint64_t raw_bytes, const uint32_t* fed_len, uint32_t n_feds,
@@ -1316,15 +1299,10 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
       event_off, 0, fed_len, n_feds, cpe, s.fed_off, status, s.ev_alloc, s.tickets, nullptr, 0, raw, s.unit_desc,
       am.stage ? s.amp_alloc : nullptr);
   if ((e = cudaGetLastError())) return e;
-  const uint64_t n_units = (uint64_t)n_events * n_feds * kFe;
-  if ((e = launch_pdl(k_chan_map, (unsigned)((n_units + kChanMapThreads - 1) / kChanMapThreads),
-                      (unsigned)kChanMapThreads, 0, st, raw, (const uint64_t*)s.fed_off, (const uint2*)s.unit_desc,
-                      n_units, s.chan_map)))
-    return e;
   e = launch_batch_fe(raw, fed_len, n_events, n_feds, clu_off, out.capacity, status, kp, s, sh, n_sm, am, st,
                       ev_begin, ev_end);
   if (e) return e;
-  return launch_order(clu_off, n_events, n_feds * (kFe / fe::kUnits), out, status, s, pack_off, am, st);
+  return launch_order(clu_off, n_events, n_feds * (kFe / (sh.units == 1 ? 1 : 2)), out, status, s, pack_off, am, st);
 }
 
 cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st) {

@@ -63,3 +63,25 @@ def test_status_bits_agree_between_header_binding_and_oracle():
         m = re.search(r"#define SST_CH_%s (0x[0-9A-Fa-f]+)u" % name, hdr)
         assert m, name
         assert int(m.group(1), 16) == getattr(sst, "SST_CH_" + name) == getattr(orc, "ST_" + name)
+
+
+def test_binding_constants_agree_with_the_header():
+    """Limits the binding checks on the host side are the header's."""
+    import re
+    import paper_2101_11489_gb300 as sst
+    hdr = open(os.path.join(ROOT, "include", "sst.h")).read()
+    m = re.search(r"#define SST_NOALLOC_MAX_FEDS (\d+)u", hdr)
+    assert m and int(m.group(1)) == sst.NOALLOC_MAX_FEDS
+    for name in ("OK", "ERR_INVALID_ARG", "ERR_NO_CALIB", "ERR_BUDGET", "ERR_TOO_LARGE", "ERR_BUSY",
+                 "ERR_NOT_READY", "ERR_TIMEOUT", "ERR_CUDA", "ERR_STATE"):
+        m = re.search(r"#define SST_%s (\d+)" % name, hdr)
+        assert m and int(m.group(1)) == getattr(sst, "SST_" + name), name
+
+
+def test_record_layouts_match_the_header():
+    """The ctypes records mirror the header's structs field for field (all fields
+    are 32- or 64-bit, so the sizes follow from the field lists)."""
+    import paper_2101_11489_gb300 as sst
+    assert ctypes.sizeof(sst.sst_tune) == 6 * 4
+    assert ctypes.sizeof(sst.sst_launch_info) == 5 * 4
+    assert ctypes.sizeof(sst.sst_event_status) == 16

@@ -153,17 +153,20 @@ def test_batch_equals_per_event(w0):
 
 
 def test_batch_launch_shapes_give_identical_results(w0):
+    """Every knob of the batched kernel (block, CTAs per SM, FE units per work
+    item) gives the same statuses and clusters as the default shape."""
     w, calib, g = w0
     evs = [eg.make_event(w, calib, 40 + i, occupancy=0.01 * (i + 1)) for i in range(3)]
+    keep = sst.sst_get_tune(g.ctx)
     ref = g.batch([(e.raw, e.fed_len) for e in evs])
-    for block, cps, tile, lanes in [(128, 4, 1024, 1), (128, 2, 4096, 8), (256, 3, 2048, 32), (256, 8, 1024, 4)]:
-        sst.sst_set_tune(g.ctx, block, cps, tile, lanes)
+    for block, cps, units in [(128, 4, 1), (128, 2, 2), (256, 3, 1), (256, 8, 2), (256, 1, 1)]:
+        sst.sst_set_tune(g.ctx, block=block, ctas_per_sm=cps, units_per_warp=units)
         got = g.batch([(e.raw, e.fed_len) for e in evs])
         for (s0, c0), (s1, c1) in zip(ref, got):
             assert s0 == s1
             for k in c0:
                 assert np.array_equal(c0[k], c1[k])
-    sst.sst_set_tune(g.ctx, 256, 3, 2048, 2)
+    sst.sst_set_tune(g.ctx, **keep)
 
 
 def _as_set(c):

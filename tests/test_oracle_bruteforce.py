@@ -3,7 +3,8 @@
 1. ``oracle/bruteforce.py``: the candidate rule written as a predicate over every
    interval of the module (arXiv 2101.11489 section 2: each cluster is bounded left
    and right around its seeds), exhaustively over all strip states of modules of up
-   to 5 strips and over random 6-strip modules, for several hole / bad-strip limits.
+   to 5 strips for several hole / bad-strip limits, over all 6-strip modules for the
+   default limits, and over random 6-strip modules.
 2. A textbook special case: with no bad strips and no holes allowed, candidates are
    exactly the maximal runs of consecutive active strips (found with numpy.diff).
 """
@@ -78,3 +79,13 @@ def test_runs_of_consecutive_actives_without_bad_strips():
         want = [(s, e - s) for s, e in zip(starts, ends) if seed[s:e].any()]
         got = orc.cluster_module(adc, noise, np.zeros(256, np.uint8), np.ones(256, np.float32), p)
         assert list(zip(got["first"].tolist(), got["width"].tolist())) == want
+
+
+def test_exhaustive_six_strip_modules_default_parameters():
+    """Every pattern of the 7 strip states over 6-strip modules (7^6 = 117,649),
+    default thresholds and limits (section 2; channel 2, seed 3, cluster 5, no
+    holes, one bad strip): the oracle's scan equals the interval predicate."""
+    p = Params()
+    for states in itertools.product(STATES, repeat=6):
+        got, want = run_both(states, p)
+        assert got == want, (states, got, want)

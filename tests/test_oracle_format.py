@@ -279,3 +279,40 @@ def test_fed_ranges_give_the_whole_event():
     assert sum(p["n_digi"] for p in parts) == d["strip"].size
     for k in ("det", "first", "width", "charge", "barycenter"):
         assert np.array_equal(np.concatenate([p[k] for p in parts]), c[k]), k
+
+
+def test_valid_non_canonical_payloads_unpack_run_by_run():
+    """Runs across strip 128, touching runs and widths up to 255 are valid (the
+    format in include/sst.h); the oracle unpacks them to exactly the digis the
+    runs list, and repacking those digis canonically gives the same digis back."""
+    import _fedbuild as fb
+    feds = fb.non_canonical_feds(np.random.default_rng(5), 3)
+    raw, fl = fb.event(feds)
+    d = orc.unpack_event(raw, fl, 3)
+    strips, adcs = fb.expected_digis(feds)
+    assert np.array_equal(d["strip"], strips) and np.array_equal(d["adc"], adcs)
+    assert not d["chan_status"].any()
+    dense = np.zeros(3 * 96 * 256, np.uint8)
+    rec = np.zeros(3 * 96 * 256, np.uint8)
+    dense[strips] = adcs
+    rec[strips] = 1
+    raw2, fl2 = orc.pack_event(dense, rec, 3)
+    assert raw2.size != raw.size  # canonical runs are cut at strip 128 and merged where they touch
+    d2 = orc.unpack_event(raw2, fl2, 3)
+    assert np.array_equal(d2["strip"], strips) and np.array_equal(d2["adc"], adcs)
+
+
+def test_touching_runs_and_the_apv_boundary_do_not_split_clusters():
+    """A cluster is a chain of linked active strips of one module: where the runs
+    of the payload start or end, or the APV boundary, plays no part."""
+    import _fedbuild as fb
+    p = orc.Params()
+    noise = np.full(96 * 256, 4.0, np.float32)
+    gain = np.ones(96 * 2, np.float32)
+    bad = np.zeros(96 * 256, np.uint8)
+    split = {0: [(126, [20, 30]), (128, [30, 20])], 1: [(10, [20]), (11, [30]), (12, [20])]}
+    whole = {0: [(126, [20, 30, 30, 20])], 1: [(10, [20, 30, 20])]}
+    for feds in ([split], [whole]):
+        raw, fl = fb.event(feds)
+        d, c = orc.process_event(raw, fl, 1, noise, gain, bad, p)
+        assert list(zip(c["det"].tolist(), c["first"].tolist(), c["width"].tolist())) == [(0, 126, 4), (1, 10, 3)]
