@@ -158,83 +158,52 @@ def time_oracle(pool, cores, events, n_sample):
 
 # ---------------------------------------------------------------- served stream
 
-def run_served(sst, ctx, events, n_feds, n_requests, rate, submitters=8, pollers=2):
-    """Submits n_requests events (cycling over `events`) with Poisson arrivals at
-    `rate` events/s (0 = as fast as possible) from `submitters` threads (arrival i
-    goes to thread i mod submitters; sst_submit runs with the GIL released) while
-    `pollers` threads take the admitted events from one queue, in admission order,
-    and poll them, which frees their space.  Returns throughput and latency
-    percentiles (submit to done, host clock, microseconds).  A thread that makes no
-    progress for a minute ends the run with an error."""
-    import queue
-    import sys
-    import threading
-    rng = np.random.default_rng(12345)
-    gaps = rng.exponential(1.0 / rate, n_requests) if rate > 0 else np.zeros(n_requests)
-    due = np.cumsum(gaps)
-    admitted = queue.SimpleQueue()
-    lat, done_t, errors = [], [], []
-    retries = [0]
-    limit_s = 60.0
-    old_switch = sys.getswitchinterval()
-    sys.setswitchinterval(5e-5)  # a waiting thread takes the GIL within 50 us
+SERVED_DISTINCT = 512  # distinct events of the served mix, cycled through the stream
 
-    def submitter(k, t0):
+
+def run_served(sst, ctx, events, n_feds, n_requests, batched_rate):
+    """The served stream through the library's native client (sst_serve_load):
+    the server's batch depth (events per launch) is picked by saturating runs, the
+    saturating throughput is its capacity, then Poisson arrivals are offered at
+    10% .. 120% of it and at the batched path's device rate when that is below
+    the top of the sweep; p50 / p99 latency from each request's arrival to its
+    completion (host clock)."""
+    def point(res):
+        return {"offered_rate": round(res["offered_rate"], 1) if res["offered_rate"] > 0 else "saturating",
+                "events": int(res["requests"]), "throughput": round(res["throughput"], 1),
+                "p50_us": round(res["p50_us"], 1), "p99_us": round(res["p99_us"], 1),
+                "p99_admitted_us": round(res["p99_admitted_us"], 1), "submit_retries": int(res["retries"])}
+
+    depth = {}
+    best = None
+    for mb in (16, 32, 64, 128):
+        sst.sst_server_start(ctx, 8 << 30, mb, 3, 4096, n_feds, zero_copy=True)
         try:
-            for i in range(k, n_requests, submitters):
-                if rate > 0:
-                    while True:
-                        left = t0 + due[i] - time.perf_counter()
-                        if left <= 0:
-                            break
-                        time.sleep(left if left > 2e-4 else 0)
-                raw, fl = events[i % len(events)]
-                t_try = time.perf_counter()
-                while True:
-                    code, tk = sst.sst_submit(ctx, raw, fl)
-                    if code == sst.SST_OK:
-                        break
-                    if time.perf_counter() - t_try > limit_s:
-                        raise RuntimeError(f"sst_submit refused for {limit_s} s (code {code})")
-                    retries[0] += 1
-                    time.sleep(20e-6)
-                admitted.put(tk)
-        except Exception as ex:  # reported by the caller
-            errors.append(repr(ex))
-
-    def poller():
-        try:
-            while True:
-                tk = admitted.get(timeout=limit_s)
-                if tk is None:
-                    return
-                code, info, _ = sst.sst_poll(ctx, tk, -1, 0)
-                if code != sst.SST_OK:
-                    raise RuntimeError(f"sst_poll returned {code}")
-                lat.append(info.t_done_us - info.t_submit_us)
-                done_t.append(time.perf_counter())
-        except Exception as ex:
-            errors.append(repr(ex))
-
-    t0 = time.perf_counter()
-    subs = [threading.Thread(target=submitter, args=(k, t0)) for k in range(submitters)]
-    polls = [threading.Thread(target=poller) for _ in range(pollers)]
-    for x in subs + polls:
-        x.start()
-    for x in subs:
-        x.join()
-    for _ in polls:
-        admitted.put(None)  # after every admitted ticket: the pollers stop once the queue is drained
-    for x in polls:
-        x.join()
-    sys.setswitchinterval(old_switch)
-    if errors or len(lat) != n_requests:
-        raise RuntimeError(f"served run incomplete: {len(lat)} of {n_requests} events; {errors[:3]}")
-    wall = max(done_t) - t0
-    lat = np.array(lat)
-    return {"offered_rate": round(rate, 1) if rate > 0 else "saturating", "events": n_requests,
-            "throughput": round(n_requests / wall, 1), "p50_us": round(float(np.percentile(lat, 50)), 1),
-            "p99_us": round(float(np.percentile(lat, 99)), 1), "submit_retries": retries[0]}
+            sst.sst_serve_load(ctx, events, 1000, 0.0, submitters=8, pollers=2)  # warm-up
+            r = sst.sst_serve_load(ctx, events, n_requests, 0.0, submitters=8, pollers=2)
+        finally:
+            sst.sst_server_stop(ctx)
+        depth[mb] = round(r["throughput"], 1)
+        if best is None or r["throughput"] > depth[best]:
+            best = mb
+    sst.sst_server_start(ctx, 8 << 30, best, 3, 4096, n_feds, zero_copy=True)
+    try:
+        sst.sst_serve_load(ctx, events, 1000, 0.0, submitters=8, pollers=2)
+        cap = sst.sst_serve_load(ctx, events, n_requests, 0.0, submitters=8, pollers=2)
+        rates = [f * cap["throughput"] for f in (0.1, 0.3, 0.5, 0.7, 0.9, 1.0, 1.2)]
+        at_batched = batched_rate if batched_rate <= 1.2 * cap["throughput"] else None
+        if at_batched:
+            rates.append(at_batched)
+        pts = []
+        for k, rate in enumerate(sorted(rates)):
+            n = int(min(n_requests, max(2000, rate * 2.0)))  # at most about 2 s per point
+            pts.append(point(sst.sst_serve_load(ctx, events, n, rate, submitters=8, pollers=2, seed=100 + k)))
+    finally:
+        sst.sst_server_stop(ctx)
+    return {"capacity": point(cap), "max_batch_events": best, "batch_depth_sweep": depth, "points": pts,
+            "p99_at_batched_rate_us": (next(p["p99_us"] for p in pts if p["offered_rate"] == round(at_batched, 1))
+                                       if at_batched else None),
+            "batched_rate": round(batched_rate, 1)}
 
 
 # ---------------------------------------------------------------- clocks
@@ -403,7 +372,7 @@ def main():
     ids = shard(rank, n_events)
     gen = pool.map(_gen_event, [(wid, i) for i in ids], chunksize=1)
     events = [(r, f) for r, f, _ in gen]
-    served_pool = pool.map(_gen_served_event, range(ids.start, ids.start + 64), chunksize=1) \
+    served_pool = pool.map(_gen_served_event, range(ids.start, ids.start + SERVED_DISTINCT), chunksize=1) \
         if args.served_events > 0 and wid == 2 else []
     calib = eg.make_calibration(w.n_feds, w.seed, w.p_bad)
 
@@ -614,27 +583,19 @@ def main():
     e2e_s = max_over_ranks([(time.perf_counter() - t0) / e2e_steps], world)[0]
     h2d_bytes = raw_h.nbytes + fl_h.nbytes + 2 * eoff.nbytes  # raw, FED lengths, event and cluster offsets
 
-    # ---- served stream: continuous batching behind sst_submit / sst_poll
+    # ---- served stream: continuous batching behind sst_submit / sst_poll, driven by
+    # the library's native Poisson client
     served = None
     if served_pool:
         # the events live in pinned memory and are lent to the server (zero-copy
         # submission): the client does no per-event copy
         pinned = [torch.from_numpy(r).pin_memory() for r, _ in served_pool]
-        lent = [(p.numpy(), f) for p, (_, f) in zip(pinned, served_pool)]
-        sst.sst_server_start(ctx, 8 << 30, 64, 3, 4096, w.n_feds, zero_copy=True)
-        try:
-            run_served(sst, ctx, lent, w.n_feds, 500, 0.0)  # warm-up
-            cap = run_served(sst, ctx, lent, w.n_feds, args.served_events, 0.0)
-            pts = [run_served(sst, ctx, lent, w.n_feds, args.served_events, f * cap["throughput"])
-                   for f in (0.5, 0.9)]
-            served = {"workload": "served-440fed-lognormal: occupancy lognormal median 1.5%, clip [0.5%, 5%], "
-                                  "64 distinct events cycled, Poisson arrivals, 8 Python submitter threads and 2 "
-                                  "poller threads, "
-                                  "zero-copy submission from pinned event buffers",
-                      "budget_bytes": 8 << 30, "max_batch_events": 64, "max_inflight": 3,
-                      "saturation": cap, "points": pts}
-        finally:
-            sst.sst_server_stop(ctx)
+        lent = [(p.numpy(), f.astype(np.uint32)) for p, (_, f) in zip(pinned, served_pool)]
+        served = run_served(sst, ctx, lent, w.n_feds, args.served_events, n_events / (ms_per_step / 1e3))
+        served["workload"] = ("served-440fed-lognormal: occupancy lognormal median 1.5%, clip [0.5%, 5%], "
+                              f"{len(lent)} distinct events cycled, Poisson arrivals, native client "
+                              "(sst_serve_load: 8 submitter and 2 poller threads), zero-copy submission from "
+                              "pinned event buffers, 8 GiB device budget, 3 batches in flight")
         del pinned, lent
 
     # ---- roofline of the dominant kernel (the batched kernel)

@@ -427,14 +427,24 @@ typedef struct {
  * calibration.  STATE if already running. */
 sst_status sst_server_start(sst_ctx* ctx, const sst_server_opts* opts);
 
-/* Drains in-flight work and stops the loop; unpolled results are discarded. */
+/* Stops the loop and frees the server; unpolled results are discarded.  Safe while
+ * other threads are inside sst_submit / sst_poll: from the call on they get
+ * STATE, pollers waiting without a timeout return, and the server is freed once
+ * no such call is inside. */
 sst_status sst_server_stop(sst_ctx* ctx);
 
-/* Submits one event from HOST memory (raw: raw_bytes bytes, fed_len: [n_feds]).
- * The bytes are copied before the call returns.  Admission: the event's device
- * footprint (raw bytes + cluster capacity raw_bytes/2 * 16 B + fixed overhead)
- * must fit the free budget.  Returns OK and a ticket, BUSY (no free slot) or
- * BUDGET (budget full now; retry after polling), or TOO_LARGE (never fits). */
+/* Submits one event from HOST memory (raw: raw_bytes bytes, fed_len: [n_feds])
+ * (section 3 and the served workload: events arrive one at a time and are
+ * processed concurrently).  The bytes are copied before the call returns (unless
+ * zero_copy).  Admission by memory: sst_server_start divides the device budget
+ * into max_inflight batch slots of equal size, each holding a raw arena of
+ * budget / (25 max_inflight) bytes and the cluster and staging arrays for it, so
+ * that the device memory in use never exceeds the budget; admitted events wait
+ * for a slot in a pinned host pool of max_inflight + 1 raw arenas (at most 2 GiB).
+ * Returns OK and a ticket; BUSY when all max_requests request slots are taken;
+ * BUDGET when the event does not fit the host pool now (retry after polling);
+ * TOO_LARGE when it exceeds one raw arena (it never fits); STATE when no server
+ * runs.  Thread safe. */
 sst_status sst_submit(sst_ctx* ctx, const uint8_t* raw, uint64_t raw_bytes, const uint32_t* fed_len,
                       uint64_t* ticket);
 
@@ -446,10 +456,39 @@ typedef struct {
 
 /* Waits up to timeout_us (0 = just check, < 0 = forever) for ticket's result.
  * On OK copies the status and up to `capacity` clusters to the HOST arrays (any
- * may be NULL to skip) and releases the slot and budget.  NOT_READY on timeout;
- * INVALID_ARG for an unknown ticket. */
+ * may be NULL to skip) and releases the request slot and the event's host bytes.
+ * NOT_READY on timeout; INVALID_ARG for an unknown ticket; STATE when the server
+ * is (or gets) stopped.  Thread safe. */
 sst_status sst_poll(sst_ctx* ctx, uint64_t ticket, int64_t timeout_us, sst_result_info* info, uint32_t* det,
                     uint16_t* first, uint16_t* width, uint32_t* charge, float* barycenter, uint64_t capacity);
+
+/* ---- a native client for the served path ---------------------------------------
+ * Measures the server as a stream of requests sees it (section 3: events processed
+ * concurrently as they come), with no client of another language in the way.  The
+ * server must be running.  Request i is event i mod n_events (raw[e], raw_bytes[e]
+ * and fed_len[e] in HOST memory; with zero_copy they must stay unchanged until the
+ * call returns) and is due at the i-th point of a Poisson process of `rate`
+ * events/s (0: all at once, i.e. as fast as the server admits; seeded by `seed`).
+ * `submitters` threads (1..64) submit the requests in turn, each at its due time,
+ * retrying while the server answers BUSY or BUDGET; `pollers` threads (1..16)
+ * collect them in admission order.  latency_us (NULL or [n_requests]) receives
+ * each request's latency from its due time to its completion.  Returns when every
+ * request is collected; INVALID_ARG for bad arguments, STATE without a server,
+ * TIMEOUT when submissions are refused for a minute, or the first failing
+ * submit / poll status. */
+typedef struct {
+  double offered_rate;    /* events/s asked for (0: saturating) */
+  double throughput;      /* events/s: requests / (last completion - start) */
+  double p50_us, p99_us;  /* latency from the due time to completion (host clock) */
+  double mean_us, max_us;
+  double p50_admitted_us, p99_admitted_us; /* latency from admission to completion */
+  uint64_t requests;
+  uint64_t retries;       /* submissions refused (BUSY or BUDGET) and retried */
+} sst_load_result;
+sst_status sst_serve_load(sst_ctx* ctx, const uint8_t* const* raw, const uint64_t* raw_bytes,
+                          const uint32_t* const* fed_len, uint32_t n_events, uint64_t n_requests, double rate,
+                          uint32_t submitters, uint32_t pollers, uint64_t seed, double* latency_us,
+                          sst_load_result* out);
 
 #ifdef __cplusplus
 }

@@ -96,6 +96,13 @@ class sst_server_opts(ctypes.Structure):
                 ("zero_copy", ctypes.c_uint32)]
 
 
+class sst_load_result(ctypes.Structure):
+    _fields_ = [("offered_rate", ctypes.c_double), ("throughput", ctypes.c_double), ("p50_us", ctypes.c_double),
+                ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double), ("max_us", ctypes.c_double),
+                ("p50_admitted_us", ctypes.c_double), ("p99_admitted_us", ctypes.c_double),
+                ("requests", ctypes.c_uint64), ("retries", ctypes.c_uint64)]
+
+
 class sst_result_info(ctypes.Structure):
     _fields_ = [("status", sst_event_status), ("t_submit_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
 
@@ -139,6 +146,7 @@ def load_library():
         "sst_server_stop": ([vp], i32),
         "sst_submit": ([vp, vp, u64, vp, P(u64)], i32),
         "sst_poll": ([vp, u64, i64, P(sst_result_info), vp, vp, vp, vp, vp, u64], i32),
+        "sst_serve_load": ([vp, vp, vp, vp, u32, u64, ctypes.c_double, u32, u32, u64, vp, P(sst_load_result)], i32),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -153,7 +161,7 @@ def exported_symbols() -> list[str]:
             "sst_cluster",
             "sst_batch", "sst_batch_host", "sst_batch_host_submit", "sst_batch_host_wait", "sst_pitch_upload", "sst_local_x", "sst_set_tune", "sst_get_tune", "sst_autotune", "sst_autotune_host", "sst_get_launch_info", "sst_profile_enable", "sst_profile_read", "sst_testing_set_wait",
             "sst_server_start", "sst_server_stop",
-            "sst_submit", "sst_poll"]
+            "sst_submit", "sst_poll", "sst_serve_load"]
 
 
 def _check(ctx, code: int, what: str):
@@ -408,6 +416,28 @@ def sst_submit(ctx: int, raw: np.ndarray, fed_len: np.ndarray) -> tuple[int, int
     if code not in (SST_OK, SST_ERR_BUSY, SST_ERR_BUDGET, SST_ERR_TOO_LARGE):
         _check(ctx, code, "sst_submit")
     return code, t.value
+
+
+def sst_serve_load(ctx: int, events, n_requests: int, rate: float, submitters: int = 8, pollers: int = 2,
+                   seed: int = 1, latencies: bool = False):
+    """The native Poisson client on the running server: events = [(raw u8, fed_len u32)] in host memory
+    (request i is event i mod len(events)); rate in events/s, 0 = saturating.  Returns a dict of the
+    sst_load_result fields (and the per-request latencies in microseconds when asked)."""
+    n = len(events)
+    raws = (ctypes.c_void_p * n)(*[_hp(r) for r, _ in events])
+    sizes = (ctypes.c_uint64 * n)(*[int(r.size) for r, _ in events])
+    fls = (ctypes.c_void_p * n)(*[_hp(np.ascontiguousarray(f)) for _, f in events])
+    for _, f in events:
+        assert f.dtype == np.uint32 and f.flags["C_CONTIGUOUS"], "fed_len must be contiguous uint32"
+    lat = np.zeros(n_requests, np.float64) if latencies else None
+    out = sst_load_result()
+    code = load_library().sst_serve_load(ctx, raws, sizes, fls, n, n_requests, float(rate), submitters, pollers,
+                                         seed, _hp(lat) if lat is not None else None, ctypes.byref(out))
+    _check(ctx, code, "sst_serve_load")
+    res = {k: getattr(out, k) for k, _ in sst_load_result._fields_}
+    if lat is not None:
+        res["latency_us"] = lat
+    return res
 
 
 def sst_poll(ctx: int, ticket: int, timeout_us: int, capacity: int = 0):

@@ -12,7 +12,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsst.so")
-SOURCES = ["sst_kernels.cu", "sst_api.cu", "sst_server.cpp", "sst_host.cpp", "sst_noalloc.cu", "sst_geom.cu"]
+SOURCES = ["sst_kernels.cu", "sst_api.cu", "sst_server.cpp", "sst_host.cpp", "sst_noalloc.cu", "sst_geom.cu",
+           "sst_load.cpp"]
 HEADERS = ["sst_internal.h", "sst_fe.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -8,9 +8,15 @@
 // device cluster arrays and pinned host mirrors for its results; events waiting for
 // a slot sit in a pinned host pool.  Nothing is allocated per event.
 //
-// Admission (sst_submit): an event is taken when a request slot is free (else
-// BUSY) and its bytes fit in the host pool (else BUDGET, retry after polling);
-// an event larger than a slot's raw arena is never admissible (TOO_LARGE).
+// Admission (sst_submit): the device budget is fixed at start (the slots); an event
+// is taken when a request slot is free (else BUSY) and its bytes fit in the pinned
+// host pool that holds events waiting for a slot (else BUDGET, retry after
+// polling); an event larger than a slot's raw arena is never admissible
+// (TOO_LARGE).
+//
+// Lifetime: callers inside sst_submit / sst_poll are counted; sst_server_stop
+// detaches the server from the context (later calls get STATE), wakes waiting
+// pollers and frees the server only once no caller is inside.
 //
 // The loop thread launches a batch as soon as a slot is free and events are
 // pending (FIFO, up to max_batch_events and the slot's raw arena): it copies the
@@ -33,6 +39,11 @@
 #include "sst_internal.h"
 
 namespace {
+
+// The context's server, counted as in use until release_server (nullptr when no
+// server runs).
+sst_server* acquire_server(sst_ctx* ctx);
+void release_server(sst_ctx* ctx, sst_server* sv);
 
 double now_us() {
   using namespace std::chrono;
@@ -150,6 +161,8 @@ struct sst_server {
   RangeAlloc res_alloc;
   std::map<size_t, std::pair<size_t, int>> regions;  // results region -> (bytes, events not yet polled)
   size_t max_event_bytes = 0;
+  int users = 0;  // callers inside sst_submit / sst_poll (under ctx->mu)
+  std::condition_variable cv_users;
 };
 
 namespace {
@@ -376,13 +389,24 @@ void release(sst_server* sv, int ri) {
 
 }  // namespace
 
+namespace {
+sst_status submit_one(sst_ctx* ctx, sst_server* sv, const uint8_t* raw, uint64_t raw_bytes, const uint32_t* fed_len,
+                      uint64_t* ticket);
+sst_status poll_one(sst_ctx* ctx, sst_server* sv, uint64_t ticket, int64_t timeout_us, sst_result_info* info,
+                    uint32_t* det, uint16_t* first, uint16_t* width, uint32_t* charge, float* barycenter,
+                    uint64_t capacity);
+}  // namespace
+
 extern "C" {
 
 sst_status sst_server_stop(sst_ctx* ctx);
 
 sst_status sst_server_start(sst_ctx* ctx, const sst_server_opts* opts) {
   if (!ctx || !opts) return SST_ERR_INVALID_ARG;
-  if (ctx->server) return sst::set_err(ctx, SST_ERR_STATE, "sst_server_start: already running");
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (ctx->server) return sst::set_err(ctx, SST_ERR_STATE, "sst_server_start: already running");
+  }
   if (!ctx->has_calib) return sst::set_err(ctx, SST_ERR_NO_CALIB, "sst_server_start: no calibration");
   const sst_server_opts& o = *opts;
   if (o.mem_budget_bytes < (64ull << 20) || o.max_batch_events == 0 || o.max_batch_events > 4096 ||
@@ -421,22 +445,31 @@ sst_status sst_server_start(sst_ctx* ctx, const sst_server_opts* opts) {
     return sst::cuda_err(ctx, e, "sst_server_start");
   }
   sv->reqs.resize(o.max_requests);
-  ctx->server = sv;
   sv->loop = std::thread(loop_main, sv);
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->server = sv;
+  }
   if (prev >= 0) cudaSetDevice(prev);
   return SST_OK;
 }
 
 sst_status sst_server_stop(sst_ctx* ctx) {
   if (!ctx) return SST_ERR_INVALID_ARG;
-  sst_server* sv = ctx->server;
-  if (!sv) return SST_OK;
+  sst_server* sv = nullptr;
   {
-    std::lock_guard<std::mutex> lock(sv->mu);
-    sv->stop = true;
+    std::unique_lock<std::mutex> g(ctx->mu);
+    sv = ctx->server;
+    if (!sv) return SST_OK;
+    ctx->server = nullptr;  // new submit / poll calls get STATE from here on
+    {
+      std::lock_guard<std::mutex> lock(sv->mu);
+      sv->stop = true;
+    }
+    sv->cv_loop.notify_all();
+    sv->cv_done.notify_all();  // pollers waiting without a timeout return
+    sv->cv_users.wait(g, [&] { return sv->users == 0; });
   }
-  sv->cv_loop.notify_all();
-  sv->cv_done.notify_all();
   sv->loop.join();
   int prev = -1;
   cudaGetDevice(&prev);
@@ -445,7 +478,6 @@ sst_status sst_server_stop(sst_ctx* ctx) {
   if (sv->host_pool) cudaFreeHost(sv->host_pool);
   if (sv->res_pool) cudaFreeHost(sv->res_pool);
   if (prev >= 0) cudaSetDevice(prev);
-  ctx->server = nullptr;
   delete sv;
   return SST_OK;
 }
@@ -453,8 +485,41 @@ sst_status sst_server_stop(sst_ctx* ctx) {
 sst_status sst_submit(sst_ctx* ctx, const uint8_t* raw, uint64_t raw_bytes, const uint32_t* fed_len,
                       uint64_t* ticket) {
   if (!ctx || !raw || !fed_len || !ticket) return SST_ERR_INVALID_ARG;
-  sst_server* sv = ctx->server;
+  sst_server* sv = acquire_server(ctx);
   if (!sv) return sst::set_err(ctx, SST_ERR_STATE, "sst_submit: server not running");
+  const sst_status r = submit_one(ctx, sv, raw, raw_bytes, fed_len, ticket);
+  release_server(ctx, sv);
+  return r;
+}
+
+sst_status sst_poll(sst_ctx* ctx, uint64_t ticket, int64_t timeout_us, sst_result_info* info, uint32_t* det,
+                    uint16_t* first, uint16_t* width, uint32_t* charge, float* barycenter, uint64_t capacity) {
+  if (!ctx) return SST_ERR_INVALID_ARG;
+  sst_server* sv = acquire_server(ctx);
+  if (!sv) return sst::set_err(ctx, SST_ERR_STATE, "sst_poll: server not running");
+  const sst_status r = poll_one(ctx, sv, ticket, timeout_us, info, det, first, width, charge, barycenter, capacity);
+  release_server(ctx, sv);
+  return r;
+}
+
+}  // extern "C"
+
+namespace {
+
+sst_server* acquire_server(sst_ctx* ctx) {
+  std::lock_guard<std::mutex> g(ctx->mu);
+  sst_server* sv = ctx->server;
+  if (sv) sv->users++;
+  return sv;
+}
+
+void release_server(sst_ctx* ctx, sst_server* sv) {
+  std::lock_guard<std::mutex> g(ctx->mu);
+  if (--sv->users == 0) sv->cv_users.notify_all();
+}
+
+sst_status submit_one(sst_ctx* ctx, sst_server* sv, const uint8_t* raw, uint64_t raw_bytes, const uint32_t* fed_len,
+                      uint64_t* ticket) {
   if (raw_bytes > sv->max_event_bytes) return SST_ERR_TOO_LARGE;
   int ri = -1;
   size_t off = 0;
@@ -490,11 +555,9 @@ sst_status sst_submit(sst_ctx* ctx, const uint8_t* raw, uint64_t raw_bytes, cons
   return SST_OK;
 }
 
-sst_status sst_poll(sst_ctx* ctx, uint64_t ticket, int64_t timeout_us, sst_result_info* info, uint32_t* det,
-                    uint16_t* first, uint16_t* width, uint32_t* charge, float* barycenter, uint64_t capacity) {
-  if (!ctx) return SST_ERR_INVALID_ARG;
-  sst_server* sv = ctx->server;
-  if (!sv) return sst::set_err(ctx, SST_ERR_STATE, "sst_poll: server not running");
+sst_status poll_one(sst_ctx* ctx, sst_server* sv, uint64_t ticket, int64_t timeout_us, sst_result_info* info,
+                    uint32_t* det, uint16_t* first, uint16_t* width, uint32_t* charge, float* barycenter,
+                    uint64_t capacity) {
   std::unique_lock<std::mutex> lock(sv->mu);
   int ri = -1;
   for (size_t i = 0; i < sv->reqs.size(); i++)
@@ -510,7 +573,8 @@ sst_status sst_poll(sst_ctx* ctx, uint64_t ticket, int64_t timeout_us, sst_resul
     sv->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), done);
   if (!sv->fatal.empty()) return sst::set_err(ctx, SST_ERR_CUDA, sv->fatal);
   Req& r = sv->reqs[ri];
-  if (r.state != ReqState::kDone) return SST_ERR_NOT_READY;
+  if (r.state != ReqState::kDone)
+    return sv->stop ? sst::set_err(ctx, SST_ERR_STATE, "sst_poll: server stopped") : SST_ERR_NOT_READY;
   const sst_event_status st = r.status;
   const uint64_t a = r.first;
   const uint64_t n = st.n_clusters < capacity ? st.n_clusters : capacity;
@@ -529,4 +593,5 @@ sst_status sst_poll(sst_ctx* ctx, uint64_t ticket, int64_t timeout_us, sst_resul
   return SST_OK;
 }
 
-}  // extern "C"
+}  // namespace
+

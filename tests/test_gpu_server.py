@@ -121,3 +121,105 @@ def test_zero_copy_submission_equals_the_oracle():
     finally:
         sst.sst_server_stop(g.ctx)
         g.close()
+
+
+def test_budget_full_then_poll_then_resubmit():
+    """Admission by memory: with a small budget the host pool of admitted events
+    fills, sst_submit answers BUDGET, and after one poll the same event is admitted."""
+    w = eg.WORKLOADS[0]
+    calib = eg.make_calibration(w.n_feds, w.seed, w.p_bad)
+    g = Gpu(calib.noise, calib.gain, calib.bad)
+    try:
+        sst.sst_server_start(g.ctx, 64 << 20, 4, 1, 4096, w.n_feds)
+        e = eg.make_event(w, calib, 7, occupancy=0.02)
+        tickets = []
+        for _ in range(4096):
+            code, t = sst.sst_submit(g.ctx, e.raw, e.fed_len)
+            if code != sst.SST_OK:
+                break
+            tickets.append(t)
+        assert code == sst.SST_ERR_BUDGET and len(tickets) >= 2
+        st, _ = _poll(g, tickets.pop(0), 0)
+        code, t = sst.sst_submit(g.ctx, e.raw, e.fed_len)
+        assert code == sst.SST_OK
+        tickets.append(t)
+        _, oc, ost = g.oracle(e.raw, e.fed_len, w.n_feds)
+        assert st == ost
+        for t in tickets:
+            st, cl = _poll(g, t, e.nbytes)
+            assert st == ost
+            assert_clusters_equal(cl, oc)
+        big = np.zeros(64 << 20, np.uint8)  # larger than a batch slot's raw arena: never admissible
+        code, _ = sst.sst_submit(g.ctx, big, e.fed_len)
+        assert code == sst.SST_ERR_TOO_LARGE
+    finally:
+        sst.sst_server_stop(g.ctx)
+        g.close()
+
+
+def test_stop_while_other_threads_submit_and_poll():
+    """sst_server_stop is safe while other threads are inside sst_submit / sst_poll:
+    every call returns OK, a refusal, or STATE once the server is gone."""
+    import threading
+    w = eg.WORKLOADS[0]
+    calib = eg.make_calibration(w.n_feds, w.seed, w.p_bad)
+    g = Gpu(calib.noise, calib.gain, calib.bad)
+    e = eg.make_event(w, calib, 8, occupancy=0.01)
+    seen = []
+    try:
+        sst.sst_server_start(g.ctx, 256 << 20, 4, 2, 64, w.n_feds)
+
+        def client():
+            for _ in range(400):
+                try:
+                    code, t = sst.sst_submit(g.ctx, e.raw, e.fed_len)
+                    if code == sst.SST_OK:
+                        code = sst.sst_poll(g.ctx, t, -1, 0)[0]
+                except sst.SstError as ex:  # the binding raises the codes it does not return
+                    code = ex.code
+                seen.append(code)
+                if code == sst.SST_ERR_STATE:
+                    return
+
+        th = [threading.Thread(target=client) for _ in range(4)]
+        for t in th:
+            t.start()
+        import time
+        time.sleep(0.05)
+        sst.sst_server_stop(g.ctx)
+        for t in th:
+            t.join(timeout=60)
+            assert not t.is_alive()
+        assert set(seen) <= {sst.SST_OK, sst.SST_ERR_BUSY, sst.SST_ERR_BUDGET, sst.SST_ERR_STATE}
+        assert sst.SST_OK in seen
+        with pytest.raises(sst.SstError) as ei:
+            sst.sst_submit(g.ctx, e.raw, e.fed_len)
+        assert ei.value.code == sst.SST_ERR_STATE
+    finally:
+        sst.sst_server_stop(g.ctx)
+        g.close()
+
+
+def test_native_client_saturating_and_poisson():
+    """The native load generator (sst_serve_load) drives the server through the
+    public calls: every request is collected, latencies are ordered, and an
+    offered rate well below capacity is what comes out."""
+    w = eg.WORKLOADS[0]
+    calib = eg.make_calibration(w.n_feds, w.seed, w.p_bad)
+    g = Gpu(calib.noise, calib.gain, calib.bad)
+    try:
+        sst.sst_server_start(g.ctx, 512 << 20, 16, 3, 256, w.n_feds, zero_copy=True)
+        pinned = [torch.from_numpy(eg.make_event(w, calib, 200 + i).raw).pin_memory() for i in range(8)]
+        evs = [(p.numpy(), eg.make_event(w, calib, 200 + i).fed_len) for i, p in enumerate(pinned)]
+        sat = sst.sst_serve_load(g.ctx, evs, 2000, 0.0, submitters=4, pollers=2)
+        assert sat["requests"] == 2000 and sat["throughput"] > 1000
+        assert 0 < sat["p50_us"] <= sat["p99_us"] <= sat["max_us"]
+        rate = 0.2 * sat["throughput"]
+        r = sst.sst_serve_load(g.ctx, evs, 1000, rate, submitters=4, pollers=2, seed=3, latencies=True)
+        assert r["requests"] == 1000 and abs(r["throughput"] - rate) < 0.25 * rate
+        lat = r["latency_us"]
+        assert lat.size == 1000 and (lat > 0).all()
+        assert abs(np.percentile(lat, 99) - r["p99_us"]) <= 1e-6 * r["p99_us"] + 1.0
+    finally:
+        sst.sst_server_stop(g.ctx)
+        g.close()
