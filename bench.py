@@ -9,7 +9,10 @@ in HBM: every FED of every event is unpacked and clustered.
 Default workload: 64 full-detector events (440 FEDs x 96 channels x 256 strips),
 per-event signal occupancy uniform in [0.5%, 4%], cluster widths 1-5, 0.1% bad
 strips.  --workload batch256 selects 256 events at 5% occupancy, widths 1-12,
-2% bad strips, 3% saturated strips.
+2% bad strips, 3% saturated strips; batch64-skew the default batch with FED
+occupancies skewed so that FED payloads differ about 8x; single50 / single440 the
+plain per-event configurations (one 50-FED event at 1%, one 440-FED event at 1.5%,
+unpacked and clustered by sst_unpack + sst_cluster, one event per step).
 
 Prints one JSON line (rank 0).  `value` is events/s of the batched path (device
 time, CUDA events, L2 flushed between steps); `e2e` is the same through the C ABI
@@ -46,7 +49,11 @@ import eventgen as eg  # noqa: E402
 WORKLOADS = {
     "batch64": (2, 64),
     "batch256": (3, 256),
+    "batch64-skew": (5, 64),
+    "single50": (0, 1),
+    "single440": (1, 1),
 }
+PER_EVENT = {"single50", "single440"}  # the plain per-event configurations: one event per launch sequence
 L2_FLUSH_BYTES = 512 << 20  # written between timed steps (L2 is 129 MB)
 
 
@@ -283,6 +290,17 @@ def cpu_model() -> str:
     return "unknown"
 
 
+def fed_spread(events) -> dict:
+    """How much the FED payloads (bytes after the 32-byte header) differ: the
+    largest over the smallest within each event (median and maximum over the
+    events) and over all FEDs of the batch."""
+    fl = np.array([e[1] for e in events], dtype=np.float64) - 32
+    fl = np.maximum(fl, 1)
+    within = fl.max(axis=1) / fl.min(axis=1)
+    return {"within_event_median": round(float(np.median(within)), 2), "within_event_max": round(float(within.max()), 2),
+            "across_batch": round(float(fl.max() / fl.min()), 2)}
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -365,6 +383,8 @@ def main():
         return run_reference(args, rank, world, wid, n_events)
     if args.cpu_sweep:
         return cpu_sweep(args, wid, n_events) if rank == 0 else None
+    if args.workload in PER_EVENT:
+        return run_single(args, rank, world, local, wid)
 
     cores = os.cpu_count() or 1
     # the process pool is started (spawn) before the first CUDA call
@@ -651,6 +671,7 @@ def main():
                        "strips_per_event": w.n_feds * 96 * 256, "l2": "flushed: 512 MiB write before every step",
                        "tune": tune, "tune_source": tune_src, "launch": launch, "digis_per_step": n_digi, "clusters_per_step": n_clu,
                        "payload_bytes_per_step": int(sizes.sum()), "status_flags": flags,
+                       "fed_payload_spread": fed_spread(events),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "strips_per_s": round(total_events * w.n_feds * 96 * 256 / (ms_per_step / 1e3), 1),
             "per_event": {"value": round(pe_value * world, 1), "unit": "events/s",
@@ -687,6 +708,130 @@ def main():
             "wall_s_timed_region": round(t_wall, 4),
         }
         print(json.dumps(line), flush=True)
+    sst.sst_destroy(ctx)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_single(args, rank, world, local, wid):
+    """The plain per-event configurations: one event per step through sst_unpack +
+    sst_cluster (device buffers; the paper's per-event form), L2 flushed before
+    every step; the event of the configuration, replicated per rank."""
+    w = eg.WORKLOADS[wid]
+    calib = eg.make_calibration(w.n_feds, w.seed, w.p_bad)
+    ev = eg.make_event(w, calib, 0)
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    import paper_2101_11489_gb300 as sst
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    ctx = sst.sst_create(local, w.n_feds)
+    sst.sst_calib_upload(ctx, calib.noise, calib.gain, calib.bad, sst.params())
+    raw = torch.from_numpy(ev.raw).to(dev)
+    fl = torch.from_numpy(ev.fed_len.view(np.int32)).to(dev)
+    cap = ev.nbytes // 2 + 1
+    dbuf = sst.DigiBuffers.alloc(ev.nbytes, w.n_feds, device=dev)
+    cbuf = sst.ClusterBuffers.alloc(cap, device=dev)
+    drec, crec = dbuf.record(), cbuf.record()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        sst.sst_unpack(ctx, raw, fl, w.n_feds, drec)
+        sst.sst_cluster(ctx, drec, w.n_feds, crec)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    ev_t = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        ev_t[i][0].record(stream)
+        step()
+        ev_t[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = np.array([a.elapsed_time(b) for a, b in ev_t])
+    mean_ms = max_over_ranks([float(ms.mean())], world)[0]
+    st = dbuf.to_host()
+    n_digi, n_clu = st["n_digi"], st["n_clusters"]
+
+    # end to end through the public calls with host buffers: copy the event in
+    # (pinned), unpack + cluster, read the status, then the event's clusters out
+    raw_pin = torch.from_numpy(ev.raw).pin_memory()
+    fl_pin = torch.from_numpy(ev.fed_len.view(np.int32)).pin_memory()
+    host = sst.HostClusters.alloc(cap, pinned=True)
+    st_pin = torch.zeros(4, dtype=torch.int32).pin_memory()
+    dev_arrays = [cbuf.det, cbuf.first, cbuf.width, cbuf.charge, cbuf.barycenter]
+    host_arrays = [torch.from_numpy(getattr(host, k).view(np.uint8)) for k in ("det", "first", "width", "charge",
+                                                                             "barycenter")]
+
+    def e2e_step():
+        raw.copy_(raw_pin, non_blocking=True)
+        fl.copy_(fl_pin, non_blocking=True)
+        step()
+        st_pin.copy_(dbuf.status.view(torch.int32), non_blocking=True)
+        torch.cuda.synchronize()
+        n = int(st_pin[1])
+        for d, h in zip(dev_arrays, host_arrays):
+            nb = n * d.element_size()
+            h[:nb].copy_(d.view(torch.uint8)[:nb], non_blocking=True)
+        torch.cuda.synchronize()
+        return n
+
+    for _ in range(3):
+        e2e_step()
+    e2e_steps = max(3, min(args.steps, 200))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        n_out = e2e_step()
+    e2e_s = max_over_ranks([(time.perf_counter() - t0) / e2e_steps], world)[0]
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cores = os.cpu_count() or 1
+        pool = mp.get_context("spawn").Pool(cores, initializer=_worker_init, initargs=(wid,))
+        n_sample = cores * 4
+        v, wall, cpu_s = time_oracle(pool, cores, [(ev.raw, ev.fed_len)], n_sample)
+        pool.terminate()
+        cpu = {"value": round(v, 2), "unit": "events/s", "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+               "sample": f"the event {n_sample} times (unpack + cluster, sequential C, one event per process), "
+                         f"{wall:.1f} s wall, {cpu_s:.1f} s CPU"}
+    peak, peak_kind = measured_peaks()
+    b_alg = algorithmic_bytes([(ev.raw, ev.fed_len)], n_digi, n_clu)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "events/s unpack+cluster (per event)", "value": round(world * 1e3 / mean_ms, 1),
+            "unit": "events/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(mean_ms, 4),
+            "step_ms_percentiles": {"p10": round(float(np.percentile(ms, 10)), 4),
+                                    "median": round(float(np.median(ms)), 4),
+                                    "p90": round(float(np.percentile(ms, 90)), 4)},
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {w.name}", "events_per_step": 1, "n_feds": w.n_feds,
+                       "strips_per_event": w.n_feds * 96 * 256, "l2": "flushed: 512 MiB write before every step",
+                       "digis": int(n_digi), "clusters": int(n_clu), "payload_bytes": int(ev.nbytes),
+                       "path": "sst_unpack + sst_cluster, device buffers, one event per launch sequence",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "e2e": {"value": round(world / e2e_s, 1), "unit": "events/s",
+                    "h2d_bytes_per_step": int(ev.raw.nbytes + ev.fed_len.nbytes),
+                    "d2h_bytes_per_step": int(16 + 16 * n_out), "steps": e2e_steps,
+                    "api": "pinned copy in, sst_unpack + sst_cluster, status then the event's clusters copied out"},
+            "gpu_launches": 5 * args.steps,
+            "roofline": {"bound": "hbm", "achieved": round(b_alg / (mean_ms / 1e3) / 1e9, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(b_alg / (mean_ms / 1e3) / 1e9 / peak, 4), "traffic": None,
+                         "kernel": "the per-event launch sequence (k_fed_scan, k_unpack, k_cluster, k_order and a "
+                                   "memset): launch- and latency-bound at one event per launch",
+                         "algorithmic_bytes": int(b_alg), "peak_kind": peak_kind},
+            "cpu_baseline": cpu, "clocks": clk,
+        }), flush=True)
     sst.sst_destroy(ctx)
     if world > 1:
         import torch.distributed as dist

@@ -63,9 +63,9 @@ class Workload:
     fed_skew: float = 1.0  # >1: per-FED occupancy multiplier drawn log-uniform in [1/skew, skew]
 
 
-# The five workloads of the hot path (the numbering follows the configuration list
-# this project measures: plain small event, plain full event, batched, batched high
-# occupancy, served stream).
+# The workloads of the hot path (the numbering follows the configuration list this
+# project measures: plain small event, plain full event, batched, batched high
+# occupancy, served stream; then the batched configuration with skewed FEDs).
 WORKLOADS = {
     0: Workload("single-event-50fed", 50, 1, ("fixed", 0.01), (1, 5), 0.001, 0),
     1: Workload("single-event-440fed", 440, 1, ("fixed", 0.015), (1, 5), 0.001, 1),
@@ -73,6 +73,12 @@ WORKLOADS = {
     3: Workload("batch256-440fed-occ5-wide", 440, 256, ("fixed", 0.05), (1, 12), 0.02, 3,
                 overlap=True, sat_frac=0.03),
     4: Workload("served-440fed-lognormal", 440, 10000, ("lognormal", 0.015, 0.6, 0.005, 0.05), (1, 5), 0.001, 4),
+    # the batched configuration's stress variant: per-FED occupancy multipliers
+    # log-uniform in [1/4096, 4096] (overlapping clusters allowed), so that FED
+    # payloads differ about 8x within the batch despite the zero-suppression noise
+    # floor (without them the batched workload's FED payloads differ about 1.6x)
+    5: Workload("batch64-440fed-occ0.5-4-fedskew", 440, 64, ("uniform", 0.005, 0.04), (1, 5), 0.001, 2,
+                overlap=True, fed_skew=4096.0),
 }
 
 

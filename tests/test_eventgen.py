@@ -43,3 +43,18 @@ def test_batch_layout():
     assert b.event_off.tolist() == [0, evs[0].nbytes, evs[0].nbytes + evs[1].nbytes, b.raw.size]
     assert b.fed_len.size == 3 * w.n_feds
     assert all(int(o) % 16 == 0 for o in b.event_off)
+
+
+def test_fed_skew_variant_spreads_fed_payloads_eightfold():
+    """The batched configuration says FED payloads differ up to 8x; with the stated
+    noise model they differ far less, so the stress variant skews the FEDs'
+    occupancies (measured here on four events; the plain workload for contrast)."""
+    def spread(wid):
+        w = eg.WORKLOADS[wid]
+        calib = eg.make_calibration(w.n_feds, w.seed, w.p_bad)
+        fl = np.array([eg.make_event(w, calib, e).fed_len for e in range(4)]).astype(float) - 32
+        return (fl.max(axis=1) / fl.min(axis=1)).max(), fl.max() / fl.min()
+    within, across = spread(5)
+    assert within >= 8.0 and across >= 8.0
+    within2, across2 = spread(2)
+    assert across2 < 2.0

@@ -167,3 +167,21 @@ def test_served_mix_every_event_with_the_benchmark_options():
         g.close()
     finally:
         wl.close()
+
+
+def test_batch64_fed_skew_variant_sampled():
+    """The batched configuration with FED payloads differing about 8x (the FED-skew
+    stress variant): a sample of the events, both work-item widths."""
+    wl = Workload(5, 16)
+    try:
+        g = Gpu(wl.calib.noise, wl.calib.gain, wl.calib.bad)
+        res = wl.oracle(range(16))
+        for units in (2, 1):
+            sst.sst_set_tune(g.ctx, units_per_warp=units)
+            sth, cb, coff = batch_launch(g, wl.events, autotune=False)
+            for k, (oc, ost) in enumerate(res):
+                assert status_dict(sth[k]) == ost, k
+                assert_clusters_equal(cb.to_host(int(coff[k]), int(sth[k, 1])), oc)
+        g.close()
+    finally:
+        wl.close()
