@@ -111,6 +111,18 @@ cudaError_t ensure_scratch(Scratch& s, size_t items, size_t events, size_t stage
   return cudaSuccess;
 }
 
+cudaError_t ensure_spill(Scratch& s, size_t warps) {
+  if (warps <= s.spill_warps) return cudaSuccess;
+  cudaError_t e = cudaDeviceSynchronize();  // growing: wait for all work that may still use the old area
+  if (e) return e;
+  if (s.spill) cudaFree(s.spill);
+  s.spill = nullptr;
+  s.spill_warps = 0;
+  if ((e = cudaMalloc(&s.spill, warps * kSpillRecords * sizeof(uint4)))) return e;
+  s.spill_warps = warps;
+  return cudaSuccess;
+}
+
 cudaError_t ensure_amp_scratch(Scratch& s, size_t items, size_t events, size_t amp_bytes) {
   items = items ? items : 1;
   events = events ? events : 1;
@@ -139,6 +151,7 @@ void free_scratch(Scratch& s) {
   if (s.ev_alloc) cudaFree(s.ev_alloc);
   if (s.stage) cudaFree(s.stage);
   if (s.tickets) cudaFree(s.tickets);
+  if (s.spill) cudaFree(s.spill);
   for (void* p : {(void*)s.amp_stage, (void*)s.amp_alloc, (void*)s.seg_amp_cnt, (void*)s.seg_amp_start,
                   (void*)s.seg_amp_dest})
     if (p) cudaFree(p);
@@ -286,6 +299,7 @@ sst_status sst_cluster(sst_ctx* ctx, const sst_digis* in, uint32_t n_feds, const
   DeviceGuard g(ctx->device);
   cudaError_t e = ensure_scratch(ctx->scratch, (size_t)n_feds * kFe, 1, out->capacity);
   if (!e && out->amp) e = ensure_amp_scratch(ctx->scratch, (size_t)n_feds * kFe, 1, out->amp_capacity);
+  if (!e) e = ensure_spill(ctx->scratch, (size_t)n_feds * kFe);
   if (e) return cuda_err(ctx, e, "sst_cluster scratch");
   e = launch_cluster(*in, n_feds, *out, kparams(ctx), ctx->scratch, ctx->shape, (cudaStream_t)stream);
   return cuda_err(ctx, e, "sst_cluster");
@@ -311,6 +325,7 @@ sst_status sst_batch(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off
   const size_t items = (size_t)n_events * n_feds;
   cudaError_t e = ensure_scratch(ctx->scratch, items * kFe, n_events, out->capacity);
   if (!e && out->amp) e = ensure_amp_scratch(ctx->scratch, items * kFe, n_events, out->amp_capacity);
+  if (!e) e = ensure_spill(ctx->scratch, (size_t)ctx->n_sm * kMaxWarpsPerSm);
   if (e) return cuda_err(ctx, e, "sst_batch scratch");
   cudaEvent_t eb = nullptr, ee = nullptr;
   if (ctx->profiling) {

@@ -562,16 +562,22 @@ struct SegOut {
   uint32_t* seg_amp_start = nullptr;  // their offset in the slice, or kNoAmp
 };
 
+// The warp's index in the grid, which selects its spill area.
+__device__ __forceinline__ uint32_t spill_warp() { return blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); }
+
 // Clusters the `total` digis of one unit and stages its clusters.  `fill(c0, c1,
 // single)` prepares the tile for channel chunk [c0, c1) (single: the whole unit
 // fits one chunk) and `scan(nn, single)` runs scan_unit over its nn digis.  det0 is
 // the module id of the unit's first channel (its first channel in the calibration
 // tables).  The kept
 // clusters are first counted, then their region is allocated in one piece, then
-// they are written; a unit whose digis exceed the tile goes through its channel
-// chunks twice.  Without amplitudes, the records of the first 64 candidates (two
-// per lane) are kept in registers from the counting pass, so that only candidates
-// beyond them are formed twice (a work item of a full event has about 49).
+// they are written.  Without amplitudes, the records of the first 64 candidates
+// (two per lane) are kept in registers from the counting pass, so that only
+// candidates beyond them are formed twice (a work item of a full event has about
+// 49); a unit whose digis exceed the tile is processed chunk by chunk once, its
+// records spilled to the warp's area in global memory and copied to their region
+// (when they do not fit the area, or with amplitudes, it goes through its chunks
+// twice).
 // NCH: channels of the work item (12 or 24); AMP: amplitudes are wanted (so.amp
 // is then non-null).
 template <int NCH, bool AMP, class W, typename Fill, typename Scan>
@@ -605,14 +611,21 @@ __device__ void cluster_unit(W& w, const KParams& kp, uint32_t det0, uint32_t to
       }
     }
   } else {
+    // chunks of whole channels; without amplitudes the kept records go to the
+    // warp's spill area as they are formed (one pass), else they are counted now
+    // and formed again once their region is allocated
     load_masks<NCH>(w, kp, ch0);
+    uint4* spill = amps || !kp.spill || spill_warp() >= kp.spill_warps ? nullptr
+                                                                        : kp.spill + (size_t)spill_warp() * kSpillRecords;
     for (int c0 = 0; c0 < NCH;) {
       const int c1 = chunk_end<NCH>(w, c0);
       const int nn = (int)(w.chan_cnt[c1] - w.chan_cnt[c0]);
       if (nn > 0) {
         fill(c0, c1, false);
         const int no = scan(nn, false);
-        if (no > 0) found += form_unit<AMP>(w, kp, nn, 0, no, det0, nullptr, 0, 0, nullptr, nullptr, amps ? &wsum : nullptr);
+        if (no > 0)
+          found += form_unit<AMP>(w, kp, nn, 0, no, det0, spill, spill ? kSpillRecords : 0u, found, nullptr, nullptr,
+                                  amps ? &wsum : nullptr);
       }
       c0 = c1;
     }
@@ -657,6 +670,12 @@ __device__ void cluster_unit(W& w, const KParams& kp, uint32_t det0, uint32_t to
     if (n_own > 64) form_unit<AMP>(w, kp, n, 64, n_own, det0, so.stage, so.cap, (uint64_t)start + found0 + found1);
   } else if (single) {
     form_unit<AMP>(w, kp, n, 0, n_own, det0, so.stage, so.cap, start, nullptr, nullptr, nullptr, &ap);
+  } else if (!amps && kp.spill && spill_warp() < kp.spill_warps && found <= kSpillRecords) {
+    // every record of the chunked unit is in the warp's spill area
+    const uint4* spill = kp.spill + (size_t)spill_warp() * kSpillRecords;
+    __syncwarp();  // the lanes' spilled records are visible to the whole warp
+    for (uint32_t i = lane; i < found; i += 32)
+      if ((uint64_t)start + i < so.cap) so.stage[(uint64_t)start + i] = spill[i];
   } else {
     uint64_t base = start;
     for (int c0 = 0; c0 < NCH;) {

@@ -392,6 +392,7 @@ cudaError_t prepare_job(sst_host_pipe& p, const HostJob* job) {
   if (fits) return cudaSuccess;
   cudaError_t e = drain(p);
   if (!e) e = sst::ensure_scratch(p.scratch, (size_t)job->max_e * nf * sst::kFe, job->max_e, job->max_clu);
+  if (!e) e = sst::ensure_spill(p.scratch, (size_t)p.ctx->n_sm * sst::kMaxWarpsPerSm);
   for (PipeSlot& s : p.slots)
     if (!e) e = grow_slot(s, job->max_e, nf, job->max_bytes, job->max_clu);
   return e;

@@ -33,6 +33,8 @@ struct KParams {
   const uint32_t* badmask;  // [n_strips / 32], bit (s & 31) of word s / 32
   const float* qmul;        // [n_strips / 128]: per APV, a multiplier certified to give the
                             // gain-corrected charge of every ADC 0..253, or -gain (divide)
+  uint4* spill = nullptr;   // the launch's spill areas (one per warp of the grid, kSpillRecords records each)
+  uint32_t spill_warps = 0; // warps that have one
 };
 
 
@@ -62,6 +64,8 @@ struct Scratch {
   uint4* stage = nullptr;            // staged cluster records (16 bytes each)
   size_t stage_cap = 0;
   uint32_t* tickets = nullptr;       // [16] work counters
+  uint4* spill = nullptr;            // per warp, kSpillRecords cluster records of a chunked work item
+  size_t spill_warps = 0;            // warps that have a spill area (a warp beyond them counts its chunks twice)
   uint32_t lb_spin_limit = 0;        // polls before a look-back wait gives up (0: the default, about a second)
   int32_t lb_withhold = -1;          // failure tests: the FED that never publishes its count (-1: none)
   // optional cluster amplitudes
@@ -74,6 +78,8 @@ struct Scratch {
   size_t amp_items_cap = 0, amp_ev_cap = 0;
 };
 constexpr uint32_t kNoAmp = 0xFFFFFFFFu;
+constexpr uint32_t kSpillRecords = 1024;  // records per warp spill area (16 KiB)
+constexpr int kMaxWarpsPerSm = 32;        // resident warps of the batched kernel per SM (its register use)
 
 size_t smem_bytes(int tile);
 size_t batch_smem(int units, int block);  // shared memory per CTA of the batched kernel
@@ -138,6 +144,9 @@ sst_status set_err(sst_ctx* c, sst_status code, const std::string& msg);
 sst_status cuda_err(sst_ctx* c, cudaError_t e, const char* where);
 KParams kparams(const sst_ctx* c);
 cudaError_t ensure_scratch(Scratch& s, size_t items, size_t events, size_t stage_records);
+// Spill areas for `warps` warps (the batched kernel's resident warps, or one per FE
+// unit for the per-event cluster kernel); grows only.
+cudaError_t ensure_spill(Scratch& s, size_t warps);
 cudaError_t ensure_amp_scratch(Scratch& s, size_t items, size_t events, size_t amp_bytes);
 void free_scratch(Scratch& s);
 void free_host_pipe(sst_ctx* ctx);

@@ -1089,6 +1089,14 @@ cudaError_t launch_unpack_t(const uint8_t* raw, const uint32_t* fed_len, uint32_
   return cudaGetLastError();
 }
 
+// The kernels' parameters with the stream's spill areas.
+KParams with_spill(const KParams& kp, const Scratch& s) {
+  KParams k = kp;
+  k.spill = s.spill;
+  k.spill_warps = (uint32_t)s.spill_warps;
+  return k;
+}
+
 // The amplitude arguments of a launch: none unless the caller asked for them.
 AmpArgs amp_args(const sst_clusters& out, const Scratch& s) {
   AmpArgs a;
@@ -1132,11 +1140,12 @@ cudaError_t launch_cluster_fe(const sst_digis& in, uint32_t n_feds, const KParam
   cudaError_t e = prepare(fn, sh.block, sm, &per_sm);
   if (e) return e;
   const uint32_t units = n_feds * kFe;
+  const KParams kps = with_spill(kp, s);
   if (am.stage)
-    k_cluster<true><<<(units + nw - 1) / nw, sh.block, sm, st>>>(in, n_feds, kp, s.stage, cap, s.ev_alloc, s.fed_cnt,
+    k_cluster<true><<<(units + nw - 1) / nw, sh.block, sm, st>>>(in, n_feds, kps, s.stage, cap, s.ev_alloc, s.fed_cnt,
                                                                s.fed_start, am);
   else
-    k_cluster<false><<<(units + nw - 1) / nw, sh.block, sm, st>>>(in, n_feds, kp, s.stage, cap, s.ev_alloc,
+    k_cluster<false><<<(units + nw - 1) / nw, sh.block, sm, st>>>(in, n_feds, kps, s.stage, cap, s.ev_alloc,
                                                                 s.fed_cnt, s.fed_start, am);
   return cudaGetLastError();
 }
@@ -1155,12 +1164,13 @@ cudaError_t launch_batch_t(const uint8_t* raw, const uint32_t* fed_len, uint32_t
   const size_t ctas = (size_t)n_sm * (sh.ctas_per_sm < per_sm ? sh.ctas_per_sm : per_sm);
   const size_t need = (units + nw - 1) / nw;
   const int grid = (int)(ctas < need ? ctas : need);
+  const KParams kps = with_spill(kp, s);
   if (AMP) {
-    k_batch<AMP, U><<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out_cap, status, kp,
+    k_batch<AMP, U><<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out_cap, status, kps,
                                                 s.stage, s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets, s.unit_desc,
                                                 am);
   } else if ((e = launch_pdl(k_batch<AMP, U>, (unsigned)grid, (unsigned)sh.block, sm, st, raw, fed_len,
-                             (const uint64_t*)s.fed_off, n_events, n_feds, clu_off, out_cap, status, kp, s.stage,
+                             (const uint64_t*)s.fed_off, n_events, n_feds, clu_off, out_cap, status, kps, s.stage,
                              s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets, (const uint2*)s.unit_desc, am))) {
     return e;
   }

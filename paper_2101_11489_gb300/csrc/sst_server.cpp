@@ -228,7 +228,7 @@ HostClusters region_arrays(uint8_t* base, uint64_t n) {
   return h;
 }
 
-cudaError_t init_slot(Slot& s, const sst_server_opts& o, size_t raw_cap, uint32_t n_feds) {
+cudaError_t init_slot(Slot& s, const sst_server_opts& o, size_t raw_cap, uint32_t n_feds, int n_sm) {
   cudaError_t e;
   const uint32_t E = o.max_batch_events;
   s.raw_cap = raw_cap;
@@ -237,6 +237,7 @@ cudaError_t init_slot(Slot& s, const sst_server_opts& o, size_t raw_cap, uint32_
   if ((e = cudaEventCreateWithFlags(&s.ev_status, cudaEventDisableTiming))) return e;
   if ((e = cudaEventCreateWithFlags(&s.ev_done, cudaEventDisableTiming))) return e;
   if ((e = sst::ensure_scratch(s.scratch, (size_t)E * n_feds * sst::kFe, E, s.clu_cap))) return e;
+  if ((e = sst::ensure_spill(s.scratch, (size_t)n_sm * sst::kMaxWarpsPerSm))) return e;
   if ((e = dalloc(&s.d_raw, raw_cap))) return e;
   if ((e = dalloc(&s.d_event_off, E + 1)) || (e = dalloc(&s.d_fed_len, (size_t)E * n_feds)) ||
       (e = dalloc(&s.d_clu_off, E + 1)) || (e = dalloc(&s.d_status, E)) || (e = dalloc(&s.d_pack_off, E + 1)))
@@ -435,7 +436,7 @@ sst_status sst_server_start(sst_ctx* ctx, const sst_server_opts* opts) {
   if (!e) e = cudaHostAlloc(reinterpret_cast<void**>(&sv->res_pool), sv->res_cap, cudaHostAllocDefault);
   sv->res_alloc.reset(sv->res_cap);
   sv->slots.resize(o.max_inflight);
-  for (uint32_t i = 0; i < o.max_inflight && !e; i++) e = init_slot(sv->slots[i], o, raw_cap, o.n_feds);
+  for (uint32_t i = 0; i < o.max_inflight && !e; i++) e = init_slot(sv->slots[i], o, raw_cap, o.n_feds, ctx->n_sm);
   if (e) {
     for (Slot& s : sv->slots) free_slot(s);
     if (sv->host_pool) cudaFreeHost(sv->host_pool);
