@@ -149,9 +149,11 @@ __device__ __forceinline__ uint32_t walk_runs(const uint8_t* r, uint32_t len, ui
 // channel c's runs and counts its digis in one walk and, when the units are
 // staged and their slots fit, writes a slot descriptor for every valid run.  The
 // counts are prefix-summed into chan_cnt.  Returns the digi count; *flags / *nbad
-// receive the OR of the channel statuses and the number of bad channels.
+// receive the OR of the channel statuses and the number of bad channels.  src is
+// un.src, passed separately so that a caller that knows it is the staging buffer
+// lets the compiler read it as shared memory.
 template <class W>
-__device__ uint32_t parse_unit(W& w, const Unit& un, uint32_t* flags, uint32_t* nbad) {
+__device__ uint32_t parse_unit(W& w, const Unit& un, const uint8_t* src, uint32_t* flags, uint32_t* nbad) {
   const int lane = threadIdx.x & 31;
   uint32_t* slots = slot_area(w);
   const bool sl = use_slots<W>(un);
@@ -171,7 +173,7 @@ __device__ uint32_t parse_unit(W& w, const Unit& un, uint32_t* flags, uint32_t* 
         if (p + 2 > end) {
           good = false;
         } else {
-          l = (uint32_t)un.src[base + p] | ((uint32_t)un.src[base + p + 1] << 8);
+          l = (uint32_t)src[base + p] | ((uint32_t)src[base + p + 1] << 8);
           if (l < 3 || p + l > end) good = false;
         }
       }
@@ -191,7 +193,7 @@ __device__ uint32_t parse_unit(W& w, const Unit& un, uint32_t* flags, uint32_t* 
     const uint32_t len = st ? 0u : w.chan_len[lane];
     if (st == 0 && len >= 3) {
       const uint32_t pos = w.chan_pos[lane];
-      const uint8_t* r = un.src + pos;
+      const uint8_t* r = src + pos;
       if (r[2] != SST_ZS_CODE)
         st = SST_CH_BAD_CODE;
       else if (sl)
@@ -256,7 +258,7 @@ __device__ void mark_slots(W& w, const Unit& un) {
 // descriptor and run-start bit; the walk is bounded by the counted digis, so that
 // it cannot leave the tile.
 template <class W>
-__device__ void mark_walk(W& w, const Unit& un, int c0, int c1) {
+__device__ void mark_walk(W& w, const uint8_t* src, int c0, int c1) {
   const int lane = threadIdx.x & 31;
   if (lane < W::kRsWords) w.rs[lane] = 0u;
   __syncwarp();
@@ -265,7 +267,7 @@ __device__ void mark_walk(W& w, const Unit& un, int c0, int c1) {
     const uint32_t cnt = w.chan_cnt[c + 1] - w.chan_cnt[c];
     uint32_t o = w.chan_cnt[c] - w.chan_cnt[c0];
     const uint32_t pos = w.chan_pos[c];
-    const uint8_t* r = un.src + pos;
+    const uint8_t* r = src + pos;
     const uint32_t len_c = w.chan_len[c];
     uint32_t p = 3, left = cnt;
     while (p + 2 <= len_c && left > 0) {

@@ -934,37 +934,43 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
     fe::load_calib<W::kChW>(w, kp, ch0);
     const fe::Unit un = fe::locate(w, raw + (in_range ? fo : 0), unit_desc[item * kFe + u],
                                    unit_desc[item * kFe + u + (U - 1)], f, u);
-    uint32_t flags, nbad;
-    const uint32_t total = fe::parse_unit(w, un, &flags, &nbad);
-    if (lane == 0) {
-      if (flags) atomicOr(&status[e].flags, flags);
-      if (nbad) atomicAdd(&status[e].n_bad_channels, nbad);
-      if (total) atomicAdd(&status[e].n_digi, total);
-    }
-    const uint64_t off = clu_off[e];
-    const uint64_t end = clu_off[e + 1] < out_cap ? clu_off[e + 1] : out_cap;
-    const uint64_t cap = end > off ? end - off : 0;
-    fe::SegOut so{stage + (off < out_cap ? off : 0), cap, ev_alloc + e, seg_cnt + item * kItems + p,
-                  seg_start + item * kItems + p};
-    if (AMP) {
-      uint64_t a0, a1;
-      amp_slice(am, e, &a0, &a1);
-      so.amp = am.stage + a0;
-      so.amp_cap = a1 - a0;
-      so.amp_alloc = am.alloc + e;
-      so.seg_amp_cnt = am.cnt + item * kItems + p;
-      so.seg_amp_start = am.start + item * kItems + p;
-    }
-    const bool slots = fe::use_slots<W>(un);
-    auto fill = [&](int c0, int c1, bool single) {
-      if (single && slots) fe::mark_slots(w, un);
-      else fe::mark_walk(w, un, c0, c1);
+    // the rest of the item; src is the staging buffer for a staged item, so that
+    // its bytes are read as shared memory there (two inlined copies)
+    auto body = [&](const uint8_t* src) {
+      uint32_t flags, nbad;
+      const uint32_t total = fe::parse_unit(w, un, src, &flags, &nbad);
+      if (lane == 0) {
+        if (flags) atomicOr(&status[e].flags, flags);
+        if (nbad) atomicAdd(&status[e].n_bad_channels, nbad);
+        if (total) atomicAdd(&status[e].n_digi, total);
+      }
+      const uint64_t off = clu_off[e];
+      const uint64_t end = clu_off[e + 1] < out_cap ? clu_off[e + 1] : out_cap;
+      const uint64_t cap = end > off ? end - off : 0;
+      fe::SegOut so{stage + (off < out_cap ? off : 0), cap, ev_alloc + e, seg_cnt + item * kItems + p,
+                    seg_start + item * kItems + p};
+      if (AMP) {
+        uint64_t a0, a1;
+        amp_slice(am, e, &a0, &a1);
+        so.amp = am.stage + a0;
+        so.amp_cap = a1 - a0;
+        so.amp_alloc = am.alloc + e;
+        so.seg_amp_cnt = am.cnt + item * kItems + p;
+        so.seg_amp_start = am.start + item * kItems + p;
+      }
+      const bool slots = fe::use_slots<W>(un);
+      auto fill = [&](int c0, int c1, bool single) {
+        if (single && slots) fe::mark_slots(w, un);
+        else fe::mark_walk(w, src, c0, c1);
+      };
+      const uint32_t* cal = kp.cal + (size_t)ch0 * kStrips;
+      const float* nsqt = kp.nsq + (size_t)ch0 * kStrips;
+      const uint32_t src_end = un.off1 + un.len1;
+      auto scan = [&](int nn, bool) { return fe::scan_unit<W::kChW, true>(w, kp, cal, nsqt, src, src_end, nn); };
+      fe::cluster_unit<W::kChW, AMP>(w, kp, ch0, total, fill, scan, so, &status[e]);
     };
-    const uint32_t* cal = kp.cal + (size_t)ch0 * kStrips;
-    const float* nsqt = kp.nsq + (size_t)ch0 * kStrips;
-    const uint32_t src_end = un.off1 + un.len1;
-    auto scan = [&](int nn, bool) { return fe::scan_unit<W::kChW, true>(w, kp, cal, nsqt, un.src, src_end, nn); };
-    fe::cluster_unit<W::kChW, AMP>(w, kp, ch0, total, fill, scan, so, &status[e]);
+    if (un.staged) body(w.fe);
+    else body(un.src);
     __syncwarp();
   }
   pdl_release();
