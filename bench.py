@@ -344,14 +344,15 @@ def algorithmic_bytes(events, n_digi, n_clusters):
 def kernel_bytes(events, n_digi, n_clusters):
     """Bytes the batched kernel's own dataflow touches per launch (a finer model
     than algorithmic_bytes, for comparison with the measured DRAM traffic): the
-    payload, the per-strip calibration word and noise^2 of every recorded strip (4
-    + 4 B), the APV multipliers (8 B per channel), the channel map (64 B per FE
-    unit, written by the prologue and read), the unit descriptors and FED offsets
-    (8 B per FE unit, 8 B per FED), the staged cluster records (16 B per cluster)
-    and the event status."""
+    payload; the per-strip calibration word and noise^2 of every recorded strip (4
+    + 4 B); the APV multipliers (8 B per channel); the FE-unit descriptors the
+    prologue wrote (8 B per unit) and the FED lengths and offsets (4 + 8 B per
+    FED); the staged cluster records (16 B per cluster); the event status.  The
+    bad-strip masks are read only when clusters are widened over bad strips, which
+    the default parameters do not."""
     payload = sum(int(e[0].size) for e in events)
     n_feds = sum(int(e[1].size) for e in events)
-    return (payload + 8 * n_digi + n_feds * 96 * 8 + n_feds * 8 * (2 * 64 + 8) + 12 * n_feds + 16 * n_clusters
+    return (payload + 8 * n_digi + n_feds * 96 * 8 + n_feds * 8 * 8 + 12 * n_feds + 16 * n_clusters
             + 16 * len(events))
 
 
@@ -699,8 +700,8 @@ def main():
                          "traffic_model": {"bytes": int(b_kern), "achieved": round(b_kern / (k_ms / 1e3) / 1e9, 1),
                                            "frac": round(b_kern / (k_ms / 1e3) / 1e9 / peak, 4),
                                            "what": "the kernel's own dataflow: calibration word and noise^2 per "
-                                                   "recorded strip, APV multipliers, channel map, unit "
-                                                   "descriptors, staged cluster records"},
+                                                   "recorded strip, APV multipliers, FE-unit "
+                                                   "descriptors, FED lengths and offsets, staged cluster records"},
                          "peak_kind": peak_kind, "issue": issue},
             "served": served,
             "cpu_baseline": cpu,

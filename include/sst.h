@@ -177,11 +177,14 @@ typedef struct {
 typedef struct sst_ctx sst_ctx;
 
 /* Creates a context on CUDA device `device` for a detector of n_feds FEDs
- * (calibration covers n_feds * 96 * 256 strips).  INVALID_ARG if n_feds is 0 or
- * above SST_MAX_FEDS; CUDA if the device cannot be used. */
+ * (section 2's readout geometry: FEDs of 96 channels of 256 strips; calibration
+ * covers n_feds * 96 * 256 strips).  INVALID_ARG if n_feds is 0 or above
+ * SST_MAX_FEDS; CUDA if the device cannot be used. */
 sst_status sst_create(sst_ctx** out, int device, uint32_t n_feds);
 
-/* Waits for the context's work, stops the server if running, frees everything. */
+/* Waits for the context's work, stops the server if running, frees everything
+ * (the device memory section 3 keeps resident across events: calibration and
+ * scratch). */
 sst_status sst_destroy(sst_ctx* ctx);
 
 /* Text of the last error on this context (static storage, never NULL). */
@@ -423,7 +426,10 @@ typedef struct {
                                 must stay unchanged until sst_poll returns for the ticket */
 } sst_server_opts;
 
-/* Starts the request loop (one host thread, max_inflight streams).  Requires
+/* Starts the request loop (one host thread, max_inflight streams): section 3's
+ * events processed concurrently on one GPU as they arrive, with their transfers
+ * overlapped with the computation and device memory taken once (the paper's
+ * caching allocator), here carved from mem_budget_bytes at start.  Requires
  * calibration.  STATE if already running. */
 sst_status sst_server_start(sst_ctx* ctx, const sst_server_opts* opts);
 
@@ -454,7 +460,8 @@ typedef struct {
   double t_done_us;   /* host clock when the loop saw the event's launch complete */
 } sst_result_info;
 
-/* Waits up to timeout_us (0 = just check, < 0 = forever) for ticket's result.
+/* Waits up to timeout_us (0 = just check, < 0 = forever) for ticket's result
+ * (section 3: the served events' results, in whatever order they finish).
  * On OK copies the status and up to `capacity` clusters to the HOST arrays (any
  * may be NULL to skip) and releases the request slot and the event's host bytes.
  * NOT_READY on timeout; INVALID_ARG for an unknown ticket; STATE when the server
