@@ -464,8 +464,11 @@ typedef struct {
  * (section 3: the served events' results, in whatever order they finish).
  * On OK copies the status and up to `capacity` clusters to the HOST arrays (any
  * may be NULL to skip) and releases the request slot and the event's host bytes.
- * NOT_READY on timeout; INVALID_ARG for an unknown ticket; STATE when the server
- * is (or gets) stopped.  Thread safe. */
+ * NOT_READY on timeout; INVALID_ARG for an unknown ticket (or one that another
+ * caller collects meanwhile: a ticket's result is handed out once); STATE when
+ * the server is (or gets) stopped.  Thread safe: the copy out runs without the
+ * server's lock, so callers collecting different tickets do not wait for one
+ * another, nor hold up sst_submit. */
 sst_status sst_poll(sst_ctx* ctx, uint64_t ticket, int64_t timeout_us, sst_result_info* info, uint32_t* det,
                     uint16_t* first, uint16_t* width, uint32_t* charge, float* barycenter, uint64_t capacity);
 

@@ -26,8 +26,7 @@ KParams kparams(const sst_ctx* c) {
   k.max_holes = c->params.max_seq_holes;
   k.max_bad = c->params.max_seq_bad;
   k.max_adj = c->params.max_adj_bad;
-  k.cal = c->cal;
-  k.nsq = c->nsq;
+  k.calq = c->calq;
   k.badmask = c->badmask;
   k.qmul = c->qmul;
   return k;
@@ -207,8 +206,7 @@ sst_status sst_destroy(sst_ctx* ctx) {
     cudaEventDestroy(pr.second);
   }
   free_scratch(ctx->scratch);
-  if (ctx->cal) cudaFree(ctx->cal);
-  if (ctx->nsq) cudaFree(ctx->nsq);
+  if (ctx->calq) cudaFree(ctx->calq);
   if (ctx->badmask) cudaFree(ctx->badmask);
   if (ctx->qmul) cudaFree(ctx->qmul);
   if (ctx->pitch) cudaFree(ctx->pitch);
@@ -241,9 +239,8 @@ sst_status sst_calib_upload(sst_ctx* ctx, const float* noise, const float* gain,
   DeviceGuard g(ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
-  if (!ctx->cal) {
-    if ((e = cudaMalloc(&ctx->cal, n * sizeof(uint32_t)))) return cuda_err(ctx, e, "cudaMalloc cal");
-    if ((e = cudaMalloc(&ctx->nsq, n * sizeof(float)))) return cuda_err(ctx, e, "cudaMalloc nsq");
+  if (!ctx->calq) {
+    if ((e = cudaMalloc(&ctx->calq, n * sizeof(uint2)))) return cuda_err(ctx, e, "cudaMalloc calq");
     if ((e = cudaMalloc(&ctx->badmask, n / 8))) return cuda_err(ctx, e, "cudaMalloc badmask");
     if ((e = cudaMalloc(&ctx->qmul, n_apv * sizeof(float)))) return cuda_err(ctx, e, "cudaMalloc qmul");
   }
@@ -261,7 +258,7 @@ sst_status sst_calib_upload(sst_ctx* ctx, const float* noise, const float* gain,
   if (!e) e = cudaMemcpyAsync(ctx->qmul, qmul.data(), n_apv * sizeof(float), cudaMemcpyHostToDevice, st);
   if (!e) e = cudaMemcpyAsync(bad_dev, bad, n, cudaMemcpyHostToDevice, st);
   if (!e) e = build_badmask(bad_dev, ctx->badmask, n, st);
-  if (!e) e = build_calib(noise_dev, ctx->badmask, ctx->cal, ctx->nsq, n, *params, st);
+  if (!e) e = build_calib(noise_dev, ctx->badmask, ctx->calq, n, *params, st);
   if (!e) e = cudaStreamSynchronize(st);
   cudaFree(bad_dev);
   cudaFree(noise_dev);

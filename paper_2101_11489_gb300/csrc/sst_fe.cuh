@@ -157,9 +157,9 @@ __device__ uint32_t parse_unit(W& w, const Unit& un, const uint8_t* src, uint32_
   const int lane = threadIdx.x & 31;
   uint32_t* slots = slot_area(w);
   const bool sl = use_slots<W>(un);
-  if (sl) {
-    const uint32_t ns = n_slots(un);
-    for (uint32_t i = lane; i < ns; i += 32) slots[i] = 0u;
+  if (sl) {  // 16-byte stores: the slot area is a whole number of 16-byte vectors
+    const uint32_t nv = (n_slots(un) + 3u) / 4u;
+    for (uint32_t i = lane; i < nv; i += 32) reinterpret_cast<uint4*>(slots)[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   if ((lane & 15) == 0 && (lane >> 4) < W::kUnits) {
     const int h = lane >> 4;
@@ -309,8 +309,8 @@ __device__ void mark_walk(W& w, const uint8_t* src, int c0, int c1) {
 // The first digis of owned candidates are compacted in strip order into own[];
 // returns their number.  src / src_end: the pair's bytes (EXP).
 template <int NCH, bool EXP, class W>
-__device__ int scan_unit(W& w, const KParams& kp, const uint32_t* __restrict__ cal,
-                         const float* __restrict__ nsqt, const uint8_t* src, uint32_t src_end, int n) {
+__device__ int scan_unit(W& w, const KParams& kp, const uint2* __restrict__ calq, const uint8_t* src,
+                         uint32_t src_end, int n) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt(lane);
   const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
@@ -345,18 +345,16 @@ __device__ int scan_unit(W& w, const KParams& kp, const uint32_t* __restrict__ c
   };
   uint32_t wn = word_at(0);
   uint32_t xn = ((wn >> 8) & 31u) < (uint32_t)NCH ? (wn & 0x1FFFu) : 0u;
-  uint32_t cn = __ldg(cal + xn);
-  float zn = __ldg(nsqt + xn);
+  uint2 vn = __ldg(calq + xn);
   for (int base = 0; base < n; base += 32) {
     const int i = base + lane;
     const uint32_t word = wn;
-    const uint32_t cv = cn;
-    const float nq = zn;
+    const uint32_t cv = vn.x;
+    const float nq = __uint_as_float(vn.y);
     if (base + 32 < n) {
       wn = word_at(base + 32);
       xn = ((wn >> 8) & 31u) < (uint32_t)NCH ? (wn & 0x1FFFu) : 0u;
-      cn = __ldg(cal + xn);
-      zn = __ldg(nsqt + xn);
+      vn = __ldg(calq + xn);
     }
     const uint32_t key = word & 0x1FFFu;
     const uint32_t c = key >> 8, st = key & 255u;
@@ -368,7 +366,7 @@ __device__ int scan_unit(W& w, const KParams& kp, const uint32_t* __restrict__ c
     // gain-corrected charge with the APV's multiplier; an APV without a certified
     // multiplier (rq < 0) divides, in a branch the whole warp takes together
     const float a = __uint2float_rn(adc);
-    const float rq = w.qmul[(inr ? c : 0u) * 2 + (st >> 7)];
+    const float rq = w.qmul[inr ? key >> 7 : 0u];  // the APV of strip st of channel c: 2 c + (st >> 7)
     float xq = __fmul_rn(a, rq);
     if (__any_sync(0xffffffffu, rq < 0.f))
       if (rq < 0.f) xq = __fdiv_rn(a, -rq);
@@ -737,7 +735,8 @@ template <class W>
 constexpr bool layout_ok() {
   return 8 * sizeof(W) + 1024 <= 233472 / 4 &&  // 8 warps per CTA fit 4 CTAs per SM
          offsetof(W, bad) % 16 == 0 && offsetof(W, qmul) % 16 == 0 && sizeof(W) % 16 == 0 &&  // vector loads
-         offsetof(W, bad) == offsetof(W, own) + sizeof(uint16_t) * W::kTile && offsetof(W, own) % 4 == 0 &&
+         offsetof(W, bad) == offsetof(W, own) + sizeof(uint16_t) * W::kTile && offsetof(W, own) % 16 == 0 &&
+         W::kSlots % 4 == 0 &&  // the slot area is cleared with 16-byte stores
          W::kSlots * 4 <= sizeof(uint16_t) * W::kTile + sizeof(uint32_t) * W::kChW * kMaskWords &&  // slots
          W::kBuf % 8 == 0 && W::kBuf < 2048;  // staging in 8-byte words; ADC positions take 11 bits of a slot
 }

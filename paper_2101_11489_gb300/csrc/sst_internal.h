@@ -28,8 +28,8 @@ constexpr int kMaskWords = kStrips / 32;     // 8 words of 32 strips per channel
 struct KParams {
   float t_cluster;
   int max_holes, max_bad, max_adj;
-  const uint32_t* cal;      // [n_strips]: thr_ch | thr_seed << 8 | gap << 16 (see k_calib_pack)
-  const float* nsq;         // [n_strips]: noise^2, binary32
+  const uint2* calq;        // [n_strips]: {thr_ch | thr_seed << 8 | gap << 16, noise^2 (binary32 bits)}
+                            // (see k_calib_pack); one 8-byte load per recorded strip
   const uint32_t* badmask;  // [n_strips / 32], bit (s & 31) of word s / 32
   const float* qmul;        // [n_strips / 128]: per APV, a multiplier certified to give the
                             // gain-corrected charge of every ADC 0..253, or -gain (divide)
@@ -109,7 +109,7 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
                          const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st,
                          uint64_t* pack_off = nullptr, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st);
-cudaError_t build_calib(const float* noise_dev, const uint32_t* mask_dev, uint32_t* cal_dev, float* nsq_dev,
+cudaError_t build_calib(const float* noise_dev, const uint32_t* mask_dev, uint2* calq_dev,
                         uint64_t n_strips, const sst_params& p, cudaStream_t st);
 
 }  // namespace sst
@@ -123,8 +123,7 @@ struct sst_ctx {
   int n_sm = 0;
   bool has_calib = false;
   sst_params params{};
-  uint32_t* cal = nullptr;     // per strip: channel and seed thresholds as ADC limits, linking gap
-  float* nsq = nullptr;        // per strip: noise^2
+  uint2* calq = nullptr;       // per strip: channel and seed thresholds as ADC limits and linking gap; noise^2
   uint32_t* badmask = nullptr;
   float* qmul = nullptr;       // per APV: certified multiplier or -gain
   sst::Scratch scratch;

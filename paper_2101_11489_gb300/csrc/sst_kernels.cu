@@ -894,9 +894,8 @@ __global__ void __launch_bounds__(256, 4) k_cluster(sst_digis in, uint32_t n_fed
     so.seg_amp_cnt = am.cnt + unit;
     so.seg_amp_start = am.start + unit;
   }
-  const uint32_t* cal = kp.cal + g0;
-  const float* nsqt = kp.nsq + g0;
-  auto scan = [&](int nn, bool) { return fe::scan_unit<kChPerFe, false>(w, kp, cal, nsqt, nullptr, 0u, nn); };
+  const uint2* calq = kp.calq + g0;
+  auto scan = [&](int nn, bool) { return fe::scan_unit<kChPerFe, false>(w, kp, calq, nullptr, 0u, nn); };
   fe::cluster_unit<kChPerFe, AMP>(w, kp, ch0, total, fill, scan, so, in.status);
 }
 
@@ -963,10 +962,9 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
         if (single && slots) fe::mark_slots(w, un);
         else fe::mark_walk(w, src, c0, c1);
       };
-      const uint32_t* cal = kp.cal + (size_t)ch0 * kStrips;
-      const float* nsqt = kp.nsq + (size_t)ch0 * kStrips;
+      const uint2* calq = kp.calq + (size_t)ch0 * kStrips;
       const uint32_t src_end = un.off1 + un.len1;
-      auto scan = [&](int nn, bool) { return fe::scan_unit<W::kChW, true>(w, kp, cal, nsqt, src, src_end, nn); };
+      auto scan = [&](int nn, bool) { return fe::scan_unit<W::kChW, true>(w, kp, calq, src, src_end, nn); };
       fe::cluster_unit<W::kChW, AMP>(w, kp, ch0, total, fill, scan, so, &status[e]);
     };
     if (un.staged) body(w.fe);
@@ -988,7 +986,8 @@ __global__ void k_badmask(const uint8_t* __restrict__ bad, uint32_t* __restrict_
 //   bits 0-7   thr_ch:   channel limit, the largest ADC that is NOT active;
 //   bits 8-15  thr_seed: seed limit, the largest ADC that is NOT a seed;
 //   bits 16-23 gap:      the longest linking gap below the strip;
-// and noise^2 per strip (binary32, rounded once), summed by the cluster threshold.
+// stored beside noise^2 of the strip (binary32, rounded once; summed by the
+// cluster threshold), so that the scan gathers both with one 8-byte load.
 //
 // Limits (section 2: a strip is active / a seed when its ADC is larger than the
 // channel / seed threshold times its noise): with P = T x noise rounded once in
@@ -1008,7 +1007,7 @@ __global__ void k_badmask(const uint8_t* __restrict__ bad, uint32_t* __restrict_
 // down from t-1.  A gap is at most 254 strips (a >= 0, t <= 255), so G(t) is
 // stored capped at 254 without changing any decision.
 __global__ void k_calib_pack(const float* __restrict__ noise, const uint32_t* __restrict__ mask,
-                             uint32_t* __restrict__ cal, float* __restrict__ nsq, uint64_t n_strips, float t_ch,
+                             uint2* __restrict__ calq, uint64_t n_strips, float t_ch,
                              float t_seed, int max_holes, int max_bad) {
   const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_strips) return;
@@ -1029,8 +1028,8 @@ __global__ void k_calib_pack(const float* __restrict__ noise, const uint32_t* __
     return p >= 255.f ? 255u : (uint32_t)p;  // truncation = floor for p >= 0
   };
   const uint32_t gap = (uint32_t)(g < 254 ? g : 254);
-  cal[s] = bad ? (255u | (255u << 8) | (gap << 16)) : (limit(t_ch) | (limit(t_seed) << 8) | (gap << 16));
-  nsq[s] = __fmul_rn(nz, nz);
+  const uint32_t word = bad ? (255u | (255u << 8) | (gap << 16)) : (limit(t_ch) | (limit(t_seed) << 8) | (gap << 16));
+  calq[s] = make_uint2(word, __float_as_uint(__fmul_rn(nz, nz)));
 }
 
 // ---------------------------------------------------------------- launch helpers
@@ -1327,9 +1326,9 @@ cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n
   return cudaGetLastError();
 }
 
-cudaError_t build_calib(const float* noise_dev, const uint32_t* mask_dev, uint32_t* cal_dev, float* nsq_dev,
-                        uint64_t n_strips, const sst_params& p, cudaStream_t st) {
-  k_calib_pack<<<(unsigned)((n_strips + 255) / 256), 256, 0, st>>>(noise_dev, mask_dev, cal_dev, nsq_dev, n_strips,
+cudaError_t build_calib(const float* noise_dev, const uint32_t* mask_dev, uint2* calq_dev, uint64_t n_strips,
+                        const sst_params& p, cudaStream_t st) {
+  k_calib_pack<<<(unsigned)((n_strips + 255) / 256), 256, 0, st>>>(noise_dev, mask_dev, calq_dev, n_strips,
                                                                    p.t_channel, p.t_seed, p.max_seq_holes,
                                                                    p.max_seq_bad);
   return cudaGetLastError();

@@ -23,6 +23,8 @@
 #include <thread>
 #include <vector>
 
+#include <sys/prctl.h>
+
 #include "sst_internal.h"
 
 namespace {
@@ -79,10 +81,15 @@ extern "C" sst_status sst_serve_load(sst_ctx* ctx, const uint8_t* const* raw, co
     cv.notify_all();
   };
   auto submitter = [&](uint32_t k) {
+    // sleep precisely (1 us timer slack instead of the default 50 us), so that a
+    // submitter wakes just before its next arrival and spins only briefly: at
+    // high rates spinning submitters would otherwise take the cores the server's
+    // loop thread and the pollers need
+    prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);
     for (uint64_t i = k; i < n_requests && !failed.load(); i += submitters) {
       const double when = t0 + due[i];
       for (double now = now_us(); now < when; now = now_us()) {
-        if (when - now > 200.0) std::this_thread::sleep_for(std::chrono::microseconds((int64_t)(when - now - 100.0)));
+        if (when - now > 40.0) std::this_thread::sleep_for(std::chrono::microseconds((int64_t)(when - now - 20.0)));
       }
       const uint32_t e = (uint32_t)(i % n_events);
       uint64_t tk = 0;
@@ -99,7 +106,8 @@ extern "C" sst_status sst_serve_load(sst_ctx* ctx, const uint8_t* const* raw, co
           return;
         }
         retries++;
-        std::this_thread::sleep_for(std::chrono::microseconds(10));
+        // the server is full: back off instead of contending for its lock
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
       }
       {
         std::lock_guard<std::mutex> g(mu);

@@ -96,7 +96,7 @@ class RangeAlloc {
   size_t cap_ = 0;
 };
 
-enum class ReqState { kFree, kPending, kLaunched, kDone };
+enum class ReqState { kFree, kPending, kLaunched, kDone, kCollecting };
 enum class SlotState { kFree, kRunning, kReading };
 
 struct Req {
@@ -152,7 +152,8 @@ struct sst_server {
   std::vector<Slot> slots;
   std::vector<Req> reqs;
   std::deque<int> pending;
-  uint64_t next_ticket = 1;
+  std::vector<int> free_reqs;  // request slots not in use (a stack)
+  uint64_t next_seq = 1;       // tickets: sequence number << 20 | request slot
   uint8_t* host_pool = nullptr;
   size_t host_cap = 0;
   RangeAlloc host_alloc;
@@ -255,36 +256,53 @@ void loop_main(sst_server* sv);
 
 namespace {
 
-// Forms the next batch from the pending queue and launches it on slot si.
-// Called with the lock held.  Returns false when nothing was pending.
-bool launch_on(sst_server* sv, int si) {
+// One event of a batch being formed: where its bytes and FED lengths are (stable
+// while its request is launched: only the loop thread touches such a request).
+struct Part {
+  const uint8_t* src;
+  uint64_t bytes;
+  const uint32_t* fed_len;
+};
+
+// Takes the next batch off the pending queue for slot si (FIFO, up to
+// max_batch_events and the slot's raw arena).  Lock held.  Returns false when
+// nothing was pending.
+bool take_batch(sst_server* sv, int si, std::vector<Part>* parts) {
   Slot& s = sv->slots[si];
-  const uint32_t nf = sv->opts.n_feds;
   s.reqs.clear();
+  parts->clear();
   uint64_t bytes = 0;
   while (!sv->pending.empty() && s.reqs.size() < sv->opts.max_batch_events) {
-    const Req& r = sv->reqs[sv->pending.front()];
+    Req& r = sv->reqs[sv->pending.front()];
     if (bytes + r.bytes > s.raw_cap) break;
     bytes += r.bytes;
+    r.state = ReqState::kLaunched;
+    r.slot = si;
+    r.index = (uint32_t)s.reqs.size();
+    parts->push_back(Part{r.src ? r.src : sv->host_pool + r.host_off, r.bytes, r.fed_len.data()});
     s.reqs.push_back(sv->pending.front());
     sv->pending.pop_front();
   }
-  if (s.reqs.empty()) return false;
-  const uint32_t E = (uint32_t)s.reqs.size();
+  return !s.reqs.empty();
+}
+
+// Launches a taken batch on slot si: copies the events into the slot's arena,
+// runs the batched unpack + cluster kernels, packs the events' clusters back to
+// back and reads back the statuses.  Called WITHOUT the lock (CUDA calls only,
+// on slot state that only the loop thread touches).
+cudaError_t launch_batch_on(sst_server* sv, int si, const std::vector<Part>& parts) {
+  Slot& s = sv->slots[si];
+  const uint32_t nf = sv->opts.n_feds;
+  const uint32_t E = (uint32_t)parts.size();
   uint64_t off = 0, coff = 0;
   cudaError_t e = cudaSuccess;
   for (uint32_t i = 0; i < E; i++) {
-    Req& r = sv->reqs[s.reqs[i]];
     s.h_event_off[i] = off;
     s.h_clu_off[i] = coff;
-    std::memcpy(s.h_fed_len + (size_t)i * nf, r.fed_len.data(), nf * sizeof(uint32_t));
-    const uint8_t* src = r.src ? r.src : sv->host_pool + r.host_off;
-    if (!e) e = cudaMemcpyAsync(s.d_raw + off, src, r.bytes, cudaMemcpyHostToDevice, s.st);
-    off += r.bytes;
-    coff += r.bytes / 2 + 1;
-    r.state = ReqState::kLaunched;
-    r.slot = si;
-    r.index = i;
+    std::memcpy(s.h_fed_len + (size_t)i * nf, parts[i].fed_len, nf * sizeof(uint32_t));
+    if (!e) e = cudaMemcpyAsync(s.d_raw + off, parts[i].src, parts[i].bytes, cudaMemcpyHostToDevice, s.st);
+    off += parts[i].bytes;
+    coff += parts[i].bytes / 2 + 1;
   }
   s.h_event_off[E] = off;
   s.h_clu_off[E] = coff;
@@ -298,80 +316,118 @@ bool launch_on(sst_server* sv, int si) {
   if (!e) e = cudaMemcpyAsync(s.h_status, s.d_status, E * sizeof(sst_event_status), cudaMemcpyDeviceToHost, s.st);
   if (!e) e = cudaMemcpyAsync(s.h_pack_off, s.d_pack_off, (E + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s.st);
   if (!e) e = cudaEventRecord(s.ev_status, s.st);
-  if (e) sv->fatal = std::string("served batch launch: ") + cudaGetErrorString(e);
-  s.state = SlotState::kRunning;
-  return true;
+  return e;
 }
 
-// Advances running slots; called with the lock held.  Returns true on progress.
-bool advance(sst_server* sv) {
-  bool progress = false;
-  for (Slot& s : sv->slots) {
-    if (s.state == SlotState::kRunning) {
-      const cudaError_t q = cudaEventQuery(s.ev_status);
-      if (q == cudaErrorNotReady) continue;
-      cudaError_t e = q;
-      const uint64_t total = s.h_pack_off[s.reqs.size()];
-      size_t off = 0;
-      if (!e && !sv->res_alloc.alloc(16 * total, &off)) {
-        sv->fatal = "served batch: results pool exhausted";  // excluded by its sizing
-        e = cudaErrorMemoryAllocation;
-      }
-      s.res_off = off;
-      s.res_total = total;
-      const sst_clusters& d = s.d_out;
-      const HostClusters h = region_arrays(sv->res_pool + off, total);
-      if (!e && total) {
-        e = cudaMemcpyAsync(h.det, d.det, total * 4, cudaMemcpyDeviceToHost, s.st);
-        if (!e) e = cudaMemcpyAsync(h.first, d.first, total * 2, cudaMemcpyDeviceToHost, s.st);
-        if (!e) e = cudaMemcpyAsync(h.width, d.width, total * 2, cudaMemcpyDeviceToHost, s.st);
-        if (!e) e = cudaMemcpyAsync(h.charge, d.charge, total * 4, cudaMemcpyDeviceToHost, s.st);
-        if (!e) e = cudaMemcpyAsync(h.bary, d.barycenter, total * 4, cudaMemcpyDeviceToHost, s.st);
-      }
-      if (!e) e = cudaEventRecord(s.ev_done, s.st);
-      if (e && sv->fatal.empty()) sv->fatal = std::string("served batch: ") + cudaGetErrorString(e);
-      s.state = SlotState::kReading;
-      progress = true;
-    }
-    if (s.state == SlotState::kReading) {
-      const cudaError_t q = cudaEventQuery(s.ev_done);
-      if (q == cudaErrorNotReady) continue;
-      if (q && sv->fatal.empty()) sv->fatal = std::string("served batch: ") + cudaGetErrorString(q);
-      const double t = now_us();
-      sv->regions[s.res_off] = std::make_pair((size_t)(16 * s.res_total), (int)s.reqs.size());
-      for (size_t i = 0; i < s.reqs.size(); i++) {
-        Req& r = sv->reqs[s.reqs[i]];
-        r.state = ReqState::kDone;
-        r.t_done = t;
-        r.status = s.h_status[i];
-        r.res_off = s.res_off;
-        r.res_total = s.res_total;
-        r.first = s.h_pack_off[i];
-      }
-      s.reqs.clear();
-      s.state = SlotState::kFree;
-      progress = true;
-      sv->cv_done.notify_all();
-    }
+// Issues the read-back of a finished batch's packed clusters into its results
+// region.  Called WITHOUT the lock.
+cudaError_t read_back(sst_server* sv, Slot& s) {
+  const uint64_t total = s.res_total;
+  const sst_clusters& d = s.d_out;
+  const HostClusters h = region_arrays(sv->res_pool + s.res_off, total);
+  cudaError_t e = cudaSuccess;
+  if (total) {
+    e = cudaMemcpyAsync(h.det, d.det, total * 4, cudaMemcpyDeviceToHost, s.st);
+    if (!e) e = cudaMemcpyAsync(h.first, d.first, total * 2, cudaMemcpyDeviceToHost, s.st);
+    if (!e) e = cudaMemcpyAsync(h.width, d.width, total * 2, cudaMemcpyDeviceToHost, s.st);
+    if (!e) e = cudaMemcpyAsync(h.charge, d.charge, total * 4, cudaMemcpyDeviceToHost, s.st);
+    if (!e) e = cudaMemcpyAsync(h.bary, d.barycenter, total * 4, cudaMemcpyDeviceToHost, s.st);
   }
-  return progress;
+  if (!e) e = cudaEventRecord(s.ev_done, s.st);
+  return e;
 }
 
+void set_fatal(sst_server* sv, const char* what, cudaError_t e) {  // lock held
+  if (sv->fatal.empty()) sv->fatal = std::string(what) + cudaGetErrorString(e);
+}
+
+// The loop thread.  The lock guards the requests, the pending queue, the pools'
+// allocators and the stop flag; the slots belong to this thread.  Each pass
+// queries the slots' CUDA events without the lock, takes the lock once to account
+// for what finished and to take new batches off the queue, and issues the
+// read-backs and launches without it: a slow driver call never holds up
+// sst_submit / sst_poll, and the lock changes hands twice per pass.
 void loop_main(sst_server* sv) {
   cudaSetDevice(sv->ctx->device);
+  const size_t ns = sv->slots.size();
+  std::vector<std::vector<Part>> parts(ns);
+  std::vector<cudaError_t> q(ns), err(ns);
+  enum Todo : char { kNothing, kReadBack, kLaunch };
+  std::vector<Todo> todo(ns, kNothing);
   std::unique_lock<std::mutex> lock(sv->mu);
   while (!sv->stop) {
-    bool progress = advance(sv);
-    for (size_t si = 0; si < sv->slots.size() && !sv->pending.empty(); si++)
-      if (sv->slots[si].state == SlotState::kFree && launch_on(sv, (int)si)) progress = true;
-    if (progress) continue;
-    bool busy = false;
-    for (const Slot& s : sv->slots)
-      busy |= s.state == SlotState::kRunning || s.state == SlotState::kReading;
-    if (busy)
-      sv->cv_loop.wait_for(lock, std::chrono::microseconds(20));
-    else
-      sv->cv_loop.wait_for(lock, std::chrono::milliseconds(5));
+    lock.unlock();
+    for (size_t si = 0; si < ns; si++) {
+      const Slot& s = sv->slots[si];
+      q[si] = s.state == SlotState::kRunning   ? cudaEventQuery(s.ev_status)
+              : s.state == SlotState::kReading ? cudaEventQuery(s.ev_done)
+                                               : cudaSuccess;
+    }
+    const double t = now_us();
+    lock.lock();
+    bool progress = false;
+    for (size_t si = 0; si < ns; si++) {
+      Slot& s = sv->slots[si];
+      todo[si] = kNothing;
+      if (q[si] == cudaErrorNotReady) continue;
+      if (s.state == SlotState::kRunning) {
+        if (q[si]) set_fatal(sv, "served batch: ", q[si]);
+        s.res_total = q[si] ? 0 : s.h_pack_off[s.reqs.size()];
+        s.res_off = 0;
+        if (!q[si] && !sv->res_alloc.alloc(16 * s.res_total, &s.res_off)) {
+          sv->fatal = "served batch: results pool exhausted";  // excluded by its sizing
+          s.res_total = 0;
+        }
+        s.state = SlotState::kReading;
+        todo[si] = kReadBack;
+        progress = true;
+        continue;
+      }
+      if (s.state == SlotState::kReading) {
+        if (q[si]) set_fatal(sv, "served batch: ", q[si]);
+        sv->regions[s.res_off] = std::make_pair((size_t)(16 * s.res_total), (int)s.reqs.size());
+        for (size_t i = 0; i < s.reqs.size(); i++) {
+          Req& r = sv->reqs[s.reqs[i]];
+          r.state = ReqState::kDone;
+          r.t_done = t;
+          r.status = s.h_status[i];
+          r.res_off = s.res_off;
+          r.res_total = s.res_total;
+          r.first = s.h_pack_off[i];
+        }
+        s.reqs.clear();
+        s.state = SlotState::kFree;
+        progress = true;
+        sv->cv_done.notify_all();
+      }
+      if (s.state == SlotState::kFree && sv->fatal.empty() && take_batch(sv, (int)si, &parts[si])) {
+        s.state = SlotState::kRunning;
+        todo[si] = kLaunch;
+        progress = true;
+      }
+    }
+    if (!progress) {
+      if (sv->stop) break;
+      bool busy = false;
+      for (const Slot& s : sv->slots)
+        busy |= s.state == SlotState::kRunning || s.state == SlotState::kReading;
+      // new events notify cv_loop; batches in flight are polled every 20 us
+      if (busy)
+        sv->cv_loop.wait_for(lock, std::chrono::microseconds(20));
+      else
+        sv->cv_loop.wait_for(lock, std::chrono::milliseconds(5),
+                             [&] { return sv->stop || (!sv->pending.empty() && sv->fatal.empty()); });
+      continue;
+    }
+    lock.unlock();
+    for (size_t si = 0; si < ns; si++) {
+      err[si] = todo[si] == kReadBack ? read_back(sv, sv->slots[si])
+                : todo[si] == kLaunch ? launch_batch_on(sv, (int)si, parts[si])
+                                      : cudaSuccess;
+    }
+    lock.lock();
+    for (size_t si = 0; si < ns; si++)
+      if (err[si]) set_fatal(sv, todo[si] == kLaunch ? "served batch launch: " : "served batch: ", err[si]);
   }
 }
 
@@ -381,11 +437,13 @@ void release(sst_server* sv, int ri) {
   Req& r = sv->reqs[ri];
   sv->host_alloc.release(r.host_off, r.bytes);
   auto it = sv->regions.find(r.res_off);
-  if (r.state == ReqState::kDone && it != sv->regions.end() && --it->second.second == 0) {
+  const bool finished = r.state == ReqState::kDone || r.state == ReqState::kCollecting;
+  if (finished && it != sv->regions.end() && --it->second.second == 0) {
     sv->res_alloc.release(it->first, it->second.first);
     sv->regions.erase(it);
   }
   r = Req{};
+  sv->free_reqs.push_back(ri);
 }
 
 }  // namespace
@@ -446,6 +504,8 @@ sst_status sst_server_start(sst_ctx* ctx, const sst_server_opts* opts) {
     return sst::cuda_err(ctx, e, "sst_server_start");
   }
   sv->reqs.resize(o.max_requests);
+  sv->free_reqs.reserve(o.max_requests);
+  for (uint32_t i = o.max_requests; i-- > 0;) sv->free_reqs.push_back((int)i);
   sv->loop = std::thread(loop_main, sv);
   {
     std::lock_guard<std::mutex> g(ctx->mu);
@@ -522,32 +582,34 @@ void release_server(sst_ctx* ctx, sst_server* sv) {
 sst_status submit_one(sst_ctx* ctx, sst_server* sv, const uint8_t* raw, uint64_t raw_bytes, const uint32_t* fed_len,
                       uint64_t* ticket) {
   if (raw_bytes > sv->max_event_bytes) return SST_ERR_TOO_LARGE;
+  std::vector<uint32_t> fl(fed_len, fed_len + sv->opts.n_feds);
+  const bool lend = sv->opts.zero_copy != 0;
   int ri = -1;
   size_t off = 0;
   {
     std::lock_guard<std::mutex> lock(sv->mu);
     if (!sv->fatal.empty()) return sst::set_err(ctx, SST_ERR_CUDA, sv->fatal);
-    for (size_t i = 0; i < sv->reqs.size(); i++)
-      if (sv->reqs[i].state == ReqState::kFree) {
-        ri = (int)i;
-        break;
-      }
-    if (ri < 0) return SST_ERR_BUSY;
+    if (sv->free_reqs.empty()) return SST_ERR_BUSY;
     if (!sv->host_alloc.alloc(raw_bytes, &off)) return SST_ERR_BUDGET;
+    ri = sv->free_reqs.back();
+    sv->free_reqs.pop_back();
     Req& r = sv->reqs[ri];
-    r.state = ReqState::kPending;  // reserved; not yet queued
+    r.state = ReqState::kPending;  // reserved; queued below (at once when the caller lends its buffer)
     r.host_off = off;
     r.bytes = raw_bytes;
-    r.ticket = sv->next_ticket++;
+    r.ticket = (sv->next_seq++ << 20) | (uint64_t)ri;
     *ticket = r.ticket;
+    if (lend) {
+      r.src = raw;
+      r.fed_len.swap(fl);
+      r.t_submit = now_us();
+      sv->pending.push_back(ri);
+    }
   }
-  // copy outside the lock (unless the caller lends its buffer), then queue
-  if (!sv->opts.zero_copy) std::memcpy(sv->host_pool + off, raw, raw_bytes);
-  std::vector<uint32_t> fl(fed_len, fed_len + sv->opts.n_feds);
-  {
+  if (!lend) {  // copy outside the lock, then queue
+    std::memcpy(sv->host_pool + off, raw, raw_bytes);
     std::lock_guard<std::mutex> lock(sv->mu);
     Req& r = sv->reqs[ri];
-    r.src = sv->opts.zero_copy ? raw : nullptr;
     r.fed_len.swap(fl);
     r.t_submit = now_us();
     sv->pending.push_back(ri);
@@ -560,36 +622,46 @@ sst_status poll_one(sst_ctx* ctx, sst_server* sv, uint64_t ticket, int64_t timeo
                     uint32_t* det, uint16_t* first, uint16_t* width, uint32_t* charge, float* barycenter,
                     uint64_t capacity) {
   std::unique_lock<std::mutex> lock(sv->mu);
-  int ri = -1;
-  for (size_t i = 0; i < sv->reqs.size(); i++)
-    if (sv->reqs[i].state != ReqState::kFree && sv->reqs[i].ticket == ticket) {
-      ri = (int)i;
-      break;
-    }
-  if (ri < 0) return sst::set_err(ctx, SST_ERR_INVALID_ARG, "sst_poll: unknown ticket");
-  auto done = [&] { return sv->reqs[ri].state == ReqState::kDone || !sv->fatal.empty() || sv->stop; };
+  const uint64_t slot = ticket & ((1u << 20) - 1u);  // a ticket names its request slot
+  const int ri = slot < sv->reqs.size() ? (int)slot : -1;
+  if (ri < 0 || sv->reqs[ri].ticket != ticket || sv->reqs[ri].state == ReqState::kFree ||
+      sv->reqs[ri].state == ReqState::kCollecting)
+    return sst::set_err(ctx, SST_ERR_INVALID_ARG, "sst_poll: unknown ticket");
+  // gone: another caller collected this ticket meanwhile
+  auto gone = [&] { return sv->reqs[ri].ticket != ticket || sv->reqs[ri].state == ReqState::kCollecting; };
+  auto done = [&] { return gone() || sv->reqs[ri].state == ReqState::kDone || !sv->fatal.empty() || sv->stop; };
   if (timeout_us < 0)
     sv->cv_done.wait(lock, done);
   else if (timeout_us > 0)
     sv->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), done);
   if (!sv->fatal.empty()) return sst::set_err(ctx, SST_ERR_CUDA, sv->fatal);
+  if (gone()) return sst::set_err(ctx, SST_ERR_INVALID_ARG, "sst_poll: unknown ticket");
   Req& r = sv->reqs[ri];
   if (r.state != ReqState::kDone)
     return sv->stop ? sst::set_err(ctx, SST_ERR_STATE, "sst_poll: server stopped") : SST_ERR_NOT_READY;
+  // the results are copied out without the lock: the request is marked as being
+  // collected, which keeps its results region allocated and other callers off it
+  r.state = ReqState::kCollecting;
   const sst_event_status st = r.status;
   const uint64_t a = r.first;
   const uint64_t n = st.n_clusters < capacity ? st.n_clusters : capacity;
   const HostClusters h = region_arrays(sv->res_pool + r.res_off, r.res_total);
-  if (det) std::memcpy(det, h.det + a, n * sizeof(uint32_t));
-  if (first) std::memcpy(first, h.first + a, n * sizeof(uint16_t));
-  if (width) std::memcpy(width, h.width + a, n * sizeof(uint16_t));
-  if (charge) std::memcpy(charge, h.charge + a, n * sizeof(uint32_t));
-  if (barycenter) std::memcpy(barycenter, h.bary + a, n * sizeof(float));
   if (info) {
     info->status = st;
     info->t_submit_us = r.t_submit;
     info->t_done_us = r.t_done;
   }
+  if (n == 0 || !(det || first || width || charge || barycenter)) {  // nothing to copy
+    release(sv, ri);
+    return SST_OK;
+  }
+  lock.unlock();
+  if (det) std::memcpy(det, h.det + a, n * sizeof(uint32_t));
+  if (first) std::memcpy(first, h.first + a, n * sizeof(uint16_t));
+  if (width) std::memcpy(width, h.width + a, n * sizeof(uint16_t));
+  if (charge) std::memcpy(charge, h.charge + a, n * sizeof(uint32_t));
+  if (barycenter) std::memcpy(barycenter, h.bary + a, n * sizeof(float));
+  lock.lock();
   release(sv, ri);
   return SST_OK;
 }

@@ -223,3 +223,39 @@ def test_native_client_saturating_and_poisson():
     finally:
         sst.sst_server_stop(g.ctx)
         g.close()
+
+
+def test_a_ticket_is_collected_once_by_racing_pollers(served):
+    """Several threads poll the same tickets at once: for each ticket exactly one
+    gets OK with the oracle's clusters, every other one INVALID_ARG (the result
+    is handed out once; the copy out runs outside the server's lock)."""
+    import threading
+    w, calib, g = served
+    events = [eg.make_event(w, calib, 300 + i, occupancy=0.01) for i in range(6)]
+    tickets = []
+    for e in events:
+        code, t = sst.sst_submit(g.ctx, e.raw, e.fed_len)
+        assert code == sst.SST_OK
+        tickets.append(t)
+    got = {t: [] for t in tickets}
+
+    def poller(t, cap):
+        try:
+            code, info, cl = sst.sst_poll(g.ctx, t, -1, cap)
+            got[t].append((code, info.status.n_clusters, cl))
+        except sst.SstError as ex:
+            got[t].append((ex.code, None, None))
+
+    th = [threading.Thread(target=poller, args=(t, e.nbytes)) for t, e in zip(tickets, events) for _ in range(3)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join(timeout=60)
+        assert not x.is_alive()
+    for t, e in zip(tickets, events):
+        codes = sorted(c for c, _, _ in got[t])
+        assert codes == [sst.SST_OK, sst.SST_ERR_INVALID_ARG, sst.SST_ERR_INVALID_ARG], codes
+        _, n, cl = next(x for x in got[t] if x[0] == sst.SST_OK)
+        _, oc, ost = g.oracle(e.raw, e.fed_len, w.n_feds)
+        assert n == ost["n_clusters"]
+        assert_clusters_equal(cl, oc)
