@@ -28,6 +28,7 @@ ranks and `value` the events of all ranks over that time.
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import multiprocessing as mp
@@ -151,16 +152,25 @@ def _oracle_event(args):
     return time.perf_counter() - t0, int(c["det"].size)
 
 
-def time_oracle(pool, cores, events, n_sample):
-    """Oracle (unpack + cluster, sequential C) over n_sample events on `cores`
-    processes; returns events/s and the sample description."""
-    sample = [(events[i % len(events)][0], events[i % len(events)][1]) for i in range(n_sample)]
-    pool.map(_oracle_event, sample[:cores], chunksize=1)  # warm the workers
+CPU_SAMPLE_S = 12.0  # CPU seconds of oracle work in the timed CPU baseline
+
+
+def time_oracle(pool, cores, events, cpu_s=CPU_SAMPLE_S):
+    """Oracle (unpack + cluster, sequential C) on `cores` processes over a bounded
+    sample of the events (cycled): as many as take about cpu_s seconds of CPU,
+    judged from a warm-up pass over `cores` of them.  Returns events/s, the
+    sample size, its wall and CPU seconds."""
+    def sample(n):
+        return [(events[i % len(events)][0], events[i % len(events)][1]) for i in range(n)]
+    warm = pool.map(_oracle_event, sample(cores), chunksize=1)  # warms the workers, sizes the sample
+    per_event = max(sum(r[0] for r in warm) / cores, 1e-6)
+    n_sample = int(min(max(cpu_s / per_event, cores), 50000))
+    n_sample = -(-n_sample // cores) * cores
     t0 = time.perf_counter()
-    res = pool.map(_oracle_event, sample, chunksize=1)
+    res = pool.map(_oracle_event, sample(n_sample), chunksize=1)
     wall = time.perf_counter() - t0
     cpu = sum(r[0] for r in res)
-    return n_sample / wall, wall, cpu
+    return n_sample / wall, n_sample, wall, cpu
 
 
 # ---------------------------------------------------------------- served stream
@@ -216,39 +226,69 @@ def run_served(sst, ctx, events, n_feds, n_requests, batched_rate):
 # ---------------------------------------------------------------- clocks
 
 class Clocks:
+    """nvidia-smi samples of the GPU's clocks every 50 ms.  start() waits for the
+    first sample (the tool takes a moment to come up), so that the sampling covers
+    the timed region; stop() keeps the samples taken between the two calls (by
+    host wall clock), or the nearest one when the region was shorter than the
+    sampling interval."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
     def __init__(self, index: int):
         self.path = tempfile.mktemp(prefix="clocks", suffix=".csv")
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+        t_end = time.time() + 5.0
+        while self.proc is not None and time.time() < t_end and not self._rows():
+            time.sleep(0.02)
+        self.t0 = time.time()
+
+    def _rows(self):
+        rows = []
+        try:
+            lines = open(self.path).read().splitlines()
+        except OSError:
+            return rows
+        for line in lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 10 and f[2].replace(".", "").isdigit():
+                try:
+                    t = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    continue
+                rows.append([t] + f[1:])
+        return rows
 
     def stop(self) -> dict:
+        t1 = time.time()
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.06)  # one more sample after the region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) >= 9 and f[1].replace(".", "").isdigit():
-                rows.append(f)
+        rows = self._rows()
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in rows]
+        inside = [r for r in rows if self.t0 - 0.05 <= r[0] <= t1 + 0.05]
+        window = "timed region"
+        if not inside:  # a region shorter than the interval: the sample nearest to it
+            inside = [min(rows, key=lambda r: abs(r[0] - 0.5 * (self.t0 + t1)))]
+            window = "nearest sample (timed region %.0f ms)" % ((t1 - self.t0) * 1e3)
+        sm = [float(r[2]) for r in inside]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "samples": len(rows),
-                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()) if rows else None,
-                "reasons": reasons}
+        reasons = sorted({n for r in inside for n, v in zip(names, r[6:10]) if v.lower().startswith("active")})
+        pw = [float(r[4]) for r in inside if r[4].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(inside[0][3]), "samples": len(inside),
+                "window": window, "power_w_max": max(pw) if pw else None, "reasons": reasons}
 
 
 # ---------------------------------------------------------------- helpers
@@ -361,7 +401,7 @@ def kernel_bytes(events, n_digi, n_clusters):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sst", choices=["sst", "reference"])
     ap.add_argument("--workload", default="batch64", choices=sorted(WORKLOADS))
@@ -642,12 +682,11 @@ def main():
     # ---- oracle on the host cores (rank 0 at N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        n_sample = min(len(events), max(cores * 4, 16))
-        v, wall, cpu_s = time_oracle(pool, cores, events, n_sample)
+        v, n_sample, wall, cpu_s = time_oracle(pool, cores, events)
         cpu = {"value": round(v, 2), "unit": "events/s", "cores": cores, "kind": "oracle",
                "per_core": round(v / cores, 2), "cpu_model": cpu_model(),
-               "sample": f"{n_sample} of the {n_events} events (unpack + cluster, sequential C, one event per "
-                         f"process), {wall:.1f} s wall, {cpu_s:.1f} s CPU"}
+               "sample": f"{n_sample} events, the step's {n_events} cycled (unpack + cluster, sequential C, one "
+                         f"event per process), {wall:.1f} s wall, {cpu_s:.1f} s CPU"}
     pool.terminate()
 
     total_events = n_events * world
@@ -799,8 +838,7 @@ def run_single(args, rank, world, local, wid):
     if rank == 0 and world == 1 and not args.no_cpu:
         cores = os.cpu_count() or 1
         pool = mp.get_context("spawn").Pool(cores, initializer=_worker_init, initargs=(wid,))
-        n_sample = cores * 4
-        v, wall, cpu_s = time_oracle(pool, cores, [(ev.raw, ev.fed_len)], n_sample)
+        v, n_sample, wall, cpu_s = time_oracle(pool, cores, [(ev.raw, ev.fed_len)])
         pool.terminate()
         cpu = {"value": round(v, 2), "unit": "events/s", "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
                "sample": f"the event {n_sample} times (unpack + cluster, sequential C, one event per process), "
