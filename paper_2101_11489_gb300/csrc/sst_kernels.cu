@@ -466,7 +466,8 @@ __device__ __forceinline__ void amp_slice(const AmpArgs& am, uint32_t e, uint64_
 // magic, FED id, channel and FE-unit counts and fed_bytes match and the padded FE
 // lengths add up to the record length; otherwise every channel of the FED gets
 // SST_CH_FED_HDR.  An absent FED (len 0) has no data and no error.
-__device__ void describe_fed(const uint8_t* __restrict__ raw, uint64_t fo, uint32_t len, uint32_t fed, uint2* d) {
+__device__ uint32_t describe_fed(const uint8_t* __restrict__ raw, uint64_t fo, uint32_t len, uint32_t fed, uint2* d,
+                                 uint32_t stage_max, uint32_t units) {
   uint32_t st = 0, data = 0;
   uint32_t fe_len[kFe], start[kFe];
 #pragma unroll
@@ -501,6 +502,13 @@ __device__ void describe_fed(const uint8_t* __restrict__ raw, uint64_t fo, uint3
 #pragma unroll
   for (int v = 0; v < kFe; v++)
     d[v] = make_uint2(data ? start[v] : 0u, (data ? fe_len[v] : 0u) | (st << 16) | (data << 24));
+  // work items of `units` FE units whose bytes (first unit to the end of the last)
+  // exceed the batched kernel's staging buffer
+  uint32_t big = 0;
+  if (data)
+    for (uint32_t v = 0; v + units <= (uint32_t)kFe; v += units)
+      big += start[v + units - 1] - start[v] + fe_len[v + units - 1] > stage_max;
+  return big;
 }
 
 // a1, outer level: byte offset of every FED record (exclusive scan of fed_len per
@@ -512,15 +520,20 @@ __device__ void describe_fed(const uint8_t* __restrict__ raw, uint64_t fo, uint3
 // the launch sequence's prologue: the event's last CTA writes its status (zero but
 // SST_EV_SIZE), its first clears the staging counters (ev_alloc, amp_alloc, when
 // given), the very first clears the work tickets, and every event's n_lb
-// look-back states (lb[e * n_lb ..]) are cleared.
+// look-back states (lb[e * n_lb ..]) are cleared.  With `big`, the CTA also writes
+// big[blockIdx.x]: its FEDs' work items of `units` FE units too large for the
+// batched kernel's staging buffer (stage_max bytes).
 __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_bytes,
                            const uint32_t* __restrict__ fed_len, uint32_t n_feds, uint32_t cpe,
                            uint64_t* __restrict__ fed_off, sst_event_status* status, uint32_t* ev_alloc,
                            uint32_t* tickets, unsigned long long* lb, uint32_t n_lb, const uint8_t* __restrict__ raw,
-                           uint2* unit_desc, uint32_t* amp_alloc) {
+                           uint2* unit_desc, uint32_t* amp_alloc, uint32_t* big, uint32_t stage_max,
+                           uint32_t units) {
   __shared__ uint32_t wsum[32];
   __shared__ unsigned long long psum[32];
+  __shared__ uint32_t n_big;
   pdl_release();
+  if (threadIdx.x == 0) n_big = 0;
   const uint32_t e = blockIdx.x / cpe, c = blockIdx.x % cpe;
   const uint32_t f0 = c * blockDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -545,16 +558,22 @@ __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_
   for (int k = 0; k < (int)(blockDim.x >> 5); k++) pre += psum[k];
   const uint32_t f = f0 + threadIdx.x;
   const uint32_t len = f < n_feds ? len_e[f] : 0u;
-  uint32_t tot;
+  uint32_t tot, nb = 0;
   const uint32_t ex = block_excl_scan(len, wsum, &tot);
   if (f < n_feds) {
     const uint64_t o = ev0 + pre + ex;
     const uint64_t fo = (ev1 >= ev0 && o + len <= ev1) ? o : kBadOff;
     fed_off[(size_t)e * n_feds + f] = fo;
-    if (unit_desc) describe_fed(raw, fo, len, f, unit_desc + ((size_t)e * n_feds + f) * kFe);
+    if (unit_desc) nb = describe_fed(raw, fo, len, f, unit_desc + ((size_t)e * n_feds + f) * kFe, stage_max, units);
   }
   if (c == cpe - 1 && threadIdx.x == 0)
     status[e] = sst_event_status{0u, 0u, ev0 + pre + tot != ev1 ? SST_EV_SIZE : 0u, 0u};
+  if (big) {  // uniform: every thread of the CTA takes this branch
+    nb = __reduce_add_sync(0xffffffffu, nb);
+    if (lane == 0 && nb) atomicAdd(&n_big, nb);
+    __syncthreads();
+    if (threadIdx.x == 0) big[blockIdx.x] = n_big;
+  }
 }
 
 // a6, ordering: per event, the exclusive scan of its work items' cluster counts
@@ -899,27 +918,21 @@ __global__ void __launch_bounds__(256, 4) k_cluster(sst_digis in, uint32_t n_fed
   fe::cluster_unit<kChPerFe, AMP>(w, kp, ch0, total, fill, scan, so, in.status);
 }
 
-// a7: every FE unit of every FED of every event of a batch, unpacked and
-// clustered on chip, one warp per work item of U adjacent FE units (U = 1 or 2).
-// Persistent warps take tickets FED-major (FED, then event, then item), so that
-// the warps working at any moment share the same FED's calibration in L2.
-template <bool AMP, int U>
-__global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ raw,
-                                                  const uint32_t* __restrict__ fed_len,
-                                                  const uint64_t* __restrict__ fed_off, uint32_t n_events,
-                                                  uint32_t n_feds, const uint64_t* __restrict__ clu_off,
-                                                  uint64_t out_cap, sst_event_status* status, KParams kp,
-                                                  uint4* stage, uint32_t* ev_alloc, uint32_t* seg_cnt,
-                                                  uint32_t* seg_start, uint32_t* ticket,
-                                                  const uint2* __restrict__ unit_desc, AmpArgs am) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// The work-item loop of k_batch.  SPLIT: a staged item's code reads its bytes
+// from the staging buffer as shared memory (a second inlined copy of the item
+// code); otherwise every item reads them through a generic pointer (one copy).
+template <bool AMP, int U, bool SPLIT>
+__device__ __forceinline__ void batch_items(fe::WarpT<U>& w, const uint8_t* __restrict__ raw,
+                                            const uint64_t* __restrict__ fed_off, uint32_t n_events,
+                                            uint32_t n_feds, const uint64_t* __restrict__ clu_off, uint64_t out_cap,
+                                            sst_event_status* status, const KParams& kp, uint4* stage,
+                                            uint32_t* ev_alloc, uint32_t* seg_cnt, uint32_t* seg_start,
+                                            uint32_t* ticket, const uint2* __restrict__ unit_desc, const AmpArgs& am) {
+  const int lane = threadIdx.x & 31;
   using W = fe::WarpT<U>;
-  W& w = reinterpret_cast<W*>(smem_raw)[warp];
   constexpr uint32_t kItems = kFe / U;  // work items per FED
   const uint32_t per_fed = n_events * kItems;
   const uint32_t n_units = n_feds * per_fed;
-  pdl_wait();  // the prologue's tickets, offsets and unit descriptors
   for (;;) {
     uint32_t t = 0;
     if (lane == 0) t = atomicAdd(ticket, 1u);
@@ -967,10 +980,48 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
       auto scan = [&](int nn, bool) { return fe::scan_unit<W::kChW, true>(w, kp, calq, src, src_end, nn); };
       fe::cluster_unit<W::kChW, AMP>(w, kp, ch0, total, fill, scan, so, &status[e]);
     };
-    if (un.staged) body(w.fe);
+    if (SPLIT && un.staged) body(w.fe);
     else body(un.src);
     __syncwarp();
   }
+}
+
+// a7: every FE unit of every FED of every event of a batch, unpacked and
+// clustered on chip, one warp per work item of U adjacent FE units (U = 1 or 2).
+// Persistent warps take tickets FED-major (FED, then event, then item), so that
+// the warps working at any moment share the same FED's calibration in L2.
+template <bool AMP, int U>
+__global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ raw,
+                                                  const uint32_t* __restrict__ fed_len,
+                                                  const uint64_t* __restrict__ fed_off, uint32_t n_events,
+                                                  uint32_t n_feds, const uint64_t* __restrict__ clu_off,
+                                                  uint64_t out_cap, sst_event_status* status, KParams kp,
+                                                  uint4* stage, uint32_t* ev_alloc, uint32_t* seg_cnt,
+                                                  uint32_t* seg_start, uint32_t* ticket,
+                                                  const uint2* __restrict__ unit_desc, AmpArgs am) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  fe::WarpT<U>& w = reinterpret_cast<fe::WarpT<U>*>(smem_raw)[warp];
+  pdl_wait();  // the prologue's tickets, offsets, unit descriptors and counts
+  // Items whose bytes exceed the staging buffer are read in place from global
+  // memory, by a second inlined copy of the item code.  When such items are
+  // common (more than 1 in 32 of the sampled ones, as in batches whose FED
+  // payloads differ many times over) both copies would be hot at once and compete
+  // for the instruction cache: every item then takes the in-place copy, with its
+  // staged bytes read through a generic pointer.
+  bool mixed = false;
+  if (kp.big && kp.n_big) {
+    uint32_t nb = 0;
+    for (uint32_t i = lane; i < kp.n_big; i += 32) nb += kp.big[i];
+    nb = __reduce_add_sync(0xffffffffu, nb);
+    mixed = (uint64_t)nb * 32u > kp.big_items;
+  }
+  if (mixed)
+    batch_items<AMP, U, false>(w, raw, fed_off, n_events, n_feds, clu_off, out_cap, status, kp, stage, ev_alloc,
+                               seg_cnt, seg_start, ticket, unit_desc, am);
+  else
+    batch_items<AMP, U, true>(w, raw, fed_off, n_events, n_feds, clu_off, out_cap, status, kp, stage, ev_alloc,
+                              seg_cnt, seg_start, ticket, unit_desc, am);
   pdl_release();
 }
 
@@ -1169,7 +1220,15 @@ cudaError_t launch_batch_t(const uint8_t* raw, const uint32_t* fed_len, uint32_t
   const size_t ctas = (size_t)n_sm * (sh.ctas_per_sm < per_sm ? sh.ctas_per_sm : per_sm);
   const size_t need = (units + nw - 1) / nw;
   const int grid = (int)(ctas < need ? ctas : need);
-  const KParams kps = with_spill(kp, s);
+  KParams kps = with_spill(kp, s);
+  // the prologue's counts of work items too large to stage: the kernel samples
+  // the first 256 (whole events when there are more)
+  const uint32_t cpe = (n_feds + kFedScanThreads - 1) / kFedScanThreads;
+  const uint64_t n_parts = (uint64_t)n_events * cpe;
+  const uint32_t sampled = n_parts <= 256 ? (uint32_t)n_parts : 256u / cpe * cpe;
+  kps.big = s.fed_big;
+  kps.n_big = sampled;
+  kps.big_items = (uint32_t)((uint64_t)(sampled / cpe) * n_feds * (kFe / U));
   if (AMP) {
     k_batch<AMP, U><<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out_cap, status, kps,
                                                 s.stage, s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets, s.unit_desc,
@@ -1283,7 +1342,7 @@ cudaError_t launch_unpack(const uint8_t* raw, uint64_t raw_bytes, const uint32_t
   cudaError_t e;
   const uint32_t cpe = (n_feds + kFedScanThreads - 1) / kFedScanThreads;
   k_fed_scan<<<cpe, kFedScanThreads, 0, st>>>(nullptr, raw_bytes, fed_len, n_feds, cpe, s.fed_off, out.status, nullptr,
-                                              s.tickets, s.lb, n_feds, nullptr, nullptr, nullptr);
+                                              s.tickets, s.lb, n_feds, nullptr, nullptr, nullptr, nullptr, 0u, 1u);
   if ((e = cudaGetLastError())) return e;
   switch (sh.tile) {
     case 1024: return launch_unpack_t<1024>(raw, fed_len, n_feds, out, s, sh, st);
@@ -1312,7 +1371,8 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
   const uint32_t cpe = (n_feds + kFedScanThreads - 1) / kFedScanThreads;
   k_fed_scan<<<(unsigned)((uint64_t)n_events * cpe), kFedScanThreads, 0, st>>>(
       event_off, 0, fed_len, n_feds, cpe, s.fed_off, status, s.ev_alloc, s.tickets, nullptr, 0, raw, s.unit_desc,
-      am.stage ? s.amp_alloc : nullptr);
+      am.stage ? s.amp_alloc : nullptr, s.fed_big, sh.units == 1 ? (uint32_t)fe::WarpT<1>::kBuf : (uint32_t)fe::WarpT<2>::kBuf,
+      sh.units == 1 ? 1u : 2u);
   if ((e = cudaGetLastError())) return e;
   e = launch_batch_fe(raw, fed_len, n_events, n_feds, clu_off, out.capacity, status, kp, s, sh, n_sm, am, st,
                       ev_begin, ev_end);
