@@ -194,7 +194,7 @@ def run_served(sst, ctx, events, n_feds, n_requests, batched_rate):
     depth = {}
     best = None
     for mb in (16, 32, 64, 128):
-        sst.sst_server_start(ctx, 8 << 30, mb, 3, 4096, n_feds, zero_copy=True)
+        sst.sst_server_start(ctx, 8 << 30, mb, 3, 4096, n_feds, zero_copy="in_place")
         try:
             sst.sst_serve_load(ctx, events, 1000, 0.0, submitters=8, pollers=2)  # warm-up
             r = sst.sst_serve_load(ctx, events, n_requests, 0.0, submitters=8, pollers=2)
@@ -203,7 +203,7 @@ def run_served(sst, ctx, events, n_feds, n_requests, batched_rate):
         depth[mb] = round(r["throughput"], 1)
         if best is None or r["throughput"] > depth[best]:
             best = mb
-    sst.sst_server_start(ctx, 8 << 30, best, 3, 4096, n_feds, zero_copy=True)
+    sst.sst_server_start(ctx, 8 << 30, best, 3, 4096, n_feds, zero_copy="in_place")
     try:
         sst.sst_serve_load(ctx, events, 1000, 0.0, submitters=8, pollers=2)
         cap = sst.sst_serve_load(ctx, events, n_requests, 0.0, submitters=8, pollers=2)
@@ -648,15 +648,17 @@ def main():
     # the library's native Poisson client
     served = None
     if served_pool:
-        # the events live in pinned memory and are lent to the server (zero-copy
-        # submission): the client does no per-event copy
+        # the events live in pinned memory and are lent to the server, whose kernels
+        # read them in place over the host link (zero_copy 2): no per-event copy by
+        # the client, none by the copy engine
         pinned = [torch.from_numpy(r).pin_memory() for r, _ in served_pool]
         lent = [(p.numpy(), f.astype(np.uint32)) for p, (_, f) in zip(pinned, served_pool)]
         served = run_served(sst, ctx, lent, w.n_feds, args.served_events, n_events / (ms_per_step / 1e3))
         served["workload"] = ("served-440fed-lognormal: occupancy lognormal median 1.5%, clip [0.5%, 5%], "
                               f"{len(lent)} distinct events cycled, Poisson arrivals, native client "
-                              "(sst_serve_load: 8 submitter and 2 poller threads), zero-copy submission from "
-                              "pinned event buffers, 8 GiB device budget, 3 batches in flight")
+                              "(sst_serve_load: 8 submitter and 2 poller threads), events read in place from "
+                              "pinned event buffers, 8 GiB device budget, 3 batches in flight, kernels of one batch "
+                              "at a time")
         del pinned, lent
 
     # ---- roofline of the dominant kernel (the batched kernel)

@@ -421,9 +421,17 @@ typedef struct {
   uint32_t max_requests;     /* request slots (admitted + finished-not-polled) */
   uint32_t n_feds;           /* FEDs per event */
   uint32_t zero_copy;        /* 0: sst_submit copies the event into the server's pinned pool, the
-                                caller may reuse its buffer at once; 1: no copy, the server reads
-                                the caller's buffer (pinned memory gives full copy speed), which
-                                must stay unchanged until sst_poll returns for the ticket */
+                                caller may reuse its buffer at once; 1: no copy, the server copies
+                                from the caller's buffer to the device (pinned memory gives full
+                                copy speed); 2: in place, the kernels read the event from the
+                                caller's buffer over the host link, with no device copy: the buffer
+                                must be one page-locked allocation (cudaHostAlloc, or memory
+                                registered with cudaHostRegister), 16-byte aligned and a multiple of
+                                16 bytes long (sst_submit checks the alignment and that its first
+                                and last bytes are page-locked, else INVALID_ARG).  With 1 and 2
+                                the buffer must stay unchanged until sst_poll returns for the
+                                ticket.  In place saves the copy engine one transfer per event,
+                                which dominates for events of about a megabyte */
 } sst_server_opts;
 
 /* Starts the request loop (one host thread, max_inflight streams): section 3's

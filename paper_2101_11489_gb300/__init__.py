@@ -395,10 +395,13 @@ def sst_profile_read(ctx: int, reset: bool = True) -> tuple[int, float]:
 
 
 def sst_server_start(ctx: int, mem_budget_bytes: int, max_batch_events: int, max_inflight: int, max_requests: int,
-                     n_feds: int, zero_copy: bool = False) -> None:
-    """zero_copy: sst_submit lends the caller's buffer to the server (no copy); it
-    must stay alive and unchanged until sst_poll returns for the ticket."""
-    o = sst_server_opts(mem_budget_bytes, max_batch_events, max_inflight, max_requests, n_feds, 1 if zero_copy else 0)
+                     n_feds: int, zero_copy=False) -> None:
+    """zero_copy: False / 0 copies each event at submission; True / 1 lends the
+    caller's buffer (copied to the device from there); "in_place" / 2 lends a
+    pinned buffer that the kernels read directly.  A lent buffer must stay alive
+    and unchanged until sst_poll returns for the ticket."""
+    zc = 2 if zero_copy == "in_place" else int(zero_copy)
+    o = sst_server_opts(mem_budget_bytes, max_batch_events, max_inflight, max_requests, n_feds, zc)
     _check(ctx, load_library().sst_server_start(ctx, ctypes.byref(o)), "sst_server_start")
 
 

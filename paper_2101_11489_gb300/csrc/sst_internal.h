@@ -107,11 +107,14 @@ cudaError_t launch_cluster(const sst_digis& in, uint32_t n_feds, const sst_clust
 // written to, the slice [clu_off[e], clu_off[e+1]) of `out` (bounded by
 // out.capacity).  With pack_off (device, n_events + 1 values) the events' clusters
 // are written back to back instead, event e from pack_off[e], which the launch
-// computes.
+// computes.  With event_end (device, n_events values) event e's bytes are
+// [event_off[e], event_end[e]) of raw, so that the events need not follow one
+// another (raw may then be pinned host memory read in place).
 cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len, uint32_t n_events,
                          uint32_t n_feds, const uint64_t* clu_off, const sst_clusters& out, sst_event_status* status,
                          const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st,
-                         uint64_t* pack_off = nullptr, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
+                         uint64_t* pack_off = nullptr, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr,
+                         const uint64_t* event_end = nullptr);
 cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st);
 cudaError_t build_calib(const float* noise_dev, const uint32_t* mask_dev, uint2* calq_dev,
                         uint64_t n_strips, const sst_params& p, cudaStream_t st);

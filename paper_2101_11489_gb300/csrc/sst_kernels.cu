@@ -520,7 +520,10 @@ __device__ uint32_t describe_fed(const uint8_t* __restrict__ raw, uint64_t fo, u
 // the launch sequence's prologue: the event's last CTA writes its status (zero but
 // SST_EV_SIZE), its first clears the staging counters (ev_alloc, amp_alloc, when
 // given), the very first clears the work tickets, and every event's n_lb
-// look-back states (lb[e * n_lb ..]) are cleared.  With `big`, the CTA also writes
+// look-back states (lb[e * n_lb ..]) are cleared.  Event e's bytes are
+// [event_off[e], event_end[e]) when event_end is given (events that do not follow
+// one another, e.g. read in place from host memory), else [event_off[e],
+// event_off[e + 1]).  With `big`, the CTA also writes
 // big[blockIdx.x]: its FEDs' work items of `units` FE units too large for the
 // batched kernel's staging buffer (stage_max bytes).
 __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_bytes,
@@ -528,7 +531,7 @@ __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_
                            uint64_t* __restrict__ fed_off, sst_event_status* status, uint32_t* ev_alloc,
                            uint32_t* tickets, unsigned long long* lb, uint32_t n_lb, const uint8_t* __restrict__ raw,
                            uint2* unit_desc, uint32_t* amp_alloc, uint32_t* big, uint32_t stage_max,
-                           uint32_t units) {
+                           uint32_t units, const uint64_t* __restrict__ event_end) {
   __shared__ uint32_t wsum[32];
   __shared__ unsigned long long psum[32];
   __shared__ uint32_t n_big;
@@ -538,7 +541,7 @@ __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_
   const uint32_t f0 = c * blockDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t ev0 = event_off ? event_off[e] : 0;
-  const uint64_t ev1 = event_off ? event_off[e + 1] : raw_bytes;
+  const uint64_t ev1 = event_end ? event_end[e] : event_off ? event_off[e + 1] : raw_bytes;
   if (c == 0 && threadIdx.x == 0) {
     if (ev_alloc) ev_alloc[e] = 0;
     if (amp_alloc) amp_alloc[e] = 0;
@@ -1342,7 +1345,8 @@ cudaError_t launch_unpack(const uint8_t* raw, uint64_t raw_bytes, const uint32_t
   cudaError_t e;
   const uint32_t cpe = (n_feds + kFedScanThreads - 1) / kFedScanThreads;
   k_fed_scan<<<cpe, kFedScanThreads, 0, st>>>(nullptr, raw_bytes, fed_len, n_feds, cpe, s.fed_off, out.status, nullptr,
-                                              s.tickets, s.lb, n_feds, nullptr, nullptr, nullptr, nullptr, 0u, 1u);
+                                              s.tickets, s.lb, n_feds, nullptr, nullptr, nullptr, nullptr, 0u, 1u,
+                                              nullptr);
   if ((e = cudaGetLastError())) return e;
   switch (sh.tile) {
     case 1024: return launch_unpack_t<1024>(raw, fed_len, n_feds, out, s, sh, st);
@@ -1365,14 +1369,14 @@ cudaError_t launch_cluster(const sst_digis& in, uint32_t n_feds, const sst_clust
 cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len, uint32_t n_events,
                          uint32_t n_feds, const uint64_t* clu_off, const sst_clusters& out, sst_event_status* status,
                          const KParams& kp, const Scratch& s, const Shape& sh, int n_sm, cudaStream_t st,
-                         uint64_t* pack_off, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+                         uint64_t* pack_off, cudaEvent_t ev_begin, cudaEvent_t ev_end, const uint64_t* event_end) {
   cudaError_t e;
   const AmpArgs am = amp_args(out, s);
   const uint32_t cpe = (n_feds + kFedScanThreads - 1) / kFedScanThreads;
   k_fed_scan<<<(unsigned)((uint64_t)n_events * cpe), kFedScanThreads, 0, st>>>(
       event_off, 0, fed_len, n_feds, cpe, s.fed_off, status, s.ev_alloc, s.tickets, nullptr, 0, raw, s.unit_desc,
       am.stage ? s.amp_alloc : nullptr, s.fed_big, sh.units == 1 ? (uint32_t)fe::WarpT<1>::kBuf : (uint32_t)fe::WarpT<2>::kBuf,
-      sh.units == 1 ? 1u : 2u);
+      sh.units == 1 ? 1u : 2u, event_end);
   if ((e = cudaGetLastError())) return e;
   e = launch_batch_fe(raw, fed_len, n_events, n_feds, clu_off, out.capacity, status, kp, s, sh, n_sm, am, st,
                       ev_begin, ev_end);

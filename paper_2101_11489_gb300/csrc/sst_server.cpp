@@ -20,7 +20,8 @@
 //
 // The loop thread launches a batch as soon as a slot is free and events are
 // pending (FIFO, up to max_batch_events and the slot's raw arena): it copies the
-// events into the slot's arena, runs the batched unpack + cluster kernels, packs
+// events into the slot's arena (in place mode: the kernels read them from the
+// callers' pinned buffers instead, one copy-engine transfer per event saved), runs the batched unpack + cluster kernels, packs
 // the events' clusters back to back and reads back the statuses; when those are
 // in, it reads back exactly the packed clusters into a pinned results pool and
 // frees the slot.  Batches on different slots overlap on the GPU.  sst_poll
@@ -103,7 +104,7 @@ struct Req {
   ReqState state = ReqState::kFree;
   uint64_t ticket = 0;
   size_t host_off = 0;   // raw bytes in the host pool (reserved also in zero-copy mode, for admission)
-  const uint8_t* src = nullptr;  // zero-copy mode: the caller's bytes
+  const uint8_t* src = nullptr;  // zero-copy modes: the caller's bytes
   uint64_t bytes = 0;
   std::vector<uint32_t> fed_len;
   double t_submit = 0, t_done = 0;
@@ -119,10 +120,12 @@ struct Slot {
   SlotState state = SlotState::kFree;
   cudaStream_t st = nullptr;
   cudaEvent_t ev_status = nullptr, ev_done = nullptr;
+  cudaEvent_t ev_comp = nullptr;  // the batch's kernels done (the next batch's kernels wait for it)
   sst::Scratch scratch;
   uint8_t* d_raw = nullptr;
   size_t raw_cap = 0;
   uint64_t* d_event_off = nullptr;
+  uint64_t* d_event_end = nullptr;  // in-place batches: each event's end (events need not follow one another)
   uint32_t* d_fed_len = nullptr;
   uint64_t* d_clu_off = nullptr;
   sst_event_status* d_status = nullptr;
@@ -130,6 +133,7 @@ struct Slot {
   sst_clusters d_out{};  // the batch's clusters, events back to back (d_pack_off)
   size_t clu_cap = 0;
   uint64_t* h_event_off = nullptr;
+  uint64_t* h_event_end = nullptr;
   uint32_t* h_fed_len = nullptr;
   uint64_t* h_clu_off = nullptr;
   sst_event_status* h_status = nullptr;
@@ -162,6 +166,7 @@ struct sst_server {
   RangeAlloc res_alloc;
   std::map<size_t, std::pair<size_t, int>> regions;  // results region -> (bytes, events not yet polled)
   size_t max_event_bytes = 0;
+  int last_launch = -1;  // slot of the batch launched last (loop thread only)
   int users = 0;  // callers inside sst_submit / sst_poll (under ctx->mu)
   std::condition_variable cv_users;
 };
@@ -182,6 +187,7 @@ void free_slot(Slot& s) {
   sst::free_scratch(s.scratch);
   cudaFree(s.d_raw);
   cudaFree(s.d_event_off);
+  cudaFree(s.d_event_end);
   cudaFree(s.d_fed_len);
   cudaFree(s.d_clu_off);
   cudaFree(s.d_status);
@@ -192,12 +198,14 @@ void free_slot(Slot& s) {
   cudaFree(s.d_out.charge);
   cudaFree(s.d_out.barycenter);
   cudaFreeHost(s.h_event_off);
+  cudaFreeHost(s.h_event_end);
   cudaFreeHost(s.h_fed_len);
   cudaFreeHost(s.h_clu_off);
   cudaFreeHost(s.h_status);
   cudaFreeHost(s.h_pack_off);
   if (s.ev_status) cudaEventDestroy(s.ev_status);
   if (s.ev_done) cudaEventDestroy(s.ev_done);
+  if (s.ev_comp) cudaEventDestroy(s.ev_comp);
   if (s.st) cudaStreamDestroy(s.st);
   s = Slot{};
 }
@@ -237,14 +245,15 @@ cudaError_t init_slot(Slot& s, const sst_server_opts& o, size_t raw_cap, uint32_
   if ((e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking))) return e;
   if ((e = cudaEventCreateWithFlags(&s.ev_status, cudaEventDisableTiming))) return e;
   if ((e = cudaEventCreateWithFlags(&s.ev_done, cudaEventDisableTiming))) return e;
+  if ((e = cudaEventCreateWithFlags(&s.ev_comp, cudaEventDisableTiming))) return e;
   if ((e = sst::ensure_scratch(s.scratch, (size_t)E * n_feds * sst::kFe, E, s.clu_cap))) return e;
   if ((e = sst::ensure_spill(s.scratch, (size_t)n_sm * sst::kMaxWarpsPerSm))) return e;
   if ((e = dalloc(&s.d_raw, raw_cap))) return e;
-  if ((e = dalloc(&s.d_event_off, E + 1)) || (e = dalloc(&s.d_fed_len, (size_t)E * n_feds)) ||
+  if ((e = dalloc(&s.d_event_off, E + 1)) || (e = dalloc(&s.d_event_end, E)) || (e = dalloc(&s.d_fed_len, (size_t)E * n_feds)) ||
       (e = dalloc(&s.d_clu_off, E + 1)) || (e = dalloc(&s.d_status, E)) || (e = dalloc(&s.d_pack_off, E + 1)))
     return e;
   if ((e = alloc_clusters(&s.d_out, s.clu_cap, false))) return e;
-  if ((e = halloc(&s.h_event_off, E + 1)) || (e = halloc(&s.h_fed_len, (size_t)E * n_feds)) ||
+  if ((e = halloc(&s.h_event_off, E + 1)) || (e = halloc(&s.h_event_end, E)) || (e = halloc(&s.h_fed_len, (size_t)E * n_feds)) ||
       (e = halloc(&s.h_clu_off, E + 1)) || (e = halloc(&s.h_status, E)) || (e = halloc(&s.h_pack_off, E + 1)))
     return e;
   return cudaSuccess;
@@ -294,25 +303,44 @@ cudaError_t launch_batch_on(sst_server* sv, int si, const std::vector<Part>& par
   Slot& s = sv->slots[si];
   const uint32_t nf = sv->opts.n_feds;
   const uint32_t E = (uint32_t)parts.size();
+  // in place (zero_copy 2): the kernels read every event from the caller's pinned
+  // buffer over the host link, with offsets from the lowest of the buffers
+  const bool in_place = sv->opts.zero_copy == 2;
+  const uint8_t* base = in_place ? parts[0].src : s.d_raw;
+  for (uint32_t i = 1; in_place && i < E; i++)
+    if (parts[i].src < base) base = parts[i].src;
   uint64_t off = 0, coff = 0;
   cudaError_t e = cudaSuccess;
   for (uint32_t i = 0; i < E; i++) {
-    s.h_event_off[i] = off;
+    s.h_event_off[i] = in_place ? (uint64_t)(parts[i].src - base) : off;
+    s.h_event_end[i] = s.h_event_off[i] + parts[i].bytes;
     s.h_clu_off[i] = coff;
     std::memcpy(s.h_fed_len + (size_t)i * nf, parts[i].fed_len, nf * sizeof(uint32_t));
-    if (!e) e = cudaMemcpyAsync(s.d_raw + off, parts[i].src, parts[i].bytes, cudaMemcpyHostToDevice, s.st);
+    if (!in_place && !e)
+      e = cudaMemcpyAsync(s.d_raw + off, parts[i].src, parts[i].bytes, cudaMemcpyHostToDevice, s.st);
     off += parts[i].bytes;
     coff += parts[i].bytes / 2 + 1;
   }
-  s.h_event_off[E] = off;
+  s.h_event_off[E] = in_place ? s.h_event_end[E - 1] : off;
   s.h_clu_off[E] = coff;
   if (!e) e = cudaMemcpyAsync(s.d_event_off, s.h_event_off, (E + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, s.st);
+  if (!e && in_place)
+    e = cudaMemcpyAsync(s.d_event_end, s.h_event_end, E * sizeof(uint64_t), cudaMemcpyHostToDevice, s.st);
   if (!e) e = cudaMemcpyAsync(s.d_fed_len, s.h_fed_len, (size_t)E * nf * sizeof(uint32_t), cudaMemcpyHostToDevice, s.st);
   if (!e) e = cudaMemcpyAsync(s.d_clu_off, s.h_clu_off, (E + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, s.st);
   sst_clusters out = s.d_out;
   out.capacity = s.clu_cap;
-  if (!e) e = sst::launch_batch(s.d_raw, s.d_event_off, s.d_fed_len, E, nf, s.d_clu_off, out, s.d_status,
-                                sst::kparams(sv->ctx), s.scratch, sv->ctx->shape, sv->ctx->n_sm, s.st, s.d_pack_off);
+  // one batch's kernels at a time: each persistent launch fills the GPU, so
+  // batches run back to back at full speed and finish one after another, and a
+  // batch's copies overlap the next one's kernels (kernels of several slots
+  // running at once would finish together and leave the GPU idle while all of
+  // them copy their results back)
+  if (!e && sv->last_launch >= 0) e = cudaStreamWaitEvent(s.st, sv->slots[sv->last_launch].ev_comp, 0);
+  if (!e) e = sst::launch_batch(base, s.d_event_off, s.d_fed_len, E, nf, s.d_clu_off, out, s.d_status,
+                                sst::kparams(sv->ctx), s.scratch, sv->ctx->shape, sv->ctx->n_sm, s.st, s.d_pack_off,
+                                nullptr, nullptr, in_place ? s.d_event_end : nullptr);
+  if (!e) e = cudaEventRecord(s.ev_comp, s.st);
+  sv->last_launch = si;
   if (!e) e = cudaMemcpyAsync(s.h_status, s.d_status, E * sizeof(sst_event_status), cudaMemcpyDeviceToHost, s.st);
   if (!e) e = cudaMemcpyAsync(s.h_pack_off, s.d_pack_off, (E + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s.st);
   if (!e) e = cudaEventRecord(s.ev_status, s.st);
@@ -470,10 +498,10 @@ sst_status sst_server_start(sst_ctx* ctx, const sst_server_opts* opts) {
   const sst_server_opts& o = *opts;
   if (o.mem_budget_bytes < (64ull << 20) || o.max_batch_events == 0 || o.max_batch_events > 4096 ||
       o.max_inflight == 0 || o.max_inflight > 8 || o.max_requests == 0 || o.max_requests > (1u << 20) ||
-      o.n_feds == 0 || o.n_feds > ctx->n_feds || o.zero_copy > 1)
+      o.n_feds == 0 || o.n_feds > ctx->n_feds || o.zero_copy > 2)
     return sst::set_err(ctx, SST_ERR_INVALID_ARG,
                         "sst_server_start: need budget >= 64 MiB, 1..4096 events per batch, 1..8 in flight, "
-                        "1..2^20 requests, 1..context FEDs per event and zero_copy 0 or 1");
+                        "1..2^20 requests, 1..context FEDs per event and zero_copy 0, 1 or 2");
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(ctx->device);
@@ -579,9 +607,39 @@ void release_server(sst_ctx* ctx, sst_server* sv) {
   if (--sv->users == 0) sv->cv_users.notify_all();
 }
 
+// Whether the kernels may read [p, p + n) in place: 16-byte aligned, a multiple of
+// 16 bytes, and its first and last bytes in page-locked host memory that the
+// device sees at the same address (the caller guarantees that the whole span is one
+// such allocation).  Returns null when it may, else what is wrong.  The calling
+// thread's device is set first, so that the query sees the server's context.
+const char* pinned_span(int device, const uint8_t* p, uint64_t n) {
+  if (n == 0) return nullptr;
+  if ((uintptr_t)p & 15u) return "not 16-byte aligned";
+  if (n & 15u) return "length not a multiple of 16 bytes";
+  cudaSetDevice(device);
+  for (const uint8_t* q : {p, p + n - 1}) {
+    cudaPointerAttributes a{};
+    const cudaError_t e = cudaPointerGetAttributes(&a, q);
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // not a pointer the runtime knows: not readable in place
+      return "unknown to the CUDA runtime";
+    }
+    if (a.type != cudaMemoryTypeHost) return "not page-locked host memory";
+    if (a.devicePointer != (const void*)q) return "mapped at another address on the device";
+  }
+  return nullptr;
+}
+
 sst_status submit_one(sst_ctx* ctx, sst_server* sv, const uint8_t* raw, uint64_t raw_bytes, const uint32_t* fed_len,
                       uint64_t* ticket) {
   if (raw_bytes > sv->max_event_bytes) return SST_ERR_TOO_LARGE;
+  if (sv->opts.zero_copy == 2) {
+    const char* why = pinned_span(ctx->device, raw, raw_bytes);
+    if (why)
+      return sst::set_err(ctx, SST_ERR_INVALID_ARG,
+                          std::string("sst_submit: an event read in place must be a 16-byte aligned span of pinned "
+                                      "host memory, a multiple of 16 bytes long: ") + why);
+  }
   std::vector<uint32_t> fl(fed_len, fed_len + sv->opts.n_feds);
   const bool lend = sv->opts.zero_copy != 0;
   int ri = -1;

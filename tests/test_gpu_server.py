@@ -123,6 +123,42 @@ def test_zero_copy_submission_equals_the_oracle():
         g.close()
 
 
+def test_in_place_submission_equals_the_oracle():
+    """In place (zero_copy 2) the kernels read each event straight from the
+    caller's pinned buffer, whose bytes sit at scattered host addresses; every
+    event equals the oracle.  Buffers that are pageable or not 16-byte aligned are
+    refused at submission (nothing is read from them)."""
+    w = eg.WORKLOADS[0]
+    calib = eg.make_calibration(w.n_feds, w.seed, w.p_bad)
+    g = Gpu(calib.noise, calib.gain, calib.bad)
+    sst.sst_server_start(g.ctx, 256 << 20, 5, 2, 64, w.n_feds, zero_copy="in_place")
+    try:
+        events = [eg.make_event(w, calib, 950 + i, occupancy=0.002 + 0.004 * (i % 5)) for i in range(14)]
+        pinned = [torch.from_numpy(e.raw).pin_memory() for e in events]  # lent until polled
+        tickets = []
+        for e, p in zip(events, pinned):
+            code, t = sst.sst_submit(g.ctx, p.numpy(), e.fed_len)
+            assert code == sst.SST_OK
+            tickets.append(t)
+        for e, t in zip(events, tickets):
+            st, cl = _poll(g, t, e.nbytes)
+            _, oc, ost = g.oracle(e.raw, e.fed_len, w.n_feds)
+            assert st == ost
+            assert_clusters_equal(cl, oc)
+        e = events[0]
+        with pytest.raises(sst.SstError) as ei:  # pageable
+            sst.sst_submit(g.ctx, e.raw.copy(), e.fed_len)
+        assert ei.value.code == sst.SST_ERR_INVALID_ARG
+        big = torch.empty(e.raw.size + 16, dtype=torch.uint8).pin_memory()
+        big[1:1 + e.raw.size] = torch.from_numpy(e.raw)
+        with pytest.raises(sst.SstError) as ei:  # pinned, but not 16-byte aligned
+            sst.sst_submit(g.ctx, big.numpy()[1:1 + e.raw.size], e.fed_len)
+        assert ei.value.code == sst.SST_ERR_INVALID_ARG
+    finally:
+        sst.sst_server_stop(g.ctx)
+        g.close()
+
+
 def test_budget_full_then_poll_then_resubmit():
     """Admission by memory: with a small budget the host pool of admitted events
     fills, sst_submit answers BUDGET, and after one poll the same event is admitted."""
