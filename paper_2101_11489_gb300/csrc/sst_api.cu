@@ -102,7 +102,7 @@ cudaError_t ensure_scratch(Scratch& s, size_t items, size_t events, size_t stage
       if ((e = grow(s.fed_start, c4, items))) return e;
       if ((e = grow(s.fed_dest, c5, items))) return e;
       if ((e = grow(s.unit_desc, c6, items))) return e;
-      if ((e = grow(s.fed_big, c7, items))) return e;
+      if ((e = grow(s.big_list, c7, items))) return e;
       s.items_cap = items;
     }
     if ((e = grow(s.ev_alloc, s.ev_cap, events))) return e;
@@ -148,7 +148,7 @@ void free_scratch(Scratch& s) {
   if (s.fed_start) cudaFree(s.fed_start);
   if (s.fed_dest) cudaFree(s.fed_dest);
   if (s.unit_desc) cudaFree(s.unit_desc);
-  if (s.fed_big) cudaFree(s.fed_big);
+  if (s.big_list) cudaFree(s.big_list);
   if (s.ev_alloc) cudaFree(s.ev_alloc);
   if (s.stage) cudaFree(s.stage);
   if (s.tickets) cudaFree(s.tickets);

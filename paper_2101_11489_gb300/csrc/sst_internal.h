@@ -35,9 +35,8 @@ struct KParams {
                             // gain-corrected charge of every ADC 0..253, or -gain (divide)
   uint4* spill = nullptr;   // the launch's spill areas (one per warp of the grid, kSpillRecords records each)
   uint32_t spill_warps = 0; // warps that have one
-  const uint32_t* big = nullptr;  // batched launches: per prologue CTA, work items too large to stage
-  uint32_t n_big = 0;             // entries of big the kernel samples (at most 256)
-  uint32_t big_items = 0;         // work items those entries cover
+  const uint32_t* big_list = nullptr;  // batched launches: the work items too large to stage (their
+                                       // ticket-order indices; how many: tickets[2], from the prologue)
 };
 
 
@@ -61,7 +60,7 @@ struct Scratch {
   uint32_t* fed_start = nullptr;     // staging offset per work item, within its event's slice
   uint32_t* fed_dest = nullptr;      // output offset per work item, within its event's slice
   uint2* unit_desc = nullptr;        // per (event, FED, FE unit): offset in the FED record, length | status
-  uint32_t* fed_big = nullptr;       // per prologue CTA: its work items too large to stage (batched path)
+  uint32_t* big_list = nullptr;      // work items too large to stage (batched path; count in tickets[2])
   size_t items_cap = 0;
   uint32_t* ev_alloc = nullptr;      // staging allocation counter per event
   size_t ev_cap = 0;

@@ -466,6 +466,9 @@ __device__ __forceinline__ void amp_slice(const AmpArgs& am, uint32_t e, uint64_
 // magic, FED id, channel and FE-unit counts and fed_bytes match and the padded FE
 // lengths add up to the record length; otherwise every channel of the FED gets
 // SST_CH_FED_HDR.  An absent FED (len 0) has no data and no error.
+// Unit descriptor bit: the work item starting at this unit is too large to stage.
+constexpr uint32_t kBigItem = 1u << 25;
+
 __device__ uint32_t describe_fed(const uint8_t* __restrict__ raw, uint64_t fo, uint32_t len, uint32_t fed, uint2* d,
                                  uint32_t stage_max, uint32_t units) {
   uint32_t st = 0, data = 0;
@@ -503,11 +506,15 @@ __device__ uint32_t describe_fed(const uint8_t* __restrict__ raw, uint64_t fo, u
   for (int v = 0; v < kFe; v++)
     d[v] = make_uint2(data ? start[v] : 0u, (data ? fe_len[v] : 0u) | (st << 16) | (data << 24));
   // work items of `units` FE units whose bytes (first unit to the end of the last)
-  // exceed the batched kernel's staging buffer
+  // exceed the batched kernel's staging buffer: bit p of the result for item p,
+  // and kBigItem in the descriptor of the item's first unit
   uint32_t big = 0;
   if (data)
     for (uint32_t v = 0; v + units <= (uint32_t)kFe; v += units)
-      big += start[v + units - 1] - start[v] + fe_len[v + units - 1] > stage_max;
+      if (start[v + units - 1] - start[v] + fe_len[v + units - 1] > stage_max) {
+        big |= 1u << (v / units);
+        d[v].y |= kBigItem;
+      }
   return big;
 }
 
@@ -523,20 +530,19 @@ __device__ uint32_t describe_fed(const uint8_t* __restrict__ raw, uint64_t fo, u
 // look-back states (lb[e * n_lb ..]) are cleared.  Event e's bytes are
 // [event_off[e], event_end[e]) when event_end is given (events that do not follow
 // one another, e.g. read in place from host memory), else [event_off[e],
-// event_off[e + 1]).  With `big`, the CTA also writes
-// big[blockIdx.x]: its FEDs' work items of `units` FE units too large for the
-// batched kernel's staging buffer (stage_max bytes).
+// event_off[e + 1]).  With big_list, the work items of `units` FE units too large
+// for the batched kernel's staging buffer (stage_max bytes) are appended to it by
+// their ticket-order index (FED, then event, then item), counted in tickets[2],
+// which the launch clears before this kernel (so it is not cleared here).
 __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_bytes,
                            const uint32_t* __restrict__ fed_len, uint32_t n_feds, uint32_t cpe,
                            uint64_t* __restrict__ fed_off, sst_event_status* status, uint32_t* ev_alloc,
                            uint32_t* tickets, unsigned long long* lb, uint32_t n_lb, const uint8_t* __restrict__ raw,
-                           uint2* unit_desc, uint32_t* amp_alloc, uint32_t* big, uint32_t stage_max,
+                           uint2* unit_desc, uint32_t* amp_alloc, uint32_t* big_list, uint32_t stage_max,
                            uint32_t units, const uint64_t* __restrict__ event_end) {
   __shared__ uint32_t wsum[32];
   __shared__ unsigned long long psum[32];
-  __shared__ uint32_t n_big;
   pdl_release();
-  if (threadIdx.x == 0) n_big = 0;
   const uint32_t e = blockIdx.x / cpe, c = blockIdx.x % cpe;
   const uint32_t f0 = c * blockDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -546,7 +552,7 @@ __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_
     if (ev_alloc) ev_alloc[e] = 0;
     if (amp_alloc) amp_alloc[e] = 0;
   }
-  if (e == 0 && c == 0 && threadIdx.x < 16) tickets[threadIdx.x] = 0;
+  if (e == 0 && c == 0 && threadIdx.x < 16 && threadIdx.x != 2) tickets[threadIdx.x] = 0;
   if (lb)
     for (uint32_t i = f0 + threadIdx.x; i < n_lb; i += cpe * blockDim.x) lb[(size_t)e * n_lb + i] = 0;
   const uint32_t* len_e = fed_len + (size_t)e * n_feds;
@@ -561,22 +567,24 @@ __global__ void k_fed_scan(const uint64_t* __restrict__ event_off, uint64_t raw_
   for (int k = 0; k < (int)(blockDim.x >> 5); k++) pre += psum[k];
   const uint32_t f = f0 + threadIdx.x;
   const uint32_t len = f < n_feds ? len_e[f] : 0u;
-  uint32_t tot, nb = 0;
+  uint32_t tot;
   const uint32_t ex = block_excl_scan(len, wsum, &tot);
   if (f < n_feds) {
     const uint64_t o = ev0 + pre + ex;
     const uint64_t fo = (ev1 >= ev0 && o + len <= ev1) ? o : kBadOff;
     fed_off[(size_t)e * n_feds + f] = fo;
-    if (unit_desc) nb = describe_fed(raw, fo, len, f, unit_desc + ((size_t)e * n_feds + f) * kFe, stage_max, units);
+    if (unit_desc) {
+      const uint32_t big = describe_fed(raw, fo, len, f, unit_desc + ((size_t)e * n_feds + f) * kFe, stage_max, units);
+      if (big && big_list) {
+        const uint32_t items = kFe / units, n_events = gridDim.x / cpe;
+        uint32_t at = atomicAdd(&tickets[2], (uint32_t)__popc(big));
+        for (uint32_t b = big; b; b &= b - 1)
+          big_list[at++] = (f * n_events + e) * items + (uint32_t)(__ffs(b) - 1);
+      }
+    }
   }
   if (c == cpe - 1 && threadIdx.x == 0)
     status[e] = sst_event_status{0u, 0u, ev0 + pre + tot != ev1 ? SST_EV_SIZE : 0u, 0u};
-  if (big) {  // uniform: every thread of the CTA takes this branch
-    nb = __reduce_add_sync(0xffffffffu, nb);
-    if (lane == 0 && nb) atomicAdd(&n_big, nb);
-    __syncthreads();
-    if (threadIdx.x == 0) big[blockIdx.x] = n_big;
-  }
 }
 
 // a6, ordering: per event, the exclusive scan of its work items' cluster counts
@@ -924,31 +932,42 @@ __global__ void __launch_bounds__(256, 4) k_cluster(sst_digis in, uint32_t n_fed
 // The work-item loop of k_batch.  SPLIT: a staged item's code reads its bytes
 // from the staging buffer as shared memory (a second inlined copy of the item
 // code); otherwise every item reads them through a generic pointer (one copy).
-template <bool AMP, int U, bool SPLIT>
+// LIST: the prologue listed items too large to stage (n_big of them).
+template <bool AMP, int U, bool SPLIT, bool LIST>
 __device__ __forceinline__ void batch_items(fe::WarpT<U>& w, const uint8_t* __restrict__ raw,
                                             const uint64_t* __restrict__ fed_off, uint32_t n_events,
                                             uint32_t n_feds, const uint64_t* __restrict__ clu_off, uint64_t out_cap,
                                             sst_event_status* status, const KParams& kp, uint4* stage,
                                             uint32_t* ev_alloc, uint32_t* seg_cnt, uint32_t* seg_start,
-                                            uint32_t* ticket, const uint2* __restrict__ unit_desc, const AmpArgs& am) {
+                                            uint32_t* ticket, const uint2* __restrict__ unit_desc, const AmpArgs& am,
+                                            uint32_t n_big) {
   const int lane = threadIdx.x & 31;
   using W = fe::WarpT<U>;
   constexpr uint32_t kItems = kFe / U;  // work items per FED
   const uint32_t per_fed = n_events * kItems;
   const uint32_t n_units = n_feds * per_fed;
+  // Tickets: first the items too large to stage (the prologue's list; they take
+  // several times longer than the others), then every item in ticket order (FED,
+  // event, item), the listed ones skipped, so that the launch ends on small items.
   for (;;) {
     uint32_t t = 0;
     if (lane == 0) t = atomicAdd(ticket, 1u);
     t = __shfl_sync(0xffffffffu, t, 0);
-    if (t >= n_units) break;
+    if (t >= n_big + n_units) break;
+    const bool listed = LIST && t < n_big;
+    if (LIST) {
+      if (listed) t = kp.big_list[t];
+      else t -= n_big;
+    }
     const uint32_t f = t / per_fed, r = t % per_fed, e = r / kItems, p = r % kItems, u = p * U;
     const size_t item = (size_t)e * n_feds + f;
+    const uint2 dA = unit_desc[item * kFe + u];
+    if (LIST && !listed && (dA.y & kBigItem)) continue;  // taken from the list
     const uint64_t fo = fed_off[item];
     const bool in_range = fo != kBadOff;
     const uint32_t ch0 = f * kCh + u * kChPerFe;
     fe::load_calib<W::kChW>(w, kp, ch0);
-    const fe::Unit un = fe::locate(w, raw + (in_range ? fo : 0), unit_desc[item * kFe + u],
-                                   unit_desc[item * kFe + u + (U - 1)], f, u);
+    const fe::Unit un = fe::locate(w, raw + (in_range ? fo : 0), dA, unit_desc[item * kFe + u + (U - 1)], f, u);
     // the rest of the item; src is the staging buffer for a staged item, so that
     // its bytes are read as shared memory there (two inlined copies)
     auto body = [&](const uint8_t* src) {
@@ -1006,25 +1025,23 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   fe::WarpT<U>& w = reinterpret_cast<fe::WarpT<U>*>(smem_raw)[warp];
   pdl_wait();  // the prologue's tickets, offsets, unit descriptors and counts
-  // Items whose bytes exceed the staging buffer are read in place from global
-  // memory, by a second inlined copy of the item code.  When such items are
-  // common (more than 1 in 32 of the sampled ones, as in batches whose FED
-  // payloads differ many times over) both copies would be hot at once and compete
-  // for the instruction cache: every item then takes the in-place copy, with its
-  // staged bytes read through a generic pointer.
-  bool mixed = false;
-  if (kp.big && kp.n_big) {
-    uint32_t nb = 0;
-    for (uint32_t i = lane; i < kp.n_big; i += 32) nb += kp.big[i];
-    nb = __reduce_add_sync(0xffffffffu, nb);
-    mixed = (uint64_t)nb * 32u > kp.big_items;
-  }
+  // Items whose bytes exceed the staging buffer (the prologue lists them) are read
+  // in place from global memory, by a second inlined copy of the item code.  When
+  // such items are common (more than 1 in 32, as in batches whose FED payloads
+  // differ many times over) both copies would be hot at once and compete for the
+  // instruction cache: every item then takes the in-place copy, with its staged
+  // bytes read through a generic pointer.
+  const uint32_t n_big = kp.big_list ? ticket[2] : 0u;
+  const bool mixed = (uint64_t)n_big * 32u > (uint64_t)n_feds * n_events * (kFe / U);
   if (mixed)
-    batch_items<AMP, U, false>(w, raw, fed_off, n_events, n_feds, clu_off, out_cap, status, kp, stage, ev_alloc,
-                               seg_cnt, seg_start, ticket, unit_desc, am);
+    batch_items<AMP, U, false, true>(w, raw, fed_off, n_events, n_feds, clu_off, out_cap, status, kp, stage,
+                                     ev_alloc, seg_cnt, seg_start, ticket, unit_desc, am, n_big);
+  else if (n_big)
+    batch_items<AMP, U, true, true>(w, raw, fed_off, n_events, n_feds, clu_off, out_cap, status, kp, stage, ev_alloc,
+                                    seg_cnt, seg_start, ticket, unit_desc, am, n_big);
   else
-    batch_items<AMP, U, true>(w, raw, fed_off, n_events, n_feds, clu_off, out_cap, status, kp, stage, ev_alloc,
-                              seg_cnt, seg_start, ticket, unit_desc, am);
+    batch_items<AMP, U, true, false>(w, raw, fed_off, n_events, n_feds, clu_off, out_cap, status, kp, stage,
+                                     ev_alloc, seg_cnt, seg_start, ticket, unit_desc, am, 0u);
   pdl_release();
 }
 
@@ -1224,14 +1241,7 @@ cudaError_t launch_batch_t(const uint8_t* raw, const uint32_t* fed_len, uint32_t
   const size_t need = (units + nw - 1) / nw;
   const int grid = (int)(ctas < need ? ctas : need);
   KParams kps = with_spill(kp, s);
-  // the prologue's counts of work items too large to stage: the kernel samples
-  // the first 256 (whole events when there are more)
-  const uint32_t cpe = (n_feds + kFedScanThreads - 1) / kFedScanThreads;
-  const uint64_t n_parts = (uint64_t)n_events * cpe;
-  const uint32_t sampled = n_parts <= 256 ? (uint32_t)n_parts : 256u / cpe * cpe;
-  kps.big = s.fed_big;
-  kps.n_big = sampled;
-  kps.big_items = (uint32_t)((uint64_t)(sampled / cpe) * n_feds * (kFe / U));
+  kps.big_list = s.big_list;
   if (AMP) {
     k_batch<AMP, U><<<grid, sh.block, sm, st>>>(raw, fed_len, s.fed_off, n_events, n_feds, clu_off, out_cap, status, kps,
                                                 s.stage, s.ev_alloc, s.fed_cnt, s.fed_start, s.tickets, s.unit_desc,
@@ -1373,9 +1383,10 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
   cudaError_t e;
   const AmpArgs am = amp_args(out, s);
   const uint32_t cpe = (n_feds + kFedScanThreads - 1) / kFedScanThreads;
+  if ((e = cudaMemsetAsync(s.tickets + 2, 0, sizeof(uint32_t), st))) return e;  // the prologue's list of large items
   k_fed_scan<<<(unsigned)((uint64_t)n_events * cpe), kFedScanThreads, 0, st>>>(
       event_off, 0, fed_len, n_feds, cpe, s.fed_off, status, s.ev_alloc, s.tickets, nullptr, 0, raw, s.unit_desc,
-      am.stage ? s.amp_alloc : nullptr, s.fed_big, sh.units == 1 ? (uint32_t)fe::WarpT<1>::kBuf : (uint32_t)fe::WarpT<2>::kBuf,
+      am.stage ? s.amp_alloc : nullptr, s.big_list, sh.units == 1 ? (uint32_t)fe::WarpT<1>::kBuf : (uint32_t)fe::WarpT<2>::kBuf,
       sh.units == 1 ? 1u : 2u, event_end);
   if ((e = cudaGetLastError())) return e;
   e = launch_batch_fe(raw, fed_len, n_events, n_feds, clu_off, out.capacity, status, kp, s, sh, n_sm, am, st,
