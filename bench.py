@@ -158,7 +158,7 @@ CPU_SAMPLE_S = 12.0  # CPU seconds of oracle work in the timed CPU baseline
 def time_oracle(pool, cores, events, cpu_s=CPU_SAMPLE_S):
     """Oracle (unpack + cluster, sequential C) on `cores` processes over a bounded
     sample of the events (cycled): as many as take about cpu_s seconds of CPU,
-    judged from a warm-up pass over `cores` of them.  Returns events/s, the
+    estimated from a warm-up pass over `cores` of them.  Returns events/s, the
     sample size, its wall and CPU seconds."""
     def sample(n):
         return [(events[i % len(events)][0], events[i % len(events)][1]) for i in range(n)]
@@ -887,7 +887,10 @@ def run_reference(args, rank, world, wid, n_events):
     w = eg.WORKLOADS[wid]
     cores = os.cpu_count() or 1
     pool = mp.get_context("spawn").Pool(cores, initializer=_worker_init, initargs=(wid,))
-    sample = min(n_events, cores * 2)
+    # the whole step (the GPU arm's workload) while that keeps the run to about a
+    # minute of oracle work per 16 cores, else a bounded sample of it
+    whole = args.steps * n_events <= 20000 * max(cores, 1) // 16
+    sample = n_events if whole else min(n_events, cores * 2)
     gen = pool.map(_gen_event, [(wid, i) for i in range(sample)], chunksize=1)
     events = [(r, f) for r, f, _ in gen]
     for _ in range(args.warmup):
@@ -906,7 +909,8 @@ def run_reference(args, rank, world, wid, n_events):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {w.name}", "events_per_step": sample, "n_feds": w.n_feds},
         "cpu_baseline": {"value": round(v, 2), "unit": "events/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{sample} of the {n_events} events per step, one event per process"},
+                         "sample": (f"all {n_events} events of the step" if whole else
+                                    f"{sample} of the {n_events} events per step") + ", one event per process"},
         "e2e": {"value": round(v, 2), "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 

@@ -134,3 +134,28 @@ def test_autotune_host_picks_a_batch_depth(g4):
             assert_clusters_equal(out.view(int(ef[i]), int(sth[i, 1])), oc)
     finally:
         sst.sst_set_tune(g.ctx, **keep)
+
+
+@pytest.mark.parametrize("n_small", [40, 2])
+def test_oversized_items_first_equal_the_oracle(g4, n_small):
+    """Work items too large for the staging buffer are listed by the prologue and
+    taken first; with few of them (one dense event among 40, under 1 in 32 of the
+    items) the staged items keep their shared-memory code, with many (one among 2)
+    every item takes the in-place code.  Both batches equal the oracle event by
+    event, in every shape the autotuner sweeps over the work-item width."""
+    w, calib, g = g4
+    evs = [eg.make_event(w, calib, 400 + i, occupancy=0.004 + 0.002 * (i % 3), n_feds=N_FEDS) for i in range(n_small)]
+    dense = eg.make_event(w, calib, 499, occupancy=0.3, n_feds=N_FEDS)
+    events = [(e.raw, e.fed_len) for e in evs[: n_small // 2]] + [(dense.raw, dense.fed_len)] + \
+             [(e.raw, e.fed_len) for e in evs[n_small // 2:]]
+    keep = sst.sst_get_tune(g.ctx)
+    try:
+        for units in (2, 1):
+            sst.sst_set_tune(g.ctx, units_per_warp=units)
+            got = g.batch(events)
+            for (r, f), (st, cl) in zip(events, got):
+                _, oc, ost = g.oracle(r, f, N_FEDS)
+                assert st == ost, units
+                assert_clusters_equal(cl, oc)
+    finally:
+        sst.sst_set_tune(g.ctx, **keep)
