@@ -597,12 +597,17 @@ def main():
     # chunks of events overlapped on the library's streams)
     keep = [torch.from_numpy(a).pin_memory() for a in (raw_h, eoff.view(np.int64), fl_h.view(np.int32))]
     raw_pin, eoff_pin, fl_pin = keep[0].numpy(), keep[1].numpy().view(np.uint64), keep[2].numpy().view(np.uint32)
-    # three sets of pinned output buffers: up to three steps are in the library's
-    # pipeline, each step cut into chunks of 32 events (copies in, kernels and
+    # up to six sets of pinned output buffers: up to six steps are in the library's
+    # pipeline, each step cut into chunks of 64 events (copies in, kernels and
     # copies out of successive chunks overlap), and step i's results are read once
-    # its wait returns
-    depth = 3
-    e2e_chunk = min(32, n_events)
+    # its wait returns.  Measured on batch64 (events/s): chunks of 32 events with
+    # 3, 6 or 8 steps in flight 96-99 k (five cluster copies per chunk; the copy
+    # back is busy without a gap); chunks of 64 with 3 steps 98 k (the host's turn
+    # between a wait and the next submission leaves the pipeline idle), with 6 or
+    # 8 steps 120 k
+    e2e_cap = min(int(coff[-1]), 2 * n_clu + 4096)  # cluster records per output set
+    depth = max(3, min(6, (2 << 30) // (16 * e2e_cap)))  # at most about 2 GiB of pinned output sets
+    e2e_chunk = min(64, n_events)
     tune_e2e = dict(tune)
     tune_e2e["host_chunk_events"] = e2e_chunk
     sst.sst_set_tune(ctx, **tune_e2e)
@@ -611,7 +616,9 @@ def main():
         ef = torch.zeros(n_events + 1, dtype=torch.int64).pin_memory()
         sh = torch.zeros(n_events * 4, dtype=torch.int32).pin_memory()
         keep += [ef, sh]
-        outs.append((sst.HostClusters.alloc(int(coff[-1]), pinned=True), ef.numpy().view(np.uint64),
+        # room for twice the step's clusters (a step that needed more would report
+        # SST_EV_CLUSTER_CAPACITY, and the status check below would fail)
+        outs.append((sst.HostClusters.alloc(e2e_cap, pinned=True), ef.numpy().view(np.uint64),
                      sh.numpy().view(np.uint32).reshape(n_events, 4)))
 
     def e2e_run(n_steps):
@@ -730,8 +737,8 @@ def main():
             "e2e": {"value": round(total_events / e2e_s, 1), "unit": "events/s",
                     "h2d_bytes_per_step": int(h2d_bytes), "d2h_bytes_per_step": int(d2h_total / e2e_steps),
                     "steps": e2e_steps,
-                    "api": "sst_batch_host_submit / sst_batch_host_wait, pinned host buffers, up to 3 steps in "
-                           "flight, chunks of %d events (host_chunk_events)" % e2e_chunk},
+                    "api": "sst_batch_host_submit / sst_batch_host_wait, pinned host buffers, up to %d steps in "
+                           "flight, chunks of %d events (host_chunk_events)" % (depth, e2e_chunk)},
             "gpu_launches": 3 * args.steps,
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
