@@ -312,7 +312,7 @@ cudaError_t launch_batch_on(sst_server* sv, int si, const std::vector<Part>& par
   uint64_t off = 0, coff = 0;
   cudaError_t e = cudaSuccess;
   for (uint32_t i = 0; i < E; i++) {
-    s.h_event_off[i] = in_place ? (uint64_t)(parts[i].src - base) : off;
+    s.h_event_off[i] = in_place ? (uint64_t)((uintptr_t)parts[i].src - (uintptr_t)base) : off;
     s.h_event_end[i] = s.h_event_off[i] + parts[i].bytes;
     s.h_clu_off[i] = coff;
     std::memcpy(s.h_fed_len + (size_t)i * nf, parts[i].fed_len, nf * sizeof(uint32_t));
