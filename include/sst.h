@@ -155,21 +155,22 @@ typedef struct {
   float* barycenter;
   uint64_t capacity; /* elements of each array; also sizes the context's staging scratch */
   /* Optional per-strip amplitudes (section 2: a cluster reports its boundaries,
-   * centroid "and optionally ADC values"); amp == NULL: none are produced.  Only
-   * sst_cluster and sst_batch produce them (sst_batch_host and the served path
-   * take amp == NULL).  The amplitude of each strip of a cluster is its
+   * centroid "and optionally ADC values"); amp == NULL: none are produced.
+   * sst_cluster, sst_batch and sst_batch_host produce them (the served path does
+   * not: sst_poll returns clusters only).  The amplitude of each strip of a cluster is its
    * gain-corrected charge when the strip is active, else 0 (a hole, a bad strip
    * inside, a bad strip the cluster was widened over): cluster k's width[k]
    * amplitudes are amp[amp_first[k] ..].  Within an event they follow the
    * cluster order.  Amplitudes are allocated per work item (one FE unit per
-   * warp in sst_cluster, two in sst_batch); when an item's amplitudes do not
+   * warp in sst_cluster, two in the batched paths); when an item's amplitudes do not
    * fit, none of them is stored, its clusters get amp_first = 0xFFFFFFFF and the
    * event SST_EV_AMP_CAPACITY (the clusters themselves are unaffected). */
   uint8_t* amp;            /* [amp_capacity] */
   uint32_t* amp_first;     /* [capacity], absolute index into amp */
-  const uint64_t* amp_off; /* sst_batch: [n_events + 1] device; event e's amplitudes lie in
-                              [amp_off[e], amp_off[e+1]) (bounded by amp_capacity);
-                              sst_cluster: unused, the event has [0, amp_capacity) */
+  const uint64_t* amp_off; /* sst_batch: [n_events + 1] device, sst_batch_host: [n_events + 1]
+                              host; event e's amplitudes lie in [amp_off[e], amp_off[e+1])
+                              (bounded by amp_capacity); sst_cluster: unused, the event has
+                              [0, amp_capacity) */
   uint64_t amp_capacity;   /* bytes of amp; also sizes the context's amplitude staging */
 } sst_clusters;
 
@@ -299,8 +300,13 @@ sst_status sst_batch(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off
  * grow on demand (cudaMalloc only when a call needs more than any call before it
  * on the context) and are freed by sst_destroy.  Calls from several threads are
  * processed one batch after another, in the order they were made.
+ * Amplitudes (out->amp set): out->amp, out->amp_first and out->amp_off are host
+ * arrays with sst_batch's meaning (event e's amplitudes in its slice
+ * [amp_off[e], amp_off[e+1]) of amp, amp_first absolute indices into amp); each
+ * chunk's slices are copied back whole.
  * Errors: INVALID_ARG (null pointer, n_events == 0, n_feds outside 1..context
- * FEDs, decreasing event_off, out->amp set: amplitudes are not produced here),
+ * FEDs, decreasing event_off; with amplitudes: amp_first or amp_off null,
+ * amp_off decreasing or past amp_capacity, amp_capacity 0 or >= 2^32 - 1),
  * NO_CALIB, CUDA. */
 sst_status sst_batch_host(sst_ctx* ctx, const uint8_t* raw, const uint64_t* event_off, const uint32_t* fed_len,
                           uint32_t n_events, uint32_t n_feds, const sst_clusters* out, uint64_t* event_first,

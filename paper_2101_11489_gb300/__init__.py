@@ -542,30 +542,45 @@ class ClusterBuffers:
 
 @dataclass
 class HostClusters:
-    """Host arrays behind an sst_clusters record, optionally in pinned memory."""
+    """Host arrays behind an sst_clusters record, optionally in pinned memory, with
+    optional amplitude arrays (amp u8, amp_first u32 per cluster, amp_off u64 per
+    event + 1: the events' slices of amp, for sst_batch_host)."""
     det: np.ndarray
     first: np.ndarray
     width: np.ndarray
     charge: np.ndarray
     barycenter: np.ndarray
     _keep: object = None  # pinned tensors that own the memory
+    amp: np.ndarray = None
+    amp_first: np.ndarray = None
+    amp_off: np.ndarray = None
 
     @classmethod
-    def alloc(cls, capacity: int, pinned: bool = False):
+    def alloc(cls, capacity: int, pinned: bool = False, amp_off=None):
+        """amp_off (uint64, events + 1): also allocate amplitudes, amp_off[-1] bytes."""
         c = max(capacity, 1)
         dts = (np.uint32, np.uint16, np.uint16, np.uint32, np.float32)
         if not pinned:
-            return cls(*[np.zeros(c, d) for d in dts])
-        import torch
-        ts = [torch.empty(c * np.dtype(d).itemsize, dtype=torch.uint8, pin_memory=True) for d in dts]
-        return cls(*[t.numpy().view(d) for t, d in zip(ts, dts)], _keep=ts)
+            b = cls(*[np.zeros(c, d) for d in dts])
+        else:
+            import torch
+            ts = [torch.empty(c * np.dtype(d).itemsize, dtype=torch.uint8, pin_memory=True) for d in dts]
+            b = cls(*[t.numpy().view(d) for t, d in zip(ts, dts)], _keep=ts)
+        if amp_off is not None:
+            b.amp_off = np.ascontiguousarray(amp_off, dtype=np.uint64)
+            b.amp = np.zeros(max(int(b.amp_off[-1]), 1), np.uint8)
+            b.amp_first = np.zeros(c, np.uint32)
+        return b
 
     def record(self) -> sst_clusters:
+        amp = self.amp is not None
         return sst_clusters(_hp(self.det), _hp(self.first), _hp(self.width), _hp(self.charge), _hp(self.barycenter),
-                            self.det.size, None, None, None, 0)
+                            self.det.size, _hp(self.amp) if amp else None, _hp(self.amp_first) if amp else None,
+                            _hp(self.amp_off) if amp else None, self.amp.size if amp else 0)
 
     def view(self, start: int, n: int) -> dict:
-        return {k: getattr(self, k)[start:start + n] for k in ("det", "first", "width", "charge", "barycenter")}
+        keys = ("det", "first", "width", "charge", "barycenter") + (("amp_first",) if self.amp is not None else ())
+        return {k: getattr(self, k)[start:start + n] for k in keys}
 
 
 def params(t_channel=2.0, t_seed=3.0, t_cluster=5.0, max_seq_holes=0, max_seq_bad=1, max_adj_bad=0) -> sst_params:

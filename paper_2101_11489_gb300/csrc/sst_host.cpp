@@ -98,6 +98,16 @@ struct PipeSlot {
   size_t h_st_cap = 0;
   uint64_t* h_pack_off = nullptr;
   size_t h_po_cap = 0;
+  // amplitudes (batches that ask for them): the chunk's amplitude arena, its
+  // clusters' amp_first and its events' slices (rebased to the chunk's first)
+  uint8_t* d_amp = nullptr;
+  size_t amp_cap = 0;
+  uint32_t* d_amp_first = nullptr;
+  size_t af_cap = 0;
+  uint64_t* d_amp_off = nullptr;
+  size_t ao_cap = 0;
+  uint64_t* h_amp_off = nullptr;
+  size_t h_ao_cap = 0;
   // the chunk in flight: chunk `chunk` of `job`, or job == null when the slot is idle
   struct HostJob* job = nullptr;
   size_t chunk = 0;
@@ -109,6 +119,7 @@ struct Chunk {
   uint64_t base;       // first raw byte copied (event_off[e0] rounded down to 16)
   uint64_t bytes;      // raw bytes copied
   uint64_t clu_total;  // staging records (sum over events of bytes / 2 + 1)
+  uint64_t amp_base = 0, amp_bytes = 0;  // amplitudes: the chunk's range of the caller's amp array
 };
 
 // A batch submitted with sst_batch_host_submit: the caller's buffers, its chunks
@@ -125,6 +136,8 @@ struct HostJob {
   std::vector<Chunk> chunks;
   uint32_t max_e = 0;
   uint64_t max_bytes = 0, max_clu = 0;
+  bool amps = false;     // out.amp given: amplitudes too (out.amp_off: host, the events' slices)
+  uint64_t max_amp = 0;  // largest chunk amplitude range
   size_t next = 0;      // next chunk to issue
   size_t finished = 0;  // chunks whose clusters are on their way to the caller
   uint64_t pos = 0;     // clusters stored so far
@@ -133,14 +146,21 @@ struct HostJob {
   cudaError_t err = cudaSuccess;
 };
 
-bool slot_fits(const PipeSlot& s, uint32_t E, uint32_t nf, uint64_t bytes, uint64_t clu) {
+bool slot_fits(const PipeSlot& s, uint32_t E, uint32_t nf, uint64_t bytes, uint64_t clu, uint64_t amp) {
+  if (amp && (s.amp_cap < amp || s.af_cap < clu || s.ao_cap < E + 1u || s.h_ao_cap < E + 1u)) return false;
   return s.raw_cap >= bytes && s.fl_cap >= (size_t)E * nf && s.eo_cap >= E + 1u && s.co_cap >= E + 1u &&
          s.st_cap >= E && s.po_cap >= E + 1u && s.clu_cap >= clu && s.h_eo_cap >= E + 1u && s.h_co_cap >= E + 1u &&
          s.h_st_cap >= E && s.h_po_cap >= E + 1u && s.ev_h2d != nullptr;
 }
 
-cudaError_t grow_slot(PipeSlot& s, uint32_t E, uint32_t nf, uint64_t bytes, uint64_t clu) {
+cudaError_t grow_slot(PipeSlot& s, uint32_t E, uint32_t nf, uint64_t bytes, uint64_t clu, uint64_t amp) {
   cudaError_t e;
+  if (amp) {
+    if ((e = dgrow(s.d_amp, s.amp_cap, amp))) return e;
+    if ((e = dgrow(s.d_amp_first, s.af_cap, clu))) return e;
+    if ((e = dgrow(s.d_amp_off, s.ao_cap, E + 1))) return e;
+    if ((e = hgrow(s.h_amp_off, s.h_ao_cap, E + 1))) return e;
+  }
   for (cudaEvent_t* ev : {&s.ev_h2d, &s.ev_comp, &s.ev_status, &s.ev_d2h})
     if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming))) return e;
   if ((e = dgrow(s.d_raw, s.raw_cap, bytes))) return e;
@@ -179,6 +199,10 @@ void free_slot(PipeSlot& s) {
   cudaFreeHost(s.h_clu_off);
   cudaFreeHost(s.h_status);
   cudaFreeHost(s.h_pack_off);
+  cudaFree(s.d_amp);
+  cudaFree(s.d_amp_first);
+  cudaFree(s.d_amp_off);
+  cudaFreeHost(s.h_amp_off);
   for (cudaEvent_t ev : {s.ev_h2d, s.ev_comp, s.ev_status, s.ev_d2h})
     if (ev) cudaEventDestroy(ev);
   s = PipeSlot{};
@@ -259,6 +283,11 @@ cudaError_t enqueue_chunk(sst_ctx* ctx, sst_host_pipe& p, PipeSlot& s, HostJob* 
     return e;
   if ((e = cudaMemcpyAsync(s.d_clu_off, s.h_clu_off, (E + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, p.h2d)))
     return e;
+  if (job->amps) {  // the events' amplitude slices, rebased to the chunk's first byte
+    for (uint32_t i = 0; i <= E; i++) s.h_amp_off[i] = job->out.amp_off[c.e0 + i] - c.amp_base;
+    if ((e = cudaMemcpyAsync(s.d_amp_off, s.h_amp_off, (E + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, p.h2d)))
+      return e;
+  }
   if ((e = cudaEventRecord(s.ev_h2d, p.h2d))) return e;
   // kernels, once the inputs are in and the slot's previous clusters are out
   if ((e = cudaStreamWaitEvent(p.comp, s.ev_h2d, 0))) return e;
@@ -270,8 +299,18 @@ cudaError_t enqueue_chunk(sst_ctx* ctx, sst_host_pipe& p, PipeSlot& s, HostJob* 
   out.charge = s.d_charge;
   out.barycenter = s.d_bary;
   out.capacity = c.clu_total;
+  if (job->amps) {
+    out.amp = s.d_amp;
+    out.amp_first = s.d_amp_first;
+    out.amp_off = s.d_amp_off;
+    out.amp_capacity = c.amp_bytes ? c.amp_bytes : 1;
+  }
   if ((e = sst::launch_batch(s.d_raw, s.d_event_off, s.d_fed_len, E, nf, s.d_clu_off, out, s.d_status,
                              sst::kparams(ctx), p.scratch, ctx->shape, ctx->n_sm, p.comp, s.d_pack_off)))
+    return e;
+  // amp_first: from the chunk's arena to the caller's array
+  if (job->amps && c.amp_base &&
+      (e = sst::rebase_amp_first(s.d_amp_first, s.d_pack_off + E, (uint32_t)c.amp_base, ctx->n_sm, p.comp)))
     return e;
   if ((e = cudaEventRecord(s.ev_comp, p.comp))) return e;
   // statuses and event starts back to the host
@@ -319,7 +358,13 @@ cudaError_t finish_chunk(sst_host_pipe& p, PipeSlot& s) {
     if ((e = cudaMemcpyAsync(out->width + q, s.d_width, stored * 2, cudaMemcpyDeviceToHost, p.d2h))) return e;
     if ((e = cudaMemcpyAsync(out->charge + q, s.d_charge, stored * 4, cudaMemcpyDeviceToHost, p.d2h))) return e;
     if ((e = cudaMemcpyAsync(out->barycenter + q, s.d_bary, stored * 4, cudaMemcpyDeviceToHost, p.d2h))) return e;
+    if (job->amps &&
+        (e = cudaMemcpyAsync(out->amp_first + q, s.d_amp_first, stored * 4, cudaMemcpyDeviceToHost, p.d2h)))
+      return e;
   }
+  if (job->amps && c.amp_bytes &&
+      (e = cudaMemcpyAsync(out->amp + c.amp_base, s.d_amp, c.amp_bytes, cudaMemcpyDeviceToHost, p.d2h)))
+    return e;
   if ((e = cudaEventRecord(s.ev_d2h, p.d2h))) return e;
   job->pos += stored;
   s.job = nullptr;
@@ -388,13 +433,18 @@ cudaError_t prepare_job(sst_host_pipe& p, const HostJob* job) {
   const uint32_t nf = job->n_feds;
   bool fits = p.scratch.items_cap >= (size_t)job->max_e * nf * sst::kFe && p.scratch.ev_cap >= job->max_e &&
               p.scratch.stage_cap >= job->max_clu;
-  for (const PipeSlot& s : p.slots) fits = fits && slot_fits(s, job->max_e, nf, job->max_bytes, job->max_clu);
+  const uint64_t amp = job->amps ? (job->max_amp ? job->max_amp : 1) : 0;
+  if (amp)
+    fits = fits && p.scratch.amp_items_cap >= (size_t)job->max_e * nf * sst::kFe && p.scratch.amp_ev_cap >= job->max_e &&
+           p.scratch.amp_stage_cap >= amp;
+  for (const PipeSlot& s : p.slots) fits = fits && slot_fits(s, job->max_e, nf, job->max_bytes, job->max_clu, amp);
   if (fits) return cudaSuccess;
   cudaError_t e = drain(p);
   if (!e) e = sst::ensure_scratch(p.scratch, (size_t)job->max_e * nf * sst::kFe, job->max_e, job->max_clu);
   if (!e) e = sst::ensure_spill(p.scratch, (size_t)p.ctx->n_sm * sst::kMaxWarpsPerSm);
+  if (!e && amp) e = sst::ensure_amp_scratch(p.scratch, (size_t)job->max_e * nf * sst::kFe, job->max_e, amp);
   for (PipeSlot& s : p.slots)
-    if (!e) e = grow_slot(s, job->max_e, nf, job->max_bytes, job->max_clu);
+    if (!e) e = grow_slot(s, job->max_e, nf, job->max_bytes, job->max_clu, amp);
   return e;
 }
 
@@ -479,11 +529,18 @@ sst_status sst_batch_host_submit(sst_ctx* ctx, const uint8_t* raw, const uint64_
     return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch_host: null pointer");
   if (n_events == 0 || n_feds == 0 || n_feds > ctx->n_feds)
     return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch_host: bad n_events / n_feds");
-  if (out->amp)
-    return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch_host: amplitudes are produced by sst_batch and sst_cluster");
   for (uint32_t i = 0; i < n_events; i++)
     if (event_off[i + 1] < event_off[i])
       return set_err(ctx, SST_ERR_INVALID_ARG, "sst_batch_host: event_off decreases");
+  if (out->amp) {
+    bool ok = out->amp_first && out->amp_off && out->amp_capacity > 0 && out->amp_capacity < kNoAmp &&
+              out->amp_off[n_events] <= out->amp_capacity;
+    for (uint32_t i = 0; ok && i < n_events; i++) ok = out->amp_off[i + 1] >= out->amp_off[i];
+    if (!ok)
+      return set_err(ctx, SST_ERR_INVALID_ARG,
+                     "sst_batch_host: amp needs amp_first and a non-decreasing host amp_off within "
+                     "1 <= amp_capacity < 2^32 - 1");
+  }
   auto* job = new HostJob();
   job->raw = raw;
   job->event_off = event_off;
@@ -493,12 +550,18 @@ sst_status sst_batch_host_submit(sst_ctx* ctx, const uint8_t* raw, const uint64_
   job->out = *out;
   job->event_first = event_first;
   job->status = status;
+  job->amps = out->amp != nullptr;
   // chunks of consecutive events
   const std::vector<uint32_t> cut = plan_chunks(n_events, ctx->shape.host_chunk);
   for (size_t k = 0; k + 1 < cut.size(); k++) {
     const uint32_t e0 = cut[k], e1 = cut[k + 1];
     Chunk c{e0, e1, event_off[e0] & ~15ull, 0, 0};
     c.bytes = event_off[e1] - c.base;
+    if (job->amps) {
+      c.amp_base = out->amp_off[e0];
+      c.amp_bytes = out->amp_off[e1] - c.amp_base;
+      if (c.amp_bytes > job->max_amp) job->max_amp = c.amp_bytes;
+    }
     for (uint32_t i = e0; i < e1; i++) c.clu_total += (event_off[i + 1] - event_off[i]) / 2 + 1;
     job->chunks.push_back(c);
     if (e1 - e0 > job->max_e) job->max_e = e1 - e0;

@@ -115,6 +115,8 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
                          uint64_t* pack_off = nullptr, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr,
                          const uint64_t* event_end = nullptr);
 cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st);
+// Adds base to the first *count (device) values of amp_first, kNoAmp excepted.
+cudaError_t rebase_amp_first(uint32_t* amp_first, const uint64_t* count, uint32_t base, int n_sm, cudaStream_t st);
 cudaError_t build_calib(const float* noise_dev, const uint32_t* mask_dev, uint2* calq_dev,
                         uint64_t n_strips, const sst_params& p, cudaStream_t st);
 

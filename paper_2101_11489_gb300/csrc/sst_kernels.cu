@@ -1045,6 +1045,17 @@ __global__ void __launch_bounds__(256, 4) k_batch(const uint8_t* __restrict__ ra
   pdl_release();
 }
 
+// Host batches with amplitudes: the chunk's amp_first values index the chunk's
+// amplitude arena; adding the chunk's first byte in the caller's array makes them
+// absolute.  The first *count records are rebased (kNoAmp stays).
+__global__ void k_rebase_amp(uint32_t* __restrict__ amp_first, const uint64_t* __restrict__ count, uint32_t base) {
+  const uint64_t n = *count;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t a = amp_first[i];
+    if (a != kNoAmp) amp_first[i] = a + base;
+  }
+}
+
 __global__ void k_badmask(const uint8_t* __restrict__ bad, uint32_t* __restrict__ mask, uint64_t n_words) {
   const uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= n_words) return;
@@ -1393,6 +1404,11 @@ cudaError_t launch_batch(const uint8_t* raw, const uint64_t* event_off, const ui
                       ev_begin, ev_end);
   if (e) return e;
   return launch_order(clu_off, n_events, n_feds * (kFe / (sh.units == 1 ? 1 : 2)), out, status, s, pack_off, am, st);
+}
+
+cudaError_t rebase_amp_first(uint32_t* amp_first, const uint64_t* count, uint32_t base, int n_sm, cudaStream_t st) {
+  k_rebase_amp<<<(unsigned)(n_sm > 0 ? n_sm * 2 : 128), 256, 0, st>>>(amp_first, count, base);
+  return cudaGetLastError();
 }
 
 cudaError_t build_badmask(const uint8_t* bad_dev, uint32_t* mask_dev, uint64_t n_strips, cudaStream_t st) {

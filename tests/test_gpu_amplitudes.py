@@ -122,18 +122,42 @@ def test_amplitude_capacity_overflow_is_flagged_and_leaves_clusters_whole(w0):
     assert stored <= cap
 
 
-def test_host_batch_rejects_amplitudes(w0):
+@pytest.mark.parametrize("chunk", [2, 0])
+def test_host_batch_amplitudes_equal_the_oracle(w0, chunk):
+    """sst_batch_host with amplitudes: events in host memory, processed in chunks
+    (2 events per chunk, or the default plan), each chunk's amp_first made absolute
+    and its amplitude slices copied back; every event equals the oracle."""
+    w, calib, gd, gg = w0
+    events = [eg.make_event(w, calib, 50 + i, occupancy=0.005 + 0.02 * (i % 4)) for i in range(7)]
+    n = len(events)
+    sizes = [e.nbytes for e in events]
+    eoff = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    aoff = np.concatenate([[0], np.cumsum([4 * s for s in sizes])]).astype(np.uint64)
+    raw = np.concatenate([e.raw for e in events])
+    fl = np.concatenate([e.fed_len for e in events]).astype(np.uint32)
+    out = sst.HostClusters.alloc(int(sum(s // 2 + 1 for s in sizes)), amp_off=aoff)
+    ef = np.zeros(n + 1, np.uint64)
+    sth = np.zeros((n, 4), np.uint32)
+    keep = sst.sst_get_tune(gd.ctx)
+    try:
+        sst.sst_set_tune(gd.ctx, host_chunk_events=chunk)
+        sst.sst_batch_host(gd.ctx, raw, eoff, fl, n, w.n_feds, out, ef, sth)
+    finally:
+        sst.sst_set_tune(gd.ctx, **keep)
+    for k, e in enumerate(events):
+        c_orc, st_orc, af, amp = oracle_amps(gd, e, w.n_feds)
+        assert int(sth[k, 1]) == st_orc["n_clusters"] and int(sth[k, 2]) == st_orc["flags"]
+        ch = out.view(int(ef[k]), int(sth[k, 1]))
+        check_against_oracle(ch, out.amp, c_orc, af, amp, base=int(aoff[k]))
+
+
+def test_host_batch_rejects_inconsistent_amplitude_slices(w0):
     w, calib, gd, _ = w0
     e = eg.make_event(w, calib, 40)
-    out = sst.HostClusters.alloc(16)
-    rec = out.record()
-    buf = np.zeros(16, np.uint8)
-    rec.amp = buf.ctypes.data
-    rec.amp_first = out.det.ctypes.data
-    rec.amp_capacity = 16
-    import ctypes
-    L = sst.load_library()
     eoff = np.array([0, e.nbytes], np.uint64)
-    code = L.sst_batch_host(gd.ctx, e.raw.ctypes.data, eoff.ctypes.data, e.fed_len.ctypes.data, 1, w.n_feds,
-                            ctypes.byref(rec), np.zeros(2, np.uint64).ctypes.data, np.zeros(4, np.uint32).ctypes.data)
-    assert code == sst.SST_ERR_INVALID_ARG
+    out = sst.HostClusters.alloc(e.nbytes // 2 + 1, amp_off=np.array([0, 64], np.uint64))
+    out.amp_off[1] = out.amp.size + 1  # past amp_capacity
+    with pytest.raises(sst.SstError) as ei:
+        sst.sst_batch_host(gd.ctx, e.raw, eoff, e.fed_len, 1, w.n_feds, out, np.zeros(2, np.uint64),
+                           np.zeros(4, np.uint32))
+    assert ei.value.code == sst.SST_ERR_INVALID_ARG
