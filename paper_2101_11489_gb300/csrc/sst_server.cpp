@@ -610,24 +610,31 @@ void release_server(sst_ctx* ctx, sst_server* sv) {
 // Whether the kernels may read [p, p + n) in place: 16-byte aligned, a multiple of
 // 16 bytes, and its first and last bytes in page-locked host memory that the
 // device sees at the same address (the caller guarantees that the whole span is one
-// such allocation).  Returns null when it may, else what is wrong.  The calling
-// thread's device is set first, so that the query sees the server's context.
+// such allocation).  Returns null when it may, else what is wrong.  The query runs
+// with the server's device current (the calling thread's device is restored).
 const char* pinned_span(int device, const uint8_t* p, uint64_t n) {
   if (n == 0) return nullptr;
   if ((uintptr_t)p & 15u) return "not 16-byte aligned";
   if (n & 15u) return "length not a multiple of 16 bytes";
-  cudaSetDevice(device);
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != device) cudaSetDevice(device);
+  const char* why = nullptr;
   for (const uint8_t* q : {p, p + n - 1}) {
     cudaPointerAttributes a{};
     const cudaError_t e = cudaPointerGetAttributes(&a, q);
     if (e != cudaSuccess) {
       cudaGetLastError();  // not a pointer the runtime knows: not readable in place
-      return "unknown to the CUDA runtime";
+      why = "unknown to the CUDA runtime";
+    } else if (a.type != cudaMemoryTypeHost) {
+      why = "not page-locked host memory";
+    } else if (a.devicePointer != (const void*)q) {
+      why = "mapped at another address on the device";
     }
-    if (a.type != cudaMemoryTypeHost) return "not page-locked host memory";
-    if (a.devicePointer != (const void*)q) return "mapped at another address on the device";
+    if (why) break;
   }
-  return nullptr;
+  if (prev >= 0 && prev != device) cudaSetDevice(prev);
+  return why;
 }
 
 sst_status submit_one(sst_ctx* ctx, sst_server* sv, const uint8_t* raw, uint64_t raw_bytes, const uint32_t* fed_len,
