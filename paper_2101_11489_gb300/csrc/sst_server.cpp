@@ -618,7 +618,7 @@ const char* pinned_span(int device, const uint8_t* p, uint64_t n) {
   if (n & 15u) return "length not a multiple of 16 bytes";
   int prev = -1;
   cudaGetDevice(&prev);
-  if (prev != device) cudaSetDevice(device);
+  cudaSetDevice(device);  // also binds the device's context to a thread that has made no CUDA call yet
   const char* why = nullptr;
   for (const uint8_t* q : {p, p + n - 1}) {
     cudaPointerAttributes a{};

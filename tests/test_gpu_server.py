@@ -236,15 +236,17 @@ def test_stop_while_other_threads_submit_and_poll():
         g.close()
 
 
-def test_native_client_saturating_and_poisson():
+@pytest.mark.parametrize("zero_copy", [True, "in_place"])
+def test_native_client_saturating_and_poisson(zero_copy):
     """The native load generator (sst_serve_load) drives the server through the
-    public calls: every request is collected, latencies are ordered, and an
-    offered rate well below capacity is what comes out."""
+    public calls from its own threads (lent buffers copied, or read in place):
+    every request is collected, latencies are ordered, and an offered rate well
+    below capacity is what comes out."""
     w = eg.WORKLOADS[0]
     calib = eg.make_calibration(w.n_feds, w.seed, w.p_bad)
     g = Gpu(calib.noise, calib.gain, calib.bad)
     try:
-        sst.sst_server_start(g.ctx, 512 << 20, 16, 3, 256, w.n_feds, zero_copy=True)
+        sst.sst_server_start(g.ctx, 512 << 20, 16, 3, 256, w.n_feds, zero_copy=zero_copy)
         pinned = [torch.from_numpy(eg.make_event(w, calib, 200 + i).raw).pin_memory() for i in range(8)]
         evs = [(p.numpy(), eg.make_event(w, calib, 200 + i).fed_len) for i, p in enumerate(pinned)]
         sat = sst.sst_serve_load(g.ctx, evs, 2000, 0.0, submitters=4, pollers=2)
