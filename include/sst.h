@@ -443,8 +443,10 @@ typedef struct {
 /* Starts the request loop (one host thread, max_inflight streams): section 3's
  * events processed concurrently on one GPU as they arrive, with their transfers
  * overlapped with the computation and device memory taken once (the paper's
- * caching allocator), here carved from mem_budget_bytes at start.  Requires
- * calibration.  STATE if already running. */
+ * caching allocator), here carved from mem_budget_bytes at start.  A batch of the
+ * pending events is launched whenever a slot is free; the batches' kernels run one
+ * batch at a time (each launch fills the GPU) and each batch's copies overlap the
+ * next one's kernels.  Requires calibration.  STATE if already running. */
 sst_status sst_server_start(sst_ctx* ctx, const sst_server_opts* opts);
 
 /* Stops the loop and frees the server; unpolled results are discarded.  Safe while
@@ -460,7 +462,9 @@ sst_status sst_server_stop(sst_ctx* ctx);
  * into max_inflight batch slots of equal size, each holding a raw arena of
  * budget / (25 max_inflight) bytes and the cluster and staging arrays for it, so
  * that the device memory in use never exceeds the budget; admitted events wait
- * for a slot in a pinned host pool of max_inflight + 1 raw arenas (at most 2 GiB).
+ * for a slot in a pinned host pool of max_inflight + 1 raw arenas (at most 2 GiB;
+ * with zero_copy the event's size is reserved in it, its bytes stay with the
+ * caller).
  * Returns OK and a ticket; BUSY when all max_requests request slots are taken;
  * BUDGET when the event does not fit the host pool now (retry after polling);
  * TOO_LARGE when it exceeds one raw arena (it never fits); STATE when no server
