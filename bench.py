@@ -813,6 +813,29 @@ def run_single(args, rank, world, local, wid):
     st = dbuf.to_host()
     n_digi, n_clu = st["n_digi"], st["n_clusters"]
 
+    # the same launch sequence captured once as a CUDA graph and replayed (L2
+    # flushed before every replay): what the launch gaps of one event cost
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        step()
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    torch.cuda.synchronize()
+    g_steps = max(3, min(args.steps, 300))
+    g_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(g_steps)]
+    for i in range(g_steps):
+        flush.fill_(i & 0xFF)
+        g_ev[i][0].record(stream)
+        graph.replay()
+        g_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    g_ms = max_over_ranks([float(np.median([a.elapsed_time(b) for a, b in g_ev]))], world)[0]
+    assert dbuf.to_host()["n_clusters"] == n_clu, "graph replay differs"
+    del graph
+
     # end to end through the public calls with host buffers: copy the event in
     # (pinned), unpack + cluster, read the status, then the event's clusters out
     raw_pin = torch.from_numpy(ev.raw).pin_memory()
@@ -872,6 +895,9 @@ def run_single(args, rank, world, local, wid):
                     "h2d_bytes_per_step": int(ev.raw.nbytes + ev.fed_len.nbytes),
                     "d2h_bytes_per_step": int(16 + 16 * n_out), "steps": e2e_steps,
                     "api": "pinned copy in, sst_unpack + sst_cluster, status then the event's clusters copied out"},
+            "graph": {"value": round(world * 1e3 / g_ms, 1), "unit": "events/s", "ms_per_step": round(g_ms, 4),
+                      "steps": g_steps, "what": "the same launch sequence captured once as a CUDA graph and "
+                                                "replayed (median step)"},
             "gpu_launches": 5 * args.steps,
             "roofline": {"bound": "hbm", "achieved": round(b_alg / (mean_ms / 1e3) / 1e9, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(b_alg / (mean_ms / 1e3) / 1e9 / peak, 4), "traffic": None,
