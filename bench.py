@@ -644,7 +644,7 @@ def main():
         assert np.array_equal(o[2], st_h), "sst_batch_host statuses differ from sst_batch"
     barrier()
     t0 = time.perf_counter()
-    e2e_steps = max(3, min(args.steps, 200))
+    e2e_steps = max(100, min(args.steps, 200))  # enough steps to amortise the pipeline's fill and drain
     d2h_total = e2e_run(e2e_steps)
     barrier()
     sst.sst_set_tune(ctx, **tune)
@@ -861,7 +861,7 @@ def run_single(args, rank, world, local, wid):
 
     for _ in range(3):
         e2e_step()
-    e2e_steps = max(3, min(args.steps, 200))
+    e2e_steps = max(100, min(args.steps, 200))  # enough steps to amortise the pipeline's fill and drain
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         n_out = e2e_step()
