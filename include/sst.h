@@ -199,9 +199,9 @@ const char* sst_last_error(const sst_ctx* ctx);
  * and the thresholds.  The tables are copied to device memory and stay resident;
  * a new upload replaces them after work already queued on `stream`, and returns
  * once they are in place.  From the bad-strip flags and the hole / bad-strip
- * limits the device also builds a bit mask and, per strip, the longest gap below
- * it that still links two successive active strips (one byte per strip, 255 for a
- * bad strip), which the clusterizers read instead of walking each gap.
+ * limits the device also builds a bit mask and, per strip, a linking limit from
+ * the longest gap below it that still links two successive active strips (one
+ * byte per strip), which the clusterizers read instead of walking each gap.
  * INVALID_ARG on a null pointer, a non-finite or negative value, or parameters
  * outside their requirements; the previous calibration then stays in place. */
 sst_status sst_calib_upload(sst_ctx* ctx, const float* noise, const float* gain, const uint8_t* bad,

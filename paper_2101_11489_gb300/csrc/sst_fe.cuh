@@ -18,13 +18,14 @@
 //               run in a slot indexed by the byte position of its header / 3
 //               (headers are at least 3 bytes apart, so slots never collide and
 //               ascend in (channel, strip) order);
-//   mark_slots  one lane per slot puts each run's descriptor at the tile position
-//               of its first digi (channel base + digis of the channel before the
-//               run) and sets that position's run-start bit;
+//   mark_slots  the tile is cleared, then each lane takes four slots and puts each
+//               run's descriptor at the tile position of its first digi (channel
+//               base + digis of the channel before the run): a nonzero tile word
+//               marks a run start (no atomics);
 //   scan_unit   32 digis at a time: each lane finds its digi's run (the last
-//               run-start bit at or below it), reads its ADC byte, and applies the
-//               thresholds, the gain correction, the candidate rule and the
-//               leftmost-seed rule (warp ballots, carries across windows);
+//               nonzero tile word at or below it, by a ballot), reads its ADC byte,
+//               and applies the thresholds, the gain correction, the candidate rule
+//               and the leftmost-seed rule (warp ballots, carries across windows);
 //   form_unit   one lane per owned candidate: sums, cluster threshold, centroid.
 // Pairs whose digis exceed the tile, or whose bytes exceed the slot area, walk
 // their runs a second time per chunk of channels (mark_walk) instead of using slots.
@@ -46,15 +47,15 @@ struct __align__(16) WarpT {
   static constexpr int kChW = U * kChPerFe;         // consecutive channels per work item
   static constexpr int kTile = U == 2 ? 448 : 256;  // digis per warp tile (a chunk of whole channels)
   static constexpr int kBuf = U == 2 ? 1376 : 704;  // bytes of the units staged per warp (larger ones are read in place)
-  static constexpr int kRsWords = kTile / 32;       // run-start bits of the tile
   static constexpr int kSlots = (kTile * 2 + kChW * kMaskWords * 4) / 4;  // run-header slots in own[] + bad[]
   uint8_t fe[kBuf];                      // staged bytes of the FE units
   float qmul[kChW * 2];                  // per APV of the channels: certified multiplier, or -gain
-  uint32_t kf[kTile];   // before scan_unit: run descriptors at run starts (ADC byte position << 13 | first
-                        // strip << 5 | channel) or, without run starts, key | ADC << 16 per digi; after: one
-                        // word per digi: key (channel in the work item << 8 | strip, 13 bits; sorted) |
-                        // flags << 13 (1 active, 2 seed, 4 first strip of a candidate) | ADC << 16 |
-                        // gain-corrected charge of active digis << 24
+  uint32_t kf[kTile + 4];  // before scan_unit: run descriptors at run starts (ADC byte position << 13 |
+                           // channel << 8 | first strip), 0 elsewhere, or, in the per-event kernel,
+                           // key | ADC << 16 per digi; after: one word per digi: key (channel in the
+                           // work item << 8 | strip, 13 bits; sorted) | flags << 13 (1 active, 2 seed,
+                           // 4 first strip of a candidate) | ADC << 16 | gain-corrected charge << 24
+                           // (ADC and charge 0 for an inactive digi), then a candidate-start sentinel
   float nsq[kTile];     // noise^2 of each digi
   uint16_t own[kTile];  // first digi of every seeded candidate (run slots, with bad[], until scan_unit)
   uint32_t bad[kChW * kMaskWords];       // bad-strip masks of the channels (only when max_adj > 0)
@@ -62,7 +63,6 @@ struct __align__(16) WarpT {
   uint32_t chan_cnt[kChW + 1];           // digis per channel, then exclusive prefix
   uint16_t chan_len[kChW];
   uint8_t chan_st[kChW];
-  uint32_t rs[kRsWords];                 // run-start bits of the tile
   static_assert(kTile % 32 == 0, "whole windows of 32 digis");
 };
 using Warp = WarpT<2>;  // the per-event cluster kernel's warp (it uses 12 of the 24 channels)
@@ -100,11 +100,12 @@ __device__ __forceinline__ bool use_slots(const Unit& un) { return un.staged && 
 template <class W>
 __device__ __forceinline__ uint32_t* slot_area(W& w) { return reinterpret_cast<uint32_t*>(w.own); }
 
-// Run descriptor in a slot: ADC byte position (11 bits) << 21 | first strip << 13 |
-// channel << 8 | digis of the channel before the run.  Never 0: the ADC bytes of a
-// run start at least 5 bytes into the pair.  An empty slot is 0.
+// Run descriptor in a slot: the run's tile descriptor (ADC byte position, 11 bits,
+// << 13 | channel << 8 | first strip) << 8 | digis of the channel before the run.
+// Never 0: the ADC bytes of a run start at least 5 bytes into the pair.  An empty
+// slot is 0.
 __device__ __forceinline__ uint32_t slot_desc(uint32_t adc_pos, uint32_t first, uint32_t c, uint32_t toff) {
-  return (adc_pos << 21) | (first << 13) | (c << 8) | toff;
+  return (adc_pos << 21) | (c << 16) | (first << 8) | toff;
 }
 
 // One lane's walk over its channel's runs (record r, len bytes, the record at
@@ -122,9 +123,9 @@ __device__ __forceinline__ uint32_t walk_runs(const uint8_t* r, uint32_t len, ui
   while (p + 2 <= len) {
     const uint32_t first = r[p], wd = r[p + 1];
     const uint32_t end = first + wd, np = p + 2 + wd;
-    if (wd == 0 || end > (uint32_t)kStrips || first < prev_end || np > len) {
-      err = (wd == 0 || end > (uint32_t)kStrips) ? SST_CH_RUN_RANGE : first < prev_end ? SST_CH_RUN_ORDER
-                                                                                        : SST_CH_TRUNC;
+    const bool range = wd - 1u > (uint32_t)kStrips - 1u - first;  // width 0, or past strip 256
+    if (range || first < prev_end || np > len) {
+      err = range ? SST_CH_RUN_RANGE : first < prev_end ? SST_CH_RUN_ORDER : SST_CH_TRUNC;
       break;
     }
     if (SLOTS) slots[(pos + p) / 3u] = slot_desc(pos + p + 2, first, c, cnt);
@@ -165,25 +166,31 @@ __device__ uint32_t parse_unit(W& w, const Unit& un, const uint8_t* src, uint32_
     const int h = lane >> 4;
     const uint32_t base = h ? un.off1 : 0u;
     const uint32_t end = h ? un.len1 : un.len;
-    bool good = un.src != nullptr;
     uint32_t p = 0;
-    for (int k = 0; k < kChPerFe; k++) {
-      uint32_t l = 0;
-      if (good) {
-        if (p + 2 > end) {
-          good = false;
-        } else {
-          l = (uint32_t)src[base + p] | ((uint32_t)src[base + p + 1] << 8);
-          if (l < 3 || p + l > end) good = false;
-        }
+    int k = 0;
+    if (un.src != nullptr) {
+      // a unit that breaks the chain is marked as a whole below; the positions and
+      // lengths written for it are then never read
+#pragma unroll
+      for (; k < kChPerFe; k++) {
+        if (p + 2 > end) break;
+        const uint32_t l = (uint32_t)src[base + p] | ((uint32_t)src[base + p + 1] << 8);
+        if (l < 3 || p + l > end) break;
+        w.chan_pos[h * kChPerFe + k] = base + p;
+        w.chan_len[h * kChPerFe + k] = (uint16_t)l;
+        p += l;
       }
-      w.chan_pos[h * kChPerFe + k] = good ? base + p : 0u;
-      w.chan_len[h * kChPerFe + k] = good ? (uint16_t)l : (uint16_t)0;
-      if (good) p += l;
     }
-    if (good && p != end) good = false;
-    const uint8_t st = un.src == nullptr ? un.fed_status : (good ? (uint8_t)0 : (uint8_t)SST_CH_FRAMING);
-    for (int k = 0; k < kChPerFe; k++) w.chan_st[h * kChPerFe + k] = st;
+    const bool good = k == kChPerFe && p == end;
+    const uint32_t st = un.src == nullptr ? un.fed_status : (good ? 0u : (uint32_t)SST_CH_FRAMING);
+    uint32_t* st4 = reinterpret_cast<uint32_t*>(w.chan_st + h * kChPerFe);  // 4-byte aligned
+#pragma unroll
+    for (int v = 0; v < kChPerFe / 4; v++) st4[v] = st * 0x01010101u;
+    if (!good) {  // no data, or a broken chain: no channel of the unit is walked (its status may be 0)
+      uint32_t* len2 = reinterpret_cast<uint32_t*>(w.chan_len + h * kChPerFe);  // 4-byte aligned
+#pragma unroll
+      for (int v = 0; v < kChPerFe / 2; v++) len2[v] = 0u;
+    }
   }
   __syncwarp();
   uint32_t cnt = 0;
@@ -204,7 +211,6 @@ __device__ uint32_t parse_unit(W& w, const Unit& un, const uint8_t* src, uint32_
     w.chan_st[lane] = st;
     if (st) w.chan_len[lane] = 0;
   }
-  if (lane < W::kRsWords) w.rs[lane] = 0u;
   uint32_t total = 0;
   const uint32_t x = warp_excl_sum(cnt, &total);
   if (lane < W::kChW) w.chan_cnt[lane] = x;
@@ -228,40 +234,51 @@ __device__ __forceinline__ uint32_t tile_word(uint32_t c, uint32_t strip, uint32
   return (c << 8) | strip | (adc << 16);
 }
 
-// Tile descriptor of a run: ADC byte position << 13 | first strip << 5 | channel.
+// Tile descriptor of a run: ADC byte position << 13 | key of its first digi (channel << 8 | first strip).
 __device__ __forceinline__ uint32_t tile_desc(uint32_t adc_pos, uint32_t first, uint32_t c) {
-  return (adc_pos << 13) | (first << 5) | c;
+  return (adc_pos << 13) | (c << 8) | first;
+}
+
+// Clears the first n tile words (whole 16-byte vectors; n <= kTile), so that a
+// tile position where no run starts reads 0.
+template <class W>
+__device__ __forceinline__ void clear_tile(W& w, int n) {
+  const int lane = threadIdx.x & 31;
+  for (int v = lane; v < (n + 3) / 4; v += 32) reinterpret_cast<uint4*>(w.kf)[v] = make_uint4(0u, 0u, 0u, 0u);
+  __syncwarp();
 }
 
 // Single-chunk pair with slots (a2): every valid run's slot descriptor goes to the
-// tile position of its first digi (channel base + digis of the channel before it),
-// with its run-start bit.  A run of a channel found invalid was cleared.
+// tile position of its first digi (channel base + digis of the channel before it);
+// a run of a channel found invalid was cleared.  Each lane takes four consecutive
+// slots, so that the lanes' stores spread over the tile.  n: the pair's digis.
 template <class W>
-__device__ void mark_slots(W& w, const Unit& un) {
+__device__ void mark_slots(W& w, const Unit& un, int n) {
   const int lane = threadIdx.x & 31;
-  const uint32_t* slots = slot_area(w);
-  const int ns = (int)n_slots(un);
-  for (int k = lane; k < ns; k += 32) {
-    const uint32_t d = slots[k];
-    if (d) {
-      const uint32_t c = (d >> 8) & 31u;
-      const uint32_t t = w.chan_cnt[c] + (d & 255u);
-      w.kf[t] = tile_desc(d >> 21, (d >> 13) & 255u, c);
-      atomicOr(&w.rs[t >> 5], 1u << (t & 31u));
-    }
+  clear_tile(w, n);  // tile positions that start no run read 0
+  const uint4* slots = reinterpret_cast<const uint4*>(slot_area(w));
+  const int nv = (int)(n_slots(un) + 3u) / 4;  // parse_unit cleared whole vectors: slots past the last are 0
+  auto mark = [&](uint32_t d) {
+    if (d) w.kf[w.chan_cnt[(d >> 16) & 31u] + (d & 255u)] = d >> 8;  // the run's tile descriptor (never 0)
+  };
+  for (int v = lane; v < nv; v += 32) {
+    const uint4 q = slots[v];
+    mark(q.x);
+    mark(q.y);
+    mark(q.z);
+    mark(q.w);
   }
   __syncwarp();
 }
 
-// Chunk [c0, c1) (or a pair whose slots do not fit): lanes c0 .. c1-1 walk their
-// channel's runs again (validated by parse_unit) and write each run's tile
-// descriptor and run-start bit; the walk is bounded by the counted digis, so that
-// it cannot leave the tile.
+// Chunk [c0, c1) (or a pair whose slots do not fit): the chunk's tile words are
+// cleared, then lanes c0 .. c1-1 walk their channel's runs again (validated by
+// parse_unit) and write each run's tile descriptor where it starts; the walk is
+// bounded by the counted digis, so that it cannot leave the tile.
 template <class W>
 __device__ void mark_walk(W& w, const uint8_t* src, int c0, int c1) {
   const int lane = threadIdx.x & 31;
-  if (lane < W::kRsWords) w.rs[lane] = 0u;
-  __syncwarp();
+  clear_tile(w, (int)(w.chan_cnt[c1] - w.chan_cnt[c0]));
   const int c = c0 + lane;
   if (c < c1) {
     const uint32_t cnt = w.chan_cnt[c + 1] - w.chan_cnt[c];
@@ -273,10 +290,7 @@ __device__ void mark_walk(W& w, const uint8_t* src, int c0, int c1) {
     while (p + 2 <= len_c && left > 0) {
       const uint32_t first = r[p], wd0 = r[p + 1];
       const uint32_t wd = wd0 < left ? wd0 : left;
-      if (wd > 0) {
-        w.kf[o] = tile_desc(pos + p + 2, first, (uint32_t)c);
-        atomicOr(&w.rs[o >> 5], 1u << (o & 31u));
-      }
+      if (wd > 0) w.kf[o] = tile_desc(pos + p + 2, first, (uint32_t)c);
       o += wd;
       left -= wd;
       p += 2 + wd0;
@@ -289,20 +303,25 @@ __device__ void mark_walk(W& w, const uint8_t* src, int c0, int c1) {
 // next window's digis are expanded and their calibration gathered while the
 // current window is processed.
 //  - expansion (EXP): the digi's run is the last run start at or below it (the
-//    highest set run-start bit up to the lane, or the last run start of the
-//    windows before, carried with its descriptor); its ADC byte is read from the
-//    pair's bytes.  Without EXP the tile already holds key | ADC << 16 per digi.
+//    highest lane up to this one whose tile word is nonzero, found by a ballot, or
+//    the last run start of the windows before, carried with its descriptor); its
+//    ADC byte is read from the pair's bytes.  Without EXP the tile already holds
+//    key | ADC << 16 per digi (0 for a digi that takes no part).
 //  - thresholds: the per-strip table holds the channel and seed limits as the
 //    largest failing ADC (for an integer ADC, (float)adc > T x noise exactly when
 //    adc > floor(T x noise); a bad strip has 255, so it is never active or a
 //    seed), and the linking gap; the gain-corrected charge of active digis
 //    (saturation codes 254/255 kept) uses the APV's certified multiplier (a
-//    division, in a warp-uniform branch, for an APV without one); noise^2 comes
-//    from the per-strip table;
+//    division, when the work item has an APV without one); noise^2 comes from the
+//    per-strip table;
 //  - candidate starts: an active digi whose previous active digi in the tile lies
 //    in another channel (the tile is sorted by channel, then strip) or is not
-//    linked to it by the hole / bad-strip rules, i.e. is more than gap[strip]
-//    strips below it (the longest linking gap);
+//    linked to it by the hole / bad-strip rules.  One unsigned compare of tile
+//    keys decides both: key - prev - 1 >= lim[strip], where lim = min(G + 1, strip)
+//    and G is the longest linking gap below the strip (a previous active digi of
+//    the same channel is linked when strip - its strip <= G + 1; one of an earlier
+//    channel lies at least strip + 1 keys below, and an unsorted or repeated
+//    strip wraps the difference);
 //  - owners, the leftmost seed of every candidate: two ballots (seeds, candidate
 //    starts) and a carry across windows decide whether another seed lies between
 //    a seed's candidate start and it.
@@ -314,38 +333,42 @@ __device__ int scan_unit(W& w, const KParams& kp, const uint2* __restrict__ calq
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt(lane);
   const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
-  constexpr uint32_t kNone = 0x1FFFu;  // no digi: channel 31, out of range
+  // whether an APV of the work item has no certified multiplier (the scan then divides)
+  static_assert(NCH * 2 <= 64, "two multipliers per lane");
+  const bool any_div = __any_sync(0xffffffffu, (lane < NCH * 2 && w.qmul[lane] < 0.f) ||
+                                                  (lane + 32 < NCH * 2 && w.qmul[lane + 32] < 0.f));
   int n_own = 0, carry_start = -1;
   bool carry_seen = false;
-  uint32_t carry_key = kNone;  // key of the last active digi of the windows before
+  uint32_t carry_key = 0x1FFFu;  // key of the last active digi of the windows before (none: channel 31)
   int run_s = 0;               // expansion: last run start of the windows before, and its descriptor
   uint32_t run_d = 0;
-  // key | ADC << 16 of digi base + lane (kNone beyond n)
+  // key | ADC << 16 of digi base + lane; 0 beyond n (ADC 0: never active, never a seed)
   auto word_at = [&](int base) -> uint32_t {
     const int i = base + lane;
-    if (!EXP) return i < n ? w.kf[i] : kNone;
-    const uint32_t m = w.rs[base >> 5];
+    if (!EXP) return i < n ? w.kf[i] : 0u;
+    const uint32_t v = w.kf[i];  // a run's descriptor where it starts, else 0
+    const uint32_t m = __ballot_sync(0xffffffffu, v != 0u);
     const uint32_t le = m & upto;
+    const uint32_t dl = __shfl_sync(0xffffffffu, v, 31 - __clz(le));  // (lane 31 when le is 0: not used)
     int s = run_s;
     uint32_t d = run_d;
     if (le) {
       s = base + 31 - __clz(le);
-      d = w.kf[s];
+      d = dl;
     }
     if (m) {
       const int l = 31 - __clz(m);
       run_s = base + l;
-      run_d = __shfl_sync(0xffffffffu, d, l);
+      run_d = __shfl_sync(0xffffffffu, v, l);
     }
-    if (i >= n) return kNone;
+    if (i >= n) return 0u;
     const uint32_t k = (uint32_t)(i - s);
     const uint32_t b = (d >> 13) + k;
     const uint32_t adc = b < src_end ? (uint32_t)src[b] : 0u;
-    return ((d & 31u) << 8) | ((((d >> 5) & 255u) + k) & 255u) | (adc << 16);
+    return ((d & 0x1FFFu) + k) | (adc << 16);  // a valid run ends at strip 256 at most: no carry into the channel
   };
   uint32_t wn = word_at(0);
-  uint32_t xn = ((wn >> 8) & 31u) < (uint32_t)NCH ? (wn & 0x1FFFu) : 0u;
-  uint2 vn = __ldg(calq + xn);
+  uint2 vn = __ldg(calq + (wn & 0x1FFFu));
   for (int base = 0; base < n; base += 32) {
     const int i = base + lane;
     const uint32_t word = wn;
@@ -353,30 +376,27 @@ __device__ int scan_unit(W& w, const KParams& kp, const uint2* __restrict__ calq
     const float nq = __uint_as_float(vn.y);
     if (base + 32 < n) {
       wn = word_at(base + 32);
-      xn = ((wn >> 8) & 31u) < (uint32_t)NCH ? (wn & 0x1FFFu) : 0u;
-      vn = __ldg(calq + xn);
+      vn = __ldg(calq + (wn & 0x1FFFu));
     }
     const uint32_t key = word & 0x1FFFu;
-    const uint32_t c = key >> 8, st = key & 255u;
-    const uint32_t adc = (word >> 16) & 255u;
-    const bool inr = c < (uint32_t)NCH;
-    const bool act = inr && adc > (cv & 255u);
-    const bool sd = inr && adc > ((cv >> 8) & 255u);
-    const uint32_t gmax = (cv >> 16) & 255u;
+    const uint32_t adc = word >> 16;
+    const bool act = adc > (cv & 255u);
+    const bool sd = adc > ((cv >> 8) & 255u);
+    const uint32_t gm = (cv >> 16) & 255u;
     // gain-corrected charge with the APV's multiplier; an APV without a certified
-    // multiplier (rq < 0) divides, in a branch the whole warp takes together
+    // multiplier (rq < 0) divides, in a branch taken only for a work item with one
     const float a = __uint2float_rn(adc);
-    const float rq = w.qmul[inr ? key >> 7 : 0u];  // the APV of strip st of channel c: 2 c + (st >> 7)
+    const float rq = w.qmul[key >> 7];  // the APV of strip st of channel c: 2 c + (st >> 7)
     float xq = __fmul_rn(a, rq);
-    if (__any_sync(0xffffffffu, rq < 0.f))
+    if (any_div)
       if (rq < 0.f) xq = __fdiv_rn(a, -rq);
     const int ci = __float2int_rz(__fadd_rn(xq, 0.5f));
     const uint32_t q = !act ? 0u : (adc >= 254u ? adc : (ci > 253 ? 254u : (uint32_t)ci));
     const unsigned A = __ballot_sync(0xffffffffu, act);
     const unsigned Al = A & lt;
-    const uint32_t pk_l = __shfl_sync(0xffffffffu, key, Al ? 31 - __clz(Al) : lane);
+    const uint32_t pk_l = __shfl_sync(0xffffffffu, key, 31 - __clz(Al));  // (lane 31 when Al is 0: not used)
     const uint32_t pk = Al ? pk_l : carry_key;
-    const bool start = act && ((pk >> 8) != c || st - (pk & 255u) - 1u > gmax);
+    const bool start = act && key - pk - 1u >= gm;
     const unsigned S = __ballot_sync(0xffffffffu, sd);
     const unsigned B = __ballot_sync(0xffffffffu, start);
     const unsigned mb = B & upto;
@@ -384,7 +404,7 @@ __device__ int scan_unit(W& w, const KParams& kp, const uint2* __restrict__ calq
     int cs;
     if (mb) {
       const int ls = 31 - __clz(mb);
-      seen = (S & lt & ~lanemask_lt(ls)) != 0;
+      seen = ((S & lt) >> ls) != 0;
       cs = base + ls;
     } else {
       seen = carry_seen || (S & lt) != 0;
@@ -403,11 +423,14 @@ __device__ int scan_unit(W& w, const KParams& kp, const uint2* __restrict__ calq
     }
     if (A) carry_key = __shfl_sync(0xffffffffu, key, 31 - __clz(A));
     if (i < n) {
-      w.kf[i] = (word & 0x00FF1FFFu) | ((act ? 1u : 0u) << 13) | ((sd ? 2u : 0u) << 13) | ((start ? 4u : 0u) << 13) |
+      // an inactive digi keeps its key only (ADC, charge and noise^2 0), so that
+      // form_unit sums every digi of a candidate without a test
+      w.kf[i] = (act ? word : key) | ((act ? 1u : 0u) << 13) | ((sd ? 2u : 0u) << 13) | ((start ? 4u : 0u) << 13) |
                 (q << 24);
-      w.nsq[i] = nq;
+      w.nsq[i] = act ? nq : 0.f;
     }
   }
+  if (lane == 0) w.kf[n] = 4u << 13;  // a candidate start after the last digi ends every walk of form_unit
   __syncwarp();
   return n_own;
 }
@@ -428,9 +451,11 @@ struct AmpPos {
 };
 
 // a5 + a6: one lane per owned candidate walks it from its first strip to the
-// digi before the next candidate start (the right boundary is its last active
-// strip), summing in strip order raw ADC, noise^2 (binary32, left to right),
-// gain-corrected charge and first moment; the candidate is widened over up to
+// digi before the next candidate start (or the sentinel after the last digi; the
+// right boundary is its last active strip), summing in strip order raw ADC,
+// noise^2 (binary32, left to right), gain-corrected charge and first moment
+// (inactive digis, including those of a following channel before its first
+// candidate, add 0 to each); the candidate is widened over up to
 // max_adj adjacent bad strips; the cluster threshold decides.  Returns the number
 // kept among owners [k_begin, n_own); when `stage` is given the kept clusters are
 // written, in strip order, to stage[base + rank] for base + rank < cap.  With
@@ -457,23 +482,21 @@ __device__ uint32_t form_unit(W& w, const KParams& kp, int n, int k_begin, int n
       const uint32_t* B = w.bad + c * kMaskWords;
       int lo_i = l;
       for (int m = 0; m < kp.max_adj && lo_i - 1 >= 0 && bit(B, lo_i - 1); m++) lo_i--;
-      uint32_t s_raw = 0, moment = 0;
+      uint32_t s16 = 0, mom = 0;  // sums of ADC | q << 8 and of strip x q over the active digis
       float n2 = 0.f;
       int r = l;
-      for (;;) {
-        if (kj & (1u << 13)) {
-          const uint32_t q = kj >> 24;
-          const int st = (int)(kj & 255u);
-          s_raw += (kj >> 16) & 255u;
-          n2 = __fadd_rn(n2, w.nsq[j]);
-          q_sum += q;
-          moment += (uint32_t)(st - lo_i) * q;
-          r = st;
-        }
-        if (++j >= n) break;
-        kj = w.kf[j];
-        if (((kj >> 8) & 31u) != c || (kj & (4u << 13))) break;
+      for (;;) {  // an inactive digi adds 0 to every sum (and +0 to noise^2, which leaves it unchanged)
+        const uint32_t q = kj >> 24;
+        s16 += kj >> 16;
+        n2 = __fadd_rn(n2, w.nsq[j]);
+        q_sum += q;
+        mom += (kj & 255u) * q;
+        if (kj & (1u << 13)) r = (int)(kj & 255u);
+        kj = w.kf[++j];
+        if (kj & (4u << 13)) break;  // the next candidate (or the sentinel after the last digi)
       }
+      const uint32_t s_raw = s16 - (q_sum << 8);
+      const uint32_t moment = mom - (uint32_t)lo_i * q_sum;
       pass = __uint2float_rn(s_raw) > __fmul_rn(kp.t_cluster, __fsqrt_rn(n2));
       int hi = r;
       for (int m = 0; m < kp.max_adj && hi + 1 < kStrips && bit(B, hi + 1); m++) hi++;
@@ -738,7 +761,8 @@ constexpr bool layout_ok() {
          offsetof(W, bad) == offsetof(W, own) + sizeof(uint16_t) * W::kTile && offsetof(W, own) % 16 == 0 &&
          W::kSlots % 4 == 0 &&  // the slot area is cleared with 16-byte stores
          W::kSlots * 4 <= sizeof(uint16_t) * W::kTile + sizeof(uint32_t) * W::kChW * kMaskWords &&  // slots
-         W::kBuf % 8 == 0 && W::kBuf < 2048;  // staging in 8-byte words; ADC positions take 11 bits of a slot
+         W::kBuf % 8 == 0 && W::kBuf < 2048 &&  // staging in 8-byte words; ADC positions take 11 bits of a slot
+         offsetof(W, chan_st) % 4 == 0 && offsetof(W, chan_len) % 4 == 0 && kChPerFe % 4 == 0;  // word stores
 }
 static_assert(layout_ok<WarpT<1>>() && layout_ok<WarpT<2>>(), "per-warp shared memory layout");
 

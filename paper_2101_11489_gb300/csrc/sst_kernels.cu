@@ -910,8 +910,9 @@ __global__ void __launch_bounds__(256, 4) k_cluster(sst_digis in, uint32_t n_fed
       const size_t a = w.chan_pos[c];
       for (uint32_t k = lane; k < n; k += 32) {
         const uint32_t key = in.strip[a + k] - g0;
-        // a digi that does not belong to channel c takes no part in clustering
-        w.kf[o + k] = ((key >> 8) == (uint32_t)c ? key : 0x1FFFu) | ((uint32_t)in.adc[a + k] << 16);
+        // a digi that does not belong to channel c takes no part in clustering (ADC 0:
+        // never active, never a seed)
+        w.kf[o + k] = (key >> 8) == (uint32_t)c ? key | ((uint32_t)in.adc[a + k] << 16) : 0u;
       }
     }
     __syncwarp();
@@ -994,7 +995,7 @@ __device__ __forceinline__ void batch_items(fe::WarpT<U>& w, const uint8_t* __re
       }
       const bool slots = fe::use_slots<W>(un);
       auto fill = [&](int c0, int c1, bool single) {
-        if (single && slots) fe::mark_slots(w, un);
+        if (single && slots) fe::mark_slots(w, un, (int)total);
         else fe::mark_walk(w, src, c0, c1);
       };
       const uint2* calq = kp.calq + (size_t)ch0 * kStrips;
@@ -1086,8 +1087,8 @@ __global__ void k_badmask(const uint8_t* __restrict__ bad, uint32_t* __restrict_
 // all inactive, so they are linked exactly when their gap t-a-1 is at most G(t): a
 // gap that is valid stays valid when shortened from below, and one longer than
 // G(t) contains the strip t-G(t)-1 that breaks a limit.  One thread per strip walks
-// down from t-1.  A gap is at most 254 strips (a >= 0, t <= 255), so G(t) is
-// stored capped at 254 without changing any decision.
+// down from t-1.  The byte stored is min(G(t) + 1, t) <= 255 (G(t) <= t), the limit
+// the clusterizers compare tile keys against (see the comment below).
 __global__ void k_calib_pack(const float* __restrict__ noise, const uint32_t* __restrict__ mask,
                              uint2* __restrict__ calq, uint64_t n_strips, float t_ch,
                              float t_seed, int max_holes, int max_bad) {
@@ -1109,7 +1110,12 @@ __global__ void k_calib_pack(const float* __restrict__ noise, const uint32_t* __
     const float p = __fmul_rn(thr, nz);
     return p >= 255.f ? 255u : (uint32_t)p;  // truncation = floor for p >= 0
   };
-  const uint32_t gap = (uint32_t)(g < 254 ? g : 254);
+  // linking limit of the tile key difference: strip t is linked to the previous
+  // active strip a of its channel when t - a <= g + 1 (<= t always holds); an active
+  // strip of an earlier channel is at least t + 1 keys below, so with
+  // lim = min(g + 1, t) one unsigned compare, key - prev - 1 >= lim, marks a new
+  // candidate in both cases
+  const uint32_t gap = (uint32_t)(g + 1 < t ? g + 1 : t);
   const uint32_t word = bad ? (255u | (255u << 8) | (gap << 16)) : (limit(t_ch) | (limit(t_seed) << 8) | (gap << 16));
   calq[s] = make_uint2(word, __float_as_uint(__fmul_rn(nz, nz)));
 }

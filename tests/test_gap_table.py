@@ -10,6 +10,12 @@ t).  That is exact because a valid gap stays valid when shortened from below.  H
 G is rebuilt the same way from random bad-strip maps and compared, for pairs of
 strips, with the oracle clustering a module whose only active strips are a and t:
 one cluster [a, t] when they are linked, two single-strip clusters otherwise.
+
+The kernels store L(t) = min(G(t) + 1, t) and compare tile keys (channel << 8 |
+strip) once: key(t) - key(prev) - 1 >= L(t), unsigned, starts a new candidate.
+test_key_compare_matches_the_link_rule checks that this one compare gives the same
+decision as "another channel, or t - a - 1 > G(t)" for every strip pair, every
+G(t) <= t and previous active strips in the same, an earlier or no channel.
 """
 import numpy as np
 import pytest
@@ -86,3 +92,40 @@ def test_gap_table_special_cases():
     assert gap_table(bad, 1, 1)[22] == 3 and gap_table(bad, 0, 1)[22] == 0
     p11 = orc.Params(max_seq_holes=1, max_seq_bad=1, max_adj_bad=0)
     assert linked_by_oracle(18, 22, bad, p11) and not linked_by_oracle(17, 22, bad, p11)
+
+
+def starts_by_key_compare(key: int, prev: int, lim: int) -> bool:
+    """The kernels' test for a new candidate: one unsigned 32-bit compare."""
+    return ((key - prev - 1) % (1 << 32)) >= lim
+
+
+def test_key_compare_matches_the_link_rule():
+    none = 0x1FFF  # the scan's "no previous active digi": channel 31, above every key
+    c = 7
+    for t in range(N):
+        key = (c << 8) | t
+        for g in range(t + 1):  # G(t) <= t: the walk down from t - 1 stops at strip 0
+            lim = min(g + 1, t)
+            assert 0 <= lim <= 255
+            assert starts_by_key_compare(key, none, lim)
+            for a in range(N):
+                # same channel: a new candidate unless a < t is linked; a repeated or
+                # unsorted strip (a >= t) always starts one
+                same = (c << 8) | a
+                assert starts_by_key_compare(key, same, lim) == (a >= t or t - a - 1 > g), (t, g, a)
+                # an earlier channel: always a new candidate
+                for pc in (0, c - 1):
+                    assert starts_by_key_compare(key, (pc << 8) | a, lim), (t, g, a, pc)
+
+
+def test_key_compare_on_random_bad_maps():
+    rng = np.random.default_rng(77)
+    for holes, bad_lim, p_bad in [(0, 1, 0.3), (2, 3, 0.5), (4, 2, 0.5)]:
+        bad = (rng.random(N) < p_bad).astype(np.uint8)
+        g = gap_table(bad, holes, bad_lim)
+        lim = np.minimum(g + 1, np.arange(N))
+        assert lim.max() <= 255
+        for a in range(N):
+            for t in range(a + 1, min(N, a + 40)):
+                key, prev = (3 << 8) | t, (3 << 8) | a
+                assert starts_by_key_compare(key, prev, int(lim[t])) == (t - a - 1 > g[t])
