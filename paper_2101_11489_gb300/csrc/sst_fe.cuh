@@ -323,8 +323,8 @@ __device__ void mark_walk(W& w, const uint8_t* src, int c0, int c1) {
 //    channel lies at least strip + 1 keys below, and an unsorted or repeated
 //    strip wraps the difference);
 //  - owners, the leftmost seed of every candidate: two ballots (seeds, candidate
-//    starts) and a carry across windows decide whether another seed lies between
-//    a seed's candidate start and it.
+//    starts) and one 32-bit addition over them, with a carry across windows,
+//    decide whether another seed lies between a seed's candidate start and it.
 // The first digis of owned candidates are compacted in strip order into own[];
 // returns their number.  src / src_end: the pair's bytes (EXP).
 template <int NCH, bool EXP, class W>
@@ -338,7 +338,7 @@ __device__ int scan_unit(W& w, const KParams& kp, const uint2* __restrict__ calq
   const bool any_div = __any_sync(0xffffffffu, (lane < NCH * 2 && w.qmul[lane] < 0.f) ||
                                                   (lane + 32 < NCH * 2 && w.qmul[lane + 32] < 0.f));
   int n_own = 0, carry_start = -1;
-  bool carry_seen = false;
+  uint32_t carry_seen = 0u;  // 1: the open candidate of the windows before has a seed
   uint32_t carry_key = 0x1FFFu;  // key of the last active digi of the windows before (none: channel 31)
   int run_s = 0;               // expansion: last run start of the windows before, and its descriptor
   uint32_t run_d = 0;
@@ -399,28 +399,20 @@ __device__ int scan_unit(W& w, const KParams& kp, const uint2* __restrict__ calq
     const bool start = act && key - pk - 1u >= gm;
     const unsigned S = __ballot_sync(0xffffffffu, sd);
     const unsigned B = __ballot_sync(0xffffffffu, start);
+    // owners, the first seed of each candidate, by one addition over the window's
+    // masks: a seed generates a carry, a digi that is neither a seed nor a candidate
+    // start passes it on, a candidate start stops it; so the carry into a digi says
+    // that a seed lies between its candidate's start and it (the carry in: the open
+    // candidate of the windows before has one)
+    const unsigned x = S | ~B;
+    const unsigned sum = x + S + carry_seen;
+    const unsigned O = S & (~(sum ^ x ^ S) | B);
+    carry_seen = ((x & S) | ((x | S) & ~sum)) >> 31;  // the carry out
     const unsigned mb = B & upto;
-    bool seen;
-    int cs;
-    if (mb) {
-      const int ls = 31 - __clz(mb);
-      seen = ((S & lt) >> ls) != 0;
-      cs = base + ls;
-    } else {
-      seen = carry_seen || (S & lt) != 0;
-      cs = carry_start;
-    }
-    const bool owner = sd && !seen;
-    const unsigned O = __ballot_sync(0xffffffffu, owner);
-    if (owner) w.own[n_own + __popc(O & lt)] = (uint16_t)cs;
+    const int cs = mb ? base + 31 - __clz(mb) : carry_start;
+    if ((O >> lane) & 1u) w.own[n_own + __popc(O & lt)] = (uint16_t)cs;
     n_own += __popc(O);
-    if (B) {
-      const int lw = 31 - __clz(B);
-      carry_start = base + lw;
-      carry_seen = (S >> lw) != 0;
-    } else {
-      carry_seen = carry_seen || S != 0;
-    }
+    if (B) carry_start = base + 31 - __clz(B);
     if (A) carry_key = __shfl_sync(0xffffffffu, key, 31 - __clz(A));
     if (i < n) {
       // an inactive digi keeps its key only (ADC, charge and noise^2 0), so that
