@@ -53,7 +53,7 @@ struct __align__(16) WarpT {
   uint32_t kf[kTile + 4];  // before scan_unit: run descriptors at run starts (ADC byte position << 13 |
                            // channel << 8 | first strip), 0 elsewhere, or, in the per-event kernel,
                            // key | ADC << 16 per digi; after: one word per digi: key (channel in the
-                           // work item << 8 | strip, 13 bits; sorted) | flags << 13 (1 active, 2 seed,
+                           // work item << 8 | strip, 13 bits; sorted) | flags << 13 (1 active,
                            // 4 first strip of a candidate) | ADC << 16 | gain-corrected charge << 24
                            // (ADC and charge 0 for an inactive digi), then a candidate-start sentinel
   float nsq[kTile];     // noise^2 of each digi
@@ -412,13 +412,12 @@ __device__ int scan_unit(W& w, const KParams& kp, const uint2* __restrict__ calq
     const int cs = mb ? base + 31 - __clz(mb) : carry_start;
     if ((O >> lane) & 1u) w.own[n_own + __popc(O & lt)] = (uint16_t)cs;
     n_own += __popc(O);
-    if (B) carry_start = base + 31 - __clz(B);
-    if (A) carry_key = __shfl_sync(0xffffffffu, key, 31 - __clz(A));
+    carry_start = __shfl_sync(0xffffffffu, cs, 31);  // lane 31's candidate: the open one at the window's end
+    carry_key = __shfl_sync(0xffffffffu, act ? key : pk, 31);  // the last active digi up to the window's end
     if (i < n) {
       // an inactive digi keeps its key only (ADC, charge and noise^2 0), so that
       // form_unit sums every digi of a candidate without a test
-      w.kf[i] = (act ? word : key) | ((act ? 1u : 0u) << 13) | ((sd ? 2u : 0u) << 13) | ((start ? 4u : 0u) << 13) |
-                (q << 24);
+      w.kf[i] = (act ? word | (1u << 13) : key) | ((start ? 4u : 0u) << 13) | (q << 24);
       w.nsq[i] = act ? nq : 0.f;
     }
   }
